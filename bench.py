@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched protein database search on GB300.
+
+Workload (default): 32 protein queries, lengths log-uniform in [64, 5000],
+against a device-resident database of 500,000 targets with lognormal lengths
+(median 300, sigma 0.7, cap 35,000), residues drawn from amino-acid
+background frequencies; BLOSUM62, gap open 11 / extend 1, local alignment
+with packed 16-bit lanes and exact int32 rerun on saturation; top-10 hits per
+query with start coordinates and CIGAR.  A step is one `dsa_align` (score
+pass + saturation rerun + top-k) plus one `dsa_traceback` of the hits.
+
+Metric: GCUPS = (sum over pairs of m * n) / step time.  Printed as one JSON
+line (rank 0).  `--impl reference` times the CPU oracle on a bounded sample
+of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GCUPS (bit-exact) batched protein database search"
+WORKLOAD = ("protein_search: 32 queries (log-uniform 64..5000) x 500,000 targets "
+            "(lognormal median 300, sigma 0.7, cap 35,000), BLOSUM62 11/1, local, "
+            "packed int16x2 + exact int32 rerun, top-10 + traceback")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--targets", type=int, default=500_000)
+    ap.add_argument("--queries", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="approximate CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks --
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, bus_id=None):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if bus_id:
+            cmd += ["-i", bus_id]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------- distributed --
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def all_max(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def all_sum(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- workload --
+
+def make_workload(args, rank=0):
+    from paper_1701_01575_gb300 import workloads as W
+    return W.protein_search(seed=W.SEED_BASE + 1 + 1000 * rank, n_queries=args.queries,
+                            n_targets=args.targets)
+
+
+def cpu_sample(wl, seconds, rate_guess=0.25e9):
+    """A seeded sample of targets (all queries against each) sized to ~`seconds` of CPU."""
+    cores = os.cpu_count() or 1
+    budget = seconds * rate_guess * cores
+    qsum = int(wl.queries.lengths.sum())
+    mean_n = float(wl.db.lengths.mean())
+    k = max(8, min(wl.db.n, int(budget / (qsum * mean_n))))
+    rng = np.random.default_rng(20260101)
+    return np.sort(rng.choice(wl.db.n, size=k, replace=False)), cores
+
+
+def run_oracle_sample(wl, targets, cores):
+    import oracle
+    t0 = time.perf_counter()
+    sc, qe, te = oracle.score_all_vs_all(wl.queries, wl.db, wl.matrix, wl.gap_open, wl.gap_extend,
+                                         oracle.LOCAL, 15, targets=targets, threads=cores)
+    dt = time.perf_counter() - t0
+    cells = int(wl.queries.lengths.sum()) * int(wl.db.lengths[targets].sum())
+    return (sc, qe, te), cells, dt
+
+
+# ------------------------------------------------------------------ ours --
+
+def bench_ours(args):
+    import torch
+    from paper_1701_01575_gb300 import build, dsa
+
+    world, rank, local = dist_setup(args)
+    build.build()
+    torch.cuda.set_device(local)
+    # an explicit stream: the library orders all its work on it and the CUDA
+    # events below are recorded on it
+    stream = torch.cuda.Stream(local)
+    torch.cuda.set_stream(stream)
+    wl = make_workload(args, rank)
+    ctx = dsa.Context(local, stream=stream)
+    A = wl.alphabet_size
+    db = ctx.load_set(wl.db, A)
+    qs = ctx.load_set(wl.queries, A)
+    S, o, e = wl.matrix, wl.gap_open, wl.gap_extend
+    cells_per_step = wl.cells()
+    flags = dsa.TIMING | dsa.RESULTS_ON_DEVICE
+
+    def step():
+        r = ctx.align(db, qs, S, o, e, top_k=wl.top_k, flags=flags)
+        ctx.traceback(r)
+        return r
+
+    for _ in range(args.warmup):
+        step().free()
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(local)
+    bus = getattr(props, "pci_bus_id", None)
+    launches0 = ctx.kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(bus)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    launches = ctx.kernel_launches() - launches0
+    ms_local = ev0.elapsed_time(ev1)
+    phase = {k: [] for k in dsa.PHASES}
+    reruns = 0
+    for r in results:
+        t = r.timing()
+        for k, v in t.items():
+            if v >= 0:
+                phase[k].append(v)
+        reruns += r.stats()[1]
+    last = results[-1]
+    top_hits = last.hits()
+    for r in results:
+        r.free()
+    ms = all_max(world, ms_local)
+    total_cells = all_sum(world, float(cells_per_step * args.steps))
+    value = total_cells / (ms / 1e3) / 1e9
+
+    out = {"metric": METRIC, "value": round(value, 2), "unit": "GCUPS", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i16x2+i32",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "queries": args.queries, "targets": args.targets,
+                      "cells_per_step": cells_per_step, "parallelism": f"replicas x{world}",
+                      "l2": "inputs larger than L2 (database codes 192 MB > 129 MB L2)"},
+           "clocks": clk, "gpu_launches": int(launches)}
+
+    # roofline of the dominant kernel (packed inter-sequence kernel)
+    inter_ms = statistics.mean(phase["inter16"]) if phase["inter16"] else None
+    rate = ctx.probe_issue_rate(0)     # DPX s16x2 add-max, warp-instr / SM / clk
+    sm_mhz = clk.get("sm_mhz") or (props.clock_rate / 1e3 if hasattr(props, "clock_rate") else None)
+    if inter_ms and sm_mhz:
+        achieved = cells_per_step / (inter_ms / 1e3) / 1e9
+        # 6 algorithmic int32 ops per cell (H-o, E, F, max with diagonal, max with F/0,
+        # running best); in packed 16x2 form one instruction covers 2 cells
+        peak = props.multi_processor_count * sm_mhz * 1e6 * rate * 32 * 2 / 6 / 1e9
+        out["roofline"] = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
+                           "unit": "GCUPS", "frac": round(achieved / peak, 4), "traffic": None,
+                           "kernel": "k_inter_local16", "kernel_ms": round(inter_ms, 3),
+                           "peak_basis": f"{props.multi_processor_count} SMs x {sm_mhz:.0f} MHz x "
+                                         f"{rate:.3f} DPX warp-instr/SM/clk (measured) x 32 lanes "
+                                         "x 2 cells / 6 ops"}
+    out["phases_ms"] = {k: round(statistics.mean(v), 3) for k, v in phase.items() if v}
+    out["saturation_reruns_per_step"] = reruns / args.steps
+
+    if rank == 0 and not args.no_plain:
+        # plain per-query form: one unbatched int32 launch per query, DB in input order
+        from paper_1701_01575_gb300 import workloads as W
+        order = np.argsort(wl.queries.lengths)
+        pick = order[[len(order) // 8, 3 * len(order) // 8, 5 * len(order) // 8, 7 * len(order) // 8]]
+        sub = wl.queries.subset(pick)
+        qsub = ctx.load_set(sub, A)
+        r = ctx.align(db, qsub, S, o, e, flags=dsa.PLAIN_FORM | dsa.TIMING | dsa.RESULTS_ON_DEVICE)
+        ctx.sync()
+        r.free()
+        t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        r = ctx.align(db, qsub, S, o, e, flags=dsa.PLAIN_FORM | dsa.RESULTS_ON_DEVICE)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        r.free()
+        pms = t0.elapsed_time(t1)
+        pcells = int(sub.lengths.sum()) * int(wl.db.lengths.sum())
+        plain = pcells / (pms / 1e3) / 1e9
+        out["plain_form"] = {"value": round(plain, 2), "unit": "GCUPS",
+                             "sample": "4 of the 32 queries (length quantiles 1/8..7/8) x all "
+                                       "targets, one int32 launch per query"}
+        out["batched_over_plain"] = round(value / world / plain, 2)
+        qsub.free()
+
+    if rank == 0 and not args.no_e2e:
+        # end to end through the public API with host buffers: queries H2D, hits + CIGAR D2H
+        e2e_steps = max(1, min(3, args.steps))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for _ in range(e2e_steps):
+            r = ctx.align_batch(db, wl.queries.codes, wl.queries.offsets, S, o, e, top_k=wl.top_k)
+            ctx.traceback(r)
+            hits = r.hits()
+            cig = r.cigar()
+            h2d += wl.queries.codes.nbytes + wl.queries.offsets.nbytes
+            d2h += hits.nbytes + cig.nbytes
+            r.free()
+        dt = time.perf_counter() - t0
+        out["e2e"] = {"value": round(cells_per_step * e2e_steps / dt / 1e9, 2), "unit": "GCUPS",
+                      "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
+                      "steps": e2e_steps}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        targets, cores = cpu_sample(wl, args.cpu_seconds)
+        (osc, oqe, ote), ccells, cdt = run_oracle_sample(wl, targets, cores)
+        out["cpu_baseline"] = {"value": round(ccells / cdt / 1e9, 4), "unit": "GCUPS", "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"all {wl.queries.n} queries x {len(targets)} seeded random "
+                                         f"targets ({ccells:.3g} cells, {cdt:.1f} s)"}
+        # the same sample, checked against the GPU's dense all-pairs result (packed path)
+        r = ctx.align(db, qs, S, o, e, flags=dsa.RESULTS_ON_DEVICE)
+        dh = r.device_hits().view(-1, dsa.HIT_DTYPE.itemsize)
+        import torch as _t
+        idx = (_t.arange(wl.queries.n, device="cuda")[:, None] * wl.db.n
+               + _t.as_tensor(targets, device="cuda")[None, :]).reshape(-1)
+        sel = dh.index_select(0, idx).cpu().numpy().view(dsa.HIT_DTYPE).reshape(wl.queries.n, -1)
+        r.free()
+        mism = int((sel["score"] != osc).sum() + (sel["q_end"] != oqe).sum() + (sel["t_end"] != ote).sum())
+        out["cpu_baseline"]["parity_mismatches"] = mism
+        out["top_hits_q0"] = [(int(h["target_id"]), int(h["score"])) for h in top_hits[:3]]
+
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    qs.free(); db.free(); ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- reference --
+
+def bench_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = make_workload(args, 0)
+    per_step = max(1.0, min(20.0, 90.0 / max(1, args.steps + args.warmup)))
+    targets, cores = cpu_sample(wl, per_step)
+    for _ in range(args.warmup):
+        run_oracle_sample(wl, targets[: max(8, len(targets) // 8)], cores)
+    total_cells, total_t = 0, 0.0
+    for _ in range(args.steps):
+        _, cells, dt = run_oracle_sample(wl, targets, cores)
+        total_cells += cells
+        total_t += dt
+    value = total_cells / total_t / 1e9
+    out = {"metric": METRIC, "value": round(value, 4), "unit": "GCUPS", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(total_t / args.steps * 1e3, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": WORKLOAD, "queries": args.queries, "targets": args.targets},
+           "cpu_baseline": {"value": round(value, 4), "unit": "GCUPS", "cores": cores,
+                            "kind": "oracle",
+                            "sample": f"per step all {wl.queries.n} queries x {len(targets)} "
+                                      "seeded random targets"},
+           "e2e": {"value": round(value, 4), "unit": "GCUPS", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        bench_reference(a)
+    else:
+        bench_ours(a)

@@ -1,0 +1,203 @@
+/*
+ * dsa.h -- C ABI of libdsa: exact Gotoh affine-gap alignment of query
+ * sequences against a device-resident sequence database on one GB300 GPU.
+ *
+ * The paper (Xu et al., "DSA: Scalable Distributed Sequence Alignment System
+ * Using SIMD Instructions") aligns query sequences against reference
+ * sequences with a score matrix (Sec. II.B.1), with three algorithms --
+ * distributed Smith-Waterman, Needleman-Wunsch and semi-global (Sec. II.C.2)
+ * -- returns for each alignment the maximum score, the reference name, the
+ * location and the CIGAR (Sec. II.B.1), and reduces the per-partition results
+ * to the top K by score (Sec. II.B.2).  This header is that computation as a
+ * plain C interface; every step runs in CUDA kernels of this library.
+ *
+ * Conventions (the paper prints no recurrence; these are the library's
+ * definitions, identical to the CPU oracle used to test it):
+ *   - residues are small integer codes 0..A-1; S is an A x A int8 matrix,
+ *     row-major, rows = query residue, columns = target residue;
+ *   - a run of k gap columns costs gap_open + (k-1)*gap_extend, and
+ *     0 <= gap_extend <= gap_open (BLAST-style "open o / extend e" with cost
+ *     o + k*e is obtained by passing gap_open = o + e);
+ *   - H/E/F Gotoh recurrences, local scores floored at 0;
+ *   - global boundary H[i][0] = -(o+(i-1)e), H[0][j] = -(o+(j-1)e); in
+ *     semi-global mode a free query (target) begin sets H[i][0] (H[0][j]) to 0;
+ *   - result cell: local = best cell; global = (m, n); semi-global = best of
+ *     row m (target end free), column n (query end free) and (m, n);
+ *   - ties between optimal result cells: the smallest target end, then the
+ *     smallest query end;
+ *   - traceback starts at the result cell; priority stop > M > I > D; a gap
+ *     is taken as opened at a cell whenever opening ties extending;
+ *   - coordinates are 0-based and inclusive; begin = residues skipped before
+ *     the aligned region; a local alignment with score 0 reports -1 for all
+ *     coordinates and an empty CIGAR;
+ *   - CIGAR words are (run_length << 4) | op with op M = 0, I = 1 (query
+ *     residue against a gap), D = 2 (target residue against a gap), in
+ *     alignment order; overhangs on free ends are not part of the CIGAR.
+ *
+ * Ownership: host arrays passed in are copied before the call returns.
+ * dsa_db and dsa_res objects own device memory until freed.  All work is
+ * ordered on the context's CUDA stream.  No function aborts or throws; each
+ * returns DSA_OK (0) or a negative error code, and dsa_last_error() gives the
+ * calling thread's last message.
+ */
+#ifndef DSA_H
+#define DSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define DSA_OK 0
+#define DSA_ERR_INVALID_ARG (-1)   /* an argument breaks a documented rule */
+#define DSA_ERR_OOM (-2)           /* device allocation failed */
+#define DSA_ERR_OVER_BUDGET (-3)   /* request exceeds the context's memory budget */
+#define DSA_ERR_CUDA (-4)          /* a CUDA runtime call failed */
+#define DSA_ERR_DEVICE_TIMEOUT (-5)/* a bounded device-side wait gave up */
+#define DSA_ERR_BUSY (-6)          /* serving queue full */
+#define DSA_ERR_UNSUPPORTED (-7)   /* valid request this build does not handle */
+
+/* ---- alignment modes (Sec. II.C.2: DSW, DNW, DSG) ---- */
+#define DSA_LOCAL 0
+#define DSA_GLOBAL 1
+#define DSA_SEMIGLOBAL 2
+
+/* ---- semi-global free ends (bit set = that end's overhang is free) ---- */
+#define DSA_FREE_Q_BEGIN 1u
+#define DSA_FREE_Q_END 2u
+#define DSA_FREE_T_BEGIN 4u
+#define DSA_FREE_T_END 8u
+
+/* ---- dsa_align_* flags ---- */
+#define DSA_RESULTS_ON_DEVICE 1u  /* dsa_res_get returns device pointers */
+#define DSA_FORCE_INT32 2u        /* skip the packed 16-bit pass; every pair runs in int32 */
+#define DSA_PLAIN_FORM 4u         /* one unbatched int32 launch per query, DB in input order */
+#define DSA_PAIRS_ON_DEVICE 8u    /* `pairs` is a device pointer */
+#define DSA_TIMING 16u            /* record CUDA events around each phase (dsa_res_timing) */
+
+/* ---- hit flags ---- */
+#define DSA_HIT_RERUN_INT32 1u    /* the packed pass saturated; result is from the int32 rerun */
+#define DSA_HIT_HAS_TRACEBACK 2u  /* begin coordinates and CIGAR are filled in */
+
+typedef struct dsa_ctx dsa_ctx;
+typedef struct dsa_db dsa_db;
+typedef struct dsa_res dsa_res;
+
+/* One explicit alignment: query `query_id` against `t_len` residues of
+ * sequence `target_id` starting at residue `t_offset` (a window). */
+typedef struct {
+  uint32_t query_id;
+  uint32_t target_id;
+  uint64_t t_offset;
+  uint32_t t_len;
+  uint32_t reserved; /* must be 0 */
+} dsa_pair;
+
+/* One alignment result (the paper's alignment object, Sec. II.B.1: score,
+ * reference name -> target_id, location -> begin/end, CIGAR). */
+typedef struct {
+  int32_t score;
+  int32_t q_begin, q_end;   /* 0-based, inclusive; -1 if none / not traced */
+  int32_t t_begin, t_end;   /* relative to the pair's window (t_offset) */
+  uint32_t query_id;
+  uint32_t target_id;
+  uint32_t flags;           /* DSA_HIT_* */
+  uint64_t t_offset;        /* window offset of the pair (0 for whole targets) */
+  uint64_t cigar_off;       /* index of the first CIGAR word in the result's CIGAR array */
+  uint32_t cigar_len;       /* number of CIGAR words */
+  uint32_t reserved;
+} dsa_hit;
+
+/* Create a context on CUDA device `device`.  `mem_budget_bytes` caps the
+ * device memory this context may hold (0 = no cap).  `cuda_stream` is a
+ * cudaStream_t to order all work on (NULL = a stream the context creates). */
+int dsa_create(dsa_ctx** out, int device, size_t mem_budget_bytes, void* cuda_stream);
+int dsa_destroy(dsa_ctx* ctx);
+
+/* Message describing the calling thread's most recent error ("" if none). */
+const char* dsa_last_error(void);
+
+/* Bytes of device memory the context currently holds. */
+size_t dsa_mem_in_use(const dsa_ctx* ctx);
+
+/* Number of CUDA kernels this context has launched so far. */
+uint64_t dsa_kernel_launches(const dsa_ctx* ctx);
+
+/* Load `n_seqs` sequences to the device (the paper's map phase reading the
+ * reference set, Sec. II.B.1).  `codes` holds all residues concatenated;
+ * sequence k is codes[offsets[k] .. offsets[k+1]).  Every code must be below
+ * `alphabet_size` (1..31); every sequence must be non-empty.  The loader also
+ * builds the length-sorted, lane-interleaved copy the batched kernels read.
+ * The same call loads query sets. */
+int dsa_db_load(dsa_ctx* ctx, const uint8_t* codes, const uint64_t* offsets, uint32_t n_seqs,
+                int alphabet_size, dsa_db** out);
+int dsa_db_free(dsa_db* db);
+int dsa_db_info(const dsa_db* db, uint32_t* n_seqs, uint64_t* n_residues, int* alphabet_size);
+
+/* Align queries against the database (Sec. II.B.1 map phase + Sec. II.B.2 top K).
+ *
+ * queries: a dsa_db loaded with dsa_db_load (device resident).
+ * pairs:   NULL = every query against every target; otherwise `n_pairs`
+ *          explicit (query, target window) pairs (host pointer, or device
+ *          pointer with DSA_PAIRS_ON_DEVICE).
+ * mode / free_ends: DSA_LOCAL, DSA_GLOBAL or DSA_SEMIGLOBAL (+ DSA_FREE_* bits).
+ * matrix:  host int8 A x A substitution matrix, A = alphabet_size of both sets.
+ * top_k:   0 = one hit per pair (all x all: query-major, target-minor order;
+ *          explicit pairs: pair order).  k > 0 = per query the k best targets
+ *          ordered by (score desc, target_id asc) -- all x all only.
+ * The result holds scores and end coordinates; begin coordinates and CIGARs
+ * are filled in by dsa_traceback. */
+int dsa_align(dsa_ctx* ctx, const dsa_db* db, const dsa_db* queries, const dsa_pair* pairs,
+              uint64_t n_pairs, int mode, uint32_t free_ends, const int8_t* matrix,
+              int alphabet_size, int gap_open, int gap_extend, uint32_t top_k, uint32_t flags,
+              dsa_res** out);
+
+/* Same as dsa_align with queries given as host arrays (copied to the device
+ * inside the call). */
+int dsa_align_batch(dsa_ctx* ctx, const dsa_db* db, const uint8_t* q_codes,
+                    const uint64_t* q_offsets, uint32_t n_queries, const dsa_pair* pairs,
+                    uint64_t n_pairs, int mode, uint32_t free_ends, const int8_t* matrix,
+                    int alphabet_size, int gap_open, int gap_extend, uint32_t top_k,
+                    uint32_t flags, dsa_res** out);
+
+/* Begin coordinates and CIGAR for hits of `res` (the paper's location +
+ * CIGAR, Sec. I and II.B.1).  `which` lists hit indices (host array), NULL =
+ * every hit.  Hits with a local score of 0 get no CIGAR. */
+int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, uint64_t n);
+
+/* Access results.  Without DSA_RESULTS_ON_DEVICE the arrays are host copies
+ * owned by `res` (the call synchronizes the stream); with it they are device
+ * pointers.  `cigar` holds all CIGAR words; hit.cigar_off indexes it. */
+int dsa_res_get(dsa_res* res, const dsa_hit** hits, uint64_t* n_hits, const uint32_t** cigar,
+                uint64_t* n_cigar_words);
+/* DP cells of the score pass (sum over pairs of m*n) and the number of pairs
+ * whose packed 16-bit pass saturated and were rerun in int32. */
+int dsa_res_stats(const dsa_res* res, uint64_t* cells, uint64_t* n_rerun);
+/* Device time in milliseconds of each phase of a result made with DSA_TIMING,
+ * measured with CUDA events on the context's stream (call after dsa_sync):
+ * ms[0] packed inter-sequence kernel, ms[1] long-target wavefront kernel,
+ * ms[2] exact int32 kernels (int32 path or saturation rerun), ms[3] top-k /
+ * hit assembly, ms[4] traceback (all dsa_traceback calls).  Phases that did
+ * not run report -1.  `n` is the length of `ms` (at most 5 are written). */
+int dsa_res_timing(const dsa_res* res, double* ms, int n);
+int dsa_res_free(dsa_res* res);
+
+/* Wait for all queued work of the context; returns a device-side status if
+ * a kernel reported one (e.g. DSA_ERR_DEVICE_TIMEOUT). */
+int dsa_sync(dsa_ctx* ctx);
+
+/* Issue-rate probe used for the roofline denominator: runs a throughput
+ * microbenchmark of one instruction form on the context's device and
+ * returns warp-instructions per SM per clock.  form: 0 = s16x2 add-max
+ * (DPX), 1 = s16x2 max with ReLU (DPX), 2 = s16x2 three-way max (DPX),
+ * 3 = int32 add, 4 = int32 max, 5 = s16x2 add (SIMD video), 6 = int32
+ * add-max (DPX), 7 = the packed local cell update mix. */
+int dsa_probe_issue_rate(dsa_ctx* ctx, int form, double* warp_instr_per_sm_per_clk);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSA_H */

@@ -1,0 +1,859 @@
+// Host side of the libdsa C ABI: contexts, device-resident sequence sets,
+// planning of the score pass (packed inter-sequence kernel, long-target
+// wavefront kernel, exact int32 kernel), saturation reruns, top-k and
+// traceback orchestration.  Every arithmetic step runs in the kernels of the
+// other translation units.
+#include "dsa_internal.cuh"
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+namespace dsa {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+namespace {
+
+// Stream-ordered device buffer charged against the context's budget.
+struct DevBuf {
+  dsa_ctx* ctx = nullptr;
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { reset(); }
+  int alloc(dsa_ctx* c, size_t n) {
+    reset();
+    ctx = c;
+    bytes = n ? n : 16;
+    return ctx->alloc(&p, bytes);
+  }
+  void reset() {
+    if (p && ctx) ctx->release(p, bytes);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+template <class T>
+int upload(dsa_ctx* ctx, DevBuf& buf, const std::vector<T>& v) {
+  DSA_TRY(buf.alloc(ctx, v.size() * sizeof(T)));
+  if (!v.empty())
+    DSA_CUDA_TRY(cudaMemcpyAsync(buf.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+  return DSA_OK;
+}
+
+int set_device(dsa_ctx* ctx) {
+  DSA_CUDA_TRY(cudaSetDevice(ctx->device));
+  return DSA_OK;
+}
+
+// Pairs whose packed pass saturated: indices gathered on the device.
+__global__ void k_collect_flags(const uint8_t* __restrict__ flag, uint64_t n,
+                                uint32_t* __restrict__ list, uint32_t cap,
+                                uint32_t* __restrict__ count) {
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n;
+       x += (uint64_t)gridDim.x * blockDim.x) {
+    if (flag[x]) {
+      const uint32_t k = atomicAdd(count, 1u);
+      if (k < cap) list[k] = (uint32_t)x;
+    }
+  }
+}
+
+struct Validated {
+  int smax = 0, smin = 0;
+  uint32_t max_m = 0, max_n = 0;
+};
+
+int check_matrix(const int8_t* matrix, int A, int o, int e, Validated* v) {
+  if (!matrix) { set_error("matrix is NULL"); return DSA_ERR_INVALID_ARG; }
+  if (o < 0 || e < 0 || e > o) {
+    set_error("gap penalties must satisfy 0 <= gap_extend <= gap_open (got %d, %d)", o, e);
+    return DSA_ERR_INVALID_ARG;
+  }
+  int smax = -128, smin = 127;
+  for (int k = 0; k < A * A; ++k) {
+    smax = std::max<int>(smax, matrix[k]);
+    smin = std::min<int>(smin, matrix[k]);
+  }
+  v->smax = smax;
+  v->smin = smin;
+  return DSA_OK;
+}
+
+}  // namespace
+
+void phase_begin(dsa_res* res, Phase p) {
+  if (!res || !(res->flags & DSA_TIMING)) return;
+  if (!res->ev[2 * p]) {
+    cudaEventCreate(&res->ev[2 * p]);
+    cudaEventCreate(&res->ev[2 * p + 1]);
+  }
+  if (!res->used[p]) cudaEventRecord(res->ev[2 * p], res->ctx->stream);
+}
+
+void phase_end(dsa_res* res, Phase p) {
+  if (!res || !(res->flags & DSA_TIMING) || !res->ev[2 * p + 1]) return;
+  cudaEventRecord(res->ev[2 * p + 1], res->ctx->stream);
+  res->used[p] = true;
+}
+
+}  // namespace dsa
+
+using namespace dsa;
+
+// ---------------------------------------------------------------- context --
+
+int dsa_ctx::alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (budget && in_use + bytes > budget) {
+    set_error("request of %zu bytes exceeds the memory budget (%zu of %zu in use)", bytes, in_use,
+              budget);
+    return DSA_ERR_OVER_BUDGET;
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    return DSA_ERR_OOM;
+  }
+  in_use += bytes;
+  return DSA_OK;
+}
+
+void dsa_ctx::release(void* p, size_t bytes) {
+  if (!p) return;
+  cudaFreeAsync(p, stream);
+  std::lock_guard<std::mutex> lk(mu);
+  in_use -= bytes;
+}
+
+extern "C" const char* dsa_last_error(void) { return g_err.c_str(); }
+
+extern "C" int dsa_create(dsa_ctx** out, int device, size_t mem_budget_bytes, void* cuda_stream) {
+  if (!out) { set_error("out is NULL"); return DSA_ERR_INVALID_ARG; }
+  *out = nullptr;
+  int n_dev = 0;
+  DSA_CUDA_TRY(cudaGetDeviceCount(&n_dev));
+  if (device < 0 || device >= n_dev) {
+    set_error("device %d out of range (%d devices)", device, n_dev);
+    return DSA_ERR_INVALID_ARG;
+  }
+  DSA_CUDA_TRY(cudaSetDevice(device));
+  int major = 0, minor = 0;
+  DSA_CUDA_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device));
+  DSA_CUDA_TRY(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device));
+  if (major != 10 || minor != 3) {
+    set_error("libdsa is built for sm_103a; device %d is sm_%d%d", device, major, minor);
+    return DSA_ERR_UNSUPPORTED;
+  }
+  dsa_ctx* c = new (std::nothrow) dsa_ctx;
+  if (!c) { set_error("host allocation failed"); return DSA_ERR_OOM; }
+  c->device = device;
+  c->budget = mem_budget_bytes;
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      set_error("cudaStreamCreate failed");
+      return DSA_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  if (cudaMalloc(&c->d_status, 256) != cudaSuccess || cudaMalloc(&c->d_counters, 256) != cudaSuccess ||
+      cudaMemset(c->d_status, 0, 256) != cudaSuccess || cudaMemset(c->d_counters, 0, 256) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->d_status) cudaFree(c->d_status);
+    if (c->d_counters) cudaFree(c->d_counters);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    set_error("context allocation failed");
+    return DSA_ERR_OOM;
+  }
+  *out = c;
+  return DSA_OK;
+}
+
+extern "C" int dsa_destroy(dsa_ctx* ctx) {
+  if (!ctx) return DSA_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->d_status);
+  cudaFree(ctx->d_counters);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return DSA_OK;
+}
+
+extern "C" size_t dsa_mem_in_use(const dsa_ctx* ctx) { return ctx ? ctx->in_use : 0; }
+
+extern "C" uint64_t dsa_kernel_launches(const dsa_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" int dsa_sync(dsa_ctx* ctx) {
+  if (!ctx) { set_error("ctx is NULL"); return DSA_ERR_INVALID_ARG; }
+  DSA_TRY(set_device(ctx));
+  DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  int32_t st = 0;
+  DSA_CUDA_TRY(cudaMemcpy(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    DSA_CUDA_TRY(cudaMemset(ctx->d_status, 0, sizeof(st)));
+    set_error("a kernel reported device status %d", st);
+    return st;
+  }
+  return DSA_OK;
+}
+
+// ---------------------------------------------------------------- databases --
+
+static void db_release(dsa_db* db) {
+  dsa_ctx* c = db->ctx;
+  auto rel = [&](void* p, size_t n) { if (p) c->release(p, n); };
+  rel(db->d_codes, db->n_res + 64);
+  rel(db->d_off, (db->n + 1) * sizeof(uint64_t));
+  rel(db->d_len, db->n * sizeof(uint32_t));
+  rel(db->d_perm, db->n * sizeof(uint32_t));
+  rel(db->d_slen, db->n * sizeof(uint32_t));
+  rel(db->d_gbase, db->n_groups * sizeof(uint64_t));
+  rel(db->d_glen, db->n_groups * sizeof(uint32_t));
+  rel(db->d_il, db->il_bytes ? db->il_bytes : 16);
+}
+
+extern "C" int dsa_db_load(dsa_ctx* ctx, const uint8_t* codes, const uint64_t* offsets,
+                           uint32_t n_seqs, int alphabet_size, dsa_db** out) {
+  if (!ctx || !out || !offsets || n_seqs == 0) {
+    set_error("dsa_db_load: NULL argument or empty set");
+    return DSA_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (alphabet_size < 1 || alphabet_size > MAX_ALPHABET) {
+    set_error("alphabet_size %d outside 1..%d", alphabet_size, MAX_ALPHABET);
+    return DSA_ERR_INVALID_ARG;
+  }
+  DSA_TRY(set_device(ctx));
+  const uint64_t base = offsets[0];
+  std::vector<uint64_t> off(n_seqs + 1);
+  std::vector<uint32_t> len(n_seqs);
+  for (uint32_t k = 0; k < n_seqs; ++k) {
+    if (offsets[k + 1] <= offsets[k]) {
+      set_error("sequence %u is empty or offsets decrease", k);
+      return DSA_ERR_INVALID_ARG;
+    }
+    const uint64_t L = offsets[k + 1] - offsets[k];
+    if (L > (1ull << 30)) { set_error("sequence %u longer than 2^30", k); return DSA_ERR_INVALID_ARG; }
+    off[k] = offsets[k] - base;
+    len[k] = (uint32_t)L;
+  }
+  off[n_seqs] = offsets[n_seqs] - base;
+  const uint64_t n_res = off[n_seqs];
+  if (!codes) { set_error("codes is NULL"); return DSA_ERR_INVALID_ARG; }
+  const uint8_t* src = codes + base;
+  for (uint64_t x = 0; x < n_res; ++x) {
+    if (src[x] >= (uint8_t)alphabet_size) {
+      set_error("residue code %u at position %llu is not below alphabet_size %d", src[x],
+                (unsigned long long)x, alphabet_size);
+      return DSA_ERR_INVALID_ARG;
+    }
+  }
+  dsa_db* db = new (std::nothrow) dsa_db;
+  if (!db) { set_error("host allocation failed"); return DSA_ERR_OOM; }
+  db->ctx = ctx;
+  db->n = n_seqs;
+  db->n_res = n_res;
+  db->A = alphabet_size;
+  db->h_off = off;
+  db->h_len = len;
+
+  // length-sorted order: longest first, ties by id
+  db->h_perm.resize(n_seqs);
+  std::iota(db->h_perm.begin(), db->h_perm.end(), 0u);
+  std::stable_sort(db->h_perm.begin(), db->h_perm.end(),
+                   [&](uint32_t a, uint32_t b) { return len[a] > len[b]; });
+  std::vector<uint32_t> slen(n_seqs);
+  for (uint32_t k = 0; k < n_seqs; ++k) slen[k] = len[db->h_perm[k]];
+  db->n_groups = (n_seqs + GROUP - 1) / GROUP;
+  db->h_glen.resize(db->n_groups);
+  db->h_gbase.resize(db->n_groups);
+  uint64_t il = 0;
+  for (uint32_t g = 0; g < db->n_groups; ++g) {
+    db->h_glen[g] = slen[(size_t)g * GROUP];
+    db->h_gbase[g] = il;
+    il += (uint64_t)((db->h_glen[g] + CHUNK - 1) / CHUNK) * CHUNK * GROUP;
+  }
+  db->il_bytes = il;
+
+  int rc = DSA_OK;
+  auto fail = [&](int r) { db_release(db); delete db; return r; };
+  void* p;
+  if ((rc = ctx->alloc(&p, n_res + 64))) return fail(rc);
+  db->d_codes = (uint8_t*)p;
+  if ((rc = ctx->alloc(&p, (n_seqs + 1) * sizeof(uint64_t)))) return fail(rc);
+  db->d_off = (uint64_t*)p;
+  if ((rc = ctx->alloc(&p, n_seqs * sizeof(uint32_t)))) return fail(rc);
+  db->d_len = (uint32_t*)p;
+  if ((rc = ctx->alloc(&p, n_seqs * sizeof(uint32_t)))) return fail(rc);
+  db->d_perm = (uint32_t*)p;
+  if ((rc = ctx->alloc(&p, n_seqs * sizeof(uint32_t)))) return fail(rc);
+  db->d_slen = (uint32_t*)p;
+  if ((rc = ctx->alloc(&p, db->n_groups * sizeof(uint64_t)))) return fail(rc);
+  db->d_gbase = (uint64_t*)p;
+  if ((rc = ctx->alloc(&p, db->n_groups * sizeof(uint32_t)))) return fail(rc);
+  db->d_glen = (uint32_t*)p;
+  if ((rc = ctx->alloc(&p, il ? il : 16))) return fail(rc);
+  db->d_il = (uint8_t*)p;
+
+  cudaStream_t s = ctx->stream;
+  if (cudaMemcpyAsync(db->d_codes, src, n_res, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(db->d_codes + n_res, 0, 64, s) != cudaSuccess ||
+      cudaMemcpyAsync(db->d_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(db->d_len, len.data(), len.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(db->d_perm, db->h_perm.data(), n_seqs * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(db->d_slen, slen.data(), n_seqs * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(db->d_gbase, db->h_gbase.data(), db->n_groups * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(db->d_glen, db->h_glen.data(), db->n_groups * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    set_error("dsa_db_load: copy to device failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(DSA_ERR_CUDA);
+  }
+  if ((rc = launch_interleave(ctx, db))) return fail(rc);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error("dsa_db_load: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(DSA_ERR_CUDA);
+  }
+  *out = db;
+  return DSA_OK;
+}
+
+extern "C" int dsa_db_free(dsa_db* db) {
+  if (!db) return DSA_OK;
+  cudaSetDevice(db->ctx->device);
+  db_release(db);
+  delete db;
+  return DSA_OK;
+}
+
+extern "C" int dsa_db_info(const dsa_db* db, uint32_t* n_seqs, uint64_t* n_residues,
+                           int* alphabet_size) {
+  if (!db) { set_error("db is NULL"); return DSA_ERR_INVALID_ARG; }
+  if (n_seqs) *n_seqs = db->n;
+  if (n_residues) *n_residues = db->n_res;
+  if (alphabet_size) *alphabet_size = db->A;
+  return DSA_OK;
+}
+
+// ---------------------------------------------------------------- align --
+
+namespace {
+
+// Score pass for all queries x all targets.
+int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs, int mode,
+                     uint32_t fe, const int8_t* d_mat, int A, int o, int e, const Validated& v,
+                     uint32_t flags, Scores out, uint64_t* n_rerun) {
+  const uint32_t nq = qs->n, nt = db->n;
+  const bool packed = mode == DSA_LOCAL && !(flags & (DSA_FORCE_INT32 | DSA_PLAIN_FORM)) &&
+                      o >= 1 && o + e <= 4096 && v.smax + o < 8192 && v.smin > -8192;
+  *n_rerun = 0;
+  if (!packed) {
+    // exact int32: one launch per query over every target (input order)
+    std::vector<uint64_t> poff(nq);
+    uint64_t words = 0;
+    for (uint32_t q = 0; q < nq; ++q) {
+      poff[q] = words;
+      words += (uint64_t)A * ((qs->h_len[q] + 7u) & ~7u);
+    }
+    DevBuf d_prof, d_poff, d_scr;
+    DSA_TRY(d_prof.alloc(ctx, words * sizeof(int32_t)));
+    DSA_TRY(upload(ctx, d_poff, poff));
+    DSA_TRY(launch_profile_int32(ctx, qs, d_mat, A, d_prof.as<int32_t>(), d_poff.as<uint64_t>()));
+    DSA_TRY(d_scr.alloc(ctx, db->n_res * sizeof(int2)));
+    phase_begin(res, PH_INT32);
+    for (uint32_t q = 0; q < nq; ++q)
+      DSA_TRY(launch_generic_int32(ctx, db, qs, d_prof.as<int32_t>(), d_poff.as<uint64_t>(),
+                                   nullptr, nt, q, d_scr.as<int2>(), mode, fe, o, e, 0, out));
+    phase_end(res, PH_INT32);
+    return DSA_OK;
+  }
+
+  // ---- packed path: query pairs x blocks of 8 length-sorted groups ----
+  InterPlan plan;
+  plan.R = A + 1;
+  std::vector<uint32_t> qorder(nq);
+  std::iota(qorder.begin(), qorder.end(), 0u);
+  std::stable_sort(qorder.begin(), qorder.end(),
+                   [&](uint32_t a, uint32_t b) { return qs->h_len[a] > qs->h_len[b]; });
+  plan.n_pairs = (nq + 1) / 2;
+  std::vector<uint32_t> pair_q(2 * plan.n_pairs, 0xFFFFFFFFu), pair_ns(plan.n_pairs);
+  std::vector<uint64_t> pprof_off(plan.n_pairs);
+  uint64_t words = 0;
+  for (uint32_t p = 0; p < plan.n_pairs; ++p) {
+    pair_q[2 * p] = qorder[2 * p];
+    uint32_t m = qs->h_len[qorder[2 * p]];
+    if (2 * p + 1 < nq) {
+      pair_q[2 * p + 1] = qorder[2 * p + 1];
+      m = std::max(m, qs->h_len[qorder[2 * p + 1]]);
+    }
+    pair_ns[p] = (m + INTER_ROWS - 1) / INTER_ROWS;
+    pprof_off[p] = words;
+    words += (uint64_t)pair_ns[p] * plan.R * 32;
+  }
+  const uint32_t blocks = (db->n_groups + INTER_WARPS - 1) / INTER_WARPS;
+  struct Item { uint64_t cost; uint32_t p, g0; };
+  std::vector<Item> items;
+  items.reserve((size_t)plan.n_pairs * blocks);
+  for (uint32_t p = 0; p < plan.n_pairs; ++p)
+    for (uint32_t b = 0; b < blocks; ++b)
+      items.push_back({(uint64_t)db->h_glen[b * INTER_WARPS] * pair_ns[p], p, b * INTER_WARPS});
+  std::stable_sort(items.begin(), items.end(),
+                   [](const Item& a, const Item& b) { return a.cost > b.cost; });
+  std::vector<uint32_t> item_words(2 * items.size());
+  for (size_t k = 0; k < items.size(); ++k) {
+    item_words[2 * k] = items[k].p;
+    item_words[2 * k + 1] = items[k].g0;
+  }
+  plan.n_items = (uint32_t)items.size();
+  plan.max_glen = db->h_glen.empty() ? 0 : db->h_glen[0];
+
+  DevBuf d_pq, d_ns, d_poff, d_pprof, d_items;
+  DSA_TRY(upload(ctx, d_pq, pair_q));
+  DSA_TRY(upload(ctx, d_ns, pair_ns));
+  DSA_TRY(upload(ctx, d_poff, pprof_off));
+  DSA_TRY(upload(ctx, d_items, item_words));
+  DSA_TRY(d_pprof.alloc(ctx, words * sizeof(uint32_t)));
+  plan.d_pair_q = d_pq.as<uint32_t>();
+  plan.d_pair_ns = d_ns.as<uint32_t>();
+  plan.d_pprof_off = d_poff.as<uint64_t>();
+  plan.d_pprof = d_pprof.as<uint32_t>();
+  plan.d_items = d_items.as<uint32_t>();
+  DSA_TRY(launch_pair_profile(ctx, qs, d_mat, A, o, plan));
+  phase_begin(res, PH_INTER);
+  DSA_TRY(launch_inter_local16(ctx, db, qs, plan, o, e, v.smax, out, nt));
+  phase_end(res, PH_INTER);
+
+  // ---- exact int32 rerun of saturated pairs ----
+  const uint64_t n_out = (uint64_t)nq * nt;
+  const uint32_t cap = (uint32_t)std::min<uint64_t>(n_out, 1u << 22);
+  DevBuf d_list;
+  DSA_TRY(d_list.alloc(ctx, (size_t)cap * sizeof(uint32_t)));
+  uint32_t* d_count = ctx->d_counters + 1;
+  DSA_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(uint32_t), ctx->stream));
+  {
+    uint64_t blk = std::min<uint64_t>((n_out + 255) / 256, (uint64_t)ctx->sm_count * 16);
+    k_collect_flags<<<(unsigned)blk, 256, 0, ctx->stream>>>(out.flag, n_out, d_list.as<uint32_t>(),
+                                                             cap, d_count);
+    DSA_CUDA_TRY(cudaGetLastError());
+    ++ctx->launches;
+  }
+  uint32_t count = 0;
+  DSA_CUDA_TRY(cudaMemcpyAsync(&count, d_count, sizeof(count), cudaMemcpyDeviceToHost, ctx->stream));
+  DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  *n_rerun = count;
+  if (count == 0) return DSA_OK;
+  std::vector<PairJob> jobs;
+  if (count > cap) {
+    // too many to list: rerun everything in int32
+    return score_all_vs_all(ctx, res, db, qs, mode, fe, d_mat, A, o, e, v, flags | DSA_FORCE_INT32,
+                            out, n_rerun);
+  }
+  std::vector<uint32_t> list(count);
+  DSA_CUDA_TRY(cudaMemcpyAsync(list.data(), d_list.p, count * sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+  DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  std::sort(list.begin(), list.end());
+  jobs.resize(count);
+  uint64_t scr = 0;
+  for (uint32_t k = 0; k < count; ++k) {
+    const uint32_t q = list[k] / nt, t = list[k] % nt;
+    jobs[k] = {db->h_off[t], scr, q, db->h_len[t], list[k], 0};
+    scr += db->h_len[t];
+  }
+  std::vector<uint64_t> poff(nq);
+  uint64_t pw = 0;
+  for (uint32_t q = 0; q < nq; ++q) {
+    poff[q] = pw;
+    pw += (uint64_t)A * ((qs->h_len[q] + 7u) & ~7u);
+  }
+  DevBuf d_prof32, d_poff32, d_jobs, d_scr;
+  DSA_TRY(d_prof32.alloc(ctx, pw * sizeof(int32_t)));
+  DSA_TRY(upload(ctx, d_poff32, poff));
+  DSA_TRY(launch_profile_int32(ctx, qs, d_mat, A, d_prof32.as<int32_t>(), d_poff32.as<uint64_t>()));
+  DSA_TRY(upload(ctx, d_jobs, jobs));
+  DSA_TRY(d_scr.alloc(ctx, scr * sizeof(int2)));
+  phase_begin(res, PH_INT32);
+  DSA_TRY(launch_generic_int32(ctx, db, qs, d_prof32.as<int32_t>(), d_poff32.as<uint64_t>(),
+                               d_jobs.as<PairJob>(), count, 0, d_scr.as<int2>(), mode, fe, o, e, 1,
+                               out));
+  phase_end(res, PH_INT32);
+  return DSA_OK;
+}
+
+int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair* pairs,
+               uint64_t n_pairs, int mode, uint32_t fe, const int8_t* matrix, int A, int o, int e,
+               uint32_t top_k, uint32_t flags, dsa_res** out) {
+  if (!ctx || !db || !qs || !out) { set_error("NULL argument"); return DSA_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (mode < DSA_LOCAL || mode > DSA_SEMIGLOBAL) { set_error("bad mode %d", mode); return DSA_ERR_INVALID_ARG; }
+  if (fe > 15) { set_error("bad free_ends %u", fe); return DSA_ERR_INVALID_ARG; }
+  if (A != db->A || A != qs->A) {
+    set_error("alphabet_size %d does not match the sequence sets (%d, %d)", A, db->A, qs->A);
+    return DSA_ERR_INVALID_ARG;
+  }
+  Validated v;
+  DSA_TRY(check_matrix(matrix, A, o, e, &v));
+  DSA_TRY(set_device(ctx));
+  const bool all = pairs == nullptr;
+  if (!all && top_k) {
+    set_error("top_k applies to all-vs-all searches only");
+    return DSA_ERR_UNSUPPORTED;
+  }
+  // host copy of explicit pairs (validation and planning)
+  std::vector<dsa_pair> hp;
+  if (!all) {
+    hp.resize(n_pairs);
+    if (flags & DSA_PAIRS_ON_DEVICE) {
+      DSA_CUDA_TRY(cudaMemcpyAsync(hp.data(), pairs, n_pairs * sizeof(dsa_pair),
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+      DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    } else if (n_pairs) {
+      memcpy(hp.data(), pairs, n_pairs * sizeof(dsa_pair));
+    }
+    for (uint64_t k = 0; k < n_pairs; ++k) {
+      const dsa_pair& p = hp[k];
+      if (p.query_id >= qs->n || p.target_id >= db->n || p.t_len == 0 ||
+          p.t_offset + p.t_len > db->h_len[p.target_id]) {
+        set_error("pair %llu is out of range", (unsigned long long)k);
+        return DSA_ERR_INVALID_ARG;
+      }
+    }
+  }
+  // int32 range: (m + n) * max|value step| must stay far from 2^31
+  uint32_t max_m = 0, max_n = 0;
+  for (uint32_t x : qs->h_len) max_m = std::max(max_m, x);
+  if (all) for (uint32_t x : db->h_len) max_n = std::max(max_n, x);
+  else for (const dsa_pair& p : hp) max_n = std::max(max_n, p.t_len);
+  const int64_t w = std::max<int64_t>({(int64_t)std::abs(v.smax), (int64_t)std::abs(v.smin), o, e});
+  if (((int64_t)max_m + max_n + 2) * (w + 1) >= (1ll << 29)) {
+    set_error("scores could leave the int32 range (lengths %u + %u, weight %lld)", max_m, max_n,
+              (long long)w);
+    return DSA_ERR_UNSUPPORTED;
+  }
+
+  dsa_res* res = new (std::nothrow) dsa_res;
+  if (!res) { set_error("host allocation failed"); return DSA_ERR_OOM; }
+  res->ctx = ctx; res->db = db; res->queries = qs; res->mode = mode; res->free_ends = fe;
+  res->A = A; res->gap_open = o; res->gap_extend = e;
+  res->matrix.assign(matrix, matrix + A * A);
+  res->flags = flags;
+  auto fail = [&](int rc) {
+    if (res->d_hits) ctx->release(res->d_hits, res->n_hits * sizeof(dsa_hit));
+    delete res;
+    return rc;
+  };
+
+  DevBuf d_mat;
+  if (int rc = d_mat.alloc(ctx, A * A)) return fail(rc);
+  if (cudaMemcpyAsync(d_mat.p, matrix, A * A, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+    set_error("matrix upload failed");
+    return fail(DSA_ERR_CUDA);
+  }
+
+  const uint64_t n_out = all ? (uint64_t)qs->n * db->n : n_pairs;
+  DevBuf s_score, s_qend, s_tend, s_flag;
+  int rc;
+  if ((rc = s_score.alloc(ctx, n_out * 4)) || (rc = s_qend.alloc(ctx, n_out * 4)) ||
+      (rc = s_tend.alloc(ctx, n_out * 4)) || (rc = s_flag.alloc(ctx, n_out)))
+    return fail(rc);
+  Scores sc{s_score.as<int32_t>(), s_qend.as<int32_t>(), s_tend.as<int32_t>(), s_flag.as<uint8_t>()};
+
+  if (all) {
+    uint64_t sq = 0;
+    for (uint32_t x : qs->h_len) sq += x;
+    res->cells = sq * db->n_res;
+    if ((rc = score_all_vs_all(ctx, res, db, qs, mode, fe, d_mat.as<int8_t>(), A, o, e, v, flags,
+                               sc, &res->n_rerun)))
+      return fail(rc);
+  } else {
+    std::vector<PairJob> jobs(n_pairs);
+    uint64_t scr = 0, cells = 0;
+    for (uint64_t k = 0; k < n_pairs; ++k) {
+      const dsa_pair& p = hp[k];
+      jobs[k] = {db->h_off[p.target_id] + p.t_offset, scr, p.query_id, p.t_len, (uint32_t)k, 0};
+      scr += p.t_len;
+      cells += (uint64_t)qs->h_len[p.query_id] * p.t_len;
+    }
+    res->cells = cells;
+    std::vector<uint64_t> poff(qs->n);
+    uint64_t pw = 0;
+    for (uint32_t q = 0; q < qs->n; ++q) {
+      poff[q] = pw;
+      pw += (uint64_t)A * ((qs->h_len[q] + 7u) & ~7u);
+    }
+    DevBuf d_prof, d_poff, d_jobs, d_scr;
+    if ((rc = d_prof.alloc(ctx, pw * 4)) || (rc = upload(ctx, d_poff, poff)) ||
+        (rc = upload(ctx, d_jobs, jobs)) || (rc = d_scr.alloc(ctx, scr * sizeof(int2))))
+      return fail(rc);
+    if ((rc = launch_profile_int32(ctx, qs, d_mat.as<int8_t>(), A, d_prof.as<int32_t>(),
+                                   d_poff.as<uint64_t>())))
+      return fail(rc);
+    phase_begin(res, PH_INT32);
+    if ((rc = launch_generic_int32(ctx, db, qs, d_prof.as<int32_t>(), d_poff.as<uint64_t>(),
+                                   d_jobs.as<PairJob>(), n_pairs, 0, d_scr.as<int2>(), mode, fe, o,
+                                   e, 0, sc)))
+      return fail(rc);
+    phase_end(res, PH_INT32);
+  }
+
+  // hits
+  phase_begin(res, PH_HITS);
+  if (all && top_k) {
+    const uint32_t k = std::min<uint32_t>(top_k, db->n);
+    res->n_hits = (uint64_t)qs->n * k;
+    void* p;
+    if ((rc = ctx->alloc(&p, res->n_hits * sizeof(dsa_hit)))) return fail(rc);
+    res->d_hits = (dsa_hit*)p;
+    if ((rc = launch_topk(ctx, sc, qs->n, db->n, top_k, res->d_hits))) return fail(rc);
+  } else {
+    res->n_hits = n_out;
+    void* p;
+    if ((rc = ctx->alloc(&p, std::max<uint64_t>(1, res->n_hits) * sizeof(dsa_hit)))) return fail(rc);
+    res->d_hits = (dsa_hit*)p;
+    DevBuf d_pq, d_pt, d_po;
+    if (!all) {
+      std::vector<uint32_t> pq(n_pairs), pt(n_pairs);
+      std::vector<uint64_t> po(n_pairs);
+      for (uint64_t k = 0; k < n_pairs; ++k) {
+        pq[k] = hp[k].query_id; pt[k] = hp[k].target_id; po[k] = hp[k].t_offset;
+      }
+      if ((rc = upload(ctx, d_pq, pq)) || (rc = upload(ctx, d_pt, pt)) || (rc = upload(ctx, d_po, po)))
+        return fail(rc);
+      if ((rc = launch_fill_hits(ctx, sc, d_pq.as<uint32_t>(), d_pt.as<uint32_t>(),
+                                 d_po.as<uint64_t>(), n_out, db->n, res->d_hits)))
+        return fail(rc);
+      // keep host-side pair vectors alive until the copies have been consumed
+      if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        set_error("%s", cudaGetErrorString(cudaGetLastError()));
+        return fail(DSA_ERR_CUDA);
+      }
+    } else {
+      if ((rc = launch_fill_hits(ctx, sc, nullptr, nullptr, nullptr, n_out, db->n, res->d_hits)))
+        return fail(rc);
+    }
+  }
+  phase_end(res, PH_HITS);
+  if (cudaGetLastError() != cudaSuccess) { set_error("kernel launch failed"); return fail(DSA_ERR_CUDA); }
+  *out = res;
+  return DSA_OK;
+}
+
+}  // namespace
+
+extern "C" int dsa_align(dsa_ctx* ctx, const dsa_db* db, const dsa_db* queries,
+                         const dsa_pair* pairs, uint64_t n_pairs, int mode, uint32_t free_ends,
+                         const int8_t* matrix, int alphabet_size, int gap_open, int gap_extend,
+                         uint32_t top_k, uint32_t flags, dsa_res** out) {
+  return align_impl(ctx, db, queries, pairs, n_pairs, mode, free_ends, matrix, alphabet_size,
+                    gap_open, gap_extend, top_k, flags, out);
+}
+
+extern "C" int dsa_align_batch(dsa_ctx* ctx, const dsa_db* db, const uint8_t* q_codes,
+                               const uint64_t* q_offsets, uint32_t n_queries, const dsa_pair* pairs,
+                               uint64_t n_pairs, int mode, uint32_t free_ends, const int8_t* matrix,
+                               int alphabet_size, int gap_open, int gap_extend, uint32_t top_k,
+                               uint32_t flags, dsa_res** out) {
+  if (!ctx || !out) { set_error("NULL argument"); return DSA_ERR_INVALID_ARG; }
+  dsa_db* qs = nullptr;
+  DSA_TRY(dsa_db_load(ctx, q_codes, q_offsets, n_queries, alphabet_size, &qs));
+  int rc = align_impl(ctx, db, qs, pairs, n_pairs, mode, free_ends, matrix, alphabet_size,
+                      gap_open, gap_extend, top_k, flags, out);
+  if (rc) { dsa_db_free(qs); return rc; }
+  (*out)->owned_queries = qs;
+  return DSA_OK;
+}
+
+// ---------------------------------------------------------------- traceback --
+
+static int fetch_hits(dsa_res* res) {
+  dsa_ctx* ctx = res->ctx;
+  if (res->host_valid) return DSA_OK;
+  res->h_hits.resize(res->n_hits);
+  if (res->n_hits)
+    DSA_CUDA_TRY(cudaMemcpyAsync(res->h_hits.data(), res->d_hits, res->n_hits * sizeof(dsa_hit),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+  res->h_cigar.resize(res->n_cigar);
+  if (res->n_cigar)
+    DSA_CUDA_TRY(cudaMemcpyAsync(res->h_cigar.data(), res->d_cigar, res->n_cigar * 4,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+  DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  res->host_valid = true;
+  return DSA_OK;
+}
+
+extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, uint64_t n) {
+  if (!ctx || !res || res->ctx != ctx) { set_error("bad ctx / res"); return DSA_ERR_INVALID_ARG; }
+  DSA_TRY(set_device(ctx));
+  DSA_TRY(fetch_hits(res));
+  std::vector<uint64_t> sel;
+  if (which) {
+    for (uint64_t k = 0; k < n; ++k) {
+      if (which[k] >= res->n_hits) { set_error("hit index out of range"); return DSA_ERR_INVALID_ARG; }
+      sel.push_back(which[k]);
+    }
+  } else {
+    sel.resize(res->n_hits);
+    std::iota(sel.begin(), sel.end(), 0ull);
+  }
+  const dsa_db* db = res->db;
+  const dsa_db* qs = res->queries;
+  std::vector<TbJob> jobs;
+  uint64_t cap_total = 0;
+  for (uint64_t h : sel) {
+    const dsa_hit& hit = res->h_hits[h];
+    if (hit.flags & DSA_HIT_HAS_TRACEBACK) continue;
+    if (res->mode == DSA_LOCAL && (hit.q_end < 0 || hit.t_end < 0)) continue;
+    TbJob j{};
+    j.ie = hit.q_end + 1;
+    j.je = hit.t_end + 1;
+    j.hit = (uint32_t)h;
+    j.wpr = (uint32_t)((j.je + 7) / 8);
+    j.q_start = qs->h_off[hit.query_id];
+    j.t_start = db->h_off[hit.target_id] + hit.t_offset;
+    jobs.push_back(j);
+    cap_total += (uint64_t)j.ie + j.je + 1;
+  }
+  if (jobs.empty()) return DSA_OK;
+
+  // grow the result's CIGAR array by the capacity bound
+  const uint64_t old_n = res->n_cigar;
+  void* newp = nullptr;
+  DSA_TRY(ctx->alloc(&newp, (old_n + cap_total) * sizeof(uint32_t)));
+  if (old_n)
+    DSA_CUDA_TRY(cudaMemcpyAsync(newp, res->d_cigar, old_n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (res->d_cigar) ctx->release(res->d_cigar, res->cigar_bytes);
+  res->d_cigar = (uint32_t*)newp;
+  res->cigar_bytes = (old_n + cap_total) * sizeof(uint32_t);
+
+  DevBuf d_mat, d_total;
+  DSA_TRY(d_mat.alloc(ctx, res->A * res->A));
+  DSA_CUDA_TRY(cudaMemcpyAsync(d_mat.p, res->matrix.data(), res->A * res->A, cudaMemcpyHostToDevice,
+                               ctx->stream));
+  DSA_TRY(d_total.alloc(ctx, sizeof(uint64_t)));
+  DSA_CUDA_TRY(cudaMemcpyAsync(d_total.p, &old_n, sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
+  uint64_t total = old_n;
+
+  // chunks bounded by direction-matrix memory
+  const uint64_t dir_limit = 1ull << 30;   // words (4 GiB)
+  phase_begin(res, PH_TRACE);
+  size_t k0 = 0;
+  while (k0 < jobs.size()) {
+    uint64_t dir = 0, cig = 0, scr = 0;
+    size_t k1 = k0;
+    while (k1 < jobs.size()) {
+      const uint64_t w = (uint64_t)jobs[k1].ie * jobs[k1].wpr;
+      if (k1 > k0 && dir + w > dir_limit) break;
+      jobs[k1].dir_off = dir;
+      jobs[k1].cig_off = cig;
+      jobs[k1].scr_off = scr;
+      dir += w;
+      cig += (uint64_t)jobs[k1].ie + jobs[k1].je + 1;
+      scr += (uint64_t)jobs[k1].je;
+      ++k1;
+    }
+    std::vector<TbJob> chunk(jobs.begin() + k0, jobs.begin() + k1);
+    DevBuf d_jobs, d_dir, d_cig, d_scr;
+    DSA_TRY(upload(ctx, d_jobs, chunk));
+    DSA_TRY(d_dir.alloc(ctx, dir * 4));
+    DSA_TRY(d_cig.alloc(ctx, cig * 4));
+    DSA_TRY(d_scr.alloc(ctx, scr * sizeof(int2)));
+    DSA_TRY(launch_traceback(ctx, db, qs, d_mat.as<int8_t>(), res->A, res->gap_open,
+                             res->gap_extend, res->mode, res->free_ends, d_jobs.as<TbJob>(),
+                             (uint32_t)chunk.size(), d_dir.as<uint32_t>(), d_cig.as<uint32_t>(),
+                             d_scr.as<int2>(), res->d_hits));
+    DSA_TRY(launch_cigar_compact(ctx, res->d_hits, d_jobs.as<TbJob>(), (uint32_t)chunk.size(),
+                                 d_cig.as<uint32_t>(), res->d_cigar, total, d_total.as<uint64_t>()));
+    DSA_CUDA_TRY(cudaMemcpyAsync(&total, d_total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    k0 = k1;
+  }
+  phase_end(res, PH_TRACE);
+  res->n_cigar = total;
+  res->host_valid = false;
+  return DSA_OK;
+}
+
+extern "C" int dsa_res_get(dsa_res* res, const dsa_hit** hits, uint64_t* n_hits,
+                           const uint32_t** cigar, uint64_t* n_cigar_words) {
+  if (!res) { set_error("res is NULL"); return DSA_ERR_INVALID_ARG; }
+  DSA_TRY(set_device(res->ctx));
+  if (res->flags & DSA_RESULTS_ON_DEVICE) {
+    if (hits) *hits = res->d_hits;
+    if (cigar) *cigar = res->d_cigar;
+  } else {
+    DSA_TRY(fetch_hits(res));
+    if (hits) *hits = res->h_hits.data();
+    if (cigar) *cigar = res->h_cigar.data();
+  }
+  if (n_hits) *n_hits = res->n_hits;
+  if (n_cigar_words) *n_cigar_words = res->n_cigar;
+  return DSA_OK;
+}
+
+extern "C" int dsa_res_stats(const dsa_res* res, uint64_t* cells, uint64_t* n_rerun) {
+  if (!res) { set_error("res is NULL"); return DSA_ERR_INVALID_ARG; }
+  if (cells) *cells = res->cells;
+  if (n_rerun) *n_rerun = res->n_rerun;
+  return DSA_OK;
+}
+
+extern "C" int dsa_res_timing(const dsa_res* res, double* ms, int n) {
+  if (!res || !ms || n < 0) { set_error("bad argument"); return DSA_ERR_INVALID_ARG; }
+  for (int p = 0; p < n && p < dsa_res::NPHASE; ++p) {
+    ms[p] = -1.0;
+    if (!res->used[p]) continue;
+    float t = 0.f;
+    if (cudaEventSynchronize(res->ev[2 * p + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, res->ev[2 * p], res->ev[2 * p + 1]) != cudaSuccess) {
+      set_error("event timing failed: %s", cudaGetErrorString(cudaGetLastError()));
+      return DSA_ERR_CUDA;
+    }
+    ms[p] = t;
+  }
+  return DSA_OK;
+}
+
+extern "C" int dsa_res_free(dsa_res* res) {
+  if (!res) return DSA_OK;
+  dsa_ctx* ctx = res->ctx;
+  cudaSetDevice(ctx->device);
+  for (int k = 0; k < 2 * dsa_res::NPHASE; ++k)
+    if (res->ev[k]) cudaEventDestroy(res->ev[k]);
+  if (res->d_hits) ctx->release(res->d_hits, std::max<uint64_t>(1, res->n_hits) * sizeof(dsa_hit));
+  if (res->d_cigar) ctx->release(res->d_cigar, res->cigar_bytes);
+  if (res->owned_queries) dsa_db_free(res->owned_queries);
+  delete res;
+  return DSA_OK;
+}
+
+extern "C" int dsa_probe_issue_rate(dsa_ctx* ctx, int form, double* rate) {
+  if (!ctx || !rate) { set_error("NULL argument"); return DSA_ERR_INVALID_ARG; }
+  DSA_TRY(set_device(ctx));
+  return run_issue_probe(ctx, form, rate);
+}

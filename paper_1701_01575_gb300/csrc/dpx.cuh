@@ -1,0 +1,89 @@
+// Packed int16x2 DP primitives and TMA / mbarrier helpers shared by the
+// packed kernels.  Each 32-bit register holds two independent DP cells (two
+// queries against the same target residue); the DPX instructions compute
+// both halves at once.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dsa {
+
+__device__ __forceinline__ uint32_t pack2(int lo, int hi) {
+  return (uint32_t)(lo & 0xFFFF) | ((uint32_t)hi << 16);
+}
+__device__ __forceinline__ int lo16(uint32_t v) { return (int)(int16_t)(v & 0xFFFF); }
+__device__ __forceinline__ int hi16(uint32_t v) { return (int)(int16_t)(v >> 16); }
+
+// max(a + b, c) per halfword
+__device__ __forceinline__ uint32_t addmax2(uint32_t a, uint32_t b, uint32_t c) {
+  return __viaddmax_s16x2(a, b, c);
+}
+// max(a, b, 0) per halfword
+__device__ __forceinline__ uint32_t max2_relu(uint32_t a, uint32_t b) {
+  return __vimax_s16x2_relu(a, b);
+}
+__device__ __forceinline__ uint32_t max3_2(uint32_t a, uint32_t b, uint32_t c) {
+  return __vimax3_s16x2(a, b, c);
+}
+// a + b per halfword (no carry between halves)
+__device__ __forceinline__ uint32_t add2(uint32_t a, uint32_t b) { return __vadd2(a, b); }
+
+// ---- shared-memory addressing, mbarrier and bulk-copy PTX ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: gives up after `limit_ns` nanoseconds of wall time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+// 1-D bulk copy global -> shared, completion signalled on `bar` (tx bytes).
+// dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s
+
+}  // namespace dsa

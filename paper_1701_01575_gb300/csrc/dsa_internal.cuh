@@ -1,0 +1,215 @@
+// Internal declarations shared by the libdsa translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/dsa.h"
+
+namespace dsa {
+
+// -inf sentinels.  int32: far below any reachable score, so that adding a
+// few hundred thousand gap penalties never wraps.  int16 packed lanes: the
+// lower half of the int16 range; the packed kernels only run when every real
+// value stays above it (local mode: values never fall below -(o + e)).
+constexpr int32_t NEG32 = INT32_MIN / 4;
+constexpr int32_t NEG16 = -16384;
+
+// Launch / layout constants.
+constexpr int GROUP = 32;          // targets per interleaved group (one warp)
+constexpr int CHUNK = 16;          // residues per 16-byte interleaved word
+constexpr int MAX_ALPHABET = 31;   // code 31 is reserved for padding
+
+void set_error(const char* fmt, ...);
+
+#define DSA_CUDA_TRY(expr)                                                        \
+  do {                                                                            \
+    cudaError_t e_ = (expr);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      dsa::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),      \
+                     __FILE__, __LINE__);                                         \
+      return e_ == cudaErrorMemoryAllocation ? DSA_ERR_OOM : DSA_ERR_CUDA;         \
+    }                                                                             \
+  } while (0)
+
+#define DSA_TRY(expr)            \
+  do {                           \
+    int rc_ = (expr);            \
+    if (rc_ != DSA_OK) return rc_; \
+  } while (0)
+
+}  // namespace dsa
+
+struct dsa_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0;     // 0 = unlimited
+  size_t in_use = 0;
+  int sm_count = 0;
+  int32_t* d_status = nullptr;   // device status word written by kernels
+  uint32_t* d_counters = nullptr;  // work-queue counters (reset per launch)
+  uint64_t launches = 0;         // kernels launched through this context
+  std::mutex mu;
+
+  int alloc(void** p, size_t bytes);
+  void release(void* p, size_t bytes);
+};
+
+// A device-resident sequence set (database or queries).
+struct dsa_db {
+  dsa_ctx* ctx = nullptr;
+  uint32_t n = 0;
+  uint64_t n_res = 0;
+  int A = 0;
+  // input order
+  uint8_t* d_codes = nullptr;     // n_res (+16 pad) bytes
+  uint64_t* d_off = nullptr;      // n + 1
+  uint32_t* d_len = nullptr;      // n
+  std::vector<uint64_t> h_off;
+  std::vector<uint32_t> h_len;
+  // length-sorted (descending, ties by id), lane-interleaved copy
+  uint32_t* d_perm = nullptr;     // sorted position -> id
+  uint32_t* d_slen = nullptr;     // sorted position -> length
+  std::vector<uint32_t> h_perm;
+  uint32_t n_groups = 0;
+  uint8_t* d_il = nullptr;        // [group][chunk][lane][16 B]
+  uint64_t* d_gbase = nullptr;    // byte offset of each group in d_il
+  uint32_t* d_glen = nullptr;     // longest length in each group
+  std::vector<uint64_t> h_gbase;
+  std::vector<uint32_t> h_glen;
+  uint64_t il_bytes = 0;
+  size_t bytes_held = 0;
+};
+
+struct dsa_res {
+  dsa_ctx* ctx = nullptr;
+  const dsa_db* db = nullptr;
+  const dsa_db* queries = nullptr;
+  dsa_db* owned_queries = nullptr;   // set when dsa_align_batch uploaded them
+  int mode = 0;
+  uint32_t free_ends = 15;
+  int A = 0, gap_open = 0, gap_extend = 0;
+  std::vector<int8_t> matrix;
+  uint32_t flags = 0;
+  uint64_t n_hits = 0;
+  dsa_hit* d_hits = nullptr;
+  uint32_t* d_cigar = nullptr;
+  uint64_t n_cigar = 0;
+  uint64_t cigar_bytes = 0;
+  std::vector<dsa_hit> h_hits;
+  std::vector<uint32_t> h_cigar;
+  bool host_valid = false;
+  uint64_t cells = 0;
+  uint64_t n_rerun = 0;
+  // DSA_TIMING: one begin/end event pair per phase
+  static constexpr int NPHASE = 5;
+  cudaEvent_t ev[2 * NPHASE] = {};
+  bool used[NPHASE] = {};
+};
+
+namespace dsa {
+// Phase timer over a result's events (no-op unless the result has DSA_TIMING).
+enum Phase { PH_INTER = 0, PH_INTRA = 1, PH_INT32 = 2, PH_HITS = 3, PH_TRACE = 4 };
+void phase_begin(dsa_res* res, Phase p);
+void phase_end(dsa_res* res, Phase p);
+}  // namespace dsa
+
+namespace dsa {
+
+// ---- kernels' host-side launchers (one translation unit each) ----
+
+// Work item of the generic int32 kernel: one (query, target window) pair.
+struct PairJob {
+  uint64_t t_start;   // absolute residue offset of the target window in the DB codes
+  uint64_t scratch;   // offset (in int2 elements) of this job's boundary row
+  uint32_t q;         // query index
+  uint32_t n;         // target window length
+  uint32_t out;       // output slot
+  uint32_t pad;
+};
+
+struct Scores {      // structure-of-arrays output of the score pass
+  int32_t* score = nullptr;
+  int32_t* q_end = nullptr;
+  int32_t* t_end = nullptr;
+  uint8_t* flag = nullptr;
+};
+
+// Plain / generic exact int32 kernel: any mode, any pair list.  With
+// d_jobs == nullptr the jobs are every DB target (input order) against query
+// `fixed_q`, boundary rows at the targets' residue offsets.
+int launch_generic_int32(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int32_t* d_prof,
+                         const uint64_t* d_prof_off, const PairJob* d_jobs, uint64_t n_jobs,
+                         uint32_t fixed_q, int2* d_scratch, int mode, uint32_t fe, int o, int e,
+                         uint8_t flag_value, Scores out);
+
+// Per-query int32 profile P[a][i] = S[q_i][a] (rows a = 0..A-1, row stride = m).
+int launch_profile_int32(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix, int A,
+                         int32_t* d_prof, const uint64_t* d_prof_off);
+
+// Interleaved DB build (dsa_db_load).
+int launch_interleave(dsa_ctx* ctx, dsa_db* db);
+
+// Packed 16-bit inter-sequence local kernel (all queries x all targets).
+struct InterPlan {
+  uint32_t n_pairs = 0;            // query pairs
+  uint32_t* d_pair_q = nullptr;    // 2 per pair (0xFFFFFFFF = empty half)
+  uint32_t* d_pair_ns = nullptr;   // strips per pair
+  uint64_t* d_pprof_off = nullptr; // word offset of each pair's packed profile
+  uint32_t* d_pprof = nullptr;     // packed int16x2 profiles
+  uint32_t* d_items = nullptr;     // 2 words per item: pair, first group
+  uint32_t n_items = 0;
+  uint32_t max_glen = 0;
+  int R = 0;                       // profile rows = A + 1 (last = padding)
+};
+int launch_pair_profile(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix, int A, int o,
+                        const InterPlan& plan);
+int launch_inter_local16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const InterPlan& plan,
+                         int o, int e, int smax, Scores out, uint32_t n_targets_out);
+int inter_blocks_per_sm();
+constexpr int INTER_WARPS = 8;
+constexpr int INTER_ROWS = 32;
+
+// Long-target intra-sequence (wavefront) local kernel, packed 16-bit.
+int launch_intra_local16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const InterPlan& plan,
+                         const uint32_t* d_long_ids, uint32_t n_long, int o, int e, int smax,
+                         Scores out, uint32_t n_targets_out);
+
+// Top-k per query over a dense [n_queries][n_targets] score matrix.
+int launch_topk(dsa_ctx* ctx, const Scores& s, uint32_t n_queries, uint32_t n_targets,
+                uint32_t k, dsa_hit* d_hits);
+// Dense pair results -> hit array.
+int launch_fill_hits(dsa_ctx* ctx, const Scores& s, const uint32_t* d_pair_q,
+                     const uint32_t* d_pair_t, const uint64_t* d_pair_off, uint64_t n,
+                     uint32_t n_targets, dsa_hit* d_hits);
+
+// Traceback of hits.
+struct TbJob {
+  uint64_t q_start;   // absolute offset of the query in the query codes
+  uint64_t t_start;   // absolute offset of the target window in the DB codes
+  uint64_t dir_off;   // word offset of this job's direction matrix
+  uint64_t cig_off;   // word offset of this job's CIGAR capacity (reverse-order scratch)
+  uint64_t scr_off;   // int2 offset of this job's band-boundary row
+  int32_t ie, je;     // 1-based result cell (rectangle to recompute)
+  uint32_t hit;       // hit index
+  uint32_t wpr;       // direction words per row
+};
+int launch_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,
+                     int A, int o, int e, int mode, uint32_t fe, const TbJob* d_jobs,
+                     uint32_t n_jobs, uint32_t* d_dir, uint32_t* d_cig_tmp, int2* d_scr,
+                     dsa_hit* d_hits);
+// Reverse each job's CIGAR words into `d_cigar` starting at `base`, packed in
+// job order; total words written are added to *d_total.
+int launch_cigar_compact(dsa_ctx* ctx, dsa_hit* d_hits, const TbJob* d_jobs, uint32_t n_jobs,
+                         const uint32_t* d_cig_tmp, uint32_t* d_cigar, uint64_t base,
+                         uint64_t* d_total);
+
+// Issue-rate probe.
+int run_issue_probe(dsa_ctx* ctx, int form, double* rate);
+
+}  // namespace dsa

@@ -1,0 +1,149 @@
+// Instruction issue-rate microbenchmark: warp-instructions per SM per clock
+// of one instruction form, measured with eight interleaved dependency chains
+// per thread (each step also reads the neighbouring chain, so no chain can be
+// folded at compile time) and a 32-warp CTA per SM, so the result is the
+// pipe's throughput rather than its latency.  Its figure is the denominator of the kernels'
+// roofline (cells per second = SMs x clock x rate x cells per instruction).
+#include "dsa_internal.cuh"
+#include "dpx.cuh"
+
+#include <algorithm>
+
+namespace dsa {
+namespace {
+
+constexpr int PROBE_THREADS = 1024;
+constexpr int PROBE_BLOCKS_PER_SM = 1;   // one 32-warp CTA per SM
+constexpr int CHAINS = 8;
+
+template <int FORM>
+__device__ __forceinline__ uint32_t step(uint32_t x, uint32_t a, uint32_t b) {
+  if (FORM == 0) return __viaddmax_s16x2(x, a, b);
+  if (FORM == 1) return __vimax_s16x2_relu(x, a);
+  if (FORM == 2) return __vimax3_s16x2(x, a, b);
+  if (FORM == 3) return x + a;
+  if (FORM == 4) {   // inline PTX so the max chain cannot be folded algebraically
+    uint32_t r;
+    asm volatile("max.s32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(a));
+    return r;
+  }
+  if (FORM == 5) return __vadd2(x, a);
+  if (FORM == 6) return (uint32_t)__viaddmax_s32((int)x, (int)a, (int)b);
+  return x;
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(PROBE_THREADS) k_probe(uint32_t a, uint32_t b, int iters,
+                                                         uint32_t* sink, long long* cycles) {
+  uint32_t v[CHAINS];
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) v[c] = threadIdx.x * 7u + c;
+  __syncthreads();
+  const long long t0 = clock64();
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+#pragma unroll
+      for (int c = 0; c < CHAINS; ++c) v[c] = step<FORM>(v[c], v[(c + 1) % CHAINS], b + u);
+    }
+  }
+  // pin the results before the closing clock read
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) asm volatile("" ::"r"(v[c]));
+  __syncthreads();
+  const long long t1 = clock64();
+  uint32_t acc = 0;
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) acc ^= v[c];
+  if (acc == 0x12345678u) sink[threadIdx.x] = acc;
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
+// The packed local cell update of the inter-sequence kernel, on eight
+// independent cells per thread (5 instructions per update).
+__global__ void __launch_bounds__(PROBE_THREADS) k_probe_cell(uint32_t neg_o2, uint32_t neg_e2,
+                                                              int iters, uint32_t* sink,
+                                                              long long* cycles) {
+  uint32_t Ho[CHAINS], E[CHAINS], F[CHAINS];
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) { Ho[c] = threadIdx.x + c; E[c] = c; F[c] = 3 * c; }
+  __syncthreads();
+  const long long t0 = clock64();
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+#pragma unroll
+      for (int c = 0; c < CHAINS; ++c) {
+        const uint32_t old = Ho[c];
+        E[c] = __viaddmax_s16x2(E[c], neg_e2, old);
+        const uint32_t t = __viaddmax_s16x2(old, 0x00050005u + c, E[c]);
+        const uint32_t h = __vimax_s16x2_relu(t, F[c]);
+        Ho[c] = __vadd2(h, neg_o2);
+        F[c] = __viaddmax_s16x2(F[c], neg_e2, Ho[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) asm volatile("" ::"r"(Ho[c]), "r"(F[c]), "r"(E[c]));
+  __syncthreads();
+  const long long t1 = clock64();
+  uint32_t acc = 0;
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) acc ^= Ho[c] ^ F[c];
+  if (acc == 0x12345678u) sink[threadIdx.x] = acc;
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
+}  // namespace
+
+int run_issue_probe(dsa_ctx* ctx, int form, double* rate) {
+  if (form < 0 || form > 7) {
+    set_error("unknown probe form %d", form);
+    return DSA_ERR_INVALID_ARG;
+  }
+  const int blocks = ctx->sm_count * PROBE_BLOCKS_PER_SM;
+  const int iters = 4096;
+  void* sink = nullptr;
+  void* cyc = nullptr;
+  DSA_TRY(ctx->alloc(&sink, PROBE_THREADS * sizeof(uint32_t)));
+  int rc = ctx->alloc(&cyc, blocks * sizeof(long long));
+  if (rc) { ctx->release(sink, PROBE_THREADS * sizeof(uint32_t)); return rc; }
+  uint32_t* s = (uint32_t*)sink;
+  long long* c = (long long*)cyc;
+  const uint32_t a = 0x00030001u, b = 0x00020005u;
+  for (int rep = 0; rep < 2; ++rep) {   // first launch warms up
+    switch (form) {
+      case 0: k_probe<0><<<blocks, PROBE_THREADS, 0, ctx->stream>>>(a, b, iters, s, c); break;
+      case 1: k_probe<1><<<blocks, PROBE_THREADS, 0, ctx->stream>>>(a, b, iters, s, c); break;
+      case 2: k_probe<2><<<blocks, PROBE_THREADS, 0, ctx->stream>>>(a, b, iters, s, c); break;
+      case 3: k_probe<3><<<blocks, PROBE_THREADS, 0, ctx->stream>>>(a, b, iters, s, c); break;
+      case 4: k_probe<4><<<blocks, PROBE_THREADS, 0, ctx->stream>>>(a, b, iters, s, c); break;
+      case 5: k_probe<5><<<blocks, PROBE_THREADS, 0, ctx->stream>>>(a, b, iters, s, c); break;
+      case 6: k_probe<6><<<blocks, PROBE_THREADS, 0, ctx->stream>>>(a, b, iters, s, c); break;
+      case 7: k_probe_cell<<<blocks, PROBE_THREADS, 0, ctx->stream>>>(0xFFF5FFF5u, 0xFFFFFFFFu,
+                                                                    iters, s, c); break;
+    }
+  }
+  ctx->launches += 2;
+  cudaError_t err = cudaGetLastError();
+  std::vector<long long> h(blocks);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(h.data(), c, blocks * sizeof(long long), cudaMemcpyDeviceToHost,
+                          ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  ctx->release(sink, PROBE_THREADS * sizeof(uint32_t));
+  ctx->release(cyc, blocks * sizeof(long long));
+  if (err != cudaSuccess) {
+    set_error("issue probe: %s", cudaGetErrorString(err));
+    return DSA_ERR_CUDA;
+  }
+  std::sort(h.begin(), h.end());
+  const double mean = (double)h[h.size() / 2];   // median CTA
+  const double instr_per_thread = (double)iters * 16 * CHAINS * (form == 7 ? 5 : 1);
+  const double warp_instr_per_sm =
+      instr_per_thread * PROBE_THREADS / 32.0 * PROBE_BLOCKS_PER_SM;
+  *rate = warp_instr_per_sm / mean;
+  return DSA_OK;
+}
+
+}  // namespace dsa

@@ -1,0 +1,275 @@
+// Start coordinates and CIGAR for reported hits (the paper's "location and
+// traceback", Sec. I and the alignment object of Sec. II.B.1).
+//
+// One warp per hit recomputes the exact int32 DP over the rectangle from
+// (0, 0) to the hit's end cell as an anti-diagonal wavefront: lane k owns
+// ROWS consecutive query rows of a band of 32*ROWS rows, processes column
+// j = step - k, and hands its last row's H and F to lane k+1 through a warp
+// shuffle; bands are chained through a boundary row in global memory.  For
+// every cell it stores a 4-bit decision word:
+//   bits 0-1  source of H: 0 = diagonal (M), 1 = F (I), 2 = E (D), 3 = stop
+//             (local cell equal to 0); tested in the order stop, M, F, E;
+//   bit 2     E opened here: H[i][j-1] - o >= E[i][j-1] - e;
+//   bit 3     F opened here: H[i-1][j] - o >= F[i-1][j] - e;
+// eight cells per 32-bit word along the row.  Lane 0 then walks back from the
+// end cell (priority stop > M > I > D, opening preferred on ties) and writes
+// run-length CIGAR words in reverse order; a second kernel packs them
+// forward into the result's CIGAR array.
+#include "dsa_internal.cuh"
+
+namespace dsa {
+namespace {
+
+constexpr int ROWS = 8;
+constexpr int BAND = 32 * ROWS;
+
+__device__ __forceinline__ int32_t h_row0(int mode, uint32_t fe, int64_t j, int o, int e) {
+  if (j == 0 || mode == DSA_LOCAL || (mode == DSA_SEMIGLOBAL && (fe & DSA_FREE_T_BEGIN))) return 0;
+  return -(o + (int32_t)(j - 1) * e);
+}
+__device__ __forceinline__ int32_t h_col0(int mode, uint32_t fe, int64_t i, int o, int e) {
+  if (i == 0 || mode == DSA_LOCAL || (mode == DSA_SEMIGLOBAL && (fe & DSA_FREE_Q_BEGIN))) return 0;
+  return -(o + (int32_t)(i - 1) * e);
+}
+
+struct RevCigar {
+  uint32_t* out;
+  uint32_t n = 0;
+  int op = -1;
+  uint32_t run = 0;
+  __device__ void emit(int o) {
+    if (o == op) {
+      ++run;
+    } else {
+      flush();
+      op = o;
+      run = 1;
+    }
+  }
+  __device__ void flush() {
+    if (run) out[n++] = (run << 4) | (uint32_t)op;
+    run = 0;
+  }
+};
+
+__global__ void __launch_bounds__(128) k_traceback(
+    const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
+    const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
+    const TbJob* __restrict__ jobs, uint32_t n_jobs, uint32_t* __restrict__ dir,
+    uint32_t* __restrict__ cig_tmp, int2* __restrict__ scratch, dsa_hit* __restrict__ hits) {
+  __shared__ int8_t S[32 * 32];
+  for (int x = threadIdx.x; x < A * A; x += blockDim.x) S[x] = Sg[x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x / 32);
+  const bool local = mode == DSA_LOCAL;
+  for (uint32_t w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w < n_jobs; w += warps) {
+    const TbJob jb = jobs[w];
+    const int32_t ie = jb.ie, je = jb.je;
+    const uint8_t* q = qcodes + jb.q_start;
+    const uint8_t* t = tcodes + jb.t_start;
+    uint32_t* D = dir + jb.dir_off;
+    int2* scr = scratch + jb.scr_off;
+    const uint32_t wpr = jb.wpr;
+
+    if (ie > 0 && je > 0) {
+      for (int32_t i0 = 0; i0 < ie; i0 += BAND) {
+        const int32_t r0 = i0 + lane * ROWS;   // rows r0+1 .. r0+ROWS
+        int32_t H[ROWS], E[ROWS];
+        uint32_t nb[ROWS];
+        int qc[ROWS];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+          const int32_t i = r0 + r + 1;
+          H[r] = h_col0(mode, fe, i, o, e);
+          E[r] = NEG32;
+          nb[r] = 0;
+          qc[r] = i <= ie ? q[i - 1] : 0;
+        }
+        int32_t diag = h_col0(mode, fe, r0, o, e);
+        int32_t sendH = 0, sendF = NEG32;
+        const int32_t steps = je + 31;
+        for (int32_t s = 1; s <= steps; ++s) {
+          const int32_t upH = __shfl_up_sync(0xFFFFFFFFu, sendH, 1);
+          const int32_t upF = __shfl_up_sync(0xFFFFFFFFu, sendF, 1);
+          const int32_t j = s - lane;
+          if (j >= 1 && j <= je && r0 < ie) {
+            int32_t Hup, Fup;
+            if (lane == 0) {
+              if (i0 == 0) {
+                Hup = h_row0(mode, fe, j, o, e);
+                Fup = NEG32;
+              } else {
+                const int2 v = scr[j - 1];
+                Hup = v.x;
+                Fup = v.y;
+              }
+            } else {
+              Hup = upH;
+              Fup = upF;
+            }
+            const int a = t[j - 1];
+            int32_t d = diag;
+            diag = Hup;
+            int32_t F = Fup, Hp = Hup;
+            const int sh = 4 * ((j - 1) & 7);
+            const bool flushw = ((j & 7) == 0) || j == je;
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+              const int32_t i = r0 + r + 1;
+              if (i <= ie) {
+                const int32_t fo = Hp - o, fx = F - e;
+                F = max(fx, fo);
+                const int32_t eo = H[r] - o, ex = E[r] - e;
+                E[r] = max(ex, eo);
+                const int32_t m = d + S[qc[r] * A + a];
+                int32_t v = max(m, max(E[r], F));
+                if (local) v = max(v, 0);
+                uint32_t src;
+                if (local && v == 0) src = 3;
+                else if (v == m) src = 0;
+                else if (v == F) src = 1;
+                else src = 2;
+                const uint32_t nib = src | ((eo >= ex) ? 4u : 0u) | ((fo >= fx) ? 8u : 0u);
+                nb[r] |= nib << sh;
+                if (flushw) {
+                  D[(uint64_t)(i - 1) * wpr + (uint32_t)(j - 1) / 8u] = nb[r];
+                  nb[r] = 0;
+                }
+                d = H[r];
+                H[r] = v;
+                Hp = v;
+              }
+            }
+            sendH = Hp;
+            sendF = F;
+            if (lane == 31) scr[j - 1] = make_int2(Hp, F);
+          }
+        }
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      RevCigar c;
+      c.out = cig_tmp + jb.cig_off;
+      int32_t i = ie, j = je;
+      int st = 0;  // 0 = H, 1 = F, 2 = E
+      const bool sg = mode == DSA_SEMIGLOBAL;
+      // every residue is consumed by at most two iterations (a change of
+      // state, then the move), so 2 (ie + je) + 2 iterations always suffice;
+      // the guards below keep a corrupt decision word from indexing outside
+      // the rectangle
+      for (int64_t guard = 2 * ((int64_t)ie + je) + 2; guard > 0; --guard) {
+        if (st == 0) {
+          if (sg && ((i == 0 && (fe & DSA_FREE_T_BEGIN)) || (j == 0 && (fe & DSA_FREE_Q_BEGIN))))
+            break;
+          if (i == 0 || j == 0) {
+            if (local) break;
+            while (j > 0) { c.emit(2); --j; }
+            while (i > 0) { c.emit(1); --i; }
+            break;
+          }
+          const uint32_t nib = (D[(uint64_t)(i - 1) * wpr + (uint32_t)(j - 1) / 8u] >> (4 * ((j - 1) & 7))) & 15u;
+          const uint32_t src = nib & 3u;
+          if (src == 3) break;
+          if (src == 0) { c.emit(0); --i; --j; }
+          else st = src == 1 ? 1 : 2;
+        } else if (st == 1) {
+          if (i <= 0 || j <= 0) break;
+          const uint32_t nib = (D[(uint64_t)(i - 1) * wpr + (uint32_t)(j - 1) / 8u] >> (4 * ((j - 1) & 7))) & 15u;
+          c.emit(1);
+          if (nib & 8u) st = 0;
+          --i;
+        } else {
+          if (i <= 0 || j <= 0) break;
+          const uint32_t nib = (D[(uint64_t)(i - 1) * wpr + (uint32_t)(j - 1) / 8u] >> (4 * ((j - 1) & 7))) & 15u;
+          c.emit(2);
+          if (nib & 4u) st = 0;
+          --j;
+        }
+      }
+      c.flush();
+      dsa_hit* h = hits + jb.hit;
+      h->q_begin = i;
+      h->t_begin = j;
+      h->cigar_len = c.n;
+      h->flags |= DSA_HIT_HAS_TRACEBACK;
+    }
+  }
+}
+
+// Exclusive scan of the jobs' CIGAR word counts (single CTA), then a reversed copy.
+__global__ void __launch_bounds__(1024) k_cigar_offsets(dsa_hit* __restrict__ hits,
+                                                        const TbJob* __restrict__ jobs,
+                                                        uint32_t n, uint64_t base,
+                                                        uint64_t* __restrict__ total) {
+  __shared__ uint64_t part[1024];
+  const uint32_t per = (n + 1023) / 1024;
+  const uint32_t lo = threadIdx.x * per, hi = min(n, lo + per);
+  uint64_t sum = 0;
+  for (uint32_t x = lo; x < hi; ++x) sum += hits[jobs[x].hit].cigar_len;
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const uint64_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint64_t run = base + part[threadIdx.x] - sum;
+  for (uint32_t x = lo; x < hi; ++x) {
+    dsa_hit* h = hits + jobs[x].hit;
+    h->cigar_off = run;
+    run += h->cigar_len;
+  }
+  if (threadIdx.x == 1023) *total += part[1023];
+}
+
+__global__ void k_cigar_copy(const dsa_hit* __restrict__ hits, const TbJob* __restrict__ jobs,
+                             uint32_t n, const uint32_t* __restrict__ tmp,
+                             uint32_t* __restrict__ out) {
+  const uint32_t warps = gridDim.x * (blockDim.x / 32);
+  const int lane = threadIdx.x & 31;
+  for (uint32_t w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w < n; w += warps) {
+    const dsa_hit h = hits[jobs[w].hit];
+    const uint32_t* src = tmp + jobs[w].cig_off;
+    for (uint32_t k = lane; k < h.cigar_len; k += 32) out[h.cigar_off + k] = src[h.cigar_len - 1 - k];
+  }
+}
+
+}  // namespace
+
+int launch_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,
+                     int A, int o, int e, int mode, uint32_t fe, const TbJob* d_jobs,
+                     uint32_t n_jobs, uint32_t* d_dir, uint32_t* d_cig_tmp, int2* d_scr,
+                     dsa_hit* d_hits) {
+  if (n_jobs == 0) return DSA_OK;
+  const int threads = 128;
+  uint64_t blocks = ((uint64_t)n_jobs * 32 + threads - 1) / threads;
+  if (blocks > (uint64_t)ctx->sm_count * 16) blocks = (uint64_t)ctx->sm_count * 16;
+  k_traceback<<<(unsigned)blocks, threads, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix,
+                                                             A, o, e, mode, fe, d_jobs, n_jobs,
+                                                             d_dir, d_cig_tmp, d_scr, d_hits);
+  DSA_CUDA_TRY(cudaGetLastError());
+  ++ctx->launches;
+  return DSA_OK;
+}
+
+int launch_cigar_compact(dsa_ctx* ctx, dsa_hit* d_hits, const TbJob* d_jobs, uint32_t n_jobs,
+                         const uint32_t* d_cig_tmp, uint32_t* d_cigar, uint64_t base,
+                         uint64_t* d_total) {
+  if (n_jobs == 0) return DSA_OK;
+  k_cigar_offsets<<<1, 1024, 0, ctx->stream>>>(d_hits, d_jobs, n_jobs, base, d_total);
+  DSA_CUDA_TRY(cudaGetLastError());
+  ++ctx->launches;
+  uint64_t blocks = ((uint64_t)n_jobs * 32 + 255) / 256;
+  if (blocks > (uint64_t)ctx->sm_count * 16) blocks = (uint64_t)ctx->sm_count * 16;
+  k_cigar_copy<<<(unsigned)blocks, 256, 0, ctx->stream>>>(d_hits, d_jobs, n_jobs, d_cig_tmp,
+                                                          d_cigar);
+  DSA_CUDA_TRY(cudaGetLastError());
+  ++ctx->launches;
+  return DSA_OK;
+}
+
+}  // namespace dsa

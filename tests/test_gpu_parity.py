@@ -1,0 +1,257 @@
+"""GPU parity: libdsa (through the C ABI) against the CPU oracle, element by element.
+
+Scores, end cells, begin cells and CIGARs are integers: the bar is bit-exact.
+Sizes span several strips (32 query rows), interleave chunks (16 residues),
+warp groups (32 targets) and CTA blocks (8 groups), with ragged tails.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1701_01575_gb300 import dsa
+from paper_1701_01575_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1701_01575_gb300 import build
+    build.build()
+    c = dsa.Context(0)
+    yield c
+    c.close()
+
+
+def oracle_all(queries, db, S, o, e, mode=oracle.LOCAL, fe=15):
+    return oracle.score_all_vs_all(queries, db, S, o, e, mode, fe)
+
+
+def gpu_all(ctx, queries, db, S, o, e, mode=dsa.LOCAL, fe=15, flags=0, A=None):
+    A = A or S.shape[0]
+    d = ctx.load_set(db, A)
+    q = ctx.load_set(queries, A)
+    r = ctx.align(d, q, S, o, e, mode=mode, free_ends=fe, flags=flags)
+    h = r.hits()
+    cells, rerun = r.stats()
+    shape = (queries.n, db.n)
+    assert (h["query_id"].reshape(shape) == np.arange(queries.n)[:, None]).all()
+    assert (h["target_id"].reshape(shape) == np.arange(db.n)[None, :]).all()
+    return (h["score"].reshape(shape), h["q_end"].reshape(shape), h["t_end"].reshape(shape),
+            h["flags"].reshape(shape), rerun, r)
+
+
+def assert_same(gpu, orc, what=""):
+    for name, g, o_ in zip(("score", "q_end", "t_end"), gpu, orc):
+        bad = np.argwhere(g != o_)
+        assert len(bad) == 0, f"{what} {name}: {len(bad)} mismatches, first {bad[:5].tolist()} " \
+                              f"gpu={g[tuple(bad[0])]} oracle={o_[tuple(bad[0])]}"
+
+
+# ---------------------------------------------------------------- local, packed path
+
+def test_protein_vs_db_full(ctx):
+    """1 query (128) vs 2,000 targets U{50..500}, BLOSUM62 11/1, local."""
+    wl = W.protein_vs_db()
+    orc = oracle_all(wl.queries, wl.db, wl.matrix, 11, 1)
+    for flags in (0, dsa.FORCE_INT32, dsa.PLAIN_FORM):
+        g = gpu_all(ctx, wl.queries, wl.db, wl.matrix, 11, 1, flags=flags)
+        assert_same(g[:3], orc, f"flags={flags}")
+
+
+def test_protein_search_small(ctx):
+    """Odd query count, lengths across strip boundaries, many groups, ragged tails."""
+    rng = np.random.default_rng(11)
+    bg = W.protein_background()
+    qlens = np.array([1, 31, 32, 33, 64, 65, 200, 517, 95])
+    queries = W._make_set(rng, qlens, bg)
+    tl = np.concatenate([rng.integers(1, 40, 300), rng.integers(40, 700, 2500),
+                         [1, 15, 16, 17, 2000, 1999]])
+    db = W._make_set(rng, tl, bg)
+    S = W.blosum62()
+    orc = oracle_all(queries, db, S, 11, 1)
+    g = gpu_all(ctx, queries, db, S, 11, 1)
+    assert_same(g[:3], orc, "packed")
+    assert g[4] == 0
+
+
+@pytest.mark.parametrize("o,e", [(1, 0), (3, 3), (5, 2), (12, 1), (40, 7)])
+def test_local_gap_params_and_ties(ctx, o, e):
+    """Small alphabets force many ties: exercises the (j, i) end-cell rule."""
+    rng = np.random.default_rng(100 + o * 10 + e)
+    S = W.dna_matrix(2, -3)
+    queries = W.random_dna(rng, 5, 1, 120)
+    db = W.random_dna(rng, 700, 1, 300)
+    orc = oracle_all(queries, db, S, o, e)
+    g = gpu_all(ctx, queries, db, S, o, e)
+    assert_same(g[:3], orc, f"o={o} e={e}")
+
+
+def test_asymmetric_matrix_orientation(ctx):
+    """Rows of S are query residues, columns target residues."""
+    rng = np.random.default_rng(5)
+    S = rng.integers(-6, 7, size=(7, 7)).astype(np.int8)
+    queries = W._make_set(rng, rng.integers(1, 90, 4), np.full(7, 1 / 7))
+    db = W._make_set(rng, rng.integers(1, 200, 400), np.full(7, 1 / 7))
+    orc = oracle_all(queries, db, S, 4, 1)
+    for flags in (0, dsa.FORCE_INT32):
+        g = gpu_all(ctx, queries, db, S, 4, 1, flags=flags)
+        assert_same(g[:3], orc, f"flags={flags}")
+
+
+def test_all_zero_local(ctx):
+    S = np.full((4, 4), -1, dtype=np.int8)
+    q = W.SeqSet.from_list([np.zeros(40, np.uint8)])
+    db = W.SeqSet.from_list([np.ones(n, np.uint8) for n in (1, 5, 70)])
+    g = gpu_all(ctx, q, db, S, 3, 1)
+    assert (g[0] == 0).all() and (g[1] == -1).all() and (g[2] == -1).all()
+
+
+def test_saturation_rerun_exact(ctx):
+    """Scores above the int16 range: flagged by the packed pass, rerun exactly in int32."""
+    w = W.PROTEIN_LETTERS.index("W")
+    rng = np.random.default_rng(3)
+    bg = W.protein_background()
+    run = np.full(3500, w, np.uint8)
+    queries = W.SeqSet.from_list([run, rng.choice(20, 300, p=bg).astype(np.uint8), run[:100]])
+    db = W.SeqSet.from_list([run, np.concatenate([rng.choice(20, 50, p=bg).astype(np.uint8), run]),
+                             rng.choice(20, 400, p=bg).astype(np.uint8), run[:2990]])
+    S = W.blosum62()
+    orc = oracle_all(queries, db, S, 11, 1)
+    g = gpu_all(ctx, queries, db, S, 11, 1)
+    assert_same(g[:3], orc, "saturation")
+    assert g[0][0, 0] == 3500 * 11 and g[0][0, 1] == 3500 * 11
+    assert g[4] >= 3 and (g[3][0, :2] & dsa.HIT_RERUN_INT32).all()
+
+
+# ---------------------------------------------------------------- other modes (int32 path)
+
+@pytest.mark.parametrize("mode,fe", [(dsa.GLOBAL, 15), (dsa.SEMIGLOBAL, 15), (dsa.SEMIGLOBAL, 12),
+                                     (dsa.SEMIGLOBAL, 3), (dsa.SEMIGLOBAL, 9), (dsa.SEMIGLOBAL, 0)])
+def test_global_semiglobal_all_vs_all(ctx, mode, fe):
+    rng = np.random.default_rng(7 + fe)
+    bg = W.protein_background()
+    queries = W._make_set(rng, rng.integers(1, 70, 3), bg)
+    db = W._make_set(rng, rng.integers(1, 150, 300), bg)
+    S = W.blosum62()
+    orc = oracle_all(queries, db, S, 10, 1, mode, fe)
+    g = gpu_all(ctx, queries, db, S, 10, 1, mode=mode, fe=fe)
+    assert_same(g[:3], orc, f"mode={mode} fe={fe}")
+
+
+def test_explicit_pairs_reads_in_windows(ctx):
+    wl = W.reads_vs_windows(n_reads=3000, ref_len=200_000)
+    S = wl.matrix
+    p = wl.pairs
+    sc, qe, te = oracle.score_pairs(wl.queries.codes, wl.queries.offsets, wl.db.codes,
+                                    wl.db.offsets, p["query_id"], p["target_id"], S, 6, 1,
+                                    oracle.SEMIGLOBAL, wl.free_ends, pair_toff=p["t_offset"],
+                                    pair_tlen=p["t_len"])
+    d = ctx.load_set(wl.db, 4)
+    q = ctx.load_set(wl.queries, 4)
+    r = ctx.align(d, q, S, 6, 1, mode=dsa.SEMIGLOBAL, free_ends=wl.free_ends, pairs=p)
+    h = r.hits()
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), "pairs")
+    assert (h["t_offset"] == p["t_offset"]).all()
+
+
+# ---------------------------------------------------------------- top-k and traceback
+
+def test_topk_order(ctx):
+    rng = np.random.default_rng(21)
+    S = W.dna_matrix(1, -1)   # many tied scores
+    queries = W.random_dna(rng, 3, 10, 40)
+    db = W.random_dna(rng, 1500, 5, 60)
+    sc, qe, te = oracle_all(queries, db, S, 2, 1)
+    d = ctx.load_set(db, 4)
+    q = ctx.load_set(queries, 4)
+    for k in (1, 10, 16, 40):
+        r = ctx.align(d, q, S, 2, 1, top_k=k)
+        h = r.hits().reshape(queries.n, k)
+        for qi in range(queries.n):
+            order = sorted(range(db.n), key=lambda t: (-sc[qi, t], t))[:k]
+            assert h["target_id"][qi].tolist() == order
+            assert h["score"][qi].tolist() == [sc[qi, t] for t in order]
+            assert h["q_end"][qi].tolist() == [qe[qi, t] for t in order]
+
+
+def check_traceback(h, cig, queries, db, S, o, e, mode, fe):
+    for x in h:
+        q = queries.seq(int(x["query_id"]))
+        t = db.seq(int(x["target_id"]))[int(x["t_offset"]):]
+        if mode == oracle.LOCAL and x["score"] == 0:
+            assert x["cigar_len"] == 0
+            continue
+        qb, tb, c = oracle.traceback(q, t, S, o, e, mode, fe, int(x["q_end"]), int(x["t_end"]))
+        got = cig[int(x["cigar_off"]):int(x["cigar_off"]) + int(x["cigar_len"])]
+        assert (int(x["q_begin"]), int(x["t_begin"])) == (qb, tb)
+        assert got.tolist() == c.tolist(), (oracle.cigar_string(got), oracle.cigar_string(c))
+
+
+@pytest.mark.parametrize("mode,fe", [(dsa.LOCAL, 15), (dsa.GLOBAL, 15), (dsa.SEMIGLOBAL, 15),
+                                     (dsa.SEMIGLOBAL, 12), (dsa.SEMIGLOBAL, 3)])
+def test_traceback_matches_oracle(ctx, mode, fe):
+    rng = np.random.default_rng(31 + mode + fe)
+    S = W.dna_matrix(2, -3)
+    base = W.random_dna(rng, 4, 20, 400)
+    # related targets: mutated copies, so alignments have gaps
+    tl = []
+    for k in range(60):
+        src = base.seq(k % base.n)
+        tl.append(W.mutate(rng, src, 0.08, 0.04) if k % 3 else rng.integers(0, 4, 50).astype(np.uint8))
+    tl = [x if len(x) else np.zeros(1, np.uint8) for x in tl]
+    db = W.SeqSet.from_list(tl)
+    d = ctx.load_set(db, 4)
+    q = ctx.load_set(base, 4)
+    r = ctx.align(d, q, S, 5, 2, mode=mode, free_ends=fe)
+    ctx.traceback(r)
+    h = r.hits()
+    check_traceback(h, r.cigar(), base, db, S, 5, 2, mode, fe)
+    assert (h["flags"] & dsa.HIT_HAS_TRACEBACK).sum() >= len(h) // 2
+
+
+def test_traceback_topk_protein_long_hits(ctx):
+    """Hits spanning several traceback bands (256 rows) and wide targets."""
+    rng = np.random.default_rng(41)
+    bg = W.protein_background()
+    q0 = rng.choice(20, 900, p=bg).astype(np.uint8)
+    targets = [W.mutate(rng, q0, 0.2, 0.02, alphabet=20) for _ in range(6)]
+    targets += [rng.choice(20, n, p=bg).astype(np.uint8) for n in rng.integers(50, 1200, 200)]
+    db = W.SeqSet.from_list(targets)
+    queries = W.SeqSet.from_list([q0, rng.choice(20, 300, p=bg).astype(np.uint8)])
+    S = W.blosum62()
+    d = ctx.load_set(db, 24)
+    q = ctx.load_set(queries, 24)
+    r = ctx.align(d, q, S, 11, 1, top_k=10)
+    ctx.traceback(r)
+    h = r.hits()
+    check_traceback(h, r.cigar(), queries, db, S, 11, 1, oracle.LOCAL, 15)
+    assert h["score"][0] > 1000
+
+
+def test_issue_probe(ctx):
+    for form in range(8):
+        rate = ctx.probe_issue_rate(form)
+        assert 0.05 < rate < 16, (form, rate)
+
+
+def test_memory_budget_enforced():
+    c = dsa.Context(0, mem_budget=1 << 20)
+    rng = np.random.default_rng(0)
+    db = W.random_dna(rng, 10, 200_000, 200_000)
+    with pytest.raises(dsa.DsaError) as ei:
+        c.load_set(db, 4)
+    assert ei.value.code == dsa.ERR_OVER_BUDGET
+    c.close()
+
+
+def test_bad_arguments_rejected(ctx):
+    rng = np.random.default_rng(0)
+    db = W.random_dna(rng, 10, 5, 50)
+    with pytest.raises(dsa.DsaError):
+        ctx.load(np.array([0, 1, 9], np.uint8), np.array([0, 3], np.uint64), 4)   # code >= A
+    d = ctx.load_set(db, 4)
+    with pytest.raises(dsa.DsaError):
+        ctx.align(d, d, W.dna_matrix(1, -1), 1, 2)                               # e > o
+    with pytest.raises(dsa.DsaError):
+        ctx.align(d, d, W.blosum62(), 1, 1)                                      # A mismatch
