@@ -197,6 +197,39 @@ int dsa_sync(dsa_ctx* ctx);
  * add-max (DPX), 7 = the packed local cell update mix. */
 int dsa_probe_issue_rate(dsa_ctx* ctx, int form, double* warp_instr_per_sm_per_clk);
 
+/* Exact int32 scores and end cells of explicit pairs, allocating nothing.
+ *
+ * The paper has no counterpart to this entry point: it exists for callers
+ * that cannot allocate device memory -- an application that gives every byte
+ * of device memory to its own pool, a latency-critical serving thread that
+ * may not block on the device allocator, or code recording work while
+ * allocation is not permitted.  Every input and output is device memory the
+ * caller owns: query and target codes with their uint64 offsets (sequence k
+ * = codes[offsets[k] .. offsets[k+1])), `n_pairs` dsa_pair records, the
+ * A x A int8 matrix, and three int32 output arrays of `n_pairs` entries
+ * (score, q_end, t_end, as dsa_align reports them for explicit pairs).  The
+ * call works on the current CUDA device and enqueues one kernel on
+ * `cuda_stream` (NULL = the legacy default stream); it does not synchronize.
+ *
+ * Scratch: the query strips' boundary rows live in a fixed 32 MiB array
+ * inside the library (one per device that loads the library, held until the
+ * process exits).  `max_t_len`, an upper bound on every pair's t_len, must
+ * be at most 32768; larger values return DSA_ERR_INVALID_ARG.  The first
+ * call on each device looks up that array's device address (with the device
+ * current); make that first call before any stream capture.  Every call
+ * shares the array and no part of it needs to start at zero (each pair
+ * writes its boundary row before reading it), so calls whose kernels overlap
+ * on the GPU race on it: order them on one stream or synchronize between
+ * them.  A pair whose ids, window, lengths or codes are out of range gets
+ * score INT32_MIN and ends -2 instead of a result. */
+int dsa_score_pairs_noalloc(const uint8_t* d_q_codes, const uint64_t* d_q_offsets,
+                            uint32_t n_queries, const uint8_t* d_t_codes,
+                            const uint64_t* d_t_offsets, uint32_t n_targets,
+                            const dsa_pair* d_pairs, uint64_t n_pairs, int mode,
+                            uint32_t free_ends, const int8_t* d_matrix, int alphabet_size,
+                            int gap_open, int gap_extend, uint32_t max_t_len, int32_t* d_score,
+                            int32_t* d_q_end, int32_t* d_t_end, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,7 +37,7 @@ assert HIT_DTYPE.itemsize == 56 and PAIR_DTYPE.itemsize == 24
 SYMBOLS = ["dsa_create", "dsa_destroy", "dsa_last_error", "dsa_mem_in_use", "dsa_db_load",
            "dsa_db_free", "dsa_db_info", "dsa_align", "dsa_align_batch", "dsa_traceback",
            "dsa_res_get", "dsa_res_stats", "dsa_res_free", "dsa_sync", "dsa_probe_issue_rate",
-           "dsa_res_timing", "dsa_kernel_launches"]
+           "dsa_res_timing", "dsa_kernel_launches", "dsa_score_pairs_noalloc"]
 
 
 class DsaError(RuntimeError):
@@ -85,6 +85,9 @@ def load_library(path: str = LIB_PATH):
     lib.dsa_res_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     lib.dsa_kernel_launches.argtypes = [_vp]
     lib.dsa_kernel_launches.restype = ctypes.c_uint64
+    lib.dsa_score_pairs_noalloc.argtypes = [_vp, _vp, _u32, _vp, _vp, _u32, _vp, _u64, ctypes.c_int,
+                                            _u32, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            _u32, _vp, _vp, _vp, _vp]
     _lib = lib
     return lib
 
