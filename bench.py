@@ -219,6 +219,7 @@ def bench_ours(args):
     ms_local = ev0.elapsed_time(ev1)
     phase = {k: [] for k in dsa.PHASES}
     reruns = 0
+    pcells = results[0].phase_cells()
     for r in results:
         t = r.timing()
         for k, v in t.items():
@@ -247,7 +248,7 @@ def bench_ours(args):
     rate = ctx.probe_issue_rate(0)     # DPX s16x2 add-max, warp-instr / SM / clk
     sm_mhz = clk.get("sm_mhz") or (props.clock_rate / 1e3 if hasattr(props, "clock_rate") else None)
     if inter_ms and sm_mhz:
-        achieved = cells_per_step / (inter_ms / 1e3) / 1e9
+        achieved = pcells["inter16"] / (inter_ms / 1e3) / 1e9
         # 6 algorithmic int32 ops per cell (H-o, E, F, max with diagonal, max with F/0,
         # running best); in packed 16x2 form one instruction covers 2 cells
         peak = props.multi_processor_count * sm_mhz * 1e6 * rate * 32 * 2 / 6 / 1e9
@@ -258,6 +259,8 @@ def bench_ours(args):
                                          f"{rate:.3f} DPX warp-instr/SM/clk (measured) x 32 lanes "
                                          "x 2 cells / 6 ops"}
     out["phases_ms"] = {k: round(statistics.mean(v), 3) for k, v in phase.items() if v}
+    out["phase_gcups"] = {k: round(pcells[k] / (statistics.mean(v) / 1e3) / 1e9, 1)
+                          for k, v in phase.items() if v and pcells.get(k)}
     out["saturation_reruns_per_step"] = reruns / args.steps
 
     if rank == 0 and not args.no_plain:

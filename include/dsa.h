@@ -183,6 +183,8 @@ int dsa_res_stats(const dsa_res* res, uint64_t* cells, uint64_t* n_rerun);
  * hit assembly, ms[4] traceback (all dsa_traceback calls).  Phases that did
  * not run report -1.  `n` is the length of `ms` (at most 5 are written). */
 int dsa_res_timing(const dsa_res* res, double* ms, int n);
+/* DP cells computed in each of the phases above (same order; 0 if none). */
+int dsa_res_phase_cells(const dsa_res* res, uint64_t* cells, int n);
 int dsa_res_free(dsa_res* res);
 
 /* Wait for all queued work of the context; returns a device-side status if

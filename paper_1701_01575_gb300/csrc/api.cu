@@ -6,6 +6,7 @@
 #include "dsa_internal.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -100,18 +101,18 @@ int check_matrix(const int8_t* matrix, int A, int o, int e, Validated* v) {
 
 }  // namespace
 
-void phase_begin(dsa_res* res, Phase p) {
+void phase_begin(dsa_res* res, Phase p, cudaStream_t on) {
   if (!res || !(res->flags & DSA_TIMING)) return;
   if (!res->ev[2 * p]) {
     cudaEventCreate(&res->ev[2 * p]);
     cudaEventCreate(&res->ev[2 * p + 1]);
   }
-  if (!res->used[p]) cudaEventRecord(res->ev[2 * p], res->ctx->stream);
+  if (!res->used[p]) cudaEventRecord(res->ev[2 * p], on ? on : res->ctx->stream);
 }
 
-void phase_end(dsa_res* res, Phase p) {
+void phase_end(dsa_res* res, Phase p, cudaStream_t on) {
   if (!res || !(res->flags & DSA_TIMING) || !res->ev[2 * p + 1]) return;
-  cudaEventRecord(res->ev[2 * p + 1], res->ctx->stream);
+  cudaEventRecord(res->ev[2 * p + 1], on ? on : res->ctx->stream);
   res->used[p] = true;
 }
 
@@ -121,7 +122,7 @@ using namespace dsa;
 
 // ---------------------------------------------------------------- context --
 
-int dsa_ctx::alloc(void** p, size_t bytes) {
+int dsa_ctx::alloc(void** p, size_t bytes, cudaStream_t on) {
   *p = nullptr;
   std::lock_guard<std::mutex> lk(mu);
   if (budget && in_use + bytes > budget) {
@@ -129,7 +130,7 @@ int dsa_ctx::alloc(void** p, size_t bytes) {
               budget);
     return DSA_ERR_OVER_BUDGET;
   }
-  cudaError_t e = cudaMallocAsync(p, bytes, stream);
+  cudaError_t e = cudaMallocAsync(p, bytes, on ? on : stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -140,9 +141,9 @@ int dsa_ctx::alloc(void** p, size_t bytes) {
   return DSA_OK;
 }
 
-void dsa_ctx::release(void* p, size_t bytes) {
+void dsa_ctx::release(void* p, size_t bytes, cudaStream_t on) {
   if (!p) return;
-  cudaFreeAsync(p, stream);
+  cudaFreeAsync(p, on ? on : stream);
   std::lock_guard<std::mutex> lk(mu);
   in_use -= bytes;
 }
@@ -181,7 +182,10 @@ extern "C" int dsa_create(dsa_ctx** out, int device, size_t mem_budget_bytes, vo
     }
     c->own_stream = true;
   }
-  if (cudaMalloc(&c->d_status, 256) != cudaSuccess || cudaMalloc(&c->d_counters, 256) != cudaSuccess ||
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMalloc(&c->d_status, 256) != cudaSuccess || cudaMalloc(&c->d_counters, 256) != cudaSuccess ||
       cudaMemset(c->d_status, 0, 256) != cudaSuccess || cudaMemset(c->d_counters, 0, 256) != cudaSuccess) {
     cudaGetLastError();
     if (c->d_status) cudaFree(c->d_status);
@@ -199,8 +203,12 @@ extern "C" int dsa_destroy(dsa_ctx* ctx) {
   if (!ctx) return DSA_OK;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(ctx->side);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_counters);
+  cudaEventDestroy(ctx->fork_ev);
+  cudaEventDestroy(ctx->join_ev);
+  cudaStreamDestroy(ctx->side);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return DSA_OK;
@@ -385,6 +393,11 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
     DSA_TRY(upload(ctx, d_poff, poff));
     DSA_TRY(launch_profile_int32(ctx, qs, d_mat, A, d_prof.as<int32_t>(), d_poff.as<uint64_t>()));
     DSA_TRY(d_scr.alloc(ctx, db->n_res * sizeof(int2)));
+    if (res) {
+      uint64_t qsum = 0;
+      for (uint32_t x : qs->h_len) qsum += x;
+      res->phase_cells[PH_INT32] += qsum * db->n_res;
+    }
     phase_begin(res, PH_INT32);
     for (uint32_t q = 0; q < nq; ++q)
       DSA_TRY(launch_generic_int32(ctx, db, qs, d_prof.as<int32_t>(), d_poff.as<uint64_t>(),
@@ -393,35 +406,87 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
     return DSA_OK;
   }
 
-  // ---- packed path: query pairs x blocks of 8 length-sorted groups ----
-  InterPlan plan;
-  plan.R = A + 1;
+  // ---- packed path ----
+  const int R = A + 1;
   std::vector<uint32_t> qorder(nq);
   std::iota(qorder.begin(), qorder.end(), 0u);
   std::stable_sort(qorder.begin(), qorder.end(),
                    [&](uint32_t a, uint32_t b) { return qs->h_len[a] > qs->h_len[b]; });
-  plan.n_pairs = (nq + 1) / 2;
-  std::vector<uint32_t> pair_q(2 * plan.n_pairs, 0xFFFFFFFFu), pair_ns(plan.n_pairs);
-  std::vector<uint64_t> pprof_off(plan.n_pairs);
-  uint64_t words = 0;
-  for (uint32_t p = 0; p < plan.n_pairs; ++p) {
-    pair_q[2 * p] = qorder[2 * p];
-    uint32_t m = qs->h_len[qorder[2 * p]];
-    if (2 * p + 1 < nq) {
-      pair_q[2 * p + 1] = qorder[2 * p + 1];
-      m = std::max(m, qs->h_len[qorder[2 * p + 1]]);
-    }
-    pair_ns[p] = (m + INTER_ROWS - 1) / INTER_ROWS;
-    pprof_off[p] = words;
-    words += (uint64_t)pair_ns[p] * plan.R * 32;
+  auto strips_of = [&](uint32_t q) { return (qs->h_len[q] + INTER_ROWS - 1) / INTER_ROWS; };
+
+  // groups whose longest target exceeds the threshold go to the wavefront kernel
+  uint32_t long_thr = 4096;
+  if (const char* env = getenv("DSA_LONG_THRESHOLD")) long_thr = (uint32_t)strtoul(env, nullptr, 10);
+  uint32_t g_long = 0;
+  while (g_long < db->n_groups && db->h_glen[g_long] > long_thr) ++g_long;
+  const uint32_t n_long = std::min<uint32_t>(nt, g_long * GROUP);
+
+  // Stream plan for the inter-sequence kernel: queries are dealt, longest
+  // first, to the currently shortest of K lanes (K about total / longest, so a
+  // lane is about as long as the longest query); lanes are then paired by
+  // length into units, low half = first lane, high half = second.
+  uint64_t tot = 0, maxq = 1;
+  for (uint32_t q = 0; q < nq; ++q) {
+    tot += strips_of(q);
+    maxq = std::max<uint64_t>(maxq, strips_of(q));
   }
-  const uint32_t blocks = (db->n_groups + INTER_WARPS - 1) / INTER_WARPS;
+  uint32_t K = (uint32_t)std::max<uint64_t>(1, (tot + maxq - 1) / maxq);
+  K = std::min<uint32_t>(K, nq);
+  K = (K + 1) & ~1u;   // even: lanes come in pairs
+  std::vector<std::vector<uint32_t>> lanes(K);
+  std::vector<uint64_t> load(K, 0);
+  for (uint32_t q : qorder) {
+    const uint32_t l = (uint32_t)(std::min_element(load.begin(), load.end()) - load.begin());
+    lanes[l].push_back(q);
+    load[l] += strips_of(q);
+  }
+  std::vector<uint32_t> lorder(K);
+  std::iota(lorder.begin(), lorder.end(), 0u);
+  std::stable_sort(lorder.begin(), lorder.end(), [&](uint32_t a, uint32_t b) { return load[a] > load[b]; });
+  std::vector<StripMeta> smeta;
+  std::vector<uint32_t> s_sbase, s_ns;
+  auto lane_meta = [&](const std::vector<uint32_t>& lane, uint64_t s, uint32_t* q, uint32_t* k) {
+    uint64_t start = 0;
+    for (uint32_t x : lane) {
+      const uint32_t ns_q = strips_of(x);
+      if (s < start + ns_q) {
+        *q = x;
+        *k = (uint32_t)(s - start) | (s - start == ns_q - 1 ? LAST : 0u);
+        return;
+      }
+      start += ns_q;
+    }
+    *q = NONE;
+    *k = 0;
+  };
+  for (uint32_t u = 0; u < K / 2; ++u) {
+    const auto& la = lanes[lorder[2 * u]];
+    const auto& lb = lanes[lorder[2 * u + 1]];
+    const uint64_t ns_u = std::max(load[lorder[2 * u]], load[lorder[2 * u + 1]]);
+    if (ns_u == 0) continue;
+    s_sbase.push_back((uint32_t)smeta.size());
+    s_ns.push_back((uint32_t)ns_u);
+    for (uint64_t st = 0; st < ns_u; ++st) {
+      StripMeta m;
+      lane_meta(la, st, &m.qa, &m.ka);
+      lane_meta(lb, st, &m.qb, &m.kb);
+      smeta.push_back(m);
+    }
+  }
+  PackedPlan spl;
+  spl.R = R;
+  spl.n_units = (uint32_t)s_ns.size();
+  spl.n_strips = (uint32_t)smeta.size();
+
+  const uint32_t blocks = (db->n_groups - g_long + INTER_WARPS - 1) / INTER_WARPS;
   struct Item { uint64_t cost; uint32_t p, g0; };
   std::vector<Item> items;
-  items.reserve((size_t)plan.n_pairs * blocks);
-  for (uint32_t p = 0; p < plan.n_pairs; ++p)
-    for (uint32_t b = 0; b < blocks; ++b)
-      items.push_back({(uint64_t)db->h_glen[b * INTER_WARPS] * pair_ns[p], p, b * INTER_WARPS});
+  items.reserve((size_t)spl.n_units * blocks);
+  for (uint32_t u = 0; u < spl.n_units; ++u)
+    for (uint32_t b = 0; b < blocks; ++b) {
+      const uint32_t g0 = g_long + b * INTER_WARPS;
+      items.push_back({(uint64_t)db->h_glen[g0] * s_ns[u], u, g0});
+    }
   std::stable_sort(items.begin(), items.end(),
                    [](const Item& a, const Item& b) { return a.cost > b.cost; });
   std::vector<uint32_t> item_words(2 * items.size());
@@ -429,24 +494,94 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
     item_words[2 * k] = items[k].p;
     item_words[2 * k + 1] = items[k].g0;
   }
-  plan.n_items = (uint32_t)items.size();
-  plan.max_glen = db->h_glen.empty() ? 0 : db->h_glen[0];
+  InterWork iw;
+  iw.n_items = (uint32_t)items.size();
+  iw.max_glen = g_long < db->n_groups ? db->h_glen[g_long] : 0;
 
-  DevBuf d_pq, d_ns, d_poff, d_pprof, d_items;
-  DSA_TRY(upload(ctx, d_pq, pair_q));
-  DSA_TRY(upload(ctx, d_ns, pair_ns));
-  DSA_TRY(upload(ctx, d_poff, pprof_off));
+  // Pair plan for the wavefront kernel: one query per half (sorted neighbours).
+  PackedPlan ppl;
+  IntraWork xw;
+  std::vector<StripMeta> pmeta;
+  std::vector<uint32_t> p_sbase, p_ns, long_ids, litem_words;
+  uint64_t long_res = 0;
+  if (n_long) {
+    ppl.R = R;
+    for (uint32_t u = 0; 2 * u < nq; ++u) {
+      const uint32_t qa = qorder[2 * u];
+      const uint32_t qb = 2 * u + 1 < nq ? qorder[2 * u + 1] : NONE;
+      const uint32_t ns_u = std::max(strips_of(qa), qb != NONE ? strips_of(qb) : 0u);
+      p_sbase.push_back((uint32_t)pmeta.size());
+      p_ns.push_back(ns_u);
+      for (uint32_t st = 0; st < ns_u; ++st)
+        pmeta.push_back({qa, st | (st == ns_u - 1 ? LAST : 0u), qb, st | (st == ns_u - 1 ? LAST : 0u)});
+    }
+    ppl.n_units = (uint32_t)p_ns.size();
+    ppl.n_strips = (uint32_t)pmeta.size();
+    long_ids.assign(db->h_perm.begin(), db->h_perm.begin() + n_long);
+    struct LItem { uint64_t cost; uint32_t li, p; };
+    std::vector<LItem> litems;
+    litems.reserve((size_t)n_long * ppl.n_units);
+    for (uint32_t li = 0; li < n_long; ++li) {
+      const uint32_t L = db->h_len[long_ids[li]];
+      long_res += L;
+      xw.max_long_len = std::max(xw.max_long_len, L);
+      for (uint32_t u = 0; u < ppl.n_units; ++u) litems.push_back({(uint64_t)L * p_ns[u], li, u});
+    }
+    std::stable_sort(litems.begin(), litems.end(),
+                     [](const LItem& a, const LItem& b) { return a.cost > b.cost; });
+    litem_words.resize(2 * litems.size());
+    for (size_t k = 0; k < litems.size(); ++k) {
+      litem_words[2 * k] = litems[k].li;
+      litem_words[2 * k + 1] = litems[k].p;
+    }
+    xw.n_items = (uint32_t)litems.size();
+  }
+  uint64_t qsum = 0;
+  for (uint32_t x : qs->h_len) qsum += x;
+  if (res) {
+    res->phase_cells[PH_INTRA] = qsum * long_res;
+    res->phase_cells[PH_INTER] = qsum * (db->n_res - long_res);
+  }
+
+  DevBuf d_smeta, d_sbase, d_sns, d_sprof, d_items, d_pmeta, d_pbase, d_pns, d_pprof, d_long, d_litems;
+  DSA_TRY(upload(ctx, d_smeta, smeta));
+  DSA_TRY(upload(ctx, d_sbase, s_sbase));
+  DSA_TRY(upload(ctx, d_sns, s_ns));
   DSA_TRY(upload(ctx, d_items, item_words));
-  DSA_TRY(d_pprof.alloc(ctx, words * sizeof(uint32_t)));
-  plan.d_pair_q = d_pq.as<uint32_t>();
-  plan.d_pair_ns = d_ns.as<uint32_t>();
-  plan.d_pprof_off = d_poff.as<uint64_t>();
-  plan.d_pprof = d_pprof.as<uint32_t>();
-  plan.d_items = d_items.as<uint32_t>();
-  DSA_TRY(launch_pair_profile(ctx, qs, d_mat, A, o, plan));
+  DSA_TRY(d_sprof.alloc(ctx, (size_t)spl.n_strips * R * 32 * sizeof(uint32_t)));
+  spl.d_meta = d_smeta.as<StripMeta>();
+  spl.d_sbase = d_sbase.as<uint32_t>();
+  spl.d_ns = d_sns.as<uint32_t>();
+  spl.d_prof = d_sprof.as<uint32_t>();
+  iw.d_items = d_items.as<uint32_t>();
+  DSA_TRY(launch_strip_profile(ctx, qs, d_mat, A, o, spl));
+  if (n_long) {
+    DSA_TRY(upload(ctx, d_pmeta, pmeta));
+    DSA_TRY(upload(ctx, d_pbase, p_sbase));
+    DSA_TRY(upload(ctx, d_pns, p_ns));
+    DSA_TRY(upload(ctx, d_long, long_ids));
+    DSA_TRY(upload(ctx, d_litems, litem_words));
+    DSA_TRY(d_pprof.alloc(ctx, (size_t)ppl.n_strips * R * 32 * sizeof(uint32_t)));
+    ppl.d_meta = d_pmeta.as<StripMeta>();
+    ppl.d_sbase = d_pbase.as<uint32_t>();
+    ppl.d_ns = d_pns.as<uint32_t>();
+    ppl.d_prof = d_pprof.as<uint32_t>();
+    xw.d_long_ids = d_long.as<uint32_t>();
+    xw.d_items = d_litems.as<uint32_t>();
+    DSA_TRY(launch_strip_profile(ctx, qs, d_mat, A, o, ppl));
+    // long targets on the side stream, overlapping the inter-sequence kernel:
+    // the two kernels write disjoint targets' results
+    DSA_CUDA_TRY(cudaEventRecord(ctx->fork_ev, ctx->stream));
+    DSA_CUDA_TRY(cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0));
+    phase_begin(res, PH_INTRA, ctx->side);
+    DSA_TRY(launch_intra_local16(ctx, ctx->side, db, ppl, xw, o, e, v.smax, out, nt));
+    phase_end(res, PH_INTRA, ctx->side);
+    DSA_CUDA_TRY(cudaEventRecord(ctx->join_ev, ctx->side));
+  }
   phase_begin(res, PH_INTER);
-  DSA_TRY(launch_inter_local16(ctx, db, qs, plan, o, e, v.smax, out, nt));
+  DSA_TRY(launch_inter_local16(ctx, db, spl, iw, o, e, v.smax, out, nt));
   phase_end(res, PH_INTER);
+  if (n_long) DSA_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->join_ev, 0));
 
   // ---- exact int32 rerun of saturated pairs ----
   const uint64_t n_out = (uint64_t)nq * nt;
@@ -836,6 +971,12 @@ extern "C" int dsa_res_timing(const dsa_res* res, double* ms, int n) {
     }
     ms[p] = t;
   }
+  return DSA_OK;
+}
+
+extern "C" int dsa_res_phase_cells(const dsa_res* res, uint64_t* cells, int n) {
+  if (!res || !cells || n < 0) { set_error("bad argument"); return DSA_ERR_INVALID_ARG; }
+  for (int p = 0; p < n && p < dsa_res::NPHASE; ++p) cells[p] = res->phase_cells[p];
   return DSA_OK;
 }
 

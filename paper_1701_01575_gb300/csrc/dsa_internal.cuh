@@ -51,13 +51,15 @@ struct dsa_ctx {
   size_t budget = 0;     // 0 = unlimited
   size_t in_use = 0;
   int sm_count = 0;
+  cudaStream_t side = nullptr;   // second stream for work that overlaps the main kernels
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int32_t* d_status = nullptr;   // device status word written by kernels
   uint32_t* d_counters = nullptr;  // work-queue counters (reset per launch)
   uint64_t launches = 0;         // kernels launched through this context
   std::mutex mu;
 
-  int alloc(void** p, size_t bytes);
-  void release(void* p, size_t bytes);
+  int alloc(void** p, size_t bytes, cudaStream_t on = nullptr);
+  void release(void* p, size_t bytes, cudaStream_t on = nullptr);
 };
 
 // A device-resident sequence set (database or queries).
@@ -110,13 +112,14 @@ struct dsa_res {
   static constexpr int NPHASE = 5;
   cudaEvent_t ev[2 * NPHASE] = {};
   bool used[NPHASE] = {};
+  uint64_t phase_cells[NPHASE] = {};
 };
 
 namespace dsa {
 // Phase timer over a result's events (no-op unless the result has DSA_TIMING).
 enum Phase { PH_INTER = 0, PH_INTRA = 1, PH_INT32 = 2, PH_HITS = 3, PH_TRACE = 4 };
-void phase_begin(dsa_res* res, Phase p);
-void phase_end(dsa_res* res, Phase p);
+void phase_begin(dsa_res* res, Phase p, cudaStream_t on = nullptr);
+void phase_end(dsa_res* res, Phase p, cudaStream_t on = nullptr);
 }  // namespace dsa
 
 namespace dsa {
@@ -155,29 +158,58 @@ int launch_profile_int32(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix,
 // Interleaved DB build (dsa_db_load).
 int launch_interleave(dsa_ctx* ctx, dsa_db* db);
 
-// Packed 16-bit inter-sequence local kernel (all queries x all targets).
-struct InterPlan {
-  uint32_t n_pairs = 0;            // query pairs
-  uint32_t* d_pair_q = nullptr;    // 2 per pair (0xFFFFFFFF = empty half)
-  uint32_t* d_pair_ns = nullptr;   // strips per pair
-  uint64_t* d_pprof_off = nullptr; // word offset of each pair's packed profile
-  uint32_t* d_pprof = nullptr;     // packed int16x2 profiles
-  uint32_t* d_items = nullptr;     // 2 words per item: pair, first group
-  uint32_t n_items = 0;
-  uint32_t max_glen = 0;
+// Packed 16-bit local kernels (all queries x all targets).
+//
+// A plan is a list of units; each unit is a run of strips (32 query rows)
+// whose low 16-bit half follows one stream of queries and whose high half
+// another.  Per strip, a StripMeta record names the query of each half and
+// the strip's index inside that query; the packed profile holds, per strip,
+// R residue rows x 32 query rows of int16x2 (S + o, padding = -16384).
+struct StripMeta {
+  uint32_t qa, ka;   // low half: query id (NONE = no query), strip index in it | LAST bit
+  uint32_t qb, kb;   // high half
+};
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr uint32_t LAST = 0x80000000u;   // in ka / kb: the query ends in this strip
+
+struct PackedPlan {
+  uint32_t n_units = 0;
+  uint32_t n_strips = 0;
+  StripMeta* d_meta = nullptr;     // n_strips
+  uint32_t* d_sbase = nullptr;     // first strip of each unit
+  uint32_t* d_ns = nullptr;        // strips of each unit
+  uint32_t* d_prof = nullptr;      // n_strips x R x 32 words
   int R = 0;                       // profile rows = A + 1 (last = padding)
 };
-int launch_pair_profile(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix, int A, int o,
-                        const InterPlan& plan);
-int launch_inter_local16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const InterPlan& plan,
-                         int o, int e, int smax, Scores out, uint32_t n_targets_out);
+
+// Inter-sequence kernel work: items = (unit, first group of a block of 8).
+struct InterWork {
+  uint32_t* d_items = nullptr;     // 2 words per item
+  uint32_t n_items = 0;
+  uint32_t max_glen = 0;           // longest group it touches (boundary-row length)
+};
+// Wavefront kernel work: items = (long target index, unit).
+struct IntraWork {
+  const uint32_t* d_long_ids = nullptr;
+  uint32_t* d_items = nullptr;     // 2 words per item
+  uint32_t n_items = 0;
+  uint32_t max_long_len = 0;
+};
+
+int launch_strip_profile(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix, int A, int o,
+                         const PackedPlan& plan);
+int launch_inter_local16(dsa_ctx* ctx, const dsa_db* db, const PackedPlan& plan,
+                         const InterWork& work, int o, int e, int smax, Scores out,
+                         uint32_t n_targets_out);
 int inter_blocks_per_sm();
 constexpr int INTER_WARPS = 8;
 constexpr int INTER_ROWS = 32;
 
-// Long-target intra-sequence (wavefront) local kernel, packed 16-bit.
-int launch_intra_local16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const InterPlan& plan,
-                         const uint32_t* d_long_ids, uint32_t n_long, int o, int e, int smax,
+// Long-target intra-sequence (wavefront) kernel; each unit of `plan` must
+// hold one query per half (no stream switches).  Runs on `stream`
+// (allocation and release of its scratch are ordered there).
+int launch_intra_local16(dsa_ctx* ctx, cudaStream_t stream, const dsa_db* db,
+                         const PackedPlan& plan, const IntraWork& work, int o, int e, int smax,
                          Scores out, uint32_t n_targets_out);
 
 // Top-k per query over a dense [n_queries][n_targets] score matrix.

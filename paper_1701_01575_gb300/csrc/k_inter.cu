@@ -5,8 +5,11 @@
 //   * the database is length-sorted and interleaved so that warp w of a CTA
 //     owns 32 consecutive sorted targets, one per lane, and reads one 16-byte
 //     word (16 residues) per lane per 16 columns, coalesced;
-//   * two queries are packed into the two 16-bit halves of every DP register,
-//     so one DPX instruction advances two cells;
+//   * the two 16-bit halves of every DP register follow two query streams
+//     (queries concatenated strip by strip, balanced in length), so one DPX
+//     instruction advances two cells; per-strip metadata says when a half
+//     starts a new query (its best and its top boundary restart) or ends one
+//     (its result is written);
 //   * a query is processed in strips of 32 rows held in registers; the loop
 //     runs over the target's residues; the strip's bottom row (H - o and the
 //     next row's F) goes to a per-CTA boundary buffer and is read back by the
@@ -16,7 +19,7 @@
 //     double-buffered on two mbarriers, in 8 replicas whose start addresses
 //     are rotated by 16 bytes so that the 8 lanes of each quarter-warp read
 //     8 different bank groups whatever residues they hold;
-//   * a persistent grid pops (query pair, block of 8 groups) items from a
+//   * a persistent grid pops (stream pair, block of 8 groups) items from a
 //     work queue ordered longest-first.
 //
 // Cell update for one row (Gotoh, local), with Ho = H - o and profile S + o:
@@ -30,8 +33,8 @@
 // End cell (smallest target end j, then smallest query end i, among cells
 // holding the best score): the column maximum is compared with the running
 // best lowered by one while j is still below the best's column, so ties at an
-// earlier column also trigger; the rare trigger scans the column for its
-// first row.
+// earlier column also trigger; the rare trigger parks the column in shared
+// memory and scans it there for its first row holding the maximum.
 //
 // Saturation: in local mode no value falls below -(o + e), and a value can
 // exceed the best seen so far by at most max(S), so if the best stays at or
@@ -55,10 +58,10 @@ struct InterArgs {
   const uint32_t* perm;
   uint32_t n_targets;
   uint32_t n_groups;
-  const uint32_t* pprof;
-  const uint64_t* pprof_off;
-  const uint32_t* pair_q;
-  const uint32_t* pair_ns;
+  const uint32_t* prof;            // [strip][a][32] int16x2
+  const StripMeta* meta;
+  const uint32_t* sbase;
+  const uint32_t* nstrips;
   int R;
   uint32_t neg_o2, neg_e2;
   int o;
@@ -93,6 +96,8 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
   const int warp = tid >> 5;
   const uint32_t cstride = (uint32_t)A.R * 128u + 16u;
   const uint32_t bufbytes = NCOPY * cstride;
+  // column parking area for the end-cell search: [row][thread]
+  volatile uint32_t* const park = reinterpret_cast<volatile uint32_t*>(smem + 2 * bufbytes);
   const uint32_t strip_words = (uint32_t)A.R * 32u;
   const uint32_t neg_o2 = A.neg_o2, neg_e2 = A.neg_e2;
   const uint32_t NEG2 = pack2(NEG16, NEG16);
@@ -114,8 +119,9 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
     if (item >= A.n_items) break;
     const uint32_t p = A.items[2 * item];
     const uint32_t g0 = A.items[2 * item + 1];
-    const uint32_t ns = A.pair_ns[p];
-    const uint32_t* psrc = A.pprof + A.pprof_off[p];
+    const uint32_t ns = A.nstrips[p];
+    const uint32_t sb = A.sbase[p];
+    const uint32_t* psrc = A.prof + (size_t)sb * strip_words;
     if (tid == 0) {
       issue_strip(A, smem, &bars[0], psrc, cstride);
       if (ns > 1) issue_strip(A, smem + bufbytes, &bars[1], psrc + strip_words, cstride);
@@ -143,8 +149,15 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
         return;
       }
       const uint8_t* pbuf = smem + b * bufbytes + (lane & 7) * cstride;
-      const int i0 = (int)s * W;
-      const bool first = s == 0;
+      const StripMeta md = A.meta[sb + s];
+      const uint32_t ka = md.ka & ~LAST, kb = md.kb & ~LAST;
+      // a half whose query starts here restarts its best and takes the
+      // row-0 boundary (H = 0) instead of the previous strip's bottom row
+      if (ka == 0) { best_lo = 0; bj_lo = 0; bi_lo = 0; }
+      if (kb == 0) { best_hi = 0; bj_hi = 0; bi_hi = 0; }
+      const uint32_t keep = (ka == 0 ? 0u : 0x0000FFFFu) | (kb == 0 ? 0u : 0xFFFF0000u);
+      const bool first = keep == 0;
+      const int ia = (int)ka * W, ib = (int)kb * W;   // first row of the strip inside each query
 
       uint32_t Ho[W], E[W];
 #pragma unroll
@@ -155,6 +168,22 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
       uint32_t diag = neg_o2;
       uint2* scr = scr_base;
       uint4 rv = make_uint4(0, 0, 0, 0);
+      // Packed trigger threshold per half, tested as cm > thr: thr = best once the
+      // column has passed the best's column (only strictly better cells
+      // count), best - 1 while it is still before it (an equal cell at a
+      // smaller column wins); `flip` is the next column at which a half
+      // passes its best's column.  The slow path repeats the exact test.
+      uint32_t thr2 = 0;
+      int flip = 0;
+      auto set_thr = [&](int jj) {
+        const int tl = best_lo - (jj < bj_lo ? 1 : 0);
+        const int th = best_hi - (jj < bj_hi ? 1 : 0);
+        thr2 = pack2(tl, th);
+        flip = 0x7FFFFFFF;
+        if (bj_lo > jj) flip = bj_lo;
+        if (bj_hi > jj && bj_hi < flip) flip = bj_hi;
+      };
+      set_thr(1);
 
       for (uint32_t c4 = 0; c4 < ncol; c4 += 4) {
         if ((c4 & 15u) == 0) rv = __ldg(res + (c4 >> 4) * 32u);
@@ -164,6 +193,13 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
         if (!first) {
 #pragma unroll
           for (int k = 0; k < 4; ++k) top[k] = scr[(uint64_t)(c4 + k) * NT];
+          if (keep != 0xFFFFFFFFu) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              top[k].x = (top[k].x & keep) | (neg_o2 & ~keep);
+              top[k].y = (top[k].y & keep) | (neg_o2 & ~keep);
+            }
+          }
         } else {
 #pragma unroll
           for (int k = 0; k < 4; ++k) top[k] = make_uint2(neg_o2, neg_o2);
@@ -195,29 +231,51 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
             }
           }
           scr[(uint64_t)(c4 + k) * NT] = make_uint2(Ho[W - 1], F);
-          // end-cell tracking for column j
+          // end-cell tracking for column j: trigger when cm > thr (per half)
           const int j = (int)c4 + k + 1;
-          const int cl = lo16(cm), ch = hi16(cm);
-          const int thr_lo = best_lo - (j < bj_lo ? 1 : 0);
-          const int thr_hi = best_hi - (j < bj_hi ? 1 : 0);
-          if (cl > thr_lo || ch > thr_hi) {
+          if (j == flip) set_thr(j);
+          if (__vmaxs2(cm, thr2) != thr2) {   // some half has cm > thr
+            const int cl = lo16(cm), ch = hi16(cm);
+            const int thr_lo = best_lo - (j < bj_lo ? 1 : 0);
+            const int thr_hi = best_hi - (j < bj_hi ? 1 : 0);
+            // rare: park the column in shared memory and find its first row
+            // holding the maximum there, so the scan never competes with the
+            // DP state for registers
+#pragma unroll
+            for (int r = 0; r < W; ++r) park[r * NT + tid] = Ho[r];
             if (cl > thr_lo) {
               const int want = cl - A.o;
-              int rr = 0;
-#pragma unroll
+              int rr = W - 1;
               for (int r = W - 1; r >= 0; --r)
-                if (lo16(Ho[r]) == want) rr = r;
-              best_lo = cl; bj_lo = j; bi_lo = i0 + rr + 1;
+                if (lo16(park[r * NT + tid]) == want) rr = r;
+              best_lo = cl; bj_lo = j; bi_lo = ia + rr + 1;
             }
             if (ch > thr_hi) {
               const int want = ch - A.o;
-              int rr = 0;
-#pragma unroll
+              int rr = W - 1;
               for (int r = W - 1; r >= 0; --r)
-                if (hi16(Ho[r]) == want) rr = r;
-              best_hi = ch; bj_hi = j; bi_hi = i0 + rr + 1;
+                if (hi16(park[r * NT + tid]) == want) rr = r;
+              best_hi = ch; bj_hi = j; bi_hi = ib + rr + 1;
             }
+            set_thr(j + 1);
           }
+        }
+      }
+      if (tvalid) {   // queries that end in this strip: write their results
+        const uint32_t orig = A.perm[st];
+        if ((md.ka & LAST) && md.qa != NONE) {
+          const uint64_t idx = (uint64_t)md.qa * A.n_out_t + orig;
+          A.o_score[idx] = best_lo;
+          A.o_qend[idx] = best_lo > 0 ? bi_lo - 1 : -1;
+          A.o_tend[idx] = best_lo > 0 ? bj_lo - 1 : -1;
+          A.o_flag[idx] = best_lo > A.T ? 1 : 0;
+        }
+        if ((md.kb & LAST) && md.qb != NONE) {
+          const uint64_t idx = (uint64_t)md.qb * A.n_out_t + orig;
+          A.o_score[idx] = best_hi;
+          A.o_qend[idx] = best_hi > 0 ? bi_hi - 1 : -1;
+          A.o_tend[idx] = best_hi > 0 ? bj_hi - 1 : -1;
+          A.o_flag[idx] = best_hi > A.T ? 1 : 0;
         }
       }
       __syncthreads();
@@ -227,51 +285,35 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
       }
     }
 
-    if (tvalid) {
-      const uint32_t orig = A.perm[st];
-      const uint32_t qa = A.pair_q[2 * p], qb = A.pair_q[2 * p + 1];
-      if (qa != 0xFFFFFFFFu) {
-        const uint64_t idx = (uint64_t)qa * A.n_out_t + orig;
-        A.o_score[idx] = best_lo;
-        A.o_qend[idx] = best_lo > 0 ? bi_lo - 1 : -1;
-        A.o_tend[idx] = best_lo > 0 ? bj_lo - 1 : -1;
-        A.o_flag[idx] = best_lo > A.T ? 1 : 0;
-      }
-      if (qb != 0xFFFFFFFFu) {
-        const uint64_t idx = (uint64_t)qb * A.n_out_t + orig;
-        A.o_score[idx] = best_hi;
-        A.o_qend[idx] = best_hi > 0 ? bi_hi - 1 : -1;
-        A.o_tend[idx] = best_hi > 0 ? bj_hi - 1 : -1;
-        A.o_flag[idx] = best_hi > A.T ? 1 : 0;
-      }
-    }
   }
 }
 
-// Packed profile of query pair p: [strip][residue a][row r] int16x2 =
-// (S[qa_i][a] + o, S[qb_i][a] + o) with i = 32*strip + r; padding rows and the
-// padding residue a = A get NEG16.
-__global__ void k_pair_profile(const uint8_t* __restrict__ qcodes,
-                               const uint64_t* __restrict__ qoff, const uint32_t* __restrict__ qlen,
-                               const uint32_t* __restrict__ pair_q,
-                               const uint32_t* __restrict__ pair_ns,
-                               const uint64_t* __restrict__ pprof_off, const int8_t* __restrict__ S,
-                               int A, int R, int o, uint32_t* __restrict__ pprof) {
-  const uint32_t p = blockIdx.y;
-  const uint32_t qa = pair_q[2 * p], qb = pair_q[2 * p + 1];
-  const uint32_t total = pair_ns[p] * (uint32_t)R * 32u;
-  const int ma = qa != 0xFFFFFFFFu ? (int)qlen[qa] : 0;
-  const int mb = qb != 0xFFFFFFFFu ? (int)qlen[qb] : 0;
-  const uint8_t* qsa = ma ? qcodes + qoff[qa] : nullptr;
-  const uint8_t* qsb = mb ? qcodes + qoff[qb] : nullptr;
-  uint32_t* out = pprof + pprof_off[p];
-  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < total; x += gridDim.x * blockDim.x) {
-    const uint32_t s = x / ((uint32_t)R * 32u);
-    const int a = (int)((x / 32u) % (uint32_t)R);
-    const int i = (int)(s * 32u + (x % 32u));
-    const int lo = (a < A && i < ma) ? (int)S[qsa[i] * A + a] + o : NEG16;
-    const int hi = (a < A && i < mb) ? (int)S[qsb[i] * A + a] + o : NEG16;
-    out[x] = pack2(lo, hi);
+// Packed profile of every strip: [strip][residue a][row r] int16x2 =
+// (S[qa_i][a] + o, S[qb_i][a] + o) with i = 32 * (strip index in the query) + r;
+// rows past a query's end, absent queries and the padding residue a = A get
+// NEG16.
+__global__ void k_strip_profile(const uint8_t* __restrict__ qcodes,
+                                const uint64_t* __restrict__ qoff, const uint32_t* __restrict__ qlen,
+                                const StripMeta* __restrict__ meta, uint32_t n_strips,
+                                const int8_t* __restrict__ S, int A, int R, int o,
+                                uint32_t* __restrict__ prof) {
+  const uint64_t total = (uint64_t)n_strips * R * 32;
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < total;
+       x += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t s = (uint32_t)(x / ((uint64_t)R * 32));
+    const int a = (int)((x / 32) % (uint64_t)R);
+    const int r = (int)(x % 32);
+    const StripMeta md = meta[s];
+    int lo = NEG16, hi = NEG16;
+    if (a < A && md.qa != NONE) {
+      const int i = (int)(md.ka & ~LAST) * 32 + r;
+      if (i < (int)qlen[md.qa]) lo = (int)S[qcodes[qoff[md.qa] + i] * A + a] + o;
+    }
+    if (a < A && md.qb != NONE) {
+      const int i = (int)(md.kb & ~LAST) * 32 + r;
+      if (i < (int)qlen[md.qb]) hi = (int)S[qcodes[qoff[md.qb] + i] * A + a] + o;
+    }
+    prof[x] = pack2(lo, hi);
   }
 }
 
@@ -279,35 +321,36 @@ __global__ void k_pair_profile(const uint8_t* __restrict__ qcodes,
 
 int inter_blocks_per_sm() { return 2; }
 
-int launch_pair_profile(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix, int A, int o,
-                        const InterPlan& plan) {
-  if (plan.n_pairs == 0) return DSA_OK;
-  dim3 grid(32, plan.n_pairs);
-  k_pair_profile<<<grid, 256, 0, ctx->stream>>>(qs->d_codes, qs->d_off, qs->d_len, plan.d_pair_q,
-                                                plan.d_pair_ns, plan.d_pprof_off, d_matrix, A,
-                                                plan.R, o, plan.d_pprof);
+int launch_strip_profile(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix, int A, int o,
+                         const PackedPlan& plan) {
+  if (plan.n_strips == 0) return DSA_OK;
+  const uint64_t total = (uint64_t)plan.n_strips * plan.R * 32;
+  uint64_t blocks = std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->sm_count * 8);
+  k_strip_profile<<<(unsigned)blocks, 256, 0, ctx->stream>>>(qs->d_codes, qs->d_off, qs->d_len,
+                                                            plan.d_meta, plan.n_strips, d_matrix,
+                                                            A, plan.R, o, plan.d_prof);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   return DSA_OK;
 }
 
-int launch_inter_local16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const InterPlan& plan,
-                         int o, int e, int smax, Scores out, uint32_t n_targets_out) {
-  (void)qs;
-  if (plan.n_items == 0) return DSA_OK;
+int launch_inter_local16(dsa_ctx* ctx, const dsa_db* db, const PackedPlan& plan,
+                         const InterWork& work, int o, int e, int smax, Scores out,
+                         uint32_t n_targets_out) {
+  if (work.n_items == 0) return DSA_OK;
   InterArgs A;
   A.il = db->d_il; A.gbase = db->d_gbase; A.glen = db->d_glen; A.perm = db->d_perm;
   A.n_targets = db->n; A.n_groups = db->n_groups;
-  A.pprof = plan.d_pprof; A.pprof_off = plan.d_pprof_off; A.pair_q = plan.d_pair_q;
-  A.pair_ns = plan.d_pair_ns; A.R = plan.R;
+  A.prof = plan.d_prof; A.meta = plan.d_meta; A.sbase = plan.d_sbase; A.nstrips = plan.d_ns;
+  A.R = plan.R;
   A.neg_o2 = (uint32_t)((-o) & 0xFFFF) | ((uint32_t)((-o) & 0xFFFF) << 16);
   A.neg_e2 = (uint32_t)((-e) & 0xFFFF) | ((uint32_t)((-e) & 0xFFFF) << 16);
   A.o = o;
   A.T = 32767 - (smax > 0 ? smax : 0);
-  A.items = plan.d_items; A.n_items = plan.n_items;
+  A.items = work.d_items; A.n_items = work.n_items;
   A.counter = ctx->d_counters;
-  const int grid = (int)std::min<uint64_t>(plan.n_items, (uint64_t)ctx->sm_count * inter_blocks_per_sm());
-  const uint64_t cols = ((uint64_t)plan.max_glen + 3) & ~3ull;
+  const int grid = (int)std::min<uint64_t>(work.n_items, (uint64_t)ctx->sm_count * inter_blocks_per_sm());
+  const uint64_t cols = ((uint64_t)work.max_glen + 3) & ~3ull;
   A.scratch_cols = cols;
   const size_t scr_bytes = (size_t)grid * cols * NT * sizeof(uint2);
   void* scr = nullptr;
@@ -316,11 +359,11 @@ int launch_inter_local16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const
   A.o_score = out.score; A.o_qend = out.q_end; A.o_tend = out.t_end; A.o_flag = out.flag;
   A.n_out_t = n_targets_out;
   A.status = ctx->d_status;
-  const size_t smem = 2ull * NCOPY * ((size_t)plan.R * 128 + 16);
+  const size_t smem = 2ull * NCOPY * ((size_t)plan.R * 128 + 16) + (size_t)W * NT * sizeof(uint32_t);
   static bool attr_set = false;
   if (!attr_set) {
     DSA_CUDA_TRY(cudaFuncSetAttribute(k_inter_local16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      96 * 1024));
+                                      110 * 1024));
     attr_set = true;
   }
   DSA_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), ctx->stream));

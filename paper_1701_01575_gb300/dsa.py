@@ -37,7 +37,8 @@ assert HIT_DTYPE.itemsize == 56 and PAIR_DTYPE.itemsize == 24
 SYMBOLS = ["dsa_create", "dsa_destroy", "dsa_last_error", "dsa_mem_in_use", "dsa_db_load",
            "dsa_db_free", "dsa_db_info", "dsa_align", "dsa_align_batch", "dsa_traceback",
            "dsa_res_get", "dsa_res_stats", "dsa_res_free", "dsa_sync", "dsa_probe_issue_rate",
-           "dsa_res_timing", "dsa_kernel_launches", "dsa_score_pairs_noalloc"]
+           "dsa_res_timing", "dsa_kernel_launches", "dsa_score_pairs_noalloc",
+           "dsa_res_phase_cells"]
 
 
 class DsaError(RuntimeError):
@@ -84,6 +85,7 @@ def load_library(path: str = LIB_PATH):
     lib.dsa_probe_issue_rate.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.dsa_res_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     lib.dsa_kernel_launches.argtypes = [_vp]
+    lib.dsa_res_phase_cells.argtypes = [_vp, ctypes.POINTER(_u64), ctypes.c_int]
     lib.dsa_kernel_launches.restype = ctypes.c_uint64
     lib.dsa_score_pairs_noalloc.argtypes = [_vp, _vp, _u32, _vp, _vp, _u32, _vp, _u64, ctypes.c_int,
                                             _u32, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -168,6 +170,11 @@ class Result:
         ms = (ctypes.c_double * len(PHASES))()
         _check(_lib.dsa_res_timing(self.handle, ms, len(PHASES)))
         return {name: ms[k] for k, name in enumerate(PHASES)}
+
+    def phase_cells(self) -> dict:
+        c = (_u64 * len(PHASES))()
+        _check(_lib.dsa_res_phase_cells(self.handle, c, len(PHASES)))
+        return {name: int(c[k]) for k, name in enumerate(PHASES)}
 
     def stats(self):
         cells = _u64(); rr = _u64()

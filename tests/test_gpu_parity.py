@@ -32,6 +32,7 @@ def gpu_all(ctx, queries, db, S, o, e, mode=dsa.LOCAL, fe=15, flags=0, A=None):
     d = ctx.load_set(db, A)
     q = ctx.load_set(queries, A)
     r = ctx.align(d, q, S, o, e, mode=mode, free_ends=fe, flags=flags)
+    ctx.sync()
     h = r.hits()
     cells, rerun = r.stats()
     shape = (queries.n, db.n)
@@ -75,6 +76,54 @@ def test_protein_search_small(ctx):
     assert g[4] == 0
 
 
+@pytest.mark.parametrize("seed", [1, 2])
+def test_query_streams_many_queries(ctx, seed):
+    """Many queries of mixed lengths: each 16-bit half runs a stream of several queries."""
+    rng = np.random.default_rng(70 + seed)
+    S = W.dna_matrix(2, -3)
+    lens = np.concatenate([rng.integers(1, 40, 12), rng.integers(30, 140, 8), [32, 64, 96, 33, 1]])
+    queries = W.SeqSet.from_list([rng.integers(0, 4, n).astype(np.uint8) for n in lens])
+    db = W.random_dna(rng, 520, 1, 260)
+    orc = oracle_all(queries, db, S, 4, 1)
+    g = gpu_all(ctx, queries, db, S, 4, 1)
+    assert_same(g[:3], orc, "streams")
+
+
+@pytest.mark.parametrize("thr", ["0", "64", "100000"])
+def test_long_target_threshold_variants(ctx, thr, monkeypatch):
+    """Targets above the threshold run on the wavefront kernel; every split is bit-exact."""
+    monkeypatch.setenv("DSA_LONG_THRESHOLD", thr)
+    rng = np.random.default_rng(12)
+    bg = W.protein_background()
+    queries = W._make_set(rng, np.array([1, 16, 31, 33, 300, 511, 512, 513, 700]), bg)
+    db = W._make_set(rng, np.concatenate([rng.integers(1, 200, 150), [1, 63, 64, 65, 1500, 900]]), bg)
+    S = W.blosum62()
+    orc = oracle_all(queries, db, S, 11, 1)
+    g = gpu_all(ctx, queries, db, S, 11, 1)
+    assert_same(g[:3], orc, f"thr={thr}")
+    cells = g[5].phase_cells()
+    if thr == "0":
+        assert cells["inter16"] == 0 and cells["intra16"] == g[5].stats()[0]
+    if thr == "100000":
+        assert cells["intra16"] == 0
+
+
+@pytest.mark.parametrize("o,e", [(1, 0), (5, 2), (3, 3)])
+def test_long_targets_wavefront_ties(ctx, o, e, monkeypatch):
+    """Multi-band queries (> 512 rows) against long DNA targets; small alphabet forces ties."""
+    monkeypatch.setenv("DSA_LONG_THRESHOLD", "256")
+    rng = np.random.default_rng(200 + o + e)
+    S = W.dna_matrix(2, -3)
+    queries = W.SeqSet.from_list([rng.integers(0, 4, n).astype(np.uint8) for n in (1, 40, 513, 1100, 1030)])
+    tl = [rng.integers(0, 4, n).astype(np.uint8) for n in rng.integers(257, 2500, 40)]
+    tl += [W.mutate(rng, queries.seq(3), 0.05, 0.02)]
+    db = W.SeqSet.from_list(tl)
+    orc = oracle_all(queries, db, S, o, e)
+    g = gpu_all(ctx, queries, db, S, o, e)
+    assert_same(g[:3], orc, f"o={o} e={e}")
+    assert g[5].phase_cells()["intra16"] > 0
+
+
 @pytest.mark.parametrize("o,e", [(1, 0), (3, 3), (5, 2), (12, 1), (40, 7)])
 def test_local_gap_params_and_ties(ctx, o, e):
     """Small alphabets force many ties: exercises the (j, i) end-cell rule."""
@@ -105,6 +154,12 @@ def test_all_zero_local(ctx):
     db = W.SeqSet.from_list([np.ones(n, np.uint8) for n in (1, 5, 70)])
     g = gpu_all(ctx, q, db, S, 3, 1)
     assert (g[0] == 0).all() and (g[1] == -1).all() and (g[2] == -1).all()
+
+
+def test_saturation_rerun_exact_long(ctx, monkeypatch):
+    """Saturation flagged by the wavefront kernel too."""
+    monkeypatch.setenv("DSA_LONG_THRESHOLD", "0")
+    test_saturation_rerun_exact(ctx)
 
 
 def test_saturation_rerun_exact(ctx):
