@@ -698,7 +698,8 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
   res->matrix.assign(matrix, matrix + A * A);
   res->flags = flags;
   auto fail = [&](int rc) {
-    if (res->d_hits) ctx->release(res->d_hits, res->n_hits * sizeof(dsa_hit));
+    if (res->d_hits) ctx->release(res->d_hits, std::max<uint64_t>(1, res->n_hits) * sizeof(dsa_hit));
+    if (res->d_bnd) ctx->release(res->d_bnd, res->bnd_bytes);
     delete res;
     return rc;
   };
@@ -726,15 +727,74 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
                                sc, &res->n_rerun)))
       return fail(rc);
   } else {
-    std::vector<PairJob> jobs(n_pairs);
-    uint64_t scr = 0, cells = 0;
+    std::vector<PairJob> jobs;
+    jobs.reserve(n_pairs);
+    std::vector<LongJob> ljobs;
+    uint64_t scr = 0, cells = 0, lcells = 0;
+    uint64_t bnd = 0, prog = 0, cand = 0;
+    const int band = long_band_rows();
     for (uint64_t k = 0; k < n_pairs; ++k) {
       const dsa_pair& p = hp[k];
-      jobs[k] = {db->h_off[p.target_id] + p.t_offset, scr, p.query_id, p.t_len, (uint32_t)k, 0};
-      scr += p.t_len;
-      cells += (uint64_t)qs->h_len[p.query_id] * p.t_len;
+      const uint64_t m = qs->h_len[p.query_id];
+      cells += m * p.t_len;
+      if (m * p.t_len >= LONG_PAIR_CELLS) {
+        const uint64_t nb = (m + band - 1) / band;
+        LongJob lj{qs->h_off[p.query_id], db->h_off[p.target_id] + p.t_offset, bnd, prog, cand,
+                   (int32_t)m, (int32_t)p.t_len, (uint32_t)k, 0};
+        ljobs.push_back(lj);
+        bnd += nb * p.t_len;
+        prog += nb;
+        cand += nb;
+        lcells += m * p.t_len;
+      } else {
+        jobs.push_back({db->h_off[p.target_id] + p.t_offset, scr, p.query_id, p.t_len, (uint32_t)k, 0});
+        scr += p.t_len;
+      }
     }
     res->cells = cells;
+    res->phase_cells[PH_INT32] = cells;
+    if (!ljobs.empty()) {
+      // band items, largest pairs first, bands in order inside a pair
+      std::vector<uint32_t> jorder(ljobs.size());
+      std::iota(jorder.begin(), jorder.end(), 0u);
+      std::stable_sort(jorder.begin(), jorder.end(), [&](uint32_t a, uint32_t b) {
+        return (uint64_t)ljobs[a].m * ljobs[a].n > (uint64_t)ljobs[b].m * ljobs[b].n;
+      });
+      std::vector<uint32_t> items;
+      for (uint32_t jx : jorder) {
+        const uint32_t nb = (ljobs[jx].m + band - 1) / band;
+        for (uint32_t b = 0; b < nb; ++b) { items.push_back(jx); items.push_back(b); }
+      }
+      DevBuf d_ljobs, d_items, d_prog, d_cands;
+      void* pb = nullptr;
+      if ((rc = upload(ctx, d_ljobs, ljobs)) || (rc = upload(ctx, d_items, items)) ||
+          (rc = d_prog.alloc(ctx, prog * sizeof(uint32_t))) ||
+          (rc = d_cands.alloc(ctx, cand * long_cand_size())) ||
+          (rc = ctx->alloc(&pb, bnd * sizeof(int2))))
+        return fail(rc);
+      res->d_bnd = static_cast<int2*>(pb);
+      res->bnd_bytes = bnd * sizeof(int2);
+      res->long_bnd_off.assign(n_pairs, UINT64_MAX);
+      res->long_n.assign(n_pairs, 0);
+      for (const LongJob& lj : ljobs) {
+        res->long_bnd_off[lj.out] = lj.bnd_off;
+        res->long_n[lj.out] = lj.n;
+      }
+      if (cudaMemsetAsync(d_prog.p, 0, prog * sizeof(uint32_t), ctx->stream) != cudaSuccess) {
+        set_error("memset failed");
+        return fail(DSA_ERR_CUDA);
+      }
+      phase_begin(res, PH_INTRA);
+      if ((rc = launch_long_score(ctx, db, qs, d_mat.as<int8_t>(), A, o, e, mode, fe,
+                                  d_ljobs.as<LongJob>(), (uint32_t)ljobs.size(), d_items.as<uint32_t>(),
+                                  (uint32_t)(items.size() / 2), res->d_bnd, d_prog.as<uint32_t>(),
+                                  d_cands.p, sc)))
+        return fail(rc);
+      phase_end(res, PH_INTRA);
+      res->phase_cells[PH_INTRA] = lcells;
+      res->phase_cells[PH_INT32] = cells - lcells;
+    }
+    const uint64_t n_short = jobs.size();
     std::vector<uint64_t> poff(qs->n);
     uint64_t pw = 0;
     for (uint32_t q = 0; q < qs->n; ++q) {
@@ -750,7 +810,7 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
       return fail(rc);
     phase_begin(res, PH_INT32);
     if ((rc = launch_generic_int32(ctx, db, qs, d_prof.as<int32_t>(), d_poff.as<uint64_t>(),
-                                   d_jobs.as<PairJob>(), n_pairs, 0, d_scr.as<int2>(), mode, fe, o,
+                                   d_jobs.as<PairJob>(), n_short, 0, d_scr.as<int2>(), mode, fe, o,
                                    e, 0, sc)))
       return fail(rc);
     phase_end(res, PH_INT32);
@@ -858,11 +918,27 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
   const dsa_db* db = res->db;
   const dsa_db* qs = res->queries;
   std::vector<TbJob> jobs;
+  std::vector<LongTbJob> ljobs;
   uint64_t cap_total = 0;
+  const int band = long_band_rows();
   for (uint64_t h : sel) {
     const dsa_hit& hit = res->h_hits[h];
     if (hit.flags & DSA_HIT_HAS_TRACEBACK) continue;
     if (res->mode == DSA_LOCAL && (hit.q_end < 0 || hit.t_end < 0)) continue;
+    if (!res->long_bnd_off.empty() && res->long_bnd_off[h] != UINT64_MAX) {
+      LongTbJob lj{};
+      lj.q_start = qs->h_off[hit.query_id];
+      lj.t_start = db->h_off[hit.target_id] + hit.t_offset;
+      lj.bnd_off = res->long_bnd_off[h];
+      lj.n = res->long_n[h];
+      lj.ie = hit.q_end + 1;
+      lj.je = hit.t_end + 1;
+      lj.hit = (uint32_t)h;
+      lj.wpr = (uint32_t)((lj.je + 7) / 8);
+      ljobs.push_back(lj);
+      cap_total += (uint64_t)lj.ie + lj.je + 1;
+      continue;
+    }
     TbJob j{};
     j.ie = hit.q_end + 1;
     j.je = hit.t_end + 1;
@@ -873,7 +949,7 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
     jobs.push_back(j);
     cap_total += (uint64_t)j.ie + j.je + 1;
   }
-  if (jobs.empty()) return DSA_OK;
+  if (jobs.empty() && ljobs.empty()) return DSA_OK;
 
   // grow the result's CIGAR array by the capacity bound
   const uint64_t old_n = res->n_cigar;
@@ -927,6 +1003,35 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
                                  ctx->stream));
     DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     k0 = k1;
+  }
+  if (!ljobs.empty()) {
+    // one decision buffer of BAND rows per long hit, walked band by band
+    uint64_t dir = 0, cig = 0;
+    for (LongTbJob& lj : ljobs) {
+      lj.dir_off = dir;
+      lj.cig_off = cig;
+      dir += (uint64_t)band * lj.wpr;
+      cig += (uint64_t)lj.ie + lj.je + 1;
+    }
+    std::vector<TbJob> shim(ljobs.size());   // cigar packing reads hit and cig_off
+    for (size_t k = 0; k < ljobs.size(); ++k) {
+      shim[k].hit = ljobs[k].hit;
+      shim[k].cig_off = ljobs[k].cig_off;
+    }
+    DevBuf d_lj, d_dir, d_cig, d_shim;
+    DSA_TRY(upload(ctx, d_lj, ljobs));
+    DSA_TRY(upload(ctx, d_shim, shim));
+    DSA_TRY(d_dir.alloc(ctx, dir * 4));
+    DSA_TRY(d_cig.alloc(ctx, cig * 4));
+    DSA_TRY(launch_long_traceback(ctx, db, qs, d_mat.as<int8_t>(), res->A, res->gap_open,
+                                  res->gap_extend, res->mode, res->free_ends, d_lj.as<LongTbJob>(),
+                                  (uint32_t)ljobs.size(), res->d_bnd, d_dir.as<uint32_t>(),
+                                  d_cig.as<uint32_t>(), res->d_hits));
+    DSA_TRY(launch_cigar_compact(ctx, res->d_hits, d_shim.as<TbJob>(), (uint32_t)shim.size(),
+                                 d_cig.as<uint32_t>(), res->d_cigar, total, d_total.as<uint64_t>()));
+    DSA_CUDA_TRY(cudaMemcpyAsync(&total, d_total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   }
   phase_end(res, PH_TRACE);
   res->n_cigar = total;
@@ -988,6 +1093,7 @@ extern "C" int dsa_res_free(dsa_res* res) {
     if (res->ev[k]) cudaEventDestroy(res->ev[k]);
   if (res->d_hits) ctx->release(res->d_hits, std::max<uint64_t>(1, res->n_hits) * sizeof(dsa_hit));
   if (res->d_cigar) ctx->release(res->d_cigar, res->cigar_bytes);
+  if (res->d_bnd) ctx->release(res->d_bnd, res->bnd_bytes);
   if (res->owned_queries) dsa_db_free(res->owned_queries);
   delete res;
   return DSA_OK;

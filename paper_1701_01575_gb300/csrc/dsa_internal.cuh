@@ -113,6 +113,11 @@ struct dsa_res {
   cudaEvent_t ev[2 * NPHASE] = {};
   bool used[NPHASE] = {};
   uint64_t phase_cells[NPHASE] = {};
+  // checkpoints of long explicit pairs (band boundary rows), kept for traceback
+  int2* d_bnd = nullptr;
+  size_t bnd_bytes = 0;
+  std::vector<uint64_t> long_bnd_off;   // per hit: boundary offset, or UINT64_MAX
+  std::vector<int32_t> long_n;          // per hit: window length of a long pair
 };
 
 namespace dsa {
@@ -240,6 +245,39 @@ int launch_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int
 int launch_cigar_compact(dsa_ctx* ctx, dsa_hit* d_hits, const TbJob* d_jobs, uint32_t n_jobs,
                          const uint32_t* d_cig_tmp, uint32_t* d_cigar, uint64_t base,
                          uint64_t* d_total);
+
+// Long explicit pairs: band-pipelined score pass and checkpointed traceback.
+struct LongJob {
+  uint64_t q_start, t_start;   // absolute offsets of query and target window
+  uint64_t bnd_off;            // int2 offset of the job's band boundary rows (bands x n)
+  uint64_t prog_off;           // offset of the job's per-band progress counters
+  uint64_t cand_off;           // offset of the job's per-band candidates
+  int32_t m, n;
+  uint32_t out;                // output slot (pair index)
+  uint32_t pad;
+};
+struct LongTbJob {
+  uint64_t q_start, t_start;
+  uint64_t bnd_off;            // checkpoints of the score pass
+  uint64_t dir_off;            // word offset of the band decision buffer (BAND x wpr words)
+  uint64_t cig_off;
+  int32_t n;                   // boundary row length (the pair's window length)
+  int32_t ie, je;
+  uint32_t hit;
+  uint32_t wpr;
+  uint32_t pad;
+};
+int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,
+                      int A, int o, int e, int mode, uint32_t fe, const LongJob* d_jobs,
+                      uint32_t n_jobs, const uint32_t* d_items, uint32_t n_items, int2* d_bnd,
+                      uint32_t* d_prog, void* d_cands, Scores out);
+int launch_long_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
+                          const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
+                          const LongTbJob* d_jobs, uint32_t n_jobs, const int2* d_bnd,
+                          uint32_t* d_dir, uint32_t* d_cig_tmp, dsa_hit* d_hits);
+size_t long_cand_size();
+int long_band_rows();
+constexpr uint64_t LONG_PAIR_CELLS = 1ull << 22;   // explicit pairs at least this big run banded
 
 // Issue-rate probe.
 int run_issue_probe(dsa_ctx* ctx, int form, double* rate);

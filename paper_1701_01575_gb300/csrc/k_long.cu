@@ -1,0 +1,439 @@
+// Long explicit pairs (e.g. genome fragments of 1e4-1e5 residues), exact
+// int32, any mode: a band-pipelined wavefront for the score pass and a
+// checkpointed traceback.
+//
+// Score pass.  The query rows of a pair are cut into bands of BAND = 32 x ROWS
+// rows.  One warp computes one band as an anti-diagonal wavefront (lane k owns
+// ROWS rows and processes column j = step - k; H and F of its last row go to
+// lane k+1 by warp shuffle).  Band b reads the bottom row (H, F) of band b-1
+// from a boundary row in global memory; band b-1 publishes how many columns
+// of it are complete in a progress counter (after a memory fence), and band b
+// waits on that counter with a bounded wait before it needs a column.  Work
+// items (pair, band) are taken in order from one counter by persistent
+// warps, so every band's predecessor was taken earlier by a warp that is
+// already running: the pipeline always advances.  The boundary rows are kept
+// as checkpoints for the traceback.
+//
+// Result cell.  Inside a lane, cells are visited in increasing (j, i), so a
+// lane keeps its first strictly better candidate; the lanes' and bands'
+// candidates are merged under (score desc, j asc, i asc) by k_long_reduce.
+//
+// Traceback.  From the end cell, band by band upwards: the band's rows are
+// recomputed from the checkpoint above it over columns 1..j (j = the walk's
+// current column), storing the 4-bit decision of every cell (as in the
+// short-hit traceback), then lane 0 walks until it leaves the band through its
+// top row.  Decision memory is BAND x n / 2 bytes per pair.
+#include "dsa_internal.cuh"
+#include "dpx.cuh"
+
+namespace dsa {
+namespace {
+
+constexpr int ROWS = 8;
+constexpr int BAND = 32 * ROWS;
+constexpr int WARPS = 4;
+constexpr uint32_t PUBLISH = 32;   // columns between progress updates
+
+__device__ __forceinline__ int32_t h_row0(int mode, uint32_t fe, int64_t j, int o, int e) {
+  if (j == 0 || mode == DSA_LOCAL || (mode == DSA_SEMIGLOBAL && (fe & DSA_FREE_T_BEGIN))) return 0;
+  return -(o + (int32_t)(j - 1) * e);
+}
+__device__ __forceinline__ int32_t h_col0(int mode, uint32_t fe, int64_t i, int o, int e) {
+  if (i == 0 || mode == DSA_LOCAL || (mode == DSA_SEMIGLOBAL && (fe & DSA_FREE_Q_BEGIN))) return 0;
+  return -(o + (int32_t)(i - 1) * e);
+}
+
+// (score desc, j asc, i asc); `has` false = no candidate
+struct Cand {
+  int32_t s, i, j;
+  int32_t has;
+};
+__device__ __forceinline__ bool cand_better(const Cand& a, const Cand& b) {
+  if (!a.has) return false;
+  if (!b.has) return true;
+  if (a.s != b.s) return a.s > b.s;
+  if (a.j != b.j) return a.j < b.j;
+  return a.i < b.i;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(WARPS * 32) k_long_score(
+    const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
+    const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
+    const LongJob* __restrict__ jobs, const uint32_t* __restrict__ items, uint32_t n_items,
+    uint32_t* __restrict__ counter, int2* __restrict__ bnd, uint32_t* __restrict__ prog,
+    Cand* __restrict__ cands, int32_t* __restrict__ status) {
+  __shared__ int8_t S[32 * 32];
+  for (int x = threadIdx.x; x < A * A; x += blockDim.x) S[x] = Sg[x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const bool local = mode == DSA_LOCAL;
+  const bool sg = mode == DSA_SEMIGLOBAL;
+  const bool q_end_free = sg && (fe & DSA_FREE_Q_END);
+  const bool t_end_free = sg && (fe & DSA_FREE_T_END);
+  for (;;) {
+    uint32_t it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1u);
+    it = __shfl_sync(0xFFFFFFFFu, it, 0);
+    if (it >= n_items) break;
+    const LongJob jb = jobs[items[2 * it]];
+    const uint32_t b = items[2 * it + 1];
+    const int32_t m = jb.m, n = jb.n;
+    const uint8_t* q = qcodes + jb.q_start;
+    const uint8_t* t = tcodes + jb.t_start;
+    const int32_t i0 = (int32_t)b * BAND;
+    const int32_t r0 = i0 + lane * ROWS;     // rows r0+1 .. r0+ROWS
+    const int32_t nb = (m + BAND - 1) / BAND;
+    const bool last_band = (int32_t)b == nb - 1;
+    int2* my_bnd = bnd + jb.bnd_off + (uint64_t)b * n;          // this band's bottom row
+    const int2* up_bnd = bnd + jb.bnd_off + (uint64_t)(b - 1) * n;
+    uint32_t* my_prog = prog + jb.prog_off + b;
+    const uint32_t* up_prog = prog + jb.prog_off + b - 1;
+    // the lane that holds the band's bottom row publishes it
+    const int32_t bottom = min(m, i0 + BAND);
+    const int bot_lane = (bottom - 1 - i0) / ROWS;
+
+    int32_t H[ROWS], E[ROWS];
+    int qc[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      const int32_t i = r0 + r + 1;
+      H[r] = h_col0(mode, fe, i, o, e);
+      E[r] = NEG32;
+      qc[r] = i <= m ? q[i - 1] * A : 0;
+    }
+    Cand c = {0, 0, 0, 0};
+    if (t_end_free && r0 < m && m <= r0 + ROWS) {   // H[m][0] on row m
+      c = {H[m - r0 - 1], m, 0, 1};
+    }
+    int32_t diag = h_col0(mode, fe, r0, o, e);
+    int32_t sendH = 0, sendF = NEG32;
+    uint32_t seen = 0;    // columns of the band above known to be complete
+    bool timed_out = false;
+    const int32_t steps = n + 31;
+    for (int32_t s = 1; s <= steps; ++s) {
+      int32_t Hup = __shfl_up_sync(0xFFFFFFFFu, sendH, 1);
+      int32_t Fup = __shfl_up_sync(0xFFFFFFFFu, sendF, 1);
+      const int32_t j = s - lane;
+      if (lane == 0 && j >= 1 && j <= n) {
+        if (b == 0) {
+          Hup = h_row0(mode, fe, j, o, e);
+          Fup = NEG32;
+        } else {
+          if (seen < (uint32_t)j && !timed_out) {
+            const uint64_t t0 = global_ns();
+            for (;;) {
+              seen = ld_acquire(up_prog);
+              if (seen >= (uint32_t)j) break;
+              if (global_ns() - t0 > WAIT_LIMIT_NS) {
+                timed_out = true;
+                atomicExch(status, DSA_ERR_DEVICE_TIMEOUT);
+                break;
+              }
+            }
+          }
+          const int2 v = up_bnd[j - 1];
+          Hup = v.x;
+          Fup = v.y;
+        }
+      }
+      if (j >= 1 && j <= n && r0 < m) {
+        const int a = t[j - 1];
+        int32_t d = diag;
+        diag = Hup;
+        int32_t F = Fup, Hp = Hup;
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+          const int32_t i = r0 + r + 1;
+          if (i <= m) {
+            F = max(F - e, Hp - o);
+            E[r] = max(E[r] - e, H[r] - o);
+            int32_t h = max(d + S[qc[r] + a], max(E[r], F));
+            if (local) h = max(h, 0);
+            d = H[r];
+            H[r] = h;
+            Hp = h;
+            if (local) {
+              if (h > 0 && (!c.has || h > c.s)) c = {h, i, j, 1};
+            } else if ((j == n && (q_end_free || i == m)) || (t_end_free && i == m)) {
+              if (!c.has || h > c.s) c = {h, i, j, 1};
+            }
+          }
+        }
+        sendH = Hp;
+        sendF = F;
+        if (!last_band && lane == bot_lane) {
+          my_bnd[j - 1] = make_int2(Hp, F);
+          if ((uint32_t)j % PUBLISH == 0 || j == n) {
+            __threadfence();
+            st_release(my_prog, (uint32_t)j);
+          }
+        }
+      }
+    }
+    // merge the lanes' candidates (each lane's is its first best in (j, i) order)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      Cand x;
+      x.s = __shfl_xor_sync(0xFFFFFFFFu, c.s, off);
+      x.i = __shfl_xor_sync(0xFFFFFFFFu, c.i, off);
+      x.j = __shfl_xor_sync(0xFFFFFFFFu, c.j, off);
+      x.has = __shfl_xor_sync(0xFFFFFFFFu, c.has, off);
+      if (cand_better(x, c)) c = x;
+    }
+    if (lane == 0) cands[jb.cand_off + b] = c;
+    __syncwarp();
+  }
+}
+
+__global__ void k_long_reduce(const LongJob* __restrict__ jobs, uint32_t n_jobs,
+                              const Cand* __restrict__ cands, int mode, uint32_t fe, int o, int e,
+                              int32_t* __restrict__ o_score, int32_t* __restrict__ o_qend,
+                              int32_t* __restrict__ o_tend, uint8_t* __restrict__ o_flag) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_jobs; k += gridDim.x * blockDim.x) {
+    const LongJob jb = jobs[k];
+    const int32_t nb = (jb.m + BAND - 1) / BAND;
+    Cand best = {0, 0, 0, 0};
+    if (mode == DSA_SEMIGLOBAL && (fe & DSA_FREE_Q_END))
+      best = {h_row0(mode, fe, jb.n, o, e), 0, jb.n, 1};   // H[0][n]
+    for (int32_t b = 0; b < nb; ++b) {
+      const Cand c = cands[jb.cand_off + b];
+      if (cand_better(c, best)) best = c;
+    }
+    if (mode == DSA_LOCAL && !best.has) {
+      o_score[jb.out] = 0; o_qend[jb.out] = -1; o_tend[jb.out] = -1;
+    } else {
+      o_score[jb.out] = best.s; o_qend[jb.out] = best.i - 1; o_tend[jb.out] = best.j - 1;
+    }
+    o_flag[jb.out] = 0;
+  }
+}
+
+struct RevCigar {
+  uint32_t* out;
+  uint32_t n = 0;
+  int op = -1;
+  uint32_t run = 0;
+  __device__ void emit(int o) {
+    if (o == op) {
+      ++run;
+    } else {
+      flush();
+      op = o;
+      run = 1;
+    }
+  }
+  __device__ void flush() {
+    if (run) out[n++] = (run << 4) | (uint32_t)op;
+    run = 0;
+  }
+};
+
+// Checkpointed traceback: one warp per job.
+__global__ void __launch_bounds__(32) k_long_traceback(
+    const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
+    const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
+    const LongTbJob* __restrict__ jobs, uint32_t n_jobs, const int2* __restrict__ bnd,
+    uint32_t* __restrict__ dir, uint32_t* __restrict__ cig_tmp, dsa_hit* __restrict__ hits) {
+  __shared__ int8_t S[32 * 32];
+  for (int x = threadIdx.x; x < A * A; x += blockDim.x) S[x] = Sg[x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const bool local = mode == DSA_LOCAL;
+  const bool sg = mode == DSA_SEMIGLOBAL;
+  for (uint32_t w = blockIdx.x; w < n_jobs; w += gridDim.x) {
+    const LongTbJob jb = jobs[w];
+    const uint8_t* q = qcodes + jb.q_start;
+    const uint8_t* t = tcodes + jb.t_start;
+    uint32_t* D = dir + jb.dir_off;
+    const uint32_t wpr = jb.wpr;
+    RevCigar c;
+    c.out = cig_tmp + jb.cig_off;
+    int32_t i = jb.ie, j = jb.je;
+    int st = 0;   // 0 = H, 1 = F, 2 = E
+    bool done = false;
+    while (!done) {
+      // band holding row i (rows 1-based; row 0 belongs to no band)
+      if (i == 0 || j == 0) {
+        if (lane == 0) {
+          if (st == 0 && !(sg && ((i == 0 && (fe & DSA_FREE_T_BEGIN)) || (j == 0 && (fe & DSA_FREE_Q_BEGIN)))) &&
+              !local) {
+            while (j > 0) { c.emit(2); --j; }
+            while (i > 0) { c.emit(1); --i; }
+          }
+        }
+        break;
+      }
+      const int32_t b = (i - 1) / BAND;
+      const int32_t i0 = b * BAND;
+      const int32_t rows_here = i - i0;        // recompute rows i0+1 .. i
+      const int32_t jmax = j;
+      // recompute the band over columns 1..jmax storing decisions (row-major, local rows)
+      {
+        const int32_t r0 = i0 + lane * ROWS;
+        int32_t H[ROWS], E[ROWS];
+        uint32_t nbw[ROWS];
+        int qc[ROWS];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+          const int32_t ii = r0 + r + 1;
+          H[r] = h_col0(mode, fe, ii, o, e);
+          E[r] = NEG32;
+          nbw[r] = 0;
+          qc[r] = ii <= i ? q[ii - 1] * A : 0;
+        }
+        int32_t diag = h_col0(mode, fe, r0, o, e);
+        int32_t sendH = 0, sendF = NEG32;
+        const int2* up = bnd + jb.bnd_off + (uint64_t)(b - 1) * jb.n;
+        for (int32_t s = 1; s <= jmax + 31; ++s) {
+          int32_t Hup = __shfl_up_sync(0xFFFFFFFFu, sendH, 1);
+          int32_t Fup = __shfl_up_sync(0xFFFFFFFFu, sendF, 1);
+          const int32_t jj = s - lane;
+          if (jj >= 1 && jj <= jmax && r0 < i) {
+            if (lane == 0) {
+              if (b == 0) {
+                Hup = h_row0(mode, fe, jj, o, e);
+                Fup = NEG32;
+              } else {
+                const int2 v = up[jj - 1];
+                Hup = v.x;
+                Fup = v.y;
+              }
+            }
+            const int a = t[jj - 1];
+            int32_t d = diag;
+            diag = Hup;
+            int32_t F = Fup, Hp = Hup;
+            const int sh = 4 * ((jj - 1) & 7);
+            const bool flushw = ((jj & 7) == 0) || jj == jmax;
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+              const int32_t ii = r0 + r + 1;
+              if (ii <= i) {
+                const int32_t fo = Hp - o, fx = F - e;
+                F = max(fx, fo);
+                const int32_t eo = H[r] - o, ex = E[r] - e;
+                E[r] = max(ex, eo);
+                const int32_t mm = d + S[qc[r] + a];
+                int32_t v = max(mm, max(E[r], F));
+                if (local) v = max(v, 0);
+                uint32_t src;
+                if (local && v == 0) src = 3;
+                else if (v == mm) src = 0;
+                else if (v == F) src = 1;
+                else src = 2;
+                nbw[r] |= (src | ((eo >= ex) ? 4u : 0u) | ((fo >= fx) ? 8u : 0u)) << sh;
+                if (flushw) {
+                  D[(uint64_t)(ii - i0 - 1) * wpr + (uint32_t)(jj - 1) / 8u] = nbw[r];
+                  nbw[r] = 0;
+                }
+                d = H[r];
+                H[r] = v;
+                Hp = v;
+              }
+            }
+            sendH = Hp;
+            sendF = F;
+          }
+        }
+      }
+      __syncwarp();
+      // walk inside the band until the walk leaves it upwards or stops
+      if (lane == 0) {
+        for (int64_t guard = 2 * ((int64_t)rows_here + jmax) + 4; guard > 0; --guard) {
+          if (i <= i0) break;   // left the band: continue with the band above
+          if (j == 0) break;    // column 0: handled at the loop head
+          const uint32_t nib = (D[(uint64_t)(i - i0 - 1) * wpr + (uint32_t)(j - 1) / 8u] >> (4 * ((j - 1) & 7))) & 15u;
+          if (st == 0) {
+            const uint32_t src = nib & 3u;
+            if (src == 3) { done = true; break; }
+            if (src == 0) { c.emit(0); --i; --j; }
+            else st = src == 1 ? 1 : 2;
+          } else if (st == 1) {
+            c.emit(1);
+            if (nib & 8u) st = 0;
+            --i;
+          } else {
+            c.emit(2);
+            if (nib & 4u) st = 0;
+            --j;
+          }
+        }
+        if (!done && st == 0 && sg && ((i == 0 && (fe & DSA_FREE_T_BEGIN)) || (j == 0 && (fe & DSA_FREE_Q_BEGIN))))
+          done = true;
+        if (!done && local && (i == 0 || j == 0)) done = true;
+      }
+      i = __shfl_sync(0xFFFFFFFFu, i, 0);
+      j = __shfl_sync(0xFFFFFFFFu, j, 0);
+      st = __shfl_sync(0xFFFFFFFFu, st, 0);
+      done = __shfl_sync(0xFFFFFFFFu, (int)done, 0) != 0;
+      __syncwarp();
+    }
+    if (lane == 0) {
+      c.flush();
+      dsa_hit* h = hits + jb.hit;
+      h->q_begin = i;
+      h->t_begin = j;
+      h->cigar_len = c.n;
+      h->flags |= DSA_HIT_HAS_TRACEBACK;
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,
+                      int A, int o, int e, int mode, uint32_t fe, const LongJob* d_jobs,
+                      uint32_t n_jobs, const uint32_t* d_items, uint32_t n_items, int2* d_bnd,
+                      uint32_t* d_prog, void* d_cands, Scores out) {
+  if (n_items == 0) return DSA_OK;
+  // every warp must be resident at once (bands wait on their predecessors):
+  // the grid never exceeds what the device holds simultaneously
+  int per_sm = 0;
+  DSA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_long_score, WARPS * 32, 0));
+  const uint64_t resident = (uint64_t)std::max(1, per_sm) * ctx->sm_count;
+  const unsigned grid = (unsigned)std::min<uint64_t>(resident, (n_items + WARPS - 1) / WARPS);
+  uint32_t* counter = ctx->d_counters + 3;
+  DSA_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(uint32_t), ctx->stream));
+  k_long_score<<<grid, WARPS * 32, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e,
+                                                      mode, fe, d_jobs, d_items, n_items, counter,
+                                                      d_bnd, d_prog, static_cast<Cand*>(d_cands),
+                                                      ctx->d_status);
+  DSA_CUDA_TRY(cudaGetLastError());
+  ++ctx->launches;
+  const unsigned rb = (unsigned)std::min<uint64_t>((n_jobs + 127) / 128, 1024);
+  k_long_reduce<<<rb, 128, 0, ctx->stream>>>(d_jobs, n_jobs, static_cast<const Cand*>(d_cands),
+                                              mode, fe, o, e, out.score, out.q_end, out.t_end,
+                                              out.flag);
+  DSA_CUDA_TRY(cudaGetLastError());
+  ++ctx->launches;
+  return DSA_OK;
+}
+
+size_t long_cand_size() { return sizeof(Cand); }
+int long_band_rows() { return BAND; }
+
+int launch_long_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
+                          const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
+                          const LongTbJob* d_jobs, uint32_t n_jobs, const int2* d_bnd,
+                          uint32_t* d_dir, uint32_t* d_cig_tmp, dsa_hit* d_hits) {
+  if (n_jobs == 0) return DSA_OK;
+  const unsigned grid = (unsigned)std::min<uint64_t>(n_jobs, (uint64_t)ctx->sm_count * 32);
+  k_long_traceback<<<grid, 32, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e,
+                                                  mode, fe, d_jobs, n_jobs, d_bnd, d_dir,
+                                                  d_cig_tmp, d_hits);
+  DSA_CUDA_TRY(cudaGetLastError());
+  ++ctx->launches;
+  return DSA_OK;
+}
+
+}  // namespace dsa

@@ -310,3 +310,54 @@ def test_bad_arguments_rejected(ctx):
         ctx.align(d, d, W.dna_matrix(1, -1), 1, 2)                               # e > o
     with pytest.raises(dsa.DsaError):
         ctx.align(d, d, W.blosum62(), 1, 1)                                      # A mismatch
+
+
+# ---------------------------------------------------------------- long explicit pairs
+
+@pytest.mark.parametrize("mode,fe", [(dsa.GLOBAL, 15), (dsa.LOCAL, 15), (dsa.SEMIGLOBAL, 15),
+                                     (dsa.SEMIGLOBAL, 12), (dsa.SEMIGLOBAL, 3)])
+def test_long_pairs_banded_score_and_traceback(ctx, mode, fe):
+    """Pairs of 2,000-6,000 bp (band pipeline across warps, checkpointed traceback)."""
+    wl = W.long_pairs(seed=W.SEED_BASE + 30 + mode, n_pairs=5, lo=2000, hi=6000, mode=mode)
+    p = wl.pairs
+    assert (wl.queries.lengths * p["t_len"].astype(np.int64) >= (1 << 22)).any()
+    sc, qe, te = oracle.score_pairs(wl.queries.codes, wl.queries.offsets, wl.db.codes, wl.db.offsets,
+                                    p["query_id"], p["target_id"], wl.matrix, 5, 2, mode, fe,
+                                    pair_toff=p["t_offset"], pair_tlen=p["t_len"])
+    d = ctx.load_set(wl.db, 4)
+    q = ctx.load_set(wl.queries, 4)
+    r = ctx.align(d, q, wl.matrix, 5, 2, mode=mode, free_ends=fe, pairs=p)
+    ctx.sync()
+    h = r.hits()
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), f"long mode={mode}")
+    assert r.phase_cells()["intra16"] > 0
+    ctx.traceback(r)
+    ctx.sync()
+    check_traceback(r.hits(), r.cigar(), wl.queries, wl.db, wl.matrix, 5, 2, mode, fe)
+
+
+def test_long_and_short_pairs_mixed(ctx):
+    """One call with pairs on both sides of the banded-path threshold."""
+    rng = np.random.default_rng(99)
+    S = W.dna_matrix(2, -3)
+    a = rng.integers(0, 4, 3000).astype(np.uint8)
+    seqs = [a, W.mutate(rng, a, 0.05, 0.01), rng.integers(0, 4, 200).astype(np.uint8)]
+    qs = W.SeqSet.from_list([seqs[0], seqs[2]])
+    db = W.SeqSet.from_list([seqs[1], seqs[2]])
+    pairs = np.zeros(4, dtype=W.PAIR_DTYPE)
+    pairs["query_id"] = [0, 1, 0, 1]
+    pairs["target_id"] = [0, 1, 1, 0]
+    pairs["t_len"] = [db.lengths[0], db.lengths[1], db.lengths[1], 1500]
+    pairs["t_offset"] = [0, 0, 0, 700]
+    for mode in (dsa.GLOBAL, dsa.LOCAL):
+        sc, qe, te = oracle.score_pairs(qs.codes, qs.offsets, db.codes, db.offsets, pairs["query_id"],
+                                        pairs["target_id"], S, 5, 2, mode, 15,
+                                        pair_toff=pairs["t_offset"], pair_tlen=pairs["t_len"])
+        d = ctx.load_set(db, 4)
+        q = ctx.load_set(qs, 4)
+        r = ctx.align(d, q, S, 5, 2, mode=mode, pairs=pairs)
+        ctx.traceback(r)
+        ctx.sync()
+        h = r.hits()
+        assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), f"mixed mode={mode}")
+        check_traceback(h, r.cigar(), qs, db, S, 5, 2, mode, 15)
