@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="approximate CPU time of the oracle sample")
+    ap.add_argument("--workload", default="protein_search",
+                    choices=["protein_search", "protein_vs_db", "reads_vs_windows", "long_pairs",
+                             "long_pairs_local"],
+                    help="the measured workload (default: the batched protein search)")
     return ap.parse_args()
 
 
@@ -145,8 +149,27 @@ def all_sum(world, x: float) -> float:
 
 def make_workload(args, rank=0):
     from paper_1701_01575_gb300 import workloads as W
+    if args.workload == "protein_vs_db":
+        return W.protein_vs_db(seed=W.SEED_BASE + 0 + 1000 * rank)
+    if args.workload == "reads_vs_windows":
+        return W.reads_vs_windows(seed=W.SEED_BASE + 2 + 1000 * rank)
+    if args.workload in ("long_pairs", "long_pairs_local"):
+        mode = W.MODE_LOCAL if args.workload == "long_pairs_local" else W.MODE_GLOBAL
+        return W.long_pairs(seed=W.SEED_BASE + 3 + 1000 * rank, mode=mode)
     return W.protein_search(seed=W.SEED_BASE + 1 + 1000 * rank, n_queries=args.queries,
                             n_targets=args.targets)
+
+
+WORKLOAD_TEXT = {
+    "protein_vs_db": "protein_vs_db: 1 query of 128 x 2,000 targets U{50..500}, BLOSUM62 11/1, local",
+    "reads_vs_windows": ("reads_vs_windows: 1,000,000 reads (150/250 bp, 1% subs, 0.1% indels) vs "
+                         "500 bp windows of a 10 Mb genome, +1/-4, 6/1, semi-global (target ends "
+                         "free), score + traceback of every read"),
+    "long_pairs": ("long_pairs: 64 DNA pairs log-uniform 1e4..1e5 (5% subs, 1% indels), +2/-3, "
+                   "5/2, global, score + traceback"),
+    "long_pairs_local": ("long_pairs: 64 DNA pairs log-uniform 1e4..1e5 (5% subs, 1% indels), "
+                         "+2/-3, 5/2, local, score + traceback"),
+}
 
 
 def cpu_sample(wl, seconds, rate_guess=0.25e9):
@@ -192,8 +215,13 @@ def bench_ours(args):
     cells_per_step = wl.cells()
     flags = dsa.TIMING | dsa.RESULTS_ON_DEVICE
 
+    pairs_dev = None
+    if wl.pairs is not None:
+        pairs_dev = torch.as_tensor(wl.pairs.view(np.uint8), device="cuda")
+
     def step():
-        r = ctx.align(db, qs, S, o, e, top_k=wl.top_k, flags=flags)
+        r = ctx.align(db, qs, S, o, e, mode=wl.mode, free_ends=wl.free_ends, pairs=pairs_dev,
+                      top_k=wl.top_k, flags=flags)
         ctx.traceback(r)
         return r
 
@@ -234,17 +262,22 @@ def bench_ours(args):
     total_cells = all_sum(world, float(cells_per_step * args.steps))
     value = total_cells / (ms / 1e3) / 1e9
 
-    out = {"metric": METRIC, "value": round(value, 2), "unit": "GCUPS", "n_gpus": world,
+    wtext = WORKLOAD if args.workload == "protein_search" else WORKLOAD_TEXT[args.workload]
+    out = {"metric": METRIC if args.workload == "protein_search" else
+           f"GCUPS (bit-exact) {args.workload}", "value": round(value, 2), "unit": "GCUPS", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i16x2+i32",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "queries": args.queries, "targets": args.targets,
+           "config": {"workload": wtext, "queries": wl.queries.n, "targets": wl.db.n,
                       "cells_per_step": cells_per_step, "parallelism": f"replicas x{world}",
-                      "l2": "inputs larger than L2 (database codes 192 MB > 129 MB L2)"},
+                      "l2": "inputs larger than L2" if wl.db.codes.nbytes + wl.queries.codes.nbytes > (129 << 20)
+                      else "inputs smaller than L2 (small workload)"},
            "clocks": clk, "gpu_launches": int(launches)}
 
     # roofline of the dominant kernel (packed inter-sequence kernel)
     inter_ms = statistics.mean(phase["inter16"]) if phase["inter16"] else None
+    if args.workload != "protein_search":
+        inter_ms = None
     rate = ctx.probe_issue_rate(0)     # DPX s16x2 add-max, warp-instr / SM / clk
     sm_mhz = clk.get("sm_mhz") or (props.clock_rate / 1e3 if hasattr(props, "clock_rate") else None)
     if inter_ms and sm_mhz:
@@ -263,7 +296,7 @@ def bench_ours(args):
                           for k, v in phase.items() if v and pcells.get(k)}
     out["saturation_reruns_per_step"] = reruns / args.steps
 
-    if rank == 0 and not args.no_plain:
+    if rank == 0 and not args.no_plain and args.workload == "protein_search":
         # plain per-query form: one unbatched int32 launch per query, DB in input order
         from paper_1701_01575_gb300 import workloads as W
         order = np.argsort(wl.queries.lengths)
@@ -288,7 +321,7 @@ def bench_ours(args):
         out["batched_over_plain"] = round(value / world / plain, 2)
         qsub.free()
 
-    if rank == 0 and not args.no_e2e:
+    if rank == 0 and not args.no_e2e and args.workload == "protein_search":
         # end to end through the public API with host buffers: queries H2D, hits + CIGAR D2H
         e2e_steps = max(1, min(3, args.steps))
         torch.cuda.synchronize()
@@ -307,7 +340,7 @@ def bench_ours(args):
                       "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
                       "steps": e2e_steps}
 
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and args.workload == "protein_search":
         targets, cores = cpu_sample(wl, args.cpu_seconds)
         (osc, oqe, ote), ccells, cdt = run_oracle_sample(wl, targets, cores)
         out["cpu_baseline"] = {"value": round(ccells / cdt / 1e9, 4), "unit": "GCUPS", "cores": cores,

@@ -199,6 +199,68 @@ int dsa_sync(dsa_ctx* ctx);
  * add-max (DPX), 7 = the packed local cell update mix. */
 int dsa_probe_issue_rate(dsa_ctx* ctx, int form, double* warp_instr_per_sm_per_clk);
 
+/* ---- serving: continuous batching of alignment requests ----
+ *
+ * A server owns `n_slots` worker slots, each with its own stream.  Submitted
+ * requests wait in a FIFO; a free slot takes the oldest pending request and
+ * every later pending request compatible with it (same database, kind and
+ * scoring) up to the batch limits, provided the batch's estimated device
+ * footprint fits in the free memory (cudaMemGetInfo minus `mem_reserve`, or
+ * `mem_budget` if non-zero) next to what running batches reserved; it then
+ * runs them as one dsa_align (+ dsa_traceback) call.  Batches of different
+ * slots overlap on the device.  Each request's results are identical to
+ * those it gets alone: scores are exact and top-k uses a total order. */
+typedef struct dsa_server dsa_server;
+
+#define DSA_REQ_SEARCH 0   /* queries vs every target of `db`, top_k hits per query */
+#define DSA_REQ_PAIRS 1    /* explicit (query, target window) pairs, one hit per pair */
+
+typedef struct {
+  int kind;                       /* DSA_REQ_SEARCH or DSA_REQ_PAIRS */
+  const dsa_db* db;
+  const uint8_t* q_codes;         /* host; copied by dsa_submit */
+  const uint64_t* q_offsets;
+  uint32_t n_queries;
+  const dsa_pair* pairs;          /* host, DSA_REQ_PAIRS; query_id is request-local */
+  uint64_t n_pairs;
+  int mode;
+  uint32_t free_ends;
+  const int8_t* matrix;           /* host, alphabet_size^2; copied */
+  int alphabet_size;
+  int gap_open, gap_extend;
+  uint32_t top_k;                 /* DSA_REQ_SEARCH */
+  int traceback;                  /* non-zero: begin coordinates and CIGARs */
+} dsa_request;
+
+typedef struct {
+  uint32_t n_slots;               /* concurrent batches (default 2) */
+  uint32_t max_batch_queries;     /* DSA_REQ_SEARCH batch limit (default 64) */
+  uint64_t max_batch_pairs;       /* DSA_REQ_PAIRS batch limit (default 2,000,000) */
+  size_t mem_reserve;             /* bytes kept free (default 4 GiB) */
+  size_t mem_budget;              /* if non-zero: total bytes batches may reserve */
+  uint32_t max_pending;           /* dsa_submit returns DSA_ERR_BUSY beyond this (default 100000) */
+} dsa_server_config;
+
+/* Times of one request, in seconds on the server's clock: arrival (submit),
+ * admission (its batch started) and finish (results on the host). */
+typedef struct {
+  double arrive, admit, finish;
+  uint32_t batch_requests;        /* requests in its batch */
+  int status;                     /* DSA_OK or the batch's error */
+} dsa_request_times;
+
+int dsa_server_create(int device, const dsa_server_config* cfg, dsa_server** out);
+int dsa_submit(dsa_server* srv, const dsa_request* req, uint64_t* ticket);
+/* DSA_OK and *out = the request's result (host arrays, request-local query
+ * ids; free with dsa_res_free) once it is done; DSA_ERR_BUSY while it is not.
+ * A finished request is handed out once. */
+int dsa_poll(dsa_server* srv, uint64_t ticket, dsa_res** out, dsa_request_times* times);
+/* Block until every submitted request has finished. */
+int dsa_server_drain(dsa_server* srv);
+/* Seconds on the server's clock (the clock of dsa_request_times). */
+double dsa_server_now(const dsa_server* srv);
+int dsa_server_destroy(dsa_server* srv);
+
 /* Exact int32 scores and end cells of explicit pairs, allocating nothing.
  *
  * The paper has no counterpart to this entry point: it exists for callers

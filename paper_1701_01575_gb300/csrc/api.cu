@@ -902,7 +902,10 @@ static int fetch_hits(dsa_res* res) {
 }
 
 extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, uint64_t n) {
-  if (!ctx || !res || res->ctx != ctx) { set_error("bad ctx / res"); return DSA_ERR_INVALID_ARG; }
+  if (!ctx || !res || res->ctx != ctx) {
+    set_error("bad ctx / res (results handed out by a server are host-only)");
+    return DSA_ERR_INVALID_ARG;
+  }
   DSA_TRY(set_device(ctx));
   DSA_TRY(fetch_hits(res));
   std::vector<uint64_t> sel;
@@ -1005,33 +1008,51 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
     k0 = k1;
   }
   if (!ljobs.empty()) {
-    // one decision buffer of BAND rows per long hit, walked band by band
-    uint64_t dir = 0, cig = 0;
-    for (LongTbJob& lj : ljobs) {
-      lj.dir_off = dir;
-      lj.cig_off = cig;
-      dir += (uint64_t)band * lj.wpr;
-      cig += (uint64_t)lj.ie + lj.je + 1;
+    // decision matrices of whole rectangles, in chunks of at most 32 GiB
+    const uint64_t limit = 8ull << 30;   // words
+    size_t k0 = 0;
+    while (k0 < ljobs.size()) {
+      uint64_t dir = 0, cig = 0;
+      size_t k1 = k0;
+      std::vector<uint32_t> items;
+      while (k1 < ljobs.size()) {
+        LongTbJob& lj = ljobs[k1];
+        const uint64_t w = (uint64_t)lj.ie * lj.wpr;
+        if (k1 > k0 && dir + w > limit) break;
+        lj.dir_off = dir;
+        lj.cig_off = cig;
+        dir += w;
+        cig += (uint64_t)lj.ie + lj.je + 1;
+        const uint32_t nb = (uint32_t)((lj.ie + band - 1) / band);
+        for (uint32_t b = 0; b < nb; ++b) { items.push_back((uint32_t)(k1 - k0)); items.push_back(b); }
+        ++k1;
+      }
+      std::vector<LongTbJob> chunk(ljobs.begin() + k0, ljobs.begin() + k1);
+      std::vector<TbJob> shim(chunk.size());   // the CIGAR packer reads hit and cig_off
+      for (size_t k = 0; k < chunk.size(); ++k) {
+        shim[k].hit = chunk[k].hit;
+        shim[k].cig_off = chunk[k].cig_off;
+      }
+      DevBuf d_lj, d_items, d_dir, d_cig, d_shim;
+      DSA_TRY(upload(ctx, d_lj, chunk));
+      DSA_TRY(upload(ctx, d_items, items));
+      DSA_TRY(upload(ctx, d_shim, shim));
+      DSA_TRY(d_dir.alloc(ctx, dir * 4));
+      DSA_TRY(d_cig.alloc(ctx, cig * 4));
+      DSA_TRY(launch_long_traceback(ctx, db, qs, d_mat.as<int8_t>(), res->A, res->gap_open,
+                                    res->gap_extend, res->mode, res->free_ends,
+                                    d_lj.as<LongTbJob>(), (uint32_t)chunk.size(),
+                                    d_items.as<uint32_t>(), (uint32_t)(items.size() / 2),
+                                    res->d_bnd, d_dir.as<uint32_t>(), d_cig.as<uint32_t>(),
+                                    res->d_hits));
+      DSA_TRY(launch_cigar_compact(ctx, res->d_hits, d_shim.as<TbJob>(), (uint32_t)shim.size(),
+                                   d_cig.as<uint32_t>(), res->d_cigar, total,
+                                   d_total.as<uint64_t>()));
+      DSA_CUDA_TRY(cudaMemcpyAsync(&total, d_total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+      DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      k0 = k1;
     }
-    std::vector<TbJob> shim(ljobs.size());   // cigar packing reads hit and cig_off
-    for (size_t k = 0; k < ljobs.size(); ++k) {
-      shim[k].hit = ljobs[k].hit;
-      shim[k].cig_off = ljobs[k].cig_off;
-    }
-    DevBuf d_lj, d_dir, d_cig, d_shim;
-    DSA_TRY(upload(ctx, d_lj, ljobs));
-    DSA_TRY(upload(ctx, d_shim, shim));
-    DSA_TRY(d_dir.alloc(ctx, dir * 4));
-    DSA_TRY(d_cig.alloc(ctx, cig * 4));
-    DSA_TRY(launch_long_traceback(ctx, db, qs, d_mat.as<int8_t>(), res->A, res->gap_open,
-                                  res->gap_extend, res->mode, res->free_ends, d_lj.as<LongTbJob>(),
-                                  (uint32_t)ljobs.size(), res->d_bnd, d_dir.as<uint32_t>(),
-                                  d_cig.as<uint32_t>(), res->d_hits));
-    DSA_TRY(launch_cigar_compact(ctx, res->d_hits, d_shim.as<TbJob>(), (uint32_t)shim.size(),
-                                 d_cig.as<uint32_t>(), res->d_cigar, total, d_total.as<uint64_t>()));
-    DSA_CUDA_TRY(cudaMemcpyAsync(&total, d_total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                                 ctx->stream));
-    DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   }
   phase_end(res, PH_TRACE);
   res->n_cigar = total;
@@ -1042,7 +1063,7 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
 extern "C" int dsa_res_get(dsa_res* res, const dsa_hit** hits, uint64_t* n_hits,
                            const uint32_t** cigar, uint64_t* n_cigar_words) {
   if (!res) { set_error("res is NULL"); return DSA_ERR_INVALID_ARG; }
-  DSA_TRY(set_device(res->ctx));
+  if (res->ctx) DSA_TRY(set_device(res->ctx));
   if (res->flags & DSA_RESULTS_ON_DEVICE) {
     if (hits) *hits = res->d_hits;
     if (cigar) *cigar = res->d_cigar;
@@ -1088,6 +1109,10 @@ extern "C" int dsa_res_phase_cells(const dsa_res* res, uint64_t* cells, int n) {
 extern "C" int dsa_res_free(dsa_res* res) {
   if (!res) return DSA_OK;
   dsa_ctx* ctx = res->ctx;
+  if (!ctx) {   // host-only result (serving): nothing on the device
+    delete res;
+    return DSA_OK;
+  }
   cudaSetDevice(ctx->device);
   for (int k = 0; k < 2 * dsa_res::NPHASE; ++k)
     if (res->ev[k]) cudaEventDestroy(res->ev[k]);

@@ -259,7 +259,7 @@ struct LongJob {
 struct LongTbJob {
   uint64_t q_start, t_start;
   uint64_t bnd_off;            // checkpoints of the score pass
-  uint64_t dir_off;            // word offset of the band decision buffer (BAND x wpr words)
+  uint64_t dir_off;            // word offset of the decision matrix (ie x wpr words)
   uint64_t cig_off;
   int32_t n;                   // boundary row length (the pair's window length)
   int32_t ie, je;
@@ -271,10 +271,12 @@ int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const in
                       int A, int o, int e, int mode, uint32_t fe, const LongJob* d_jobs,
                       uint32_t n_jobs, const uint32_t* d_items, uint32_t n_items, int2* d_bnd,
                       uint32_t* d_prog, void* d_cands, Scores out);
+// items: 2 words (job, band) per band of every job
 int launch_long_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
                           const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
-                          const LongTbJob* d_jobs, uint32_t n_jobs, const int2* d_bnd,
-                          uint32_t* d_dir, uint32_t* d_cig_tmp, dsa_hit* d_hits);
+                          const LongTbJob* d_jobs, uint32_t n_jobs, const uint32_t* d_items,
+                          uint32_t n_items, const int2* d_bnd, uint32_t* d_dir,
+                          uint32_t* d_cig_tmp, dsa_hit* d_hits);
 size_t long_cand_size();
 int long_band_rows();
 constexpr uint64_t LONG_PAIR_CELLS = 1ull << 22;   // explicit pairs at least this big run banded

@@ -143,17 +143,17 @@ __global__ void k_profile_int32(const uint8_t* __restrict__ qcodes, const uint64
                                 const uint32_t* __restrict__ qlen, uint32_t nq,
                                 const int8_t* __restrict__ S, int A, int32_t* __restrict__ prof,
                                 const uint64_t* __restrict__ prof_off) {
-  const uint32_t q = blockIdx.y;
-  if (q >= nq) return;
-  const int32_t m = (int32_t)qlen[q];
-  const int32_t mpad = (m + 7) & ~7;
-  const uint8_t* qs = qcodes + qoff[q];
-  int32_t* P = prof + prof_off[q];
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < (int64_t)A * mpad;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    const int a = (int)(x / mpad);
-    const int i = (int)(x % mpad);
-    P[x] = i < m ? (int32_t)S[qs[i] * A + a] : 0;
+  for (uint32_t q = blockIdx.y; q < nq; q += gridDim.y) {
+    const int32_t m = (int32_t)qlen[q];
+    const int32_t mpad = (m + 7) & ~7;
+    const uint8_t* qs = qcodes + qoff[q];
+    int32_t* P = prof + prof_off[q];
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < (int64_t)A * mpad;
+         x += (int64_t)gridDim.x * blockDim.x) {
+      const int a = (int)(x / mpad);
+      const int i = (int)(x % mpad);
+      P[x] = i < m ? (int32_t)S[qs[i] * A + a] : 0;
+    }
   }
 }
 
@@ -212,7 +212,7 @@ int launch_generic_int32(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const
 int launch_profile_int32(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix, int A,
                          int32_t* d_prof, const uint64_t* d_prof_off) {
   if (qs->n == 0) return DSA_OK;
-  dim3 grid(64, qs->n);
+  dim3 grid(qs->n > 4096 ? 1 : 64, std::min<uint32_t>(qs->n, 65535));
   k_profile_int32<<<grid, 256, 0, ctx->stream>>>(qs->d_codes, qs->d_off, qs->d_len, qs->n,
                                                  d_matrix, A, d_prof, d_prof_off);
   DSA_CUDA_TRY(cudaGetLastError());

@@ -18,11 +18,11 @@
 // lane keeps its first strictly better candidate; the lanes' and bands'
 // candidates are merged under (score desc, j asc, i asc) by k_long_reduce.
 //
-// Traceback.  From the end cell, band by band upwards: the band's rows are
-// recomputed from the checkpoint above it over columns 1..j (j = the walk's
-// current column), storing the 4-bit decision of every cell (as in the
-// short-hit traceback), then lane 0 walks until it leaves the band through its
-// top row.  Decision memory is BAND x n / 2 bytes per pair.
+// Traceback.  The checkpoints make every band independent: all bands of all
+// hits are recomputed at once (one warp each) over the rectangle up to the
+// end cell, storing the 4-bit decision of every cell (as in the short-hit
+// traceback), then one thread per hit walks back.  Decision memory is half a
+// byte per cell of the rectangle, handled in chunks of bounded size.
 #include "dsa_internal.cuh"
 #include "dpx.cuh"
 
@@ -237,155 +237,149 @@ struct RevCigar {
   }
 };
 
-// Checkpointed traceback: one warp per job.
-__global__ void __launch_bounds__(32) k_long_traceback(
+// Checkpointed traceback, part 1: every band of every hit is recomputed at
+// once (one warp per band, rows of the band x columns 1..je), starting from
+// the checkpoint row above it, and the 4-bit decision of every cell of the
+// rectangle up to the end cell is stored.
+__global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
-    const LongTbJob* __restrict__ jobs, uint32_t n_jobs, const int2* __restrict__ bnd,
-    uint32_t* __restrict__ dir, uint32_t* __restrict__ cig_tmp, dsa_hit* __restrict__ hits) {
+    const LongTbJob* __restrict__ jobs, const uint32_t* __restrict__ items, uint32_t n_items,
+    const int2* __restrict__ bnd, uint32_t* __restrict__ dir) {
   __shared__ int8_t S[32 * 32];
   for (int x = threadIdx.x; x < A * A; x += blockDim.x) S[x] = Sg[x];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const bool local = mode == DSA_LOCAL;
-  const bool sg = mode == DSA_SEMIGLOBAL;
-  for (uint32_t w = blockIdx.x; w < n_jobs; w += gridDim.x) {
-    const LongTbJob jb = jobs[w];
+  const uint32_t warps = gridDim.x * WARPS;
+  for (uint32_t it = blockIdx.x * WARPS + (threadIdx.x >> 5); it < n_items; it += warps) {
+    const LongTbJob jb = jobs[items[2 * it]];
+    const int32_t b = (int32_t)items[2 * it + 1];
+    const int32_t ie = jb.ie, je = jb.je;
     const uint8_t* q = qcodes + jb.q_start;
     const uint8_t* t = tcodes + jb.t_start;
     uint32_t* D = dir + jb.dir_off;
     const uint32_t wpr = jb.wpr;
-    RevCigar c;
-    c.out = cig_tmp + jb.cig_off;
-    int32_t i = jb.ie, j = jb.je;
-    int st = 0;   // 0 = H, 1 = F, 2 = E
-    bool done = false;
-    while (!done) {
-      // band holding row i (rows 1-based; row 0 belongs to no band)
-      if (i == 0 || j == 0) {
+    const int32_t i0 = b * BAND;
+    const int32_t r0 = i0 + lane * ROWS;
+    const int2* up = bnd + jb.bnd_off + (uint64_t)(b - 1) * jb.n;
+    int32_t H[ROWS], E[ROWS];
+    uint32_t nbw[ROWS];
+    int qc[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      const int32_t ii = r0 + r + 1;
+      H[r] = h_col0(mode, fe, ii, o, e);
+      E[r] = NEG32;
+      nbw[r] = 0;
+      qc[r] = ii <= ie ? q[ii - 1] * A : 0;
+    }
+    int32_t diag = h_col0(mode, fe, r0, o, e);
+    int32_t sendH = 0, sendF = NEG32;
+    for (int32_t s = 1; s <= je + 31; ++s) {
+      int32_t Hup = __shfl_up_sync(0xFFFFFFFFu, sendH, 1);
+      int32_t Fup = __shfl_up_sync(0xFFFFFFFFu, sendF, 1);
+      const int32_t jj = s - lane;
+      if (jj >= 1 && jj <= je && r0 < ie) {
         if (lane == 0) {
-          if (st == 0 && !(sg && ((i == 0 && (fe & DSA_FREE_T_BEGIN)) || (j == 0 && (fe & DSA_FREE_Q_BEGIN)))) &&
-              !local) {
-            while (j > 0) { c.emit(2); --j; }
-            while (i > 0) { c.emit(1); --i; }
+          if (b == 0) {
+            Hup = h_row0(mode, fe, jj, o, e);
+            Fup = NEG32;
+          } else {
+            const int2 v = up[jj - 1];
+            Hup = v.x;
+            Fup = v.y;
           }
         }
-        break;
-      }
-      const int32_t b = (i - 1) / BAND;
-      const int32_t i0 = b * BAND;
-      const int32_t rows_here = i - i0;        // recompute rows i0+1 .. i
-      const int32_t jmax = j;
-      // recompute the band over columns 1..jmax storing decisions (row-major, local rows)
-      {
-        const int32_t r0 = i0 + lane * ROWS;
-        int32_t H[ROWS], E[ROWS];
-        uint32_t nbw[ROWS];
-        int qc[ROWS];
+        const int a = t[jj - 1];
+        int32_t d = diag;
+        diag = Hup;
+        int32_t F = Fup, Hp = Hup;
+        const int sh = 4 * ((jj - 1) & 7);
+        const bool flushw = ((jj & 7) == 0) || jj == je;
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
           const int32_t ii = r0 + r + 1;
-          H[r] = h_col0(mode, fe, ii, o, e);
-          E[r] = NEG32;
-          nbw[r] = 0;
-          qc[r] = ii <= i ? q[ii - 1] * A : 0;
-        }
-        int32_t diag = h_col0(mode, fe, r0, o, e);
-        int32_t sendH = 0, sendF = NEG32;
-        const int2* up = bnd + jb.bnd_off + (uint64_t)(b - 1) * jb.n;
-        for (int32_t s = 1; s <= jmax + 31; ++s) {
-          int32_t Hup = __shfl_up_sync(0xFFFFFFFFu, sendH, 1);
-          int32_t Fup = __shfl_up_sync(0xFFFFFFFFu, sendF, 1);
-          const int32_t jj = s - lane;
-          if (jj >= 1 && jj <= jmax && r0 < i) {
-            if (lane == 0) {
-              if (b == 0) {
-                Hup = h_row0(mode, fe, jj, o, e);
-                Fup = NEG32;
-              } else {
-                const int2 v = up[jj - 1];
-                Hup = v.x;
-                Fup = v.y;
-              }
+          if (ii <= ie) {
+            const int32_t fo = Hp - o, fx = F - e;
+            F = max(fx, fo);
+            const int32_t eo = H[r] - o, ex = E[r] - e;
+            E[r] = max(ex, eo);
+            const int32_t mm = d + S[qc[r] + a];
+            int32_t v = max(mm, max(E[r], F));
+            if (local) v = max(v, 0);
+            uint32_t src;
+            if (local && v == 0) src = 3;
+            else if (v == mm) src = 0;
+            else if (v == F) src = 1;
+            else src = 2;
+            nbw[r] |= (src | ((eo >= ex) ? 4u : 0u) | ((fo >= fx) ? 8u : 0u)) << sh;
+            if (flushw) {
+              D[(uint64_t)(ii - 1) * wpr + (uint32_t)(jj - 1) / 8u] = nbw[r];
+              nbw[r] = 0;
             }
-            const int a = t[jj - 1];
-            int32_t d = diag;
-            diag = Hup;
-            int32_t F = Fup, Hp = Hup;
-            const int sh = 4 * ((jj - 1) & 7);
-            const bool flushw = ((jj & 7) == 0) || jj == jmax;
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-              const int32_t ii = r0 + r + 1;
-              if (ii <= i) {
-                const int32_t fo = Hp - o, fx = F - e;
-                F = max(fx, fo);
-                const int32_t eo = H[r] - o, ex = E[r] - e;
-                E[r] = max(ex, eo);
-                const int32_t mm = d + S[qc[r] + a];
-                int32_t v = max(mm, max(E[r], F));
-                if (local) v = max(v, 0);
-                uint32_t src;
-                if (local && v == 0) src = 3;
-                else if (v == mm) src = 0;
-                else if (v == F) src = 1;
-                else src = 2;
-                nbw[r] |= (src | ((eo >= ex) ? 4u : 0u) | ((fo >= fx) ? 8u : 0u)) << sh;
-                if (flushw) {
-                  D[(uint64_t)(ii - i0 - 1) * wpr + (uint32_t)(jj - 1) / 8u] = nbw[r];
-                  nbw[r] = 0;
-                }
-                d = H[r];
-                H[r] = v;
-                Hp = v;
-              }
-            }
-            sendH = Hp;
-            sendF = F;
+            d = H[r];
+            H[r] = v;
+            Hp = v;
           }
         }
+        sendH = Hp;
+        sendF = F;
       }
-      __syncwarp();
-      // walk inside the band until the walk leaves it upwards or stops
-      if (lane == 0) {
-        for (int64_t guard = 2 * ((int64_t)rows_here + jmax) + 4; guard > 0; --guard) {
-          if (i <= i0) break;   // left the band: continue with the band above
-          if (j == 0) break;    // column 0: handled at the loop head
-          const uint32_t nib = (D[(uint64_t)(i - i0 - 1) * wpr + (uint32_t)(j - 1) / 8u] >> (4 * ((j - 1) & 7))) & 15u;
-          if (st == 0) {
-            const uint32_t src = nib & 3u;
-            if (src == 3) { done = true; break; }
-            if (src == 0) { c.emit(0); --i; --j; }
-            else st = src == 1 ? 1 : 2;
-          } else if (st == 1) {
-            c.emit(1);
-            if (nib & 8u) st = 0;
-            --i;
-          } else {
-            c.emit(2);
-            if (nib & 4u) st = 0;
-            --j;
-          }
-        }
-        if (!done && st == 0 && sg && ((i == 0 && (fe & DSA_FREE_T_BEGIN)) || (j == 0 && (fe & DSA_FREE_Q_BEGIN))))
-          done = true;
-        if (!done && local && (i == 0 || j == 0)) done = true;
-      }
-      i = __shfl_sync(0xFFFFFFFFu, i, 0);
-      j = __shfl_sync(0xFFFFFFFFu, j, 0);
-      st = __shfl_sync(0xFFFFFFFFu, st, 0);
-      done = __shfl_sync(0xFFFFFFFFu, (int)done, 0) != 0;
-      __syncwarp();
-    }
-    if (lane == 0) {
-      c.flush();
-      dsa_hit* h = hits + jb.hit;
-      h->q_begin = i;
-      h->t_begin = j;
-      h->cigar_len = c.n;
-      h->flags |= DSA_HIT_HAS_TRACEBACK;
     }
     __syncwarp();
+  }
+}
+
+// Checkpointed traceback, part 2: one thread per hit walks the stored
+// decisions from the end cell (stop > M > I > D, open preferred on ties).
+__global__ void k_long_tb_walk(const LongTbJob* __restrict__ jobs, uint32_t n_jobs, int mode,
+                               uint32_t fe, const uint32_t* __restrict__ dir,
+                               uint32_t* __restrict__ cig_tmp, dsa_hit* __restrict__ hits) {
+  const bool local = mode == DSA_LOCAL;
+  const bool sg = mode == DSA_SEMIGLOBAL;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_jobs; k += gridDim.x * blockDim.x) {
+    const LongTbJob jb = jobs[k];
+    const uint32_t* D = dir + jb.dir_off;
+    const uint32_t wpr = jb.wpr;
+    RevCigar c;
+    c.out = cig_tmp + jb.cig_off;
+    int32_t i = jb.ie, j = jb.je;
+    int st = 0;
+    for (int64_t guard = 2 * ((int64_t)jb.ie + jb.je) + 2; guard > 0; --guard) {
+      if (st == 0) {
+        if (sg && ((i == 0 && (fe & DSA_FREE_T_BEGIN)) || (j == 0 && (fe & DSA_FREE_Q_BEGIN)))) break;
+        if (i == 0 || j == 0) {
+          if (local) break;
+          while (j > 0) { c.emit(2); --j; }
+          while (i > 0) { c.emit(1); --i; }
+          break;
+        }
+        const uint32_t nib = (D[(uint64_t)(i - 1) * wpr + (uint32_t)(j - 1) / 8u] >> (4 * ((j - 1) & 7))) & 15u;
+        const uint32_t src = nib & 3u;
+        if (src == 3) break;
+        if (src == 0) { c.emit(0); --i; --j; }
+        else st = src == 1 ? 1 : 2;
+      } else if (st == 1) {
+        if (i <= 0 || j <= 0) break;
+        const uint32_t nib = (D[(uint64_t)(i - 1) * wpr + (uint32_t)(j - 1) / 8u] >> (4 * ((j - 1) & 7))) & 15u;
+        c.emit(1);
+        if (nib & 8u) st = 0;
+        --i;
+      } else {
+        if (i <= 0 || j <= 0) break;
+        const uint32_t nib = (D[(uint64_t)(i - 1) * wpr + (uint32_t)(j - 1) / 8u] >> (4 * ((j - 1) & 7))) & 15u;
+        c.emit(2);
+        if (nib & 4u) st = 0;
+        --j;
+      }
+    }
+    c.flush();
+    dsa_hit* h = hits + jb.hit;
+    h->q_begin = i;
+    h->t_begin = j;
+    h->cigar_len = c.n;
+    h->flags |= DSA_HIT_HAS_TRACEBACK;
   }
 }
 
@@ -424,13 +418,19 @@ int long_band_rows() { return BAND; }
 
 int launch_long_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
                           const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
-                          const LongTbJob* d_jobs, uint32_t n_jobs, const int2* d_bnd,
-                          uint32_t* d_dir, uint32_t* d_cig_tmp, dsa_hit* d_hits) {
+                          const LongTbJob* d_jobs, uint32_t n_jobs, const uint32_t* d_items,
+                          uint32_t n_items, const int2* d_bnd, uint32_t* d_dir,
+                          uint32_t* d_cig_tmp, dsa_hit* d_hits) {
   if (n_jobs == 0) return DSA_OK;
-  const unsigned grid = (unsigned)std::min<uint64_t>(n_jobs, (uint64_t)ctx->sm_count * 32);
-  k_long_traceback<<<grid, 32, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e,
-                                                  mode, fe, d_jobs, n_jobs, d_bnd, d_dir,
-                                                  d_cig_tmp, d_hits);
+  const unsigned grid = (unsigned)std::min<uint64_t>((n_items + WARPS - 1) / WARPS,
+                                                     (uint64_t)ctx->sm_count * 16);
+  k_long_tb_fill<<<grid, WARPS * 32, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e,
+                                                        mode, fe, d_jobs, d_items, n_items, d_bnd,
+                                                        d_dir);
+  DSA_CUDA_TRY(cudaGetLastError());
+  ++ctx->launches;
+  k_long_tb_walk<<<(n_jobs + 63) / 64, 64, 0, ctx->stream>>>(d_jobs, n_jobs, mode, fe, d_dir,
+                                                             d_cig_tmp, d_hits);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   return DSA_OK;

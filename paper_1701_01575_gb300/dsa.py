@@ -38,7 +38,29 @@ SYMBOLS = ["dsa_create", "dsa_destroy", "dsa_last_error", "dsa_mem_in_use", "dsa
            "dsa_db_free", "dsa_db_info", "dsa_align", "dsa_align_batch", "dsa_traceback",
            "dsa_res_get", "dsa_res_stats", "dsa_res_free", "dsa_sync", "dsa_probe_issue_rate",
            "dsa_res_timing", "dsa_kernel_launches", "dsa_score_pairs_noalloc",
-           "dsa_res_phase_cells"]
+           "dsa_res_phase_cells", "dsa_server_create", "dsa_submit", "dsa_poll",
+           "dsa_server_drain", "dsa_server_now", "dsa_server_destroy"]
+REQ_SEARCH, REQ_PAIRS = 0, 1
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("db", ctypes.c_void_p), ("q_codes", ctypes.c_void_p),
+                ("q_offsets", ctypes.c_void_p), ("n_queries", ctypes.c_uint32),
+                ("pairs", ctypes.c_void_p), ("n_pairs", ctypes.c_uint64), ("mode", ctypes.c_int),
+                ("free_ends", ctypes.c_uint32), ("matrix", ctypes.c_void_p),
+                ("alphabet_size", ctypes.c_int), ("gap_open", ctypes.c_int),
+                ("gap_extend", ctypes.c_int), ("top_k", ctypes.c_uint32), ("traceback", ctypes.c_int)]
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_uint32), ("max_batch_queries", ctypes.c_uint32),
+                ("max_batch_pairs", ctypes.c_uint64), ("mem_reserve", ctypes.c_size_t),
+                ("mem_budget", ctypes.c_size_t), ("max_pending", ctypes.c_uint32)]
+
+
+class _Times(ctypes.Structure):
+    _fields_ = [("arrive", ctypes.c_double), ("admit", ctypes.c_double), ("finish", ctypes.c_double),
+                ("batch_requests", ctypes.c_uint32), ("status", ctypes.c_int)]
 
 
 class DsaError(RuntimeError):
@@ -86,6 +108,13 @@ def load_library(path: str = LIB_PATH):
     lib.dsa_res_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     lib.dsa_kernel_launches.argtypes = [_vp]
     lib.dsa_res_phase_cells.argtypes = [_vp, ctypes.POINTER(_u64), ctypes.c_int]
+    lib.dsa_server_create.argtypes = [ctypes.c_int, ctypes.POINTER(_ServerConfig), ctypes.POINTER(_vp)]
+    lib.dsa_submit.argtypes = [_vp, ctypes.POINTER(_Request), ctypes.POINTER(_u64)]
+    lib.dsa_poll.argtypes = [_vp, _u64, ctypes.POINTER(_vp), ctypes.POINTER(_Times)]
+    lib.dsa_server_drain.argtypes = [_vp]
+    lib.dsa_server_now.argtypes = [_vp]
+    lib.dsa_server_now.restype = ctypes.c_double
+    lib.dsa_server_destroy.argtypes = [_vp]
     lib.dsa_kernel_launches.restype = ctypes.c_uint64
     lib.dsa_score_pairs_noalloc.argtypes = [_vp, _vp, _u32, _vp, _vp, _u32, _vp, _u64, ctypes.c_int,
                                             _u32, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -305,6 +334,103 @@ class Context:
         r = ctypes.c_double()
         _check(_lib.dsa_probe_issue_rate(self.handle, form, ctypes.byref(r)))
         return r.value
+
+
+class HostResult:
+    """A result handed out by a Server: host arrays, request-local query ids."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def _raw(self):
+        hp = _vp(); nh = _u64(); cp = _vp(); nc = _u64()
+        _check(_lib.dsa_res_get(self.handle, ctypes.byref(hp), ctypes.byref(nh), ctypes.byref(cp),
+                                ctypes.byref(nc)))
+        return hp.value, nh.value, cp.value, nc.value
+
+    def hits(self) -> np.ndarray:
+        hp, nh, cp, nc = self._raw()
+        if nh == 0:
+            return np.zeros(0, HIT_DTYPE)
+        buf = (ctypes.c_uint8 * (nh * HIT_DTYPE.itemsize)).from_address(hp)
+        return np.frombuffer(buf, dtype=HIT_DTYPE).copy()
+
+    def cigar(self) -> np.ndarray:
+        hp, nh, cp, nc = self._raw()
+        if nc == 0:
+            return np.zeros(0, np.uint32)
+        return np.frombuffer((ctypes.c_uint32 * nc).from_address(cp), dtype=np.uint32).copy()
+
+    def free(self):
+        if self.handle:
+            _lib.dsa_res_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (dsa_server_*)."""
+
+    def __init__(self, device: int = 0, n_slots: int = 2, max_batch_queries: int = 64,
+                 max_batch_pairs: int = 2_000_000, mem_reserve: int = 0, mem_budget: int = 0,
+                 max_pending: int = 0):
+        load_library()
+        cfg = _ServerConfig(n_slots, max_batch_queries, max_batch_pairs, mem_reserve, mem_budget,
+                            max_pending)
+        h = _vp()
+        _check(_lib.dsa_server_create(device, ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, db: Database, q_codes, q_offsets, matrix, gap_open: int, gap_extend: int,
+               mode: int = LOCAL, free_ends: int = 15, top_k: int = 0, pairs=None,
+               traceback: bool = True) -> int:
+        qc = np.ascontiguousarray(q_codes, dtype=np.uint8)
+        qo = np.ascontiguousarray(q_offsets, dtype=np.uint64)
+        mat = np.ascontiguousarray(matrix, dtype=np.int8)
+        pr = None if pairs is None else np.ascontiguousarray(pairs).astype(PAIR_DTYPE)
+        req = _Request(REQ_PAIRS if pr is not None else REQ_SEARCH, db.handle, _ptr(qc), _ptr(qo),
+                       len(qo) - 1, _ptr(pr) if pr is not None else None,
+                       len(pr) if pr is not None else 0, mode, free_ends, _ptr(mat), mat.shape[0],
+                       gap_open, gap_extend, top_k, int(bool(traceback)))
+        t = _u64()
+        _check(_lib.dsa_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int):
+        """(HostResult, times dict) when done, (None, None) while pending."""
+        h = _vp()
+        tm = _Times()
+        rc = _lib.dsa_poll(self.handle, ticket, ctypes.byref(h), ctypes.byref(tm))
+        if rc == ERR_BUSY:
+            return None, None
+        times = {"arrive": tm.arrive, "admit": tm.admit, "finish": tm.finish,
+                 "batch_requests": tm.batch_requests, "status": tm.status}
+        if rc != OK:
+            return None, times
+        return HostResult(h.value), times
+
+    def drain(self):
+        _check(_lib.dsa_server_drain(self.handle))
+
+    def now(self) -> float:
+        return _lib.dsa_server_now(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.dsa_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cigar_of(hit, cigar: np.ndarray) -> np.ndarray:

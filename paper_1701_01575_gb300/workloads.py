@@ -238,6 +238,42 @@ def _geometric_len(rng) -> int:
     return int(rng.geometric(0.5))
 
 
+def _apply_events(rng, src: np.ndarray, positions, out_len: Optional[int], alphabet: int):
+    """Indels at the given source positions (insertion or deletion with equal
+    odds, length geometric p=0.5 on {1,2,...}); stops after out_len residues."""
+    n = len(src)
+    pos = 0
+    pieces = []
+    emitted = 0
+    for p in positions:
+        if p < pos:
+            continue
+        if out_len is not None and emitted + (p - pos) >= out_len:
+            break
+        pieces.append(src[pos:p])
+        emitted += p - pos
+        pos = p
+        k = _geometric_len(rng)
+        if rng.random() < 0.5:  # insertion of k random residues
+            pieces.append(rng.integers(0, alphabet, size=k).astype(np.uint8))
+            emitted += k
+        else:                   # deletion of k source residues
+            pos = min(n, pos + k)
+    pieces.append(src[pos:])
+    out = np.concatenate(pieces) if pieces else np.zeros(0, np.uint8)
+    if out_len is not None:
+        out = out[:out_len]
+    return out.copy()
+
+
+def _substitute(rng, out: np.ndarray, sub_rate: float, alphabet: int) -> np.ndarray:
+    subs = np.flatnonzero(rng.random(len(out)) < sub_rate)
+    if len(subs):
+        shift = rng.integers(1, alphabet, size=len(subs)).astype(np.uint8)
+        out[subs] = (out[subs] + shift) % alphabet
+    return out.astype(np.uint8)
+
+
 def mutate(rng, src: np.ndarray, sub_rate: float, indel_rate: float,
            out_len: Optional[int] = None, alphabet: int = 4) -> np.ndarray:
     """Copy ``src`` with substitutions (to a different residue) and indels.
@@ -246,38 +282,9 @@ def mutate(rng, src: np.ndarray, sub_rate: float, indel_rate: float,
     happens (insertion or deletion with equal odds, length geometric p=0.5 on
     {1,2,...}).  If ``out_len`` is given, the walk stops once that many
     residues have been emitted (``src`` must be long enough)."""
-    n = len(src)
-    pos = 0
-    pieces = []
-    emitted = 0
-    limit = out_len if out_len is not None else None
-    # event positions, drawn ahead in bulk
-    ev = np.flatnonzero(rng.random(n) < indel_rate)
-    for p in ev:
-        if p < pos:
-            continue
-        if limit is not None and emitted + (p - pos) >= limit:
-            break
-        pieces.append(src[pos:p])
-        emitted += p - pos
-        pos = p
-        k = _geometric_len(rng)
-        if rng.random() < 0.5:  # insertion of k random residues
-            ins = rng.integers(0, alphabet, size=k).astype(np.uint8)
-            pieces.append(ins)
-            emitted += k
-        else:                   # deletion of k source residues
-            pos = min(n, pos + k)
-    pieces.append(src[pos:])
-    out = np.concatenate(pieces) if pieces else np.zeros(0, np.uint8)
-    if limit is not None:
-        out = out[:limit]
-    out = out.copy()
-    subs = np.flatnonzero(rng.random(len(out)) < sub_rate)
-    if len(subs):
-        shift = rng.integers(1, alphabet, size=len(subs)).astype(np.uint8)
-        out[subs] = (out[subs] + shift) % alphabet
-    return out.astype(np.uint8)
+    ev = np.flatnonzero(rng.random(len(src)) < indel_rate)
+    out = _apply_events(rng, src, ev, out_len, alphabet)
+    return _substitute(rng, out, sub_rate, alphabet)
 
 
 def reads_vs_windows(seed: int = SEED_BASE + 2, n_reads: int = 1_000_000,
@@ -293,14 +300,28 @@ def reads_vs_windows(seed: int = SEED_BASE + 2, n_reads: int = 1_000_000,
     rng.shuffle(lens)
     slack = 64
     origins = rng.integers(0, ref_len - lens - slack, size=n_reads)
-    # reads without indel events are plain substitutions of the source slice
-    reads = []
-    sub_draw = rng.random
-    for k in range(n_reads):
+    # indel events per read over its source slice (length L + slack); reads
+    # without events are the slice with substitutions, built in bulk
+    n_events = rng.binomial(lens + slack, indel_rate)
+    off = np.zeros(n_reads + 1, dtype=np.uint64)
+    off[1:] = np.cumsum(lens)
+    codes = np.empty(int(off[-1]), dtype=np.uint8)
+    for L in np.unique(lens):
+        idx = np.flatnonzero((lens == L) & (n_events == 0))
+        if len(idx) == 0:
+            continue
+        block = ref[origins[idx][:, None] + np.arange(L)[None, :]]
+        hit = rng.random(block.shape) < sub_rate
+        shift = rng.integers(1, 4, size=int(hit.sum())).astype(np.uint8)
+        block[hit] = (block[hit] + shift) % 4
+        codes[off[idx].astype(np.int64)[:, None] + np.arange(L)[None, :]] = block
+    for k in np.flatnonzero(n_events > 0):
         L = int(lens[k]); o = int(origins[k])
         src = ref[o:o + L + slack]
-        reads.append(mutate(rng, src, sub_rate, indel_rate, out_len=L))
-    queries = SeqSet.from_list(reads)
+        ev = np.sort(rng.choice(L + slack, size=int(n_events[k]), replace=False))
+        r = _substitute(rng, _apply_events(rng, src, ev, L, 4), sub_rate, 4)
+        codes[int(off[k]):int(off[k]) + L] = r
+    queries = SeqSet(codes, off)
     db = SeqSet(ref, np.array([0, ref_len], dtype=np.uint64))
     pairs = np.zeros(n_reads, dtype=PAIR_DTYPE)
     pairs["query_id"] = np.arange(n_reads, dtype=np.uint32)
@@ -309,7 +330,6 @@ def reads_vs_windows(seed: int = SEED_BASE + 2, n_reads: int = 1_000_000,
     start = np.clip(start, 0, ref_len - window)
     pairs["t_offset"] = start.astype(np.uint64)
     pairs["t_len"] = window
-    del sub_draw
     return Workload("reads_vs_windows", queries, db, dna_matrix(1, -4), 6, 1, MODE_SEMIGLOBAL,
                     free_ends=FREE_T_BEGIN | FREE_T_END, pairs=pairs,
                     meta=dict(seed=seed, n_reads=n_reads, ref_len=ref_len,
@@ -338,6 +358,54 @@ def long_pairs(seed: int = SEED_BASE + 3, n_pairs: int = 64, lo: int = 10_000,
     pairs["t_len"] = db.lengths.astype(np.uint32)
     return Workload("long_pairs", queries, db, dna_matrix(2, -3), 5, 2, mode, pairs=pairs,
                     meta=dict(seed=seed, n_pairs=n_pairs, lo=lo, hi=hi))
+
+
+def reads_from_reference(rng, ref: np.ndarray, n_reads: int, read_len: int = 150,
+                         window: int = 500, sub_rate: float = 0.01, indel_rate: float = 0.001):
+    """Reads sampled from `ref` (forward strand) with their windows: (SeqSet, pairs)."""
+    slack = 64
+    reads = []
+    origins = rng.integers(0, len(ref) - read_len - slack, size=n_reads)
+    for o in origins:
+        reads.append(mutate(rng, ref[int(o):int(o) + read_len + slack], sub_rate, indel_rate,
+                            out_len=read_len))
+    qs = SeqSet.from_list(reads)
+    pairs = np.zeros(n_reads, dtype=PAIR_DTYPE)
+    pairs["query_id"] = np.arange(n_reads, dtype=np.uint32)
+    start = np.clip(origins + (qs.lengths - window) // 2, 0, len(ref) - window)
+    pairs["t_offset"] = start.astype(np.uint64)
+    pairs["t_len"] = window
+    return qs, pairs
+
+
+@dataclasses.dataclass
+class Request:
+    kind: str               # "protein" or "dna"
+    queries: SeqSet
+    pairs: Optional[np.ndarray]
+    arrival: float          # seconds after the stream start
+
+
+def serving_stream(seed: int = SEED_BASE + 4, n_requests: int = 100, rate: float = 10.0,
+                   protein_frac: float = 0.7, plo: int = 50, phi: int = 2000,
+                   dlo: int = 1000, dhi: int = 100_000, genome: Optional[np.ndarray] = None):
+    """Poisson arrivals (rate per second) of protein queries (log-uniform lengths,
+    searched against a protein database) and DNA read batches (log-uniform counts of
+    150 bp reads against 500 bp windows of `genome`)."""
+    rng = np.random.default_rng(seed)
+    bg = protein_background()
+    t = 0.0
+    out = []
+    for _ in range(n_requests):
+        t += float(rng.exponential(1.0 / rate))
+        if rng.random() < protein_frac or genome is None:
+            q = _make_set(rng, log_uniform_int(rng, plo, phi, 1), bg)
+            out.append(Request("protein", q, None, t))
+        else:
+            n = int(log_uniform_int(rng, dlo, dhi, 1)[0])
+            q, pairs = reads_from_reference(rng, genome, n)
+            out.append(Request("dna", q, pairs, t))
+    return out
 
 
 def random_protein_pairs(rng, n: int, lo: int, hi: int) -> SeqSet:
