@@ -49,9 +49,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="approximate CPU time of the oracle sample")
+    ap.add_argument("--requests", type=int, default=120,
+                    help="serving: requests per measured load level")
     ap.add_argument("--workload", default="protein_search",
                     choices=["protein_search", "protein_vs_db", "reads_vs_windows", "long_pairs",
-                             "long_pairs_local"],
+                             "long_pairs_local", "serving"],
                     help="the measured workload (default: the batched protein search)")
     return ap.parse_args()
 
@@ -367,6 +369,91 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- serving --
+
+def bench_serving(args):
+    """Serving loop: capacity, then Poisson loads at 0.5 and 0.8 of it."""
+    import threading
+    from paper_1701_01575_gb300 import build, dsa
+    from paper_1701_01575_gb300 import workloads as W
+    build.build()
+    rng = np.random.default_rng(W.SEED_BASE + 4)
+    pwl = W.protein_search(seed=W.SEED_BASE + 1, n_queries=1, n_targets=args.targets)
+    genome = rng.integers(0, 4, 10_000_000).astype(np.uint8)
+    gdb = W.SeqSet(genome, np.array([0, len(genome)], dtype=np.uint64))
+    ctx = dsa.Context(0)
+    d_p = ctx.load_set(pwl.db, 24)
+    d_g = ctx.load_set(gdb, 4)
+    db_res = int(pwl.db.codes.nbytes)
+    S_p, S_d = W.blosum62(), W.dna_matrix(1, -4)
+
+    def cells(r):
+        if r.kind == "protein":
+            return int(r.queries.lengths.sum()) * db_res
+        return int(r.queries.lengths.sum()) * 500
+
+    def submit(srv, r):
+        if r.kind == "protein":
+            return srv.submit(d_p, r.queries.codes, r.queries.offsets, S_p, 11, 1, top_k=10,
+                              traceback=True)
+        return srv.submit(d_g, r.queries.codes, r.queries.offsets, S_d, 6, 1, mode=dsa.SEMIGLOBAL,
+                          free_ends=W.FREE_T_BEGIN | W.FREE_T_END, pairs=r.pairs, traceback=True)
+
+    def run(reqs, rate):
+        srv = dsa.Server(0, n_slots=2)
+        t0 = srv.now()
+        tickets = []
+        for r in reqs:
+            if rate:
+                delay = t0 + r.arrival - srv.now()
+                if delay > 0:
+                    time.sleep(delay)
+            tickets.append(submit(srv, r))
+        srv.drain()
+        lat, fin, arr, batch = [], [], [], []
+        for t in tickets:
+            res, tm = srv.poll(t)
+            assert res is not None, tm
+            lat.append(tm["finish"] - tm["arrive"])
+            fin.append(tm["finish"])
+            arr.append(tm["arrive"])
+            batch.append(tm["batch_requests"])
+            res.free()
+        srv.close()
+        span = max(fin) - min(arr)
+        total = sum(cells(r) for r in reqs)
+        lat = np.array(lat)
+        return {"requests": len(reqs), "span_s": round(span, 3),
+                "gcups": round(total / span / 1e9, 1),
+                "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 2),
+                "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 2),
+                "max_ms": round(float(lat.max()) * 1e3, 2),
+                "mean_batch": round(float(np.mean(batch)), 2)}
+
+    n = args.requests
+    warm = W.serving_stream(seed=W.SEED_BASE + 40, n_requests=8, rate=1e9, genome=genome)
+    run(warm, 0)
+    burst = W.serving_stream(seed=W.SEED_BASE + 41, n_requests=n, rate=1e9, genome=genome)
+    cap = run(burst, 0)
+    C = cap["requests"] / cap["span_s"]
+    loads = {}
+    for frac in (0.5, 0.8):
+        reqs = W.serving_stream(seed=W.SEED_BASE + 42 + int(frac * 10), n_requests=n,
+                                rate=frac * C, genome=genome)
+        loads[f"{frac}C"] = dict(run(reqs, frac * C), rate_per_s=round(frac * C, 2))
+    out = {"metric": "serving: p50/p99 request latency and GCUPS at 0.8 of capacity",
+           "value": loads["0.8C"]["p99_ms"], "unit": "ms (p99)", "n_gpus": 1,
+           "higher_is_better": False, "data": "synthetic", "dtype": "i16x2+i32",
+           "config": {"workload": "serving: Poisson arrivals, 70% protein queries "
+                                  "(log-uniform 50..2000) vs 500,000 targets top-10 + traceback, "
+                                  "30% DNA read batches (log-uniform 1e3..1e5 reads of 150 bp vs "
+                                  "500 bp windows of a 10 Mb genome) with traceback; 2 slots",
+                      "requests_per_level": n},
+           "capacity": dict(cap, requests_per_s=round(C, 2)), "loads": loads}
+    print(json.dumps(out), flush=True)
+    d_p.free(); d_g.free(); ctx.close()
+
+
 # ------------------------------------------------------------- reference --
 
 def bench_reference(args):
@@ -404,5 +491,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         bench_reference(a)
+    elif a.workload == "serving":
+        bench_serving(a)
     else:
         bench_ours(a)

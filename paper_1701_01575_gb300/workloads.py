@@ -287,21 +287,16 @@ def mutate(rng, src: np.ndarray, sub_rate: float, indel_rate: float,
     return _substitute(rng, out, sub_rate, alphabet)
 
 
-def reads_vs_windows(seed: int = SEED_BASE + 2, n_reads: int = 1_000_000,
-                     ref_len: int = 10_000_000, read_lens=(150, 250), window: int = 500,
-                     sub_rate: float = 0.01, indel_rate: float = 0.001) -> Workload:
-    """DNA reads sampled from a random genome, each paired with a window around its origin.
-
-    The DB is the genome (one sequence); ``pairs`` holds one (read, window) pair per
-    read with ``t_offset`` = window start.  Semi-global with free target ends."""
-    rng = np.random.default_rng(seed)
-    ref = rng.integers(0, 4, size=ref_len).astype(np.uint8)
-    lens = np.where(np.arange(n_reads) < n_reads // 2, read_lens[0], read_lens[1]).astype(np.int64)
-    rng.shuffle(lens)
+def _sample_reads(rng, ref: np.ndarray, lens: np.ndarray, window: int, sub_rate: float,
+                  indel_rate: float):
+    """Reads of the given lengths sampled from `ref` (forward strand), with their
+    windows.  Per read, indel events hit its source slice (length + 64 slack) at
+    rate `indel_rate`; reads without events are the slice with substitutions,
+    built in bulk.  Returns (SeqSet, pairs, origins)."""
+    n_reads = len(lens)
+    ref_len = len(ref)
     slack = 64
     origins = rng.integers(0, ref_len - lens - slack, size=n_reads)
-    # indel events per read over its source slice (length L + slack); reads
-    # without events are the slice with substitutions, built in bulk
     n_events = rng.binomial(lens + slack, indel_rate)
     off = np.zeros(n_reads + 1, dtype=np.uint64)
     off[1:] = np.cumsum(lens)
@@ -322,7 +317,6 @@ def reads_vs_windows(seed: int = SEED_BASE + 2, n_reads: int = 1_000_000,
         r = _substitute(rng, _apply_events(rng, src, ev, L, 4), sub_rate, 4)
         codes[int(off[k]):int(off[k]) + L] = r
     queries = SeqSet(codes, off)
-    db = SeqSet(ref, np.array([0, ref_len], dtype=np.uint64))
     pairs = np.zeros(n_reads, dtype=PAIR_DTYPE)
     pairs["query_id"] = np.arange(n_reads, dtype=np.uint32)
     pairs["target_id"] = 0
@@ -330,6 +324,22 @@ def reads_vs_windows(seed: int = SEED_BASE + 2, n_reads: int = 1_000_000,
     start = np.clip(start, 0, ref_len - window)
     pairs["t_offset"] = start.astype(np.uint64)
     pairs["t_len"] = window
+    return queries, pairs, origins
+
+
+def reads_vs_windows(seed: int = SEED_BASE + 2, n_reads: int = 1_000_000,
+                     ref_len: int = 10_000_000, read_lens=(150, 250), window: int = 500,
+                     sub_rate: float = 0.01, indel_rate: float = 0.001) -> Workload:
+    """DNA reads sampled from a random genome, each paired with a window around its origin.
+
+    The DB is the genome (one sequence); ``pairs`` holds one (read, window) pair per
+    read with ``t_offset`` = window start.  Semi-global with free target ends."""
+    rng = np.random.default_rng(seed)
+    ref = rng.integers(0, 4, size=ref_len).astype(np.uint8)
+    lens = np.where(np.arange(n_reads) < n_reads // 2, read_lens[0], read_lens[1]).astype(np.int64)
+    rng.shuffle(lens)
+    queries, pairs, origins = _sample_reads(rng, ref, lens, window, sub_rate, indel_rate)
+    db = SeqSet(ref, np.array([0, ref_len], dtype=np.uint64))
     return Workload("reads_vs_windows", queries, db, dna_matrix(1, -4), 6, 1, MODE_SEMIGLOBAL,
                     free_ends=FREE_T_BEGIN | FREE_T_END, pairs=pairs,
                     meta=dict(seed=seed, n_reads=n_reads, ref_len=ref_len,
@@ -363,19 +373,9 @@ def long_pairs(seed: int = SEED_BASE + 3, n_pairs: int = 64, lo: int = 10_000,
 def reads_from_reference(rng, ref: np.ndarray, n_reads: int, read_len: int = 150,
                          window: int = 500, sub_rate: float = 0.01, indel_rate: float = 0.001):
     """Reads sampled from `ref` (forward strand) with their windows: (SeqSet, pairs)."""
-    slack = 64
-    reads = []
-    origins = rng.integers(0, len(ref) - read_len - slack, size=n_reads)
-    for o in origins:
-        reads.append(mutate(rng, ref[int(o):int(o) + read_len + slack], sub_rate, indel_rate,
-                            out_len=read_len))
-    qs = SeqSet.from_list(reads)
-    pairs = np.zeros(n_reads, dtype=PAIR_DTYPE)
-    pairs["query_id"] = np.arange(n_reads, dtype=np.uint32)
-    start = np.clip(origins + (qs.lengths - window) // 2, 0, len(ref) - window)
-    pairs["t_offset"] = start.astype(np.uint64)
-    pairs["t_len"] = window
-    return qs, pairs
+    lens = np.full(n_reads, read_len, dtype=np.int64)
+    queries, pairs, _ = _sample_reads(rng, ref, lens, window, sub_rate, indel_rate)
+    return queries, pairs
 
 
 @dataclasses.dataclass
