@@ -31,6 +31,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GCUPS (bit-exact) batched protein database search"
+# DRAM bytes per DP cell of k_inter_local16, from the ncu capture summarised in
+# profiles/k_inter_local16_protein_8q_350k.md (372.5 GB read + written for
+# 1.194 T cells); traffic grows with the cells (boundary rows per column and
+# strip), so a launch's traffic is this figure times its cells.
+INTER_DRAM_BYTES_PER_CELL = 372.47e9 / 1.194104e12
+
 WORKLOAD = ("protein_search: 32 queries (log-uniform 64..5000) x 500,000 targets "
             "(lognormal median 300, sigma 0.7, cap 35,000), BLOSUM62 11/1, local, "
             "packed int16x2 + exact int32 rerun, top-10 + traceback")
@@ -288,7 +294,10 @@ def bench_ours(args):
         # running best); in packed 16x2 form one instruction covers 2 cells
         peak = props.multi_processor_count * sm_mhz * 1e6 * rate * 32 * 2 / 6 / 1e9
         out["roofline"] = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
-                           "unit": "GCUPS", "frac": round(achieved / peak, 4), "traffic": None,
+                           "unit": "GCUPS", "frac": round(achieved / peak, 4),
+                           "traffic": round(INTER_DRAM_BYTES_PER_CELL * pcells["inter16"]),
+                           "traffic_basis": "ncu dram__bytes_read+write of an 8-query x 350k "
+                                            "capture, scaled by cells to this launch",
                            "kernel": "k_inter_local16", "kernel_ms": round(inter_ms, 3),
                            "peak_basis": f"{props.multi_processor_count} SMs x {sm_mhz:.0f} MHz x "
                                          f"{rate:.3f} DPX warp-instr/SM/clk (measured) x 32 lanes "
