@@ -115,15 +115,19 @@ class ClockSampler:
 
 # --------------------------------------------------------------- distributed --
 
-def dist_setup(args):
+def dist_setup(args, backend="nccl"):
+    """Rank layout from the launcher's environment; process group for N > 1."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
         import torch
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return world, rank, local
 
 
@@ -133,24 +137,34 @@ def barrier(world):
         dist.barrier()
 
 
-def all_max(world, x: float) -> float:
+def _reduce(world, x: float, op) -> float:
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def all_max(world, x: float) -> float:
+    """Slowest rank's time: the job's time."""
+    import torch.distributed as dist
+    return _reduce(world, x, dist.ReduceOp.MAX if world > 1 else None)
 
 
 def all_sum(world, x: float) -> float:
-    if world == 1:
-        return x
-    import torch
+    """Work of all ranks together."""
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(world, x, dist.ReduceOp.SUM if world > 1 else None)
+
+
+def aggregate(world, ms_local: float, cells_local: float):
+    """(max ms over ranks, total cells, whole-job GCUPS) for weak scaling."""
+    ms = all_max(world, ms_local)
+    cells = all_sum(world, cells_local)
+    return ms, cells, cells / (ms / 1e3) / 1e9
 
 
 # ---------------------------------------------------------------- workload --
@@ -266,9 +280,7 @@ def bench_ours(args):
     top_hits = last.hits()
     for r in results:
         r.free()
-    ms = all_max(world, ms_local)
-    total_cells = all_sum(world, float(cells_per_step * args.steps))
-    value = total_cells / (ms / 1e3) / 1e9
+    ms, total_cells, value = aggregate(world, ms_local, float(cells_per_step * args.steps))
 
     wtext = WORKLOAD if args.workload == "protein_search" else WORKLOAD_TEXT[args.workload]
     out = {"metric": METRIC if args.workload == "protein_search" else

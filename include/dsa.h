@@ -199,6 +199,16 @@ int dsa_sync(dsa_ctx* ctx);
  * add-max (DPX), 7 = the packed local cell update mix. */
 int dsa_probe_issue_rate(dsa_ctx* ctx, int form, double* warp_instr_per_sm_per_clk);
 
+/* Self-test of the device-side failure path (no fault is raised): enqueues a
+ * kernel whose wait can never be satisfied -- kind 0 an mbarrier whose
+ * transaction bytes never arrive, kind 1 a progress flag nobody publishes --
+ * with a wait limit of `limit_ns` nanoseconds (at most 10 s).  The kernel
+ * gives up, records DSA_ERR_DEVICE_TIMEOUT in the context's status word and
+ * returns; the next dsa_sync reports that status and clears it, and the
+ * context stays usable.  These are the waits the kernels use for their TMA
+ * profile copies and for the long-pair band pipeline. */
+int dsa_selftest_wait_timeout(dsa_ctx* ctx, int kind, uint64_t limit_ns);
+
 /* ---- serving: continuous batching of alignment requests ----
  *
  * A server owns `n_slots` worker slots, each with its own stream.  Submitted

@@ -475,6 +475,7 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
   }
   PackedPlan spl;
   spl.R = R;
+  spl.rows = INTER_ROWS;
   spl.n_units = (uint32_t)s_ns.size();
   spl.n_strips = (uint32_t)smeta.size();
 
@@ -506,10 +507,12 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
   uint64_t long_res = 0;
   if (n_long) {
     ppl.R = R;
+    ppl.rows = 32;   // the wavefront kernel's lanes take half-strips of 16 rows
+    auto strips32 = [&](uint32_t q) { return (qs->h_len[q] + 31u) / 32u; };
     for (uint32_t u = 0; 2 * u < nq; ++u) {
       const uint32_t qa = qorder[2 * u];
       const uint32_t qb = 2 * u + 1 < nq ? qorder[2 * u + 1] : NONE;
-      const uint32_t ns_u = std::max(strips_of(qa), qb != NONE ? strips_of(qb) : 0u);
+      const uint32_t ns_u = std::max(strips32(qa), qb != NONE ? strips32(qb) : 0u);
       p_sbase.push_back((uint32_t)pmeta.size());
       p_ns.push_back(ns_u);
       for (uint32_t st = 0; st < ns_u; ++st)
@@ -548,7 +551,7 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
   DSA_TRY(upload(ctx, d_sbase, s_sbase));
   DSA_TRY(upload(ctx, d_sns, s_ns));
   DSA_TRY(upload(ctx, d_items, item_words));
-  DSA_TRY(d_sprof.alloc(ctx, (size_t)spl.n_strips * R * 32 * sizeof(uint32_t)));
+  DSA_TRY(d_sprof.alloc(ctx, (size_t)spl.n_strips * R * spl.rows * sizeof(uint32_t)));
   spl.d_meta = d_smeta.as<StripMeta>();
   spl.d_sbase = d_sbase.as<uint32_t>();
   spl.d_ns = d_sns.as<uint32_t>();
@@ -561,7 +564,7 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
     DSA_TRY(upload(ctx, d_pns, p_ns));
     DSA_TRY(upload(ctx, d_long, long_ids));
     DSA_TRY(upload(ctx, d_litems, litem_words));
-    DSA_TRY(d_pprof.alloc(ctx, (size_t)ppl.n_strips * R * 32 * sizeof(uint32_t)));
+    DSA_TRY(d_pprof.alloc(ctx, (size_t)ppl.n_strips * R * ppl.rows * sizeof(uint32_t)));
     ppl.d_meta = d_pmeta.as<StripMeta>();
     ppl.d_sbase = d_pbase.as<uint32_t>();
     ppl.d_ns = d_pns.as<uint32_t>();
@@ -1122,6 +1125,12 @@ extern "C" int dsa_res_free(dsa_res* res) {
   if (res->owned_queries) dsa_db_free(res->owned_queries);
   delete res;
   return DSA_OK;
+}
+
+extern "C" int dsa_selftest_wait_timeout(dsa_ctx* ctx, int kind, uint64_t limit_ns) {
+  if (!ctx) { set_error("NULL argument"); return DSA_ERR_INVALID_ARG; }
+  DSA_TRY(set_device(ctx));
+  return run_selftest_wait(ctx, kind, limit_ns);
 }
 
 extern "C" int dsa_probe_issue_rate(dsa_ctx* ctx, int form, double* rate) {

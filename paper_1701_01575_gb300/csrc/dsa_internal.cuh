@@ -165,11 +165,11 @@ int launch_interleave(dsa_ctx* ctx, dsa_db* db);
 
 // Packed 16-bit local kernels (all queries x all targets).
 //
-// A plan is a list of units; each unit is a run of strips (32 query rows)
+// A plan is a list of units; each unit is a run of strips (`rows` query rows)
 // whose low 16-bit half follows one stream of queries and whose high half
 // another.  Per strip, a StripMeta record names the query of each half and
 // the strip's index inside that query; the packed profile holds, per strip,
-// R residue rows x 32 query rows of int16x2 (S + o, padding = -16384).
+// R residue rows x `rows` query rows of int16x2 (S + o, padding = -16384).
 struct StripMeta {
   uint32_t qa, ka;   // low half: query id (NONE = no query), strip index in it | LAST bit
   uint32_t qb, kb;   // high half
@@ -183,8 +183,9 @@ struct PackedPlan {
   StripMeta* d_meta = nullptr;     // n_strips
   uint32_t* d_sbase = nullptr;     // first strip of each unit
   uint32_t* d_ns = nullptr;        // strips of each unit
-  uint32_t* d_prof = nullptr;      // n_strips x R x 32 words
+  uint32_t* d_prof = nullptr;      // n_strips x R x rows words
   int R = 0;                       // profile rows = A + 1 (last = padding)
+  int rows = 32;                   // query rows per strip
 };
 
 // Inter-sequence kernel work: items = (unit, first group of a block of 8).
@@ -208,7 +209,7 @@ int launch_inter_local16(dsa_ctx* ctx, const dsa_db* db, const PackedPlan& plan,
                          uint32_t n_targets_out);
 int inter_blocks_per_sm();
 constexpr int INTER_WARPS = 8;
-constexpr int INTER_ROWS = 32;
+constexpr int INTER_ROWS = 28;
 
 // Long-target intra-sequence (wavefront) kernel; each unit of `plan` must
 // hold one query per half (no stream switches).  Runs on `stream`
@@ -281,7 +282,8 @@ size_t long_cand_size();
 int long_band_rows();
 constexpr uint64_t LONG_PAIR_CELLS = 1ull << 22;   // explicit pairs at least this big run banded
 
-// Issue-rate probe.
+// Issue-rate probe; bounded-wait self-test.
 int run_issue_probe(dsa_ctx* ctx, int form, double* rate);
+int run_selftest_wait(dsa_ctx* ctx, int kind, uint64_t limit_ns);
 
 }  // namespace dsa

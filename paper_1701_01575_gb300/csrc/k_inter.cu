@@ -14,8 +14,8 @@
 //     runs over the target's residues; the strip's bottom row (H - o and the
 //     next row's F) goes to a per-CTA boundary buffer and is read back by the
 //     next strip;
-//   * the query profile of each strip (R residue rows x 32 query rows of
-//     int16x2 = R x 128 bytes) is staged into shared memory by TMA bulk copies,
+//   * the query profile of each strip (R residue rows x W query rows of
+//     int16x2 = R x 4W bytes) is staged into shared memory by TMA bulk copies,
 //     double-buffered on two mbarriers, in 8 replicas whose start addresses
 //     are rotated by 16 bytes so that the 8 lanes of each quarter-warp read
 //     8 different bank groups whatever residues they hold;
@@ -33,8 +33,10 @@
 // End cell (smallest target end j, then smallest query end i, among cells
 // holding the best score): the column maximum is compared with the running
 // best lowered by one while j is still below the best's column, so ties at an
-// earlier column also trigger; the rare trigger parks the column in shared
-// memory and scans it there for its first row holding the maximum.
+// earlier column also trigger.  A (rare) trigger only parks the column in its
+// half's area of shared memory; at the end of the strip the last parked
+// column of each improved half is scanned for its first row holding the
+// maximum.  No scan runs inside the column loop.
 //
 // Saturation: in local mode no value falls below -(o + e), and a value can
 // exceed the best seen so far by at most max(S), so if the best stays at or
@@ -79,9 +81,16 @@ struct InterArgs {
   int32_t* status;
 };
 
+// Bytes between profile replicas: at least one strip profile (R x W x 4 B),
+// a multiple of 16, and 16 (mod 128) so replica c starts in bank group c.
+__host__ __device__ __forceinline__ uint32_t replica_stride(int R) {
+  const uint32_t units = ((uint32_t)R * W * 4u + 15u) / 16u;
+  return ((units + 6u) / 8u * 8u + 1u) * 16u;
+}
+
 __device__ __forceinline__ void issue_strip(const InterArgs& A, uint8_t* buf, uint64_t* bar,
                                             const uint32_t* src, uint32_t cstride) {
-  const uint32_t bytes = (uint32_t)A.R * 128u;
+  const uint32_t bytes = (uint32_t)A.R * W * 4u;
   mbar_arrive_expect_tx(bar, bytes * NCOPY);
 #pragma unroll
   for (int c = 0; c < NCOPY; ++c) bulk_g2s(buf + c * cstride, src, bytes, bar);
@@ -94,11 +103,12 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const uint32_t cstride = (uint32_t)A.R * 128u + 16u;
+  const uint32_t cstride = replica_stride(A.R);
   const uint32_t bufbytes = NCOPY * cstride;
-  // column parking area for the end-cell search: [row][thread]
-  volatile uint32_t* const park = reinterpret_cast<volatile uint32_t*>(smem + 2 * bufbytes);
-  const uint32_t strip_words = (uint32_t)A.R * 32u;
+  // column parking areas for the end-cell search, one per half: [row][thread]
+  volatile uint32_t* const park_lo = reinterpret_cast<volatile uint32_t*>(smem + 2 * bufbytes);
+  volatile uint32_t* const park_hi = park_lo + W * NT;
+  const uint32_t strip_words = (uint32_t)A.R * W;
   const uint32_t neg_o2 = A.neg_o2, neg_e2 = A.neg_e2;
   const uint32_t NEG2 = pack2(NEG16, NEG16);
 
@@ -175,6 +185,7 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
       // passes its best's column.  The slow path repeats the exact test.
       uint32_t thr2 = 0;
       int flip = 0;
+      int pend = 0;   // bit 0 / 1: low / high half improved in this strip
       auto set_thr = [&](int jj) {
         const int tl = best_lo - (jj < bj_lo ? 1 : 0);
         const int th = best_hi - (jj < bj_hi ? 1 : 0);
@@ -207,7 +218,7 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const uint32_t a = (word >> (8 * k)) & 0xFFu;
-          const uint4* prow = reinterpret_cast<const uint4*>(pbuf + a * 128u);
+          const uint4* prow = reinterpret_cast<const uint4*>(pbuf + a * (W * 4u));
           uint32_t F = top[k].y;
           uint32_t d = diag;
           diag = top[k].x;
@@ -238,28 +249,37 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
             const int cl = lo16(cm), ch = hi16(cm);
             const int thr_lo = best_lo - (j < bj_lo ? 1 : 0);
             const int thr_hi = best_hi - (j < bj_hi ? 1 : 0);
-            // rare: park the column in shared memory and find its first row
-            // holding the maximum there, so the scan never competes with the
-            // DP state for registers
-#pragma unroll
-            for (int r = 0; r < W; ++r) park[r * NT + tid] = Ho[r];
+            // rare: a half improved.  Park the column in that half's area of
+            // shared memory; its first row holding the maximum is looked up
+            // once, at the end of the strip (a later trigger of the same half
+            // supersedes this one)
             if (cl > thr_lo) {
-              const int want = cl - A.o;
-              int rr = W - 1;
-              for (int r = W - 1; r >= 0; --r)
-                if (lo16(park[r * NT + tid]) == want) rr = r;
-              best_lo = cl; bj_lo = j; bi_lo = ia + rr + 1;
+#pragma unroll
+              for (int r = 0; r < W; ++r) park_lo[r * NT + tid] = Ho[r];
+              best_lo = cl; bj_lo = j; pend |= 1;
             }
             if (ch > thr_hi) {
-              const int want = ch - A.o;
-              int rr = W - 1;
-              for (int r = W - 1; r >= 0; --r)
-                if (hi16(park[r * NT + tid]) == want) rr = r;
-              best_hi = ch; bj_hi = j; bi_hi = ib + rr + 1;
+#pragma unroll
+              for (int r = 0; r < W; ++r) park_hi[r * NT + tid] = Ho[r];
+              best_hi = ch; bj_hi = j; pend |= 2;
             }
             set_thr(j + 1);
           }
         }
+      }
+      if (pend & 1) {   // first row of the last improving column, low half
+        const int want = best_lo - A.o;
+        int rr = W - 1;
+        for (int r = W - 1; r >= 0; --r)
+          if (lo16(park_lo[r * NT + tid]) == want) rr = r;
+        bi_lo = ia + rr + 1;
+      }
+      if (pend & 2) {
+        const int want = best_hi - A.o;
+        int rr = W - 1;
+        for (int r = W - 1; r >= 0; --r)
+          if (hi16(park_hi[r * NT + tid]) == want) rr = r;
+        bi_hi = ib + rr + 1;
       }
       if (tvalid) {   // queries that end in this strip: write their results
         const uint32_t orig = A.perm[st];
@@ -289,28 +309,28 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
 }
 
 // Packed profile of every strip: [strip][residue a][row r] int16x2 =
-// (S[qa_i][a] + o, S[qb_i][a] + o) with i = 32 * (strip index in the query) + r;
+// (S[qa_i][a] + o, S[qb_i][a] + o) with i = rows * (strip index in the query) + r;
 // rows past a query's end, absent queries and the padding residue a = A get
 // NEG16.
 __global__ void k_strip_profile(const uint8_t* __restrict__ qcodes,
                                 const uint64_t* __restrict__ qoff, const uint32_t* __restrict__ qlen,
                                 const StripMeta* __restrict__ meta, uint32_t n_strips,
-                                const int8_t* __restrict__ S, int A, int R, int o,
+                                const int8_t* __restrict__ S, int A, int R, int rows, int o,
                                 uint32_t* __restrict__ prof) {
-  const uint64_t total = (uint64_t)n_strips * R * 32;
+  const uint64_t total = (uint64_t)n_strips * R * rows;
   for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < total;
        x += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t s = (uint32_t)(x / ((uint64_t)R * 32));
-    const int a = (int)((x / 32) % (uint64_t)R);
-    const int r = (int)(x % 32);
+    const uint32_t s = (uint32_t)(x / ((uint64_t)R * rows));
+    const int a = (int)((x / rows) % (uint64_t)R);
+    const int r = (int)(x % rows);
     const StripMeta md = meta[s];
     int lo = NEG16, hi = NEG16;
     if (a < A && md.qa != NONE) {
-      const int i = (int)(md.ka & ~LAST) * 32 + r;
+      const int i = (int)(md.ka & ~LAST) * rows + r;
       if (i < (int)qlen[md.qa]) lo = (int)S[qcodes[qoff[md.qa] + i] * A + a] + o;
     }
     if (a < A && md.qb != NONE) {
-      const int i = (int)(md.kb & ~LAST) * 32 + r;
+      const int i = (int)(md.kb & ~LAST) * rows + r;
       if (i < (int)qlen[md.qb]) hi = (int)S[qcodes[qoff[md.qb] + i] * A + a] + o;
     }
     prof[x] = pack2(lo, hi);
@@ -324,11 +344,11 @@ int inter_blocks_per_sm() { return 2; }
 int launch_strip_profile(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix, int A, int o,
                          const PackedPlan& plan) {
   if (plan.n_strips == 0) return DSA_OK;
-  const uint64_t total = (uint64_t)plan.n_strips * plan.R * 32;
+  const uint64_t total = (uint64_t)plan.n_strips * plan.R * plan.rows;
   uint64_t blocks = std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->sm_count * 8);
   k_strip_profile<<<(unsigned)blocks, 256, 0, ctx->stream>>>(qs->d_codes, qs->d_off, qs->d_len,
                                                             plan.d_meta, plan.n_strips, d_matrix,
-                                                            A, plan.R, o, plan.d_prof);
+                                                            A, plan.R, plan.rows, o, plan.d_prof);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   return DSA_OK;
@@ -359,12 +379,12 @@ int launch_inter_local16(dsa_ctx* ctx, const dsa_db* db, const PackedPlan& plan,
   A.o_score = out.score; A.o_qend = out.q_end; A.o_tend = out.t_end; A.o_flag = out.flag;
   A.n_out_t = n_targets_out;
   A.status = ctx->d_status;
-  const size_t smem = 2ull * NCOPY * ((size_t)plan.R * 128 + 16) + (size_t)W * NT * sizeof(uint32_t);
-  static bool attr_set = false;
-  if (!attr_set) {
+  const size_t smem = 2ull * NCOPY * replica_stride(plan.R) + 2ull * W * NT * sizeof(uint32_t);
+  static size_t attr_bytes = 0;   // largest dynamic shared memory requested so far
+  if (smem > attr_bytes) {
     DSA_CUDA_TRY(cudaFuncSetAttribute(k_inter_local16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      110 * 1024));
-    attr_set = true;
+                                      (int)smem));
+    attr_bytes = smem;
   }
   DSA_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), ctx->stream));
   k_inter_local16<<<grid, NT, smem, ctx->stream>>>(A);

@@ -56,14 +56,6 @@ __device__ __forceinline__ bool cand_better(const Cand& a, const Cand& b) {
   return a.i < b.i;
 }
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 __global__ void __launch_bounds__(WARPS * 32) k_long_score(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
@@ -131,7 +123,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
           if (seen < (uint32_t)j && !timed_out) {
             const uint64_t t0 = global_ns();
             for (;;) {
-              seen = ld_acquire(up_prog);
+              seen = ld_acquire_u32(up_prog);
               if (seen >= (uint32_t)j) break;
               if (global_ns() - t0 > WAIT_LIMIT_NS) {
                 timed_out = true;
@@ -174,7 +166,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
           my_bnd[j - 1] = make_int2(Hp, F);
           if ((uint32_t)j % PUBLISH == 0 || j == n) {
             __threadfence();
-            st_release(my_prog, (uint32_t)j);
+            st_release_u32(my_prog, (uint32_t)j);
           }
         }
       }

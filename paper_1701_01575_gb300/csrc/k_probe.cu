@@ -94,7 +94,60 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_cell(uint32_t neg_o2, u
   if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// Self-test of the bounded waits: a wait that nothing will ever satisfy must
+// give up after `limit_ns`, record DSA_ERR_DEVICE_TIMEOUT in the status word
+// and let the kernel return normally.
+//   kind 0: an mbarrier whose transaction count is never met (no copy issued);
+//   kind 1: a progress flag that no producer ever publishes.
+__global__ void k_selftest_wait(int kind, uint64_t limit_ns, uint32_t* flag, int32_t* status) {
+  __shared__ uint64_t bar;
+  if (kind == 0) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 16);   // no copy will complete it
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(status, DSA_ERR_DEVICE_TIMEOUT);
+      return;   // no copy of this CTA is in flight
+    }
+  } else {
+    if (threadIdx.x == 0) {
+      const uint64_t t0 = global_ns();
+      while (ld_acquire_u32(flag) == 0) {
+        if (global_ns() - t0 > limit_ns) {
+          atomicExch(status, DSA_ERR_DEVICE_TIMEOUT);
+          break;
+        }
+      }
+    }
+  }
+}
+
 }  // namespace
+
+int run_selftest_wait(dsa_ctx* ctx, int kind, uint64_t limit_ns) {
+  if (kind < 0 || kind > 1 || limit_ns > 10000000000ull) {
+    set_error("self-test: kind must be 0 or 1 and the limit at most 10 s");
+    return DSA_ERR_INVALID_ARG;
+  }
+  void* flag = nullptr;
+  DSA_TRY(ctx->alloc(&flag, sizeof(uint32_t)));
+  DSA_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(uint32_t), ctx->stream));
+  k_selftest_wait<<<1, 64, 0, ctx->stream>>>(kind, limit_ns, static_cast<uint32_t*>(flag),
+                                              ctx->d_status);
+  ++ctx->launches;
+  cudaError_t err = cudaGetLastError();
+  ctx->release(flag, sizeof(uint32_t));
+  if (err != cudaSuccess) {
+    set_error("self-test launch: %s", cudaGetErrorString(err));
+    return DSA_ERR_CUDA;
+  }
+  return DSA_OK;
+}
 
 int run_issue_probe(dsa_ctx* ctx, int form, double* rate) {
   if (form < 0 || form > 7) {

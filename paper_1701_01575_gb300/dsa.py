@@ -39,7 +39,8 @@ SYMBOLS = ["dsa_create", "dsa_destroy", "dsa_last_error", "dsa_mem_in_use", "dsa
            "dsa_res_get", "dsa_res_stats", "dsa_res_free", "dsa_sync", "dsa_probe_issue_rate",
            "dsa_res_timing", "dsa_kernel_launches", "dsa_score_pairs_noalloc",
            "dsa_res_phase_cells", "dsa_server_create", "dsa_submit", "dsa_poll",
-           "dsa_server_drain", "dsa_server_now", "dsa_server_destroy"]
+           "dsa_server_drain", "dsa_server_now", "dsa_server_destroy",
+           "dsa_selftest_wait_timeout"]
 REQ_SEARCH, REQ_PAIRS = 0, 1
 
 
@@ -115,6 +116,7 @@ def load_library(path: str = LIB_PATH):
     lib.dsa_server_now.argtypes = [_vp]
     lib.dsa_server_now.restype = ctypes.c_double
     lib.dsa_server_destroy.argtypes = [_vp]
+    lib.dsa_selftest_wait_timeout.argtypes = [_vp, ctypes.c_int, ctypes.c_uint64]
     lib.dsa_kernel_launches.restype = ctypes.c_uint64
     lib.dsa_score_pairs_noalloc.argtypes = [_vp, _vp, _u32, _vp, _vp, _u32, _vp, _u64, ctypes.c_int,
                                             _u32, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -329,6 +331,11 @@ class Context:
 
     def sync(self):
         _check(_lib.dsa_sync(self.handle))
+
+    def selftest_wait_timeout(self, kind: int, limit_ns: int) -> int:
+        """Run the bounded-wait self-test; returns dsa_sync's status (expected ERR_DEVICE_TIMEOUT)."""
+        _check(_lib.dsa_selftest_wait_timeout(self.handle, kind, limit_ns))
+        return _lib.dsa_sync(self.handle)
 
     def probe_issue_rate(self, form: int) -> float:
         r = ctypes.c_double()

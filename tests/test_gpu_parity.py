@@ -64,7 +64,7 @@ def test_protein_search_small(ctx):
     """Odd query count, lengths across strip boundaries, many groups, ragged tails."""
     rng = np.random.default_rng(11)
     bg = W.protein_background()
-    qlens = np.array([1, 31, 32, 33, 64, 65, 200, 517, 95])
+    qlens = np.array([1, 27, 28, 29, 31, 32, 33, 56, 57, 64, 65, 200, 517, 95])
     queries = W._make_set(rng, qlens, bg)
     tl = np.concatenate([rng.integers(1, 40, 300), rng.integers(40, 700, 2500),
                          [1, 15, 16, 17, 2000, 1999]])
@@ -361,3 +361,21 @@ def test_long_and_short_pairs_mixed(ctx):
         h = r.hits()
         assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), f"mixed mode={mode}")
         check_traceback(h, r.cigar(), qs, db, S, 5, 2, mode, 15)
+
+
+# ---------------------------------------------------------------- failure path
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_bounded_wait_gives_up_and_context_survives(ctx, kind):
+    """A wait nothing satisfies ends after its limit with DSA_ERR_DEVICE_TIMEOUT; no fault."""
+    import time
+    t0 = time.time()
+    st = ctx.selftest_wait_timeout(kind, 200_000_000)   # 0.2 s
+    assert st == dsa.ERR_DEVICE_TIMEOUT
+    assert time.time() - t0 < 5
+    ctx.sync()   # status cleared
+    # the context still aligns correctly
+    wl = W.protein_vs_db(n_targets=100)
+    g = gpu_all(ctx, wl.queries, wl.db, wl.matrix, 11, 1)
+    orc = oracle_all(wl.queries, wl.db, wl.matrix, 11, 1)
+    assert_same(g[:3], orc, "after timeout")
