@@ -178,23 +178,14 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
       uint32_t diag = neg_o2;
       uint2* scr = scr_base;
       uint4 rv = make_uint4(0, 0, 0, 0);
-      // Packed trigger threshold per half, tested as cm > thr: thr = best once the
-      // column has passed the best's column (only strictly better cells
-      // count), best - 1 while it is still before it (an equal cell at a
-      // smaller column wins); `flip` is the next column at which a half
-      // passes its best's column.  The slow path repeats the exact test.
+      // Packed trigger threshold per half, tested as cm > thr with
+      // thr = max(best - 1, 0): every column whose maximum reaches the best
+      // (or is the first positive one) triggers; the exact rule (strictly
+      // better, or equal at a smaller column) is applied in the trigger path.
       uint32_t thr2 = 0;
-      int flip = 0;
+      auto set_thr = [&]() { thr2 = pack2(max(best_lo - 1, 0), max(best_hi - 1, 0)); };
+      set_thr();
       int pend = 0;   // bit 0 / 1: low / high half improved in this strip
-      auto set_thr = [&](int jj) {
-        const int tl = best_lo - (jj < bj_lo ? 1 : 0);
-        const int th = best_hi - (jj < bj_hi ? 1 : 0);
-        thr2 = pack2(tl, th);
-        flip = 0x7FFFFFFF;
-        if (bj_lo > jj) flip = bj_lo;
-        if (bj_hi > jj && bj_hi < flip) flip = bj_hi;
-      };
-      set_thr(1);
 
       for (uint32_t c4 = 0; c4 < ncol; c4 += 4) {
         if ((c4 & 15u) == 0) rv = __ldg(res + (c4 >> 4) * 32u);
@@ -244,7 +235,6 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
           scr[(uint64_t)(c4 + k) * NT] = make_uint2(Ho[W - 1], F);
           // end-cell tracking for column j: trigger when cm > thr (per half)
           const int j = (int)c4 + k + 1;
-          if (j == flip) set_thr(j);
           if (__vmaxs2(cm, thr2) != thr2) {   // some half has cm > thr
             const int cl = lo16(cm), ch = hi16(cm);
             const int thr_lo = best_lo - (j < bj_lo ? 1 : 0);
@@ -263,7 +253,7 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
               for (int r = 0; r < W; ++r) park_hi[r * NT + tid] = Ho[r];
               best_hi = ch; bj_hi = j; pend |= 2;
             }
-            set_thr(j + 1);
+            set_thr();
           }
         }
       }
