@@ -733,13 +733,25 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
     std::vector<PairJob> jobs;
     jobs.reserve(n_pairs);
     std::vector<LongJob> ljobs;
-    uint64_t scr = 0, cells = 0, lcells = 0;
+    std::vector<uint64_t> p16;   // pairs for the packed int16 kernel
+    uint64_t scr = 0, cells = 0, lcells = 0, p16cells = 0;
     uint64_t bnd = 0, prog = 0, cand = 0;
     const int band = long_band_rows();
+    // int16 eligibility: local with the saturation flag, or any mode whose
+    // scores provably stay inside int16: (m + n) * w + o well below 2^14
+    const int64_t w16 = std::max<int64_t>({(int64_t)std::abs(v.smax), (int64_t)std::abs(v.smin), o, e});
+    const bool local16 = mode == DSA_LOCAL && o >= 1 && o + e <= 4096 && v.smax + o < 8192 && v.smin > -8192;
+    const bool packed_ok = !(flags & (DSA_FORCE_INT32 | DSA_PLAIN_FORM));
     for (uint64_t k = 0; k < n_pairs; ++k) {
       const dsa_pair& p = hp[k];
       const uint64_t m = qs->h_len[p.query_id];
       cells += m * p.t_len;
+      const bool fits16 = local16 || ((int64_t)(m + p.t_len) * w16 + o < 12000 && o + e < 4096);
+      if (packed_ok && fits16 && m >= 1 && p.t_len >= 1 && m * p.t_len < LONG_PAIR_CELLS) {
+        p16.push_back(k);
+        p16cells += m * p.t_len;
+        continue;
+      }
       if (m * p.t_len >= LONG_PAIR_CELLS) {
         const uint64_t nb = (m + band - 1) / band;
         LongJob lj{qs->h_off[p.query_id], db->h_off[p.target_id] + p.t_offset, bnd, prog, cand,
@@ -797,6 +809,82 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
       res->phase_cells[PH_INTRA] = lcells;
       res->phase_cells[PH_INT32] = cells - lcells;
     }
+    if (!p16.empty()) {
+      // sort by (query length, window length); two pairs of equal query length per thread
+      std::stable_sort(p16.begin(), p16.end(), [&](uint64_t a, uint64_t b) {
+        const uint32_t ma = qs->h_len[hp[a].query_id], mb = qs->h_len[hp[b].query_id];
+        if (ma != mb) return ma < mb;
+        return hp[a].t_len < hp[b].t_len;
+      });
+      std::vector<Pair16Job> pj;
+      pj.reserve(p16.size() / 2 + 1);
+      uint32_t max_n = 1;
+      for (size_t x = 0; x < p16.size();) {
+        const dsa_pair& a = hp[p16[x]];
+        Pair16Job j{};
+        j.m = (int32_t)qs->h_len[a.query_id];
+        j.q_lo = qs->h_off[a.query_id];
+        j.t_lo = db->h_off[a.target_id] + a.t_offset;
+        j.n_lo = (int32_t)a.t_len;
+        j.out_lo = (uint32_t)p16[x];
+        max_n = std::max(max_n, a.t_len);
+        if (x + 1 < p16.size() && qs->h_len[hp[p16[x + 1]].query_id] == (uint32_t)j.m) {
+          const dsa_pair& b = hp[p16[x + 1]];
+          j.q_hi = qs->h_off[b.query_id];
+          j.t_hi = db->h_off[b.target_id] + b.t_offset;
+          j.n_hi = (int32_t)b.t_len;
+          j.out_hi = (uint32_t)p16[x + 1];
+          max_n = std::max(max_n, b.t_len);
+          x += 2;
+        } else {
+          j.q_hi = j.q_lo;
+          j.t_hi = j.t_lo;
+          j.n_hi = 0;
+          j.out_hi = NONE;
+          x += 1;
+        }
+        pj.push_back(j);
+      }
+      DevBuf d_pj;
+      if ((rc = upload(ctx, d_pj, pj))) return fail(rc);
+      phase_begin(res, PH_INTER);
+      if ((rc = launch_pairs16(ctx, db, qs, d_mat.as<int8_t>(), A, o, e, mode, fe, v.smax,
+                               d_pj.as<Pair16Job>(), (uint32_t)pj.size(), max_n, sc)))
+        return fail(rc);
+      phase_end(res, PH_INTER);
+      res->phase_cells[PH_INTER] = p16cells;
+      res->phase_cells[PH_INT32] -= p16cells;
+      if (mode == DSA_LOCAL) {
+        // exact int32 rerun of pairs whose packed pass saturated
+        const uint32_t cap = (uint32_t)std::min<uint64_t>(n_pairs, 1u << 22);
+        DevBuf d_list;
+        if ((rc = d_list.alloc(ctx, (size_t)cap * sizeof(uint32_t)))) return fail(rc);
+        uint32_t* d_count = ctx->d_counters + 1;
+        if (cudaMemsetAsync(d_count, 0, sizeof(uint32_t), ctx->stream) != cudaSuccess) return fail(DSA_ERR_CUDA);
+        const uint64_t blk = std::min<uint64_t>((n_pairs + 255) / 256, (uint64_t)ctx->sm_count * 16);
+        k_collect_flags<<<(unsigned)blk, 256, 0, ctx->stream>>>(sc.flag, n_pairs, d_list.as<uint32_t>(),
+                                                                 cap, d_count);
+        ++ctx->launches;
+        uint32_t count = 0;
+        if (cudaMemcpyAsync(&count, d_count, sizeof(count), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+          set_error("rerun count: %s", cudaGetErrorString(cudaGetLastError()));
+          return fail(DSA_ERR_CUDA);
+        }
+        res->n_rerun = count;
+        if (count > cap) { set_error("too many saturated pairs (%u)", count); return fail(DSA_ERR_UNSUPPORTED); }
+        if (count) {
+          std::vector<uint32_t> list(count);
+          if (cudaMemcpy(list.data(), d_list.p, count * sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(DSA_ERR_CUDA);
+          for (uint32_t k : list) {
+            const dsa_pair& p = hp[k];
+            jobs.push_back({db->h_off[p.target_id] + p.t_offset, scr, p.query_id, p.t_len, k, 1});
+            scr += p.t_len;
+          }
+        }
+      }
+    }
     const uint64_t n_short = jobs.size();
     std::vector<uint64_t> poff(qs->n);
     uint64_t pw = 0;
@@ -808,8 +896,8 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
     if ((rc = d_prof.alloc(ctx, pw * 4)) || (rc = upload(ctx, d_poff, poff)) ||
         (rc = upload(ctx, d_jobs, jobs)) || (rc = d_scr.alloc(ctx, scr * sizeof(int2))))
       return fail(rc);
-    if ((rc = launch_profile_int32(ctx, qs, d_mat.as<int8_t>(), A, d_prof.as<int32_t>(),
-                                   d_poff.as<uint64_t>())))
+    if (n_short && (rc = launch_profile_int32(ctx, qs, d_mat.as<int8_t>(), A, d_prof.as<int32_t>(),
+                                              d_poff.as<uint64_t>())))
       return fail(rc);
     phase_begin(res, PH_INT32);
     if ((rc = launch_generic_int32(ctx, db, qs, d_prof.as<int32_t>(), d_poff.as<uint64_t>(),

@@ -138,7 +138,7 @@ struct PairJob {
   uint32_t q;         // query index
   uint32_t n;         // target window length
   uint32_t out;       // output slot
-  uint32_t pad;
+  uint32_t pad;       // 1: rerun of a saturated packed result (sets the hit's rerun flag)
 };
 
 struct Scores {      // structure-of-arrays output of the score pass
@@ -281,6 +281,19 @@ int launch_long_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
 size_t long_cand_size();
 int long_band_rows();
 constexpr uint64_t LONG_PAIR_CELLS = 1ull << 22;   // explicit pairs at least this big run banded
+
+// Packed int16x2 kernel for explicit short pairs: two pairs of equal query
+// length per thread.  q_* / t_* are absolute offsets of the query and of the
+// target window; out_hi = NONE when the high half is empty.
+struct Pair16Job {
+  uint64_t q_lo, q_hi, t_lo, t_hi;
+  int32_t m, n_lo, n_hi;
+  uint32_t out_lo, out_hi;
+  uint32_t pad;
+};
+int launch_pairs16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix, int A,
+                   int o, int e, int mode, uint32_t fe, int smax, const Pair16Job* d_jobs,
+                   uint32_t n_jobs, uint32_t max_n, Scores out);
 
 // Issue-rate probe; bounded-wait self-test.
 int run_issue_probe(dsa_ctx* ctx, int form, double* rate);

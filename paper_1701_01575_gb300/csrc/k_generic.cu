@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(128) k_generic_int32(
       job.q = fixed_q;
       job.n = t_len[jid];
       job.out = (uint32_t)((uint64_t)fixed_q * n_t + jid);
+      job.pad = 0;
     }
     const int32_t m = (int32_t)qlen[job.q];
     const int32_t n = (int32_t)job.n;
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(128) k_generic_int32(
     } else {
       o_score[out] = b.s; o_qend[out] = b.i - 1; o_tend[out] = b.j - 1;
     }
-    o_flag[out] = flag_value;
+    o_flag[out] = flag_value | (uint8_t)job.pad;   // pad = 1 marks a saturation rerun
   }
 }
 

@@ -379,3 +379,91 @@ def test_bounded_wait_gives_up_and_context_survives(ctx, kind):
     g = gpu_all(ctx, wl.queries, wl.db, wl.matrix, 11, 1)
     orc = oracle_all(wl.queries, wl.db, wl.matrix, 11, 1)
     assert_same(g[:3], orc, "after timeout")
+
+
+# ---------------------------------------------------------------- packed explicit pairs
+
+def _pairs_case(rng, qs, db, n, vary_len=True):
+    pairs = np.zeros(n, dtype=W.PAIR_DTYPE)
+    pairs["query_id"] = rng.integers(0, qs.n, n)
+    pairs["target_id"] = rng.integers(0, db.n, n)
+    tl = db.lengths[pairs["target_id"].astype(np.int64)]
+    off = (rng.random(n) * (tl // 3)).astype(np.int64) if vary_len else np.zeros(n, np.int64)
+    pairs["t_offset"] = off
+    ln = tl - off
+    if vary_len:
+        ln = np.maximum(1, ln - (rng.random(n) * ln // 3).astype(np.int64))
+    pairs["t_len"] = ln
+    return pairs
+
+
+@pytest.mark.parametrize("mode,fe", [(dsa.LOCAL, 15), (dsa.GLOBAL, 15), (dsa.SEMIGLOBAL, 15),
+                                     (dsa.SEMIGLOBAL, 12), (dsa.SEMIGLOBAL, 3), (dsa.SEMIGLOBAL, 9)])
+def test_packed_pairs_all_modes(ctx, mode, fe):
+    """Two pairs of equal query length per thread; odd counts, uneven windows, ties."""
+    rng = np.random.default_rng(500 + mode * 16 + fe)
+    S = W.dna_matrix(2, -3)
+    qs = W.SeqSet.from_list([rng.integers(0, 4, n).astype(np.uint8)
+                             for n in np.concatenate([rng.integers(1, 60, 30), [15, 16, 17, 31, 32, 33]])])
+    db = W.random_dna(rng, 40, 20, 300)
+    pairs = _pairs_case(rng, qs, db, 901)
+    sc, qe, te = oracle.score_pairs(qs.codes, qs.offsets, db.codes, db.offsets, pairs["query_id"],
+                                    pairs["target_id"], S, 5, 2, mode, fe, pair_toff=pairs["t_offset"],
+                                    pair_tlen=pairs["t_len"])
+    d = ctx.load_set(db, 4)
+    q = ctx.load_set(qs, 4)
+    r = ctx.align(d, q, S, 5, 2, mode=mode, free_ends=fe, pairs=pairs)
+    ctx.sync()
+    h = r.hits()
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), f"packed pairs mode={mode} fe={fe}")
+    assert r.phase_cells()["inter16"] > 0
+    if mode != dsa.LOCAL:
+        ctx.traceback(r)
+        check_traceback(r.hits()[:200], r.cigar(), qs, db, S, 5, 2, mode, fe)
+
+
+def test_packed_pairs_protein_local(ctx):
+    rng = np.random.default_rng(42)
+    bg = W.protein_background()
+    qs = W.SeqSet.from_list([rng.choice(20, n, p=bg).astype(np.uint8) for n in rng.integers(1, 300, 20)])
+    db = W.SeqSet.from_list([rng.choice(20, n, p=bg).astype(np.uint8) for n in rng.integers(10, 600, 30)])
+    pairs = _pairs_case(rng, qs, db, 500)
+    S = W.blosum62()
+    sc, qe, te = oracle.score_pairs(qs.codes, qs.offsets, db.codes, db.offsets, pairs["query_id"],
+                                    pairs["target_id"], S, 11, 1, oracle.LOCAL, 15,
+                                    pair_toff=pairs["t_offset"], pair_tlen=pairs["t_len"])
+    d = ctx.load_set(db, 24)
+    q = ctx.load_set(qs, 24)
+    r = ctx.align(d, q, S, 11, 1, pairs=pairs)
+    ctx.sync()
+    h = r.hits()
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), "protein pairs")
+    assert r.phase_cells()["inter16"] > 0
+
+
+def test_packed_pairs_saturation_rerun(ctx):
+    """Local pairs whose best passes 32767 - max S are flagged and rerun in int32."""
+    rng = np.random.default_rng(43)
+    S = W.dna_matrix(100, -90)
+    run = np.zeros(400, np.uint8)
+    qs = W.SeqSet.from_list([run, run[:380], rng.integers(0, 4, 380).astype(np.uint8)]
+                            + [rng.integers(0, 4, n).astype(np.uint8) for n in rng.integers(1, 200, 10)])
+    db = W.SeqSet.from_list([np.concatenate([rng.integers(0, 4, 50).astype(np.uint8), run, run[:7]]),
+                             rng.integers(0, 4, 900).astype(np.uint8)])
+    pairs = np.zeros(40, dtype=W.PAIR_DTYPE)
+    pairs["query_id"] = np.concatenate([[0, 1, 2], rng.integers(0, qs.n, 37)])
+    pairs["target_id"] = np.concatenate([[0, 0, 1], rng.integers(0, 2, 37)])
+    pairs["t_offset"] = 0
+    pairs["t_len"] = db.lengths[pairs["target_id"].astype(np.int64)]
+    sc, qe, te = oracle.score_pairs(qs.codes, qs.offsets, db.codes, db.offsets, pairs["query_id"],
+                                    pairs["target_id"], S, 50, 5, oracle.LOCAL, 15,
+                                    pair_toff=pairs["t_offset"], pair_tlen=pairs["t_len"])
+    d = ctx.load_set(db, 4)
+    q = ctx.load_set(qs, 4)
+    r = ctx.align(d, q, S, 50, 5, pairs=pairs)
+    ctx.sync()
+    h = r.hits()
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), "saturating pairs")
+    assert h["score"][0] == 40000 and (h["flags"][0] & dsa.HIT_RERUN_INT32)
+    assert not (h["flags"][2] & dsa.HIT_RERUN_INT32)
+    assert r.stats()[1] >= 2
