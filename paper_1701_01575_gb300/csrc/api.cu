@@ -1012,9 +1012,15 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
   const dsa_db* db = res->db;
   const dsa_db* qs = res->queries;
   std::vector<TbJob> jobs;
+  jobs.reserve(sel.size());
   std::vector<LongTbJob> ljobs;
   uint64_t cap_total = 0;
   const int band = long_band_rows();
+  // exact column band for a free target begin (see k_traceback.cu); needs e > 0
+  int smax_pos = 0;
+  for (int8_t v : res->matrix) smax_pos = std::max<int>(smax_pos, v);
+  const bool band_ok = res->mode == DSA_SEMIGLOBAL && (res->free_ends & DSA_FREE_T_BEGIN) &&
+                       res->gap_extend > 0;
   for (uint64_t h : sel) {
     const dsa_hit& hit = res->h_hits[h];
     if (hit.flags & DSA_HIT_HAS_TRACEBACK) continue;
@@ -1037,9 +1043,20 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
     j.ie = hit.q_end + 1;
     j.je = hit.t_end + 1;
     j.hit = (uint32_t)h;
-    j.wpr = (uint32_t)((j.je + 7) / 8);
     j.q_start = qs->h_off[hit.query_id];
     j.t_start = db->h_off[hit.target_id] + hit.t_offset;
+    if (band_ok) {
+      // deletions on any path reaching the hit: score <= ie * max(S, 0) - (o + (k - 1) e)
+      const int64_t slack = (int64_t)j.ie * smax_pos - hit.score;
+      const int64_t kmax = slack < res->gap_open ? 0 : (slack - res->gap_open) / res->gap_extend + 1;
+      const int64_t jlo = (int64_t)j.je - j.ie - kmax;
+      if (jlo > 0) {
+        j.jlo = (int32_t)jlo;
+        j.t_start += (uint64_t)jlo;
+        j.je -= (int32_t)jlo;
+      }
+    }
+    j.wpr = (uint32_t)((j.je + 7) / 8);
     jobs.push_back(j);
     cap_total += (uint64_t)j.ie + j.je + 1;
   }
@@ -1066,6 +1083,94 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
   // chunks bounded by direction-matrix memory
   const uint64_t dir_limit = 1ull << 30;   // words (4 GiB)
   phase_begin(res, PH_TRACE);
+
+  // Many small rectangles: one thread per hit (groups of 32 hits of similar
+  // size share an interleaved decision layout).  Few or large ones: one warp
+  // per hit.
+  uint64_t thread_min = 16384;
+  if (const char* env = getenv("DSA_TB_THREAD_MIN")) thread_min = strtoull(env, nullptr, 10);
+  std::vector<TbJob> tjobs;
+  {
+    auto small = [](const TbJob& j) { return j.ie <= 4096 && (uint64_t)j.ie * j.je <= (1u << 20); };
+    const uint64_t n_small = (uint64_t)std::count_if(jobs.begin(), jobs.end(), small);
+    if (n_small >= std::max<uint64_t>(thread_min, 1)) {
+      // counting sort by (ie desc, je desc): groups of 32 hits of similar size
+      std::vector<TbJob> rest;
+      rest.reserve(jobs.size() - n_small);
+      std::vector<uint32_t> idx, tmp;
+      idx.reserve(n_small);
+      int32_t je_max = 0;
+      for (uint32_t x = 0; x < jobs.size(); ++x) {
+        if (small(jobs[x])) {
+          idx.push_back(x);
+          je_max = std::max(je_max, jobs[x].je);
+        } else {
+          rest.push_back(jobs[x]);
+        }
+      }
+      tmp.resize(idx.size());
+      auto pass = [&](auto key, int32_t kmax) {
+        std::vector<uint32_t> cnt((size_t)kmax + 2, 0);
+        for (uint32_t x : idx) ++cnt[kmax - key(jobs[x]) + 1];
+        for (size_t b = 1; b < cnt.size(); ++b) cnt[b] += cnt[b - 1];
+        for (uint32_t x : idx) tmp[cnt[kmax - key(jobs[x])]++] = x;
+        idx.swap(tmp);
+      };
+      pass([](const TbJob& j) { return j.je; }, je_max);
+      pass([](const TbJob& j) { return j.ie; }, 4096);
+      tjobs.resize(idx.size());
+      for (size_t x = 0; x < idx.size(); ++x) tjobs[x] = jobs[idx[x]];
+      jobs.swap(rest);
+    }
+  }
+  if (!tjobs.empty()) {
+    size_t k0 = 0;
+    while (k0 < tjobs.size()) {
+      uint64_t dir = 0, cig = 0, scr = 0;
+      size_t k1 = k0;
+      while (k1 < tjobs.size()) {
+        const size_t g1 = std::min(tjobs.size(), k1 + 32);
+        int32_t ie_max = 1, je_max = 1;
+        for (size_t x = k1; x < g1; ++x) {
+          ie_max = std::max(ie_max, tjobs[x].ie);
+          je_max = std::max(je_max, tjobs[x].je);
+        }
+        const uint64_t strips = ((uint64_t)ie_max + 15) / 16;
+        const uint64_t w = strips * (uint64_t)je_max * 64;
+        if (k1 > k0 && dir + w > dir_limit) break;
+        for (size_t x = k1; x < g1; ++x) {
+          const uint32_t lane = (uint32_t)(x - k1);
+          tjobs[x].dir_off = dir + lane;
+          tjobs[x].wpr = (uint32_t)je_max;
+          tjobs[x].scr_off = scr + lane;
+          tjobs[x].cig_off = cig;
+          cig += (uint64_t)tjobs[x].ie + tjobs[x].je + 1;
+        }
+        dir += w;
+        scr += (uint64_t)je_max * 32;
+        k1 = g1;
+      }
+      std::vector<TbJob> chunk(tjobs.begin() + k0, tjobs.begin() + k1);
+      DevBuf d_jobs, d_dir, d_cig, d_scr;
+      DSA_TRY(upload(ctx, d_jobs, chunk));
+      DSA_TRY(d_dir.alloc(ctx, dir * 4));
+      DSA_TRY(d_cig.alloc(ctx, cig * 4));
+      DSA_TRY(d_scr.alloc(ctx, scr * sizeof(int2)));
+      DSA_TRY(launch_traceback_thread(ctx, db, qs, d_mat.as<int8_t>(), res->A, res->gap_open,
+                                      res->gap_extend, res->mode, res->free_ends,
+                                      d_jobs.as<TbJob>(), (uint32_t)chunk.size(),
+                                      d_dir.as<uint32_t>(), d_cig.as<uint32_t>(), d_scr.as<int2>(),
+                                      res->d_hits));
+      DSA_TRY(launch_cigar_compact(ctx, res->d_hits, d_jobs.as<TbJob>(), (uint32_t)chunk.size(),
+                                   d_cig.as<uint32_t>(), res->d_cigar, total,
+                                   d_total.as<uint64_t>()));
+      DSA_CUDA_TRY(cudaMemcpyAsync(&total, d_total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+      DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      k0 = k1;
+    }
+  }
+
   size_t k0 = 0;
   while (k0 < jobs.size()) {
     uint64_t dir = 0, cig = 0, scr = 0;

@@ -236,6 +236,9 @@ struct TbJob {
   int32_t ie, je;     // 1-based result cell (rectangle to recompute)
   uint32_t hit;       // hit index
   uint32_t wpr;       // direction words per row
+  int32_t jlo;        // first target column of the recomputed band (0 = whole rectangle);
+                      // > 0: column jlo is a wall (H = -inf below row 0)
+  uint32_t pad;
 };
 int launch_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,
                      int A, int o, int e, int mode, uint32_t fe, const TbJob* d_jobs,
@@ -243,6 +246,12 @@ int launch_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int
                      dsa_hit* d_hits);
 // Reverse each job's CIGAR words into `d_cigar` starting at `base`, packed in
 // job order; total words written are added to *d_total.
+// One thread per hit; TbJob.dir_off = group base + lane, .wpr = the group's
+// column count, .scr_off = group scratch base + lane (layouts interleaved by 32).
+int launch_traceback_thread(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
+                            const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
+                            const TbJob* d_jobs, uint32_t n_jobs, uint32_t* d_dir,
+                            uint32_t* d_cig_tmp, int2* d_scr, dsa_hit* d_hits);
 int launch_cigar_compact(dsa_ctx* ctx, dsa_hit* d_hits, const TbJob* d_jobs, uint32_t n_jobs,
                          const uint32_t* d_cig_tmp, uint32_t* d_cigar, uint64_t base,
                          uint64_t* d_total);

@@ -49,7 +49,8 @@ struct C16 {
   }
 };
 
-__global__ void __launch_bounds__(NT) k_pairs16(
+template <bool LOCAL>
+__global__ void __launch_bounds__(NT, 4) k_pairs16(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe, int T,
     const Pair16Job* __restrict__ jobs, uint32_t n_jobs, uint2* __restrict__ scratch,
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(NT) k_pairs16(
   for (int x = threadIdx.x; x < A * A; x += blockDim.x) Sp[x] = (int16_t)(Sg[x] + o);
   __syncthreads();
   const int tid = threadIdx.x;
-  const bool local = mode == DSA_LOCAL;
+  constexpr bool local = LOCAL;
   const bool sg = mode == DSA_SEMIGLOBAL;
   const bool q_end_free = sg && (fe & DSA_FREE_Q_END);
   const bool t_end_free = sg && (fe & DSA_FREE_T_END);
@@ -105,9 +106,19 @@ __global__ void __launch_bounds__(NT) k_pairs16(
       uint32_t diag = pack2(hd, hd);
       int pend = 0;
       uint32_t thr2 = pack2(max(best_lo - 1, 0), max(best_hi - 1, 0));
+      // loads run one column ahead of the arithmetic (target residues and the
+      // boundary row handed down by the previous strip)
+      uint32_t n_alo = tlo[0], n_ahi = nhi > 0 ? thi[0] : 0u;
+      uint2 n_v = i0 > 0 ? scr[0] : make_uint2(0u, 0u);
       for (int32_t j = 1; j <= nmax; ++j) {
-        const uint32_t a_lo = j <= nlo ? tlo[j - 1] : 0u;
-        const uint32_t a_hi = j <= nhi ? thi[j - 1] : 0u;
+        const uint32_t a_lo = j <= nlo ? n_alo : 0u;
+        const uint32_t a_hi = j <= nhi ? n_ahi : 0u;
+        const uint2 v = n_v;
+        if (j < nmax) {
+          n_alo = j < nlo ? tlo[j] : 0u;
+          n_ahi = j < nhi ? thi[j] : 0u;
+          if (i0 > 0) n_v = scr[(uint64_t)j * stride];
+        }
         uint32_t topHo, F;
         if (i0 == 0) {
           const int32_t h0l = h_row0(mode, fe, min(j, nlo), o, e) - o;
@@ -115,7 +126,6 @@ __global__ void __launch_bounds__(NT) k_pairs16(
           topHo = pack2(h0l, h0h);
           F = topHo;   // F of row 1 = H[0][j] - o
         } else {
-          const uint2 v = scr[(uint64_t)(j - 1) * stride];
           topHo = v.x;
           F = v.y;
         }
@@ -230,7 +240,8 @@ int launch_pairs16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_
   const size_t scr_bytes = (size_t)blocks * NT * max_n * sizeof(uint2);
   void* scr = nullptr;
   DSA_TRY(ctx->alloc(&scr, scr_bytes));
-  k_pairs16<<<(unsigned)blocks, NT, 0, ctx->stream>>>(
+  auto kern = mode == DSA_LOCAL ? k_pairs16<true> : k_pairs16<false>;
+  kern<<<(unsigned)blocks, NT, 0, ctx->stream>>>(
       qs->d_codes, db->d_codes, d_matrix, A, o, e, mode, fe, 32767 - std::max(0, smax), d_jobs,
       n_jobs, static_cast<uint2*>(scr), max_n, out.score, out.q_end, out.t_end, out.flag);
   ++ctx->launches;

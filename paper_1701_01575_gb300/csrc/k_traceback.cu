@@ -81,12 +81,12 @@ __global__ void __launch_bounds__(128) k_traceback(
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
           const int32_t i = r0 + r + 1;
-          H[r] = h_col0(mode, fe, i, o, e);
+          H[r] = jb.jlo > 0 ? NEG32 : h_col0(mode, fe, i, o, e);
           E[r] = NEG32;
           nb[r] = 0;
           qc[r] = i <= ie ? q[i - 1] : 0;
         }
-        int32_t diag = h_col0(mode, fe, r0, o, e);
+        int32_t diag = (jb.jlo > 0 && r0 > 0) ? NEG32 : h_col0(mode, fe, r0, o, e);
         int32_t sendH = 0, sendF = NEG32;
         const int32_t steps = je + 31;
         for (int32_t s = 1; s <= steps; ++s) {
@@ -192,11 +192,160 @@ __global__ void __launch_bounds__(128) k_traceback(
       c.flush();
       dsa_hit* h = hits + jb.hit;
       h->q_begin = i;
-      h->t_begin = j;
+      h->t_begin = j + jb.jlo;
       h->cigar_len = c.n;
       h->flags |= DSA_HIT_HAS_TRACEBACK;
     }
   }
+}
+
+// Band (both kernels): with a free target begin, a hit's score bounds the
+// deletions of any path that reaches it (each M scores at most max S, a run
+// of k deletions costs at least o + (k-1)e), so every optimal path starts at
+// a column >= jlo = je - ie - kmax.  The DP restricted to columns jlo..je with
+// a wall at column jlo has the same values on every cell of an optimal path
+// and the same ties, hence the same decisions along the walk; the host then
+// passes t_start + jlo and je - jlo, and t_begin is shifted back by jlo.
+//
+// Thread-per-hit variant for large batches of small rectangles (reads in
+// windows): one thread recomputes its hit's rectangle in strips of TROWS
+// query rows held in registers, column by column, with the same 4-bit
+// decisions as above.  The decisions of a strip column (TROWS nibbles, two
+// words) go to a layout interleaved over the 32 hits of a warp,
+//   word (strip s, column j, half h) of lane l at
+//   dir_off + ((s * cols + j - 1) * 2 + h) * 32     (dir_off = group base + l),
+// so every store of the warp is one 128-byte line; the strip's bottom row
+// (H, F) is handed to the next strip through an interleaved scratch row.
+// Each thread then walks its own hit back, so the 32 walks of a warp run side
+// by side instead of one after another.
+constexpr int TROWS = 16;
+
+__global__ void __launch_bounds__(128) k_traceback_thread(
+    const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
+    const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
+    const TbJob* __restrict__ jobs, uint32_t n_jobs, uint32_t* __restrict__ dir,
+    uint32_t* __restrict__ cig_tmp, int2* __restrict__ scratch, dsa_hit* __restrict__ hits) {
+  __shared__ int32_t S[32 * 32];
+  for (int x = threadIdx.x; x < A * A; x += blockDim.x) S[x] = Sg[x];
+  __syncthreads();
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_jobs) return;
+  const bool local = mode == DSA_LOCAL;
+  const TbJob jb = jobs[k];
+  const int32_t ie = jb.ie, je = jb.je;
+  const uint8_t* q = qcodes + jb.q_start;
+  const uint8_t* t = tcodes + jb.t_start;
+  uint32_t* D = dir + jb.dir_off;
+  int2* scr = scratch + jb.scr_off;
+  const uint64_t cols = jb.wpr;   // columns of the group's layout (>= je)
+
+  if (ie > 0 && je > 0) {
+    for (int32_t i0 = 0, s = 0; i0 < ie; i0 += TROWS, ++s) {
+      const int rows = min(TROWS, ie - i0);
+      const bool last = i0 + rows == ie;
+      int32_t H[TROWS], E[TROWS];
+      int qa[TROWS];
+#pragma unroll
+      for (int r = 0; r < TROWS; ++r) {
+        H[r] = jb.jlo > 0 ? NEG32 : h_col0(mode, fe, i0 + r + 1, o, e);
+        E[r] = NEG32;
+        qa[r] = r < rows ? q[i0 + r] * A : 0;
+      }
+      int32_t diag = (jb.jlo > 0 && i0 > 0) ? NEG32 : h_col0(mode, fe, i0, o, e);
+      uint32_t* Ds = D + (uint64_t)s * cols * 64;
+      // loads run one column ahead of the arithmetic
+      int n_a = t[0];
+      int2 n_v = i0 > 0 ? scr[0] : make_int2(0, 0);
+      for (int32_t j = 1; j <= je; ++j) {
+        const int a = n_a;
+        const int2 v = n_v;
+        if (j < je) {
+          n_a = t[j];
+          if (i0 > 0) n_v = scr[(uint64_t)j * 32];
+        }
+        int32_t Hp, F;
+        if (i0 == 0) {
+          Hp = h_row0(mode, fe, j, o, e);
+          F = NEG32;
+        } else {
+          Hp = v.x;
+          F = v.y;
+        }
+        int32_t d = diag;
+        diag = Hp;
+        uint32_t w0 = 0, w1 = 0;
+#pragma unroll
+        for (int r = 0; r < TROWS; ++r) {
+          if (r < rows) {
+            const int32_t fo = Hp - o, fx = F - e;
+            F = max(fx, fo);
+            const int32_t eo = H[r] - o, ex = E[r] - e;
+            E[r] = max(ex, eo);
+            const int32_t m = d + S[qa[r] + a];
+            int32_t v = max(m, max(E[r], F));
+            if (local) v = max(v, 0);
+            uint32_t src;
+            if (local && v == 0) src = 3;
+            else if (v == m) src = 0;
+            else if (v == F) src = 1;
+            else src = 2;
+            const uint32_t nib = src | ((eo >= ex) ? 4u : 0u) | ((fo >= fx) ? 8u : 0u);
+            if (r < 8) w0 |= nib << (4 * r);
+            else w1 |= nib << (4 * (r - 8));
+            d = H[r];
+            H[r] = v;
+            Hp = v;
+          }
+        }
+        Ds[(uint64_t)(j - 1) * 64] = w0;
+        if (rows > 8) Ds[(uint64_t)(j - 1) * 64 + 32] = w1;
+        if (!last) scr[(uint64_t)(j - 1) * 32] = make_int2(Hp, F);
+      }
+    }
+  }
+  auto nibble = [&](int32_t i, int32_t j) -> uint32_t {
+    const uint32_t r = (uint32_t)(i - 1) % TROWS, s = (uint32_t)(i - 1) / TROWS;
+    const uint32_t w = D[(((uint64_t)s * cols + (uint32_t)(j - 1)) * 2 + (r >> 3)) * 32];
+    return (w >> (4 * (r & 7))) & 15u;
+  };
+  RevCigar c;
+  c.out = cig_tmp + jb.cig_off;
+  int32_t i = ie, j = je;
+  int st = 0;  // 0 = H, 1 = F, 2 = E
+  const bool sg = mode == DSA_SEMIGLOBAL;
+  for (int64_t guard = 2 * ((int64_t)ie + je) + 2; guard > 0; --guard) {
+    if (st == 0) {
+      if (sg && ((i == 0 && (fe & DSA_FREE_T_BEGIN)) || (j == 0 && (fe & DSA_FREE_Q_BEGIN)))) break;
+      if (i == 0 || j == 0) {
+        if (local) break;
+        while (j > 0) { c.emit(2); --j; }
+        while (i > 0) { c.emit(1); --i; }
+        break;
+      }
+      const uint32_t src = nibble(i, j) & 3u;
+      if (src == 3) break;
+      if (src == 0) { c.emit(0); --i; --j; }
+      else st = src == 1 ? 1 : 2;
+    } else if (st == 1) {
+      if (i <= 0 || j <= 0) break;
+      const uint32_t nib = nibble(i, j);
+      c.emit(1);
+      if (nib & 8u) st = 0;
+      --i;
+    } else {
+      if (i <= 0 || j <= 0) break;
+      const uint32_t nib = nibble(i, j);
+      c.emit(2);
+      if (nib & 4u) st = 0;
+      --j;
+    }
+  }
+  c.flush();
+  dsa_hit* h = hits + jb.hit;
+  h->q_begin = i;
+  h->t_begin = j + jb.jlo;
+  h->cigar_len = c.n;
+  h->flags |= DSA_HIT_HAS_TRACEBACK;
 }
 
 // Exclusive scan of the jobs' CIGAR word counts (single CTA), then a reversed copy.
@@ -251,6 +400,20 @@ int launch_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int
   k_traceback<<<(unsigned)blocks, threads, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix,
                                                              A, o, e, mode, fe, d_jobs, n_jobs,
                                                              d_dir, d_cig_tmp, d_scr, d_hits);
+  DSA_CUDA_TRY(cudaGetLastError());
+  ++ctx->launches;
+  return DSA_OK;
+}
+
+int launch_traceback_thread(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
+                            const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
+                            const TbJob* d_jobs, uint32_t n_jobs, uint32_t* d_dir,
+                            uint32_t* d_cig_tmp, int2* d_scr, dsa_hit* d_hits) {
+  if (n_jobs == 0) return DSA_OK;
+  const unsigned blocks = (n_jobs + 127) / 128;
+  k_traceback_thread<<<blocks, 128, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e,
+                                                      mode, fe, d_jobs, n_jobs, d_dir, d_cig_tmp,
+                                                      d_scr, d_hits);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   return DSA_OK;

@@ -243,9 +243,12 @@ def check_traceback(h, cig, queries, db, S, o, e, mode, fe):
         assert got.tolist() == c.tolist(), (oracle.cigar_string(got), oracle.cigar_string(c))
 
 
+@pytest.mark.parametrize("per_thread", [False, True])
 @pytest.mark.parametrize("mode,fe", [(dsa.LOCAL, 15), (dsa.GLOBAL, 15), (dsa.SEMIGLOBAL, 15),
                                      (dsa.SEMIGLOBAL, 12), (dsa.SEMIGLOBAL, 3)])
-def test_traceback_matches_oracle(ctx, mode, fe):
+def test_traceback_matches_oracle(ctx, mode, fe, per_thread, monkeypatch):
+    """Warp-per-hit and thread-per-hit traceback (the latter forced on small batches)."""
+    monkeypatch.setenv("DSA_TB_THREAD_MIN", "1" if per_thread else "1000000000")
     rng = np.random.default_rng(31 + mode + fe)
     S = W.dna_matrix(2, -3)
     base = W.random_dna(rng, 4, 20, 400)
@@ -467,3 +470,33 @@ def test_packed_pairs_saturation_rerun(ctx):
     assert h["score"][0] == 40000 and (h["flags"][0] & dsa.HIT_RERUN_INT32)
     assert not (h["flags"][2] & dsa.HIT_RERUN_INT32)
     assert r.stats()[1] >= 2
+
+
+@pytest.mark.parametrize("mode,fe", [(dsa.SEMIGLOBAL, 12), (dsa.GLOBAL, 15), (dsa.LOCAL, 15),
+                                     (dsa.SEMIGLOBAL, 15)])
+def test_thread_traceback_reads_in_windows(ctx, mode, fe, monkeypatch):
+    """Thread-per-hit traceback on read/window pairs: 1..70-row reads (one strip,
+    several strips, ragged last strip, fewer than 9 rows), partial last group."""
+    monkeypatch.setenv("DSA_TB_THREAD_MIN", "1")
+    rng = np.random.default_rng(70 + mode * 16 + fe)
+    genome = rng.integers(0, 4, 20000).astype(np.uint8)
+    db = W.SeqSet.from_list([genome])
+    reads, starts = [], []
+    for n in np.concatenate([rng.integers(1, 71, 200), [1, 8, 9, 16, 17, 32, 33]]):
+        st = int(rng.integers(0, 20000 - 200))
+        reads.append(W.mutate(rng, genome[st + 20: st + 20 + n], 0.04, 0.03))
+        starts.append(st)
+    reads = [x if len(x) else np.zeros(1, np.uint8) for x in reads]
+    qs = W.SeqSet.from_list(reads)
+    pairs = np.zeros(qs.n, dtype=W.PAIR_DTYPE)
+    pairs["query_id"] = np.arange(qs.n)
+    pairs["t_offset"] = starts
+    pairs["t_len"] = 60 + rng.integers(0, 140, qs.n)
+    S = W.dna_matrix(1, -4)
+    d = ctx.load_set(db, 4)
+    q = ctx.load_set(qs, 4)
+    r = ctx.align(d, q, S, 6, 1, mode=mode, free_ends=fe, pairs=pairs)
+    ctx.traceback(r)
+    h = r.hits()
+    check_traceback(h, r.cigar(), qs, db, S, 6, 1, mode, fe)
+    assert (h["flags"] & dsa.HIT_HAS_TRACEBACK).sum() >= len(h) // 2
