@@ -551,7 +551,7 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
   DSA_TRY(upload(ctx, d_sbase, s_sbase));
   DSA_TRY(upload(ctx, d_sns, s_ns));
   DSA_TRY(upload(ctx, d_items, item_words));
-  DSA_TRY(d_sprof.alloc(ctx, (size_t)spl.n_strips * R * spl.rows * sizeof(uint32_t)));
+  DSA_TRY(d_sprof.alloc(ctx, (size_t)spl.n_strips * R * spl.pitch * sizeof(uint32_t)));
   spl.d_meta = d_smeta.as<StripMeta>();
   spl.d_sbase = d_sbase.as<uint32_t>();
   spl.d_ns = d_sns.as<uint32_t>();
@@ -564,7 +564,7 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
     DSA_TRY(upload(ctx, d_pns, p_ns));
     DSA_TRY(upload(ctx, d_long, long_ids));
     DSA_TRY(upload(ctx, d_litems, litem_words));
-    DSA_TRY(d_pprof.alloc(ctx, (size_t)ppl.n_strips * R * ppl.rows * sizeof(uint32_t)));
+    DSA_TRY(d_pprof.alloc(ctx, (size_t)ppl.n_strips * R * ppl.pitch * sizeof(uint32_t)));
     ppl.d_meta = d_pmeta.as<StripMeta>();
     ppl.d_sbase = d_pbase.as<uint32_t>();
     ppl.d_ns = d_pns.as<uint32_t>();

@@ -183,9 +183,10 @@ struct PackedPlan {
   StripMeta* d_meta = nullptr;     // n_strips
   uint32_t* d_sbase = nullptr;     // first strip of each unit
   uint32_t* d_ns = nullptr;        // strips of each unit
-  uint32_t* d_prof = nullptr;      // n_strips x R x rows words
+  uint32_t* d_prof = nullptr;      // n_strips x R x pitch words
   int R = 0;                       // profile rows = A + 1 (last = padding)
   int rows = 32;                   // query rows per strip
+  int pitch = 32;                  // words per profile row (rows padded to 128 bytes)
 };
 
 // Inter-sequence kernel work: items = (unit, first group of a block of 8).

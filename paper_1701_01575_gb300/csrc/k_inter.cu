@@ -81,16 +81,23 @@ struct InterArgs {
   int32_t* status;
 };
 
-// Bytes between profile replicas: at least one strip profile (R x W x 4 B),
+// Profile rows are padded to 128 bytes (PITCH words): with 8 replicas whose
+// starts are 16 bytes apart mod 128, the 16-byte word k of row a in replica c
+// then sits in bank group (c + k) mod 8 whatever a is, so the 8 lanes of a
+// quarter-warp never share a bank group.
+constexpr int PITCH = 32;
+static_assert(W <= PITCH, "strip rows must fit one padded profile row");
+
+// Bytes between profile replicas: at least one strip profile (R x PITCH x 4 B),
 // a multiple of 16, and 16 (mod 128) so replica c starts in bank group c.
 __host__ __device__ __forceinline__ uint32_t replica_stride(int R) {
-  const uint32_t units = ((uint32_t)R * W * 4u + 15u) / 16u;
+  const uint32_t units = ((uint32_t)R * PITCH * 4u + 15u) / 16u;
   return ((units + 6u) / 8u * 8u + 1u) * 16u;
 }
 
 __device__ __forceinline__ void issue_strip(const InterArgs& A, uint8_t* buf, uint64_t* bar,
                                             const uint32_t* src, uint32_t cstride) {
-  const uint32_t bytes = (uint32_t)A.R * W * 4u;
+  const uint32_t bytes = (uint32_t)A.R * PITCH * 4u;
   mbar_arrive_expect_tx(bar, bytes * NCOPY);
 #pragma unroll
   for (int c = 0; c < NCOPY; ++c) bulk_g2s(buf + c * cstride, src, bytes, bar);
@@ -108,7 +115,7 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
   // column parking areas for the end-cell search, one per half: [row][thread]
   volatile uint32_t* const park_lo = reinterpret_cast<volatile uint32_t*>(smem + 2 * bufbytes);
   volatile uint32_t* const park_hi = park_lo + W * NT;
-  const uint32_t strip_words = (uint32_t)A.R * W;
+  const uint32_t strip_words = (uint32_t)A.R * PITCH;
   const uint32_t neg_o2 = A.neg_o2, neg_e2 = A.neg_e2;
   const uint32_t NEG2 = pack2(NEG16, NEG16);
 
@@ -209,7 +216,7 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const uint32_t a = (word >> (8 * k)) & 0xFFu;
-          const uint4* prow = reinterpret_cast<const uint4*>(pbuf + a * (W * 4u));
+          const uint4* prow = reinterpret_cast<const uint4*>(pbuf + a * (PITCH * 4u));
           uint32_t F = top[k].y;
           uint32_t d = diag;
           diag = top[k].x;
@@ -305,21 +312,23 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
 __global__ void k_strip_profile(const uint8_t* __restrict__ qcodes,
                                 const uint64_t* __restrict__ qoff, const uint32_t* __restrict__ qlen,
                                 const StripMeta* __restrict__ meta, uint32_t n_strips,
-                                const int8_t* __restrict__ S, int A, int R, int rows, int o,
-                                uint32_t* __restrict__ prof) {
-  const uint64_t total = (uint64_t)n_strips * R * rows;
+                                const int8_t* __restrict__ S, int A, int R, int rows, int pitch,
+                                int o, uint32_t* __restrict__ prof) {
+  const uint64_t total = (uint64_t)n_strips * R * pitch;
   for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < total;
        x += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t s = (uint32_t)(x / ((uint64_t)R * rows));
-    const int a = (int)((x / rows) % (uint64_t)R);
-    const int r = (int)(x % rows);
+    const uint32_t s = (uint32_t)(x / ((uint64_t)R * pitch));
+    const int a = (int)((x / pitch) % (uint64_t)R);
+    const int r = (int)(x % pitch);
     const StripMeta md = meta[s];
     int lo = NEG16, hi = NEG16;
-    if (a < A && md.qa != NONE) {
+    if (r >= rows) {
+      // row padding, never read
+    } else if (a < A && md.qa != NONE) {
       const int i = (int)(md.ka & ~LAST) * rows + r;
       if (i < (int)qlen[md.qa]) lo = (int)S[qcodes[qoff[md.qa] + i] * A + a] + o;
     }
-    if (a < A && md.qb != NONE) {
+    if (r < rows && a < A && md.qb != NONE) {
       const int i = (int)(md.kb & ~LAST) * rows + r;
       if (i < (int)qlen[md.qb]) hi = (int)S[qcodes[qoff[md.qb] + i] * A + a] + o;
     }
@@ -334,11 +343,12 @@ int inter_blocks_per_sm() { return 2; }
 int launch_strip_profile(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix, int A, int o,
                          const PackedPlan& plan) {
   if (plan.n_strips == 0) return DSA_OK;
-  const uint64_t total = (uint64_t)plan.n_strips * plan.R * plan.rows;
+  const uint64_t total = (uint64_t)plan.n_strips * plan.R * plan.pitch;
   uint64_t blocks = std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->sm_count * 8);
   k_strip_profile<<<(unsigned)blocks, 256, 0, ctx->stream>>>(qs->d_codes, qs->d_off, qs->d_len,
                                                             plan.d_meta, plan.n_strips, d_matrix,
-                                                            A, plan.R, plan.rows, o, plan.d_prof);
+                                                            A, plan.R, plan.rows, plan.pitch, o,
+                                                            plan.d_prof);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   return DSA_OK;
