@@ -13,7 +13,8 @@
 //   * a query is processed in strips of 32 rows held in registers; the loop
 //     runs over the target's residues; the strip's bottom row (H - o and the
 //     next row's F) goes to a per-CTA boundary buffer and is read back by the
-//     next strip;
+//     next strip through a small shared-memory ring that per-thread
+//     asynchronous copies fill two 4-column blocks ahead of the arithmetic;
 //   * the query profile of each strip (R residue rows x W query rows of
 //     int16x2 = R x 4W bytes) is staged into shared memory by TMA bulk copies,
 //     double-buffered on two mbarriers, in 8 replicas whose start addresses
@@ -52,6 +53,7 @@ constexpr int W = INTER_ROWS;    // query rows per strip
 constexpr int NW = INTER_WARPS;  // warps per CTA
 constexpr int NT = NW * 32;
 constexpr int NCOPY = 8;         // profile replicas (one per lane of a quarter-warp)
+constexpr uint32_t RING = 3;     // boundary-row ring slots (blocks of 4 columns)
 
 struct InterArgs {
   const uint8_t* il;
@@ -112,9 +114,12 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
   const int warp = tid >> 5;
   const uint32_t cstride = replica_stride(A.R);
   const uint32_t bufbytes = NCOPY * cstride;
-  // column parking areas for the end-cell search, one per half: [row][thread]
-  volatile uint32_t* const park_lo = reinterpret_cast<volatile uint32_t*>(smem + 2 * bufbytes);
-  volatile uint32_t* const park_hi = park_lo + W * NT;
+  // column parking areas for the end-cell search, one 16-bit half each: [row][thread]
+  volatile int16_t* const park_lo = reinterpret_cast<volatile int16_t*>(smem + 2 * bufbytes);
+  volatile int16_t* const park_hi = park_lo + W * NT;
+  // boundary-row ring: RING blocks of 4 columns, [slot][k][thread], filled by
+  // per-thread asynchronous copies two blocks ahead of the arithmetic
+  uint2* const ring = reinterpret_cast<uint2*>(smem + 2 * bufbytes + 2 * W * NT * sizeof(int16_t)) + tid;
   const uint32_t strip_words = (uint32_t)A.R * PITCH;
   const uint32_t neg_o2 = A.neg_o2, neg_e2 = A.neg_e2;
   const uint32_t NEG2 = pack2(NEG16, NEG16);
@@ -194,14 +199,30 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
       set_thr();
       int pend = 0;   // bit 0 / 1: low / high half improved in this strip
 
-      for (uint32_t c4 = 0; c4 < ncol; c4 += 4) {
+      // the previous strip's bottom row, block c4x of 4 columns, into ring slot
+      auto fetch = [&](uint32_t c4x, uint32_t slot) {
+        if (c4x < ncol) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            cp_async8(ring + (slot * 4 + k) * NT, scr + (uint64_t)(c4x + k) * NT);
+        }
+        cp_async_commit();
+      };
+      if (!first) {
+        fetch(0, 0);
+        fetch(4, 1);
+      }
+      uint32_t slot = 0;
+      for (uint32_t c4 = 0; c4 < ncol; c4 += 4, slot = slot == RING - 1 ? 0 : slot + 1) {
         if ((c4 & 15u) == 0) rv = __ldg(res + (c4 >> 4) * 32u);
         const uint32_t sel = (c4 >> 2) & 3u;
         const uint32_t word = sel == 0 ? rv.x : sel == 1 ? rv.y : sel == 2 ? rv.z : rv.w;
         uint2 top[4];
         if (!first) {
+          fetch(c4 + 8, slot == 0 ? RING - 1 : slot - 1);   // slot (slot + 2) mod 3
+          cp_async_wait<2>();                               // block c4 has landed
 #pragma unroll
-          for (int k = 0; k < 4; ++k) top[k] = scr[(uint64_t)(c4 + k) * NT];
+          for (int k = 0; k < 4; ++k) top[k] = ring[(slot * 4 + k) * NT];
           if (keep != 0xFFFFFFFFu) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -252,30 +273,31 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
             // supersedes this one)
             if (cl > thr_lo) {
 #pragma unroll
-              for (int r = 0; r < W; ++r) park_lo[r * NT + tid] = Ho[r];
+              for (int r = 0; r < W; ++r) park_lo[r * NT + tid] = (int16_t)lo16(Ho[r]);
               best_lo = cl; bj_lo = j; pend |= 1;
             }
             if (ch > thr_hi) {
 #pragma unroll
-              for (int r = 0; r < W; ++r) park_hi[r * NT + tid] = Ho[r];
+              for (int r = 0; r < W; ++r) park_hi[r * NT + tid] = (int16_t)hi16(Ho[r]);
               best_hi = ch; bj_hi = j; pend |= 2;
             }
             set_thr();
           }
         }
       }
+      cp_async_wait<0>();   // nothing in flight into the ring past the strip
       if (pend & 1) {   // first row of the last improving column, low half
         const int want = best_lo - A.o;
         int rr = W - 1;
         for (int r = W - 1; r >= 0; --r)
-          if (lo16(park_lo[r * NT + tid]) == want) rr = r;
+          if (park_lo[r * NT + tid] == want) rr = r;
         bi_lo = ia + rr + 1;
       }
       if (pend & 2) {
         const int want = best_hi - A.o;
         int rr = W - 1;
         for (int r = W - 1; r >= 0; --r)
-          if (hi16(park_hi[r * NT + tid]) == want) rr = r;
+          if (park_hi[r * NT + tid] == want) rr = r;
         bi_hi = ib + rr + 1;
       }
       if (tvalid) {   // queries that end in this strip: write their results
@@ -379,7 +401,8 @@ int launch_inter_local16(dsa_ctx* ctx, const dsa_db* db, const PackedPlan& plan,
   A.o_score = out.score; A.o_qend = out.q_end; A.o_tend = out.t_end; A.o_flag = out.flag;
   A.n_out_t = n_targets_out;
   A.status = ctx->d_status;
-  const size_t smem = 2ull * NCOPY * replica_stride(plan.R) + 2ull * W * NT * sizeof(uint32_t);
+  const size_t smem = 2ull * NCOPY * replica_stride(plan.R) + 2ull * W * NT * sizeof(int16_t) +
+                      (size_t)RING * 4 * NT * sizeof(uint2);
   static size_t attr_bytes = 0;   // largest dynamic shared memory requested so far
   if (smem > attr_bytes) {
     DSA_CUDA_TRY(cudaFuncSetAttribute(k_inter_local16, cudaFuncAttributeMaxDynamicSharedMemorySize,
