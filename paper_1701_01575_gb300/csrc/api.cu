@@ -28,6 +28,30 @@ void set_error(const char* fmt, ...) {
 
 namespace {
 
+// Stable ascending order of 64-bit keys: identity when they already are in
+// order, else an LSD radix sort on 11-bit digits (digits shared by every key
+// are skipped).
+std::vector<uint32_t> radix_order(const std::vector<uint64_t>& key) {
+  const size_t n = key.size();
+  std::vector<uint32_t> idx(n);
+  std::iota(idx.begin(), idx.end(), 0u);
+  if (std::is_sorted(key.begin(), key.end())) return idx;
+  uint64_t all_or = 0, all_and = ~0ull;
+  for (uint64_t k : key) { all_or |= k; all_and &= k; }
+  const uint64_t varying = all_or ^ all_and;
+  std::vector<uint32_t> tmp(n);
+  std::vector<uint32_t> cnt(2049);
+  for (int shift = 0; shift < 64; shift += 11) {
+    if (((varying >> shift) & 0x7FFull) == 0) continue;
+    std::fill(cnt.begin(), cnt.end(), 0u);
+    for (size_t x = 0; x < n; ++x) ++cnt[((key[idx[x]] >> shift) & 0x7FF) + 1];
+    for (size_t b = 1; b < cnt.size(); ++b) cnt[b] += cnt[b - 1];
+    for (size_t x = 0; x < n; ++x) tmp[cnt[(key[idx[x]] >> shift) & 0x7FF]++] = idx[x];
+    idx.swap(tmp);
+  }
+  return idx;
+}
+
 // Stream-ordered device buffer charged against the context's budget.
 struct DevBuf {
   dsa_ctx* ctx = nullptr;
@@ -50,6 +74,13 @@ struct DevBuf {
   }
   template <class T> T* as() const { return static_cast<T*>(p); }
 };
+
+template <class T>
+int upload(dsa_ctx* ctx, DevBuf& buf, const T* p, size_t n) {
+  DSA_TRY(buf.alloc(ctx, n * sizeof(T)));
+  if (n) DSA_CUDA_TRY(cudaMemcpyAsync(buf.p, p, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  return DSA_OK;
+}
 
 template <class T>
 int upload(dsa_ctx* ctx, DevBuf& buf, const std::vector<T>& v) {
@@ -130,7 +161,7 @@ int dsa_ctx::alloc(void** p, size_t bytes, cudaStream_t on) {
               budget);
     return DSA_ERR_OVER_BUDGET;
   }
-  cudaError_t e = cudaMallocAsync(p, bytes, on ? on : stream);
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, on ? on : stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -182,6 +213,22 @@ extern "C" int dsa_create(dsa_ctx** out, int device, size_t mem_budget_bytes, vo
     }
     c->own_stream = true;
   }
+  {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    uint64_t keep = mem_budget_bytes ? (uint64_t)mem_budget_bytes : UINT64_MAX;
+    if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess ||
+        cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+      cudaGetLastError();
+      if (c->pool) cudaMemPoolDestroy(c->pool);
+      if (c->own_stream) cudaStreamDestroy(c->stream);
+      delete c;
+      set_error("memory pool creation failed");
+      return DSA_ERR_CUDA;
+    }
+  }
   if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess ||
@@ -191,6 +238,7 @@ extern "C" int dsa_create(dsa_ctx** out, int device, size_t mem_budget_bytes, vo
     if (c->d_status) cudaFree(c->d_status);
     if (c->d_counters) cudaFree(c->d_counters);
     if (c->own_stream) cudaStreamDestroy(c->stream);
+    cudaMemPoolDestroy(c->pool);
     delete c;
     set_error("context allocation failed");
     return DSA_ERR_OOM;
@@ -210,6 +258,9 @@ extern "C" int dsa_destroy(dsa_ctx* ctx) {
   cudaEventDestroy(ctx->join_ev);
   cudaStreamDestroy(ctx->side);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  // allocations still outstanding (none when every db / result was freed
+  // first) keep the pool alive until they are freed
+  cudaMemPoolDestroy(ctx->pool);
   delete ctx;
   return DSA_OK;
 }
@@ -810,12 +861,18 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
       res->phase_cells[PH_INT32] = cells - lcells;
     }
     if (!p16.empty()) {
-      // sort by (query length, window length); two pairs of equal query length per thread
-      std::stable_sort(p16.begin(), p16.end(), [&](uint64_t a, uint64_t b) {
-        const uint32_t ma = qs->h_len[hp[a].query_id], mb = qs->h_len[hp[b].query_id];
-        if (ma != mb) return ma < mb;
-        return hp[a].t_len < hp[b].t_len;
-      });
+      // order by (query length, window length); two pairs of equal query length per thread
+      {
+        std::vector<uint64_t> key(p16.size());
+        for (size_t x = 0; x < p16.size(); ++x) {
+          const dsa_pair& pp = hp[p16[x]];
+          key[x] = ((uint64_t)qs->h_len[pp.query_id] << 32) | pp.t_len;
+        }
+        const std::vector<uint32_t> ord = radix_order(key);
+        std::vector<uint64_t> sorted(p16.size());
+        for (size_t x = 0; x < ord.size(); ++x) sorted[x] = p16[ord[x]];
+        p16.swap(sorted);
+      }
       std::vector<Pair16Job> pj;
       pj.reserve(p16.size() / 2 + 1);
       uint32_t max_n = 1;
@@ -886,25 +943,27 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
       }
     }
     const uint64_t n_short = jobs.size();
-    std::vector<uint64_t> poff(qs->n);
-    uint64_t pw = 0;
-    for (uint32_t q = 0; q < qs->n; ++q) {
-      poff[q] = pw;
-      pw += (uint64_t)A * ((qs->h_len[q] + 7u) & ~7u);
+    if (n_short > 0) {   // pairs left for the int32 kernel
+      std::vector<uint64_t> poff(qs->n);
+      uint64_t pw = 0;
+      for (uint32_t q = 0; q < qs->n; ++q) {
+        poff[q] = pw;
+        pw += (uint64_t)A * ((qs->h_len[q] + 7u) & ~7u);
+      }
+      DevBuf d_prof, d_poff, d_jobs, d_scr;
+      if ((rc = d_prof.alloc(ctx, pw * 4)) || (rc = upload(ctx, d_poff, poff)) ||
+          (rc = upload(ctx, d_jobs, jobs)) || (rc = d_scr.alloc(ctx, scr * sizeof(int2))))
+        return fail(rc);
+      if ((rc = launch_profile_int32(ctx, qs, d_mat.as<int8_t>(), A, d_prof.as<int32_t>(),
+                                     d_poff.as<uint64_t>())))
+        return fail(rc);
+      phase_begin(res, PH_INT32);
+      if ((rc = launch_generic_int32(ctx, db, qs, d_prof.as<int32_t>(), d_poff.as<uint64_t>(),
+                                     d_jobs.as<PairJob>(), n_short, 0, d_scr.as<int2>(), mode, fe, o,
+                                     e, 0, sc)))
+        return fail(rc);
+      phase_end(res, PH_INT32);
     }
-    DevBuf d_prof, d_poff, d_jobs, d_scr;
-    if ((rc = d_prof.alloc(ctx, pw * 4)) || (rc = upload(ctx, d_poff, poff)) ||
-        (rc = upload(ctx, d_jobs, jobs)) || (rc = d_scr.alloc(ctx, scr * sizeof(int2))))
-      return fail(rc);
-    if (n_short && (rc = launch_profile_int32(ctx, qs, d_mat.as<int8_t>(), A, d_prof.as<int32_t>(),
-                                              d_poff.as<uint64_t>())))
-      return fail(rc);
-    phase_begin(res, PH_INT32);
-    if ((rc = launch_generic_int32(ctx, db, qs, d_prof.as<int32_t>(), d_poff.as<uint64_t>(),
-                                   d_jobs.as<PairJob>(), n_short, 0, d_scr.as<int2>(), mode, fe, o,
-                                   e, 0, sc)))
-      return fail(rc);
-    phase_end(res, PH_INT32);
   }
 
   // hits
@@ -1011,8 +1070,15 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
   }
   const dsa_db* db = res->db;
   const dsa_db* qs = res->queries;
-  std::vector<TbJob> jobs;
-  jobs.reserve(sel.size());
+  // Many small rectangles: one thread per hit (groups of 32 hits of similar
+  // size share an interleaved decision layout).  Few or large ones: one warp
+  // per hit.
+  uint64_t thread_min = 16384;
+  if (const char* env = getenv("DSA_TB_THREAD_MIN")) thread_min = strtoull(env, nullptr, 10);
+  auto small = [](const TbJob& j) { return j.ie <= 4096 && (uint64_t)j.ie * j.je <= (1u << 20); };
+  std::vector<TbJob>& tjobs = ctx->h_tb;   // thread-per-hit candidates
+  tjobs.clear();
+  std::vector<TbJob> jobs;                 // warp-per-hit
   std::vector<LongTbJob> ljobs;
   uint64_t cap_total = 0;
   const int band = long_band_rows();
@@ -1057,10 +1123,14 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
       }
     }
     j.wpr = (uint32_t)((j.je + 7) / 8);
-    jobs.push_back(j);
+    (small(j) ? tjobs : jobs).push_back(j);
     cap_total += (uint64_t)j.ie + j.je + 1;
   }
-  if (jobs.empty() && ljobs.empty()) return DSA_OK;
+  if (tjobs.size() < std::max<uint64_t>(thread_min, 1)) {
+    jobs.insert(jobs.end(), tjobs.begin(), tjobs.end());
+    tjobs.clear();
+  }
+  if (jobs.empty() && tjobs.empty() && ljobs.empty()) return DSA_OK;
 
   // grow the result's CIGAR array by the capacity bound
   const uint64_t old_n = res->n_cigar;
@@ -1084,43 +1154,31 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
   const uint64_t dir_limit = 1ull << 30;   // words (4 GiB)
   phase_begin(res, PH_TRACE);
 
-  // Many small rectangles: one thread per hit (groups of 32 hits of similar
-  // size share an interleaved decision layout).  Few or large ones: one warp
-  // per hit.
-  uint64_t thread_min = 16384;
-  if (const char* env = getenv("DSA_TB_THREAD_MIN")) thread_min = strtoull(env, nullptr, 10);
-  std::vector<TbJob> tjobs;
   {
-    auto small = [](const TbJob& j) { return j.ie <= 4096 && (uint64_t)j.ie * j.je <= (1u << 20); };
-    const uint64_t n_small = (uint64_t)std::count_if(jobs.begin(), jobs.end(), small);
-    if (n_small >= std::max<uint64_t>(thread_min, 1)) {
-      // counting sort by (ie desc, je desc): groups of 32 hits of similar size
-      std::vector<TbJob> rest;
-      rest.reserve(jobs.size() - n_small);
-      std::vector<uint32_t> idx, tmp;
-      idx.reserve(n_small);
-      int32_t je_max = 0;
-      for (uint32_t x = 0; x < jobs.size(); ++x) {
-        if (small(jobs[x])) {
-          idx.push_back(x);
-          je_max = std::max(je_max, jobs[x].je);
-        } else {
-          rest.push_back(jobs[x]);
+    if (!tjobs.empty()) {
+      // groups of 32 hits share a layout padded to their largest (ie, je):
+      // keep the given order when that pads little, else order by (ie, je)
+      // descending
+      uint64_t cells = 0, padded = 0;
+      for (size_t g = 0; g < tjobs.size(); g += 32) {
+        int32_t im = 0, jm = 0;
+        const size_t g1 = std::min(tjobs.size(), g + 32);
+        for (size_t x = g; x < g1; ++x) {
+          im = std::max(im, tjobs[x].ie);
+          jm = std::max(jm, tjobs[x].je);
+          cells += (uint64_t)tjobs[x].ie * tjobs[x].je;
         }
+        padded += (uint64_t)im * jm * (g1 - g);
       }
-      tmp.resize(idx.size());
-      auto pass = [&](auto key, int32_t kmax) {
-        std::vector<uint32_t> cnt((size_t)kmax + 2, 0);
-        for (uint32_t x : idx) ++cnt[kmax - key(jobs[x]) + 1];
-        for (size_t b = 1; b < cnt.size(); ++b) cnt[b] += cnt[b - 1];
-        for (uint32_t x : idx) tmp[cnt[kmax - key(jobs[x])]++] = x;
-        idx.swap(tmp);
-      };
-      pass([](const TbJob& j) { return j.je; }, je_max);
-      pass([](const TbJob& j) { return j.ie; }, 4096);
-      tjobs.resize(idx.size());
-      for (size_t x = 0; x < idx.size(); ++x) tjobs[x] = jobs[idx[x]];
-      jobs.swap(rest);
+      if (padded > cells + cells / 4) {
+        std::vector<uint64_t> key(tjobs.size());
+        for (size_t x = 0; x < tjobs.size(); ++x)
+          key[x] = ~(((uint64_t)(uint32_t)tjobs[x].ie << 32) | (uint32_t)tjobs[x].je);
+        const std::vector<uint32_t> ord = radix_order(key);
+        std::vector<TbJob> sorted(tjobs.size());
+        for (size_t x = 0; x < ord.size(); ++x) sorted[x] = tjobs[ord[x]];
+        tjobs.swap(sorted);
+      }
     }
   }
   if (!tjobs.empty()) {
@@ -1150,18 +1208,18 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
         scr += (uint64_t)je_max * 32;
         k1 = g1;
       }
-      std::vector<TbJob> chunk(tjobs.begin() + k0, tjobs.begin() + k1);
+      const size_t n_chunk = k1 - k0;
       DevBuf d_jobs, d_dir, d_cig, d_scr;
-      DSA_TRY(upload(ctx, d_jobs, chunk));
+      DSA_TRY(upload(ctx, d_jobs, tjobs.data() + k0, n_chunk));
       DSA_TRY(d_dir.alloc(ctx, dir * 4));
       DSA_TRY(d_cig.alloc(ctx, cig * 4));
       DSA_TRY(d_scr.alloc(ctx, scr * sizeof(int2)));
       DSA_TRY(launch_traceback_thread(ctx, db, qs, d_mat.as<int8_t>(), res->A, res->gap_open,
                                       res->gap_extend, res->mode, res->free_ends,
-                                      d_jobs.as<TbJob>(), (uint32_t)chunk.size(),
+                                      d_jobs.as<TbJob>(), (uint32_t)n_chunk,
                                       d_dir.as<uint32_t>(), d_cig.as<uint32_t>(), d_scr.as<int2>(),
                                       res->d_hits));
-      DSA_TRY(launch_cigar_compact(ctx, res->d_hits, d_jobs.as<TbJob>(), (uint32_t)chunk.size(),
+      DSA_TRY(launch_cigar_compact(ctx, res->d_hits, d_jobs.as<TbJob>(), (uint32_t)n_chunk,
                                    d_cig.as<uint32_t>(), res->d_cigar, total,
                                    d_total.as<uint64_t>()));
       DSA_CUDA_TRY(cudaMemcpyAsync(&total, d_total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost,

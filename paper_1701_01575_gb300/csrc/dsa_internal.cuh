@@ -42,6 +42,8 @@ void set_error(const char* fmt, ...);
     if (rc_ != DSA_OK) return rc_; \
   } while (0)
 
+struct TbJob;
+
 }  // namespace dsa
 
 struct dsa_ctx {
@@ -56,6 +58,11 @@ struct dsa_ctx {
   int32_t* d_status = nullptr;   // device status word written by kernels
   uint32_t* d_counters = nullptr;  // work-queue counters (reset per launch)
   uint64_t launches = 0;         // kernels launched through this context
+  // the context's own stream-ordered memory pool; it keeps freed memory
+  // mapped (up to the budget) instead of returning it at every synchronize
+  cudaMemPool_t pool = nullptr;
+  // host staging reused across calls (large fresh vectors cost page faults)
+  std::vector<dsa::TbJob> h_tb;
   std::mutex mu;
 
   int alloc(void** p, size_t bytes, cudaStream_t on = nullptr);

@@ -472,17 +472,20 @@ def test_packed_pairs_saturation_rerun(ctx):
     assert r.stats()[1] >= 2
 
 
+@pytest.mark.parametrize("uniform", [False, True])
 @pytest.mark.parametrize("mode,fe", [(dsa.SEMIGLOBAL, 12), (dsa.GLOBAL, 15), (dsa.LOCAL, 15),
                                      (dsa.SEMIGLOBAL, 15)])
-def test_thread_traceback_reads_in_windows(ctx, mode, fe, monkeypatch):
+def test_thread_traceback_reads_in_windows(ctx, mode, fe, uniform, monkeypatch):
     """Thread-per-hit traceback on read/window pairs: 1..70-row reads (one strip,
-    several strips, ragged last strip, fewer than 9 rows), partial last group."""
+    several strips, ragged last strip, fewer than 9 rows), partial last group;
+    uniform = equal read and window lengths (hits keep their given order)."""
     monkeypatch.setenv("DSA_TB_THREAD_MIN", "1")
-    rng = np.random.default_rng(70 + mode * 16 + fe)
+    rng = np.random.default_rng(70 + mode * 16 + fe + 7 * uniform)
     genome = rng.integers(0, 4, 20000).astype(np.uint8)
     db = W.SeqSet.from_list([genome])
     reads, starts = [], []
-    for n in np.concatenate([rng.integers(1, 71, 200), [1, 8, 9, 16, 17, 32, 33]]):
+    lens = np.full(203, 40) if uniform else np.concatenate([rng.integers(1, 71, 200), [1, 8, 9, 16, 17, 32, 33]])
+    for n in lens:
         st = int(rng.integers(0, 20000 - 200))
         reads.append(W.mutate(rng, genome[st + 20: st + 20 + n], 0.04, 0.03))
         starts.append(st)
@@ -491,7 +494,7 @@ def test_thread_traceback_reads_in_windows(ctx, mode, fe, monkeypatch):
     pairs = np.zeros(qs.n, dtype=W.PAIR_DTYPE)
     pairs["query_id"] = np.arange(qs.n)
     pairs["t_offset"] = starts
-    pairs["t_len"] = 60 + rng.integers(0, 140, qs.n)
+    pairs["t_len"] = 80 if uniform else 60 + rng.integers(0, 140, qs.n)
     S = W.dna_matrix(1, -4)
     d = ctx.load_set(db, 4)
     q = ctx.load_set(qs, 4)
