@@ -32,10 +32,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GCUPS (bit-exact) batched protein database search"
 # DRAM bytes per DP cell of k_inter_local16, from the ncu capture summarised in
-# profiles/k_inter_local16_protein_8q_350k.md (423.3 GB read + written for
+# profiles/k_inter_local16_protein_8q_350k.md (416.4 GB read + written for
 # 1.194 T cells); traffic grows with the cells (boundary rows per column and
 # strip), so a launch's traffic is this figure times its cells.
-INTER_DRAM_BYTES_PER_CELL = 423.31e9 / 1.194104e12
+INTER_DRAM_BYTES_PER_CELL = 416.35e9 / 1.194104e12
 
 WORKLOAD = ("protein_search: 32 queries (log-uniform 64..5000) x 500,000 targets "
             "(lognormal median 300, sigma 0.7, cap 35,000), BLOSUM62 11/1, local, "
