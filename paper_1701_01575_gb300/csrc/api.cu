@@ -1087,6 +1087,11 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
   for (int8_t v : res->matrix) smax_pos = std::max<int>(smax_pos, v);
   const bool band_ok = res->mode == DSA_SEMIGLOBAL && (res->free_ends & DSA_FREE_T_BEGIN) &&
                        res->gap_extend > 0;
+  // diagonal band of long pairs whose paths start at (0, 0)
+  const bool diag_ok = (res->mode == DSA_GLOBAL ||
+                        (res->mode == DSA_SEMIGLOBAL &&
+                         !(res->free_ends & (DSA_FREE_Q_BEGIN | DSA_FREE_T_BEGIN)))) &&
+                       smax_pos + 2 * res->gap_extend > 0;
   for (uint64_t h : sel) {
     const dsa_hit& hit = res->h_hits[h];
     if (hit.flags & DSA_HIT_HAS_TRACEBACK) continue;
@@ -1100,7 +1105,31 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
       lj.ie = hit.q_end + 1;
       lj.je = hit.t_end + 1;
       lj.hit = (uint32_t)h;
-      lj.wpr = (uint32_t)((lj.je + 7) / 8);
+      lj.dlo = 0;
+      lj.wc = lj.je;
+      if (diag_ok && lj.ie > 0 && lj.je > 0) {
+        // A path from (0, 0) to (ie, je) with g gap columns has (ie + je - g) / 2
+        // M columns, so 2 score <= max(S, 0) (ie + je) - g (max(S, 0) + 2e)
+        // - 2 (o - e) [g > 0]; a cell (i, j) on it has |d| + |dn - d| <= g with
+        // d = j - i, dn = je - ie.  Every optimal path therefore stays in the
+        // diagonals dlo..dhi below.
+        const int64_t num = (int64_t)smax_pos * ((int64_t)lj.ie + lj.je) - 2 * (int64_t)hit.score -
+                            2 * ((int64_t)res->gap_open - res->gap_extend);
+        const int64_t den = (int64_t)smax_pos + 2 * (int64_t)res->gap_extend;
+        const int64_t gmax = num < 0 ? 0 : num / den;
+        const int64_t dn = (int64_t)lj.je - lj.ie;
+        if (gmax >= std::llabs(dn)) {
+          const int64_t half = (gmax - std::llabs(dn)) / 2;
+          const int64_t dlo = std::min<int64_t>(0, dn) - half;
+          const int64_t dhi = std::max<int64_t>(0, dn) + half;
+          const int64_t wc = (int64_t)band + dhi - dlo;
+          if (wc < lj.je) {
+            lj.dlo = (int32_t)dlo;
+            lj.wc = (int32_t)wc;
+          }
+        }
+      }
+      lj.wpr = (uint32_t)((lj.wc + 7) / 8);
       ljobs.push_back(lj);
       cap_total += (uint64_t)lj.ie + lj.je + 1;
       continue;

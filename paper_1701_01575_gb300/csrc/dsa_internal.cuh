@@ -282,7 +282,12 @@ struct LongTbJob {
   int32_t n;                   // boundary row length (the pair's window length)
   int32_t ie, je;
   uint32_t hit;
-  uint32_t wpr;
+  uint32_t wpr;                // decision words per row: ceil(wc / 8)
+  // Diagonal band: rows of band b (BAND rows from i0 = b * BAND) keep the wc
+  // columns from jlo_b = clamp(i0 + 1 + dlo, 1, je - wc + 1); wc = je and
+  // dlo = 0 recompute whole rows.
+  int32_t dlo;
+  int32_t wc;
   uint32_t pad;
 };
 int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,

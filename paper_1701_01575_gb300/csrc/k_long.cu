@@ -233,6 +233,12 @@ struct RevCigar {
 // once (one warp per band, rows of the band x columns 1..je), starting from
 // the checkpoint row above it, and the 4-bit decision of every cell of the
 // rectangle up to the end cell is stored.
+// First stored column of the rows of band b (see LongTbJob).
+__device__ __forceinline__ int32_t band_jlo(const LongTbJob& jb, int32_t b) {
+  const int32_t want = b * BAND + 1 + jb.dlo;
+  return max(1, min(want, jb.je - jb.wc + 1));
+}
+
 __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
@@ -255,24 +261,27 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
     const int32_t i0 = b * BAND;
     const int32_t r0 = i0 + lane * ROWS;
     const int2* up = bnd + jb.bnd_off + (uint64_t)(b - 1) * jb.n;
+    // columns jlo .. jlo + wc - 1 of this band; a wall (-inf) left of jlo > 1
+    const int32_t jlo = band_jlo(jb, b), jhi = jlo + jb.wc - 1;
+    const bool wall = jlo > 1;
     int32_t H[ROWS], E[ROWS];
     uint32_t nbw[ROWS];
     int qc[ROWS];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
       const int32_t ii = r0 + r + 1;
-      H[r] = h_col0(mode, fe, ii, o, e);
+      H[r] = wall ? NEG32 : h_col0(mode, fe, ii, o, e);
       E[r] = NEG32;
       nbw[r] = 0;
       qc[r] = ii <= ie ? q[ii - 1] * A : 0;
     }
-    int32_t diag = h_col0(mode, fe, r0, o, e);
+    int32_t diag = wall ? NEG32 : h_col0(mode, fe, r0, o, e);
     int32_t sendH = 0, sendF = NEG32;
-    for (int32_t s = 1; s <= je + 31; ++s) {
+    for (int32_t s = 1; s <= jb.wc + 31; ++s) {
       int32_t Hup = __shfl_up_sync(0xFFFFFFFFu, sendH, 1);
       int32_t Fup = __shfl_up_sync(0xFFFFFFFFu, sendF, 1);
-      const int32_t jj = s - lane;
-      if (jj >= 1 && jj <= je && r0 < ie) {
+      const int32_t jj = jlo - 1 + s - lane;
+      if (jj >= jlo && jj <= jhi && r0 < ie) {
         if (lane == 0) {
           if (b == 0) {
             Hup = h_row0(mode, fe, jj, o, e);
@@ -287,8 +296,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
         int32_t d = diag;
         diag = Hup;
         int32_t F = Fup, Hp = Hup;
-        const int sh = 4 * ((jj - 1) & 7);
-        const bool flushw = ((jj & 7) == 0) || jj == je;
+        const int32_t jc = jj - jlo;   // stored column
+        const int sh = 4 * (jc & 7);
+        const bool flushw = ((jc & 7) == 7) || jj == jhi;
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
           const int32_t ii = r0 + r + 1;
@@ -307,7 +317,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
             else src = 2;
             nbw[r] |= (src | ((eo >= ex) ? 4u : 0u) | ((fo >= fx) ? 8u : 0u)) << sh;
             if (flushw) {
-              D[(uint64_t)(ii - 1) * wpr + (uint32_t)(jj - 1) / 8u] = nbw[r];
+              D[(uint64_t)(ii - 1) * wpr + (uint32_t)jc / 8u] = nbw[r];
               nbw[r] = 0;
             }
             d = H[r];
@@ -334,6 +344,15 @@ __global__ void k_long_tb_walk(const LongTbJob* __restrict__ jobs, uint32_t n_jo
     const LongTbJob jb = jobs[k];
     const uint32_t* D = dir + jb.dir_off;
     const uint32_t wpr = jb.wpr;
+    // decision nibble of (i, j); false when (i, j) lies outside the stored
+    // band (only a corrupt decision could lead there)
+    auto nibble = [&](int32_t i, int32_t j, uint32_t& nib) -> bool {
+      const int32_t jlo = band_jlo(jb, (i - 1) / BAND);
+      if (j < jlo || j >= jlo + jb.wc) return false;
+      const uint32_t jc = (uint32_t)(j - jlo);
+      nib = (D[(uint64_t)(i - 1) * wpr + jc / 8u] >> (4 * (jc & 7))) & 15u;
+      return true;
+    };
     RevCigar c;
     c.out = cig_tmp + jb.cig_off;
     int32_t i = jb.ie, j = jb.je;
@@ -347,20 +366,21 @@ __global__ void k_long_tb_walk(const LongTbJob* __restrict__ jobs, uint32_t n_jo
           while (i > 0) { c.emit(1); --i; }
           break;
         }
-        const uint32_t nib = (D[(uint64_t)(i - 1) * wpr + (uint32_t)(j - 1) / 8u] >> (4 * ((j - 1) & 7))) & 15u;
+        uint32_t nib;
+        if (!nibble(i, j, nib)) break;
         const uint32_t src = nib & 3u;
         if (src == 3) break;
         if (src == 0) { c.emit(0); --i; --j; }
         else st = src == 1 ? 1 : 2;
       } else if (st == 1) {
-        if (i <= 0 || j <= 0) break;
-        const uint32_t nib = (D[(uint64_t)(i - 1) * wpr + (uint32_t)(j - 1) / 8u] >> (4 * ((j - 1) & 7))) & 15u;
+        uint32_t nib;
+        if (i <= 0 || j <= 0 || !nibble(i, j, nib)) break;
         c.emit(1);
         if (nib & 8u) st = 0;
         --i;
       } else {
-        if (i <= 0 || j <= 0) break;
-        const uint32_t nib = (D[(uint64_t)(i - 1) * wpr + (uint32_t)(j - 1) / 8u] >> (4 * ((j - 1) & 7))) & 15u;
+        uint32_t nib;
+        if (i <= 0 || j <= 0 || !nibble(i, j, nib)) break;
         c.emit(2);
         if (nib & 4u) st = 0;
         --j;

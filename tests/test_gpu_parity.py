@@ -318,7 +318,7 @@ def test_bad_arguments_rejected(ctx):
 # ---------------------------------------------------------------- long explicit pairs
 
 @pytest.mark.parametrize("mode,fe", [(dsa.GLOBAL, 15), (dsa.LOCAL, 15), (dsa.SEMIGLOBAL, 15),
-                                     (dsa.SEMIGLOBAL, 12), (dsa.SEMIGLOBAL, 3)])
+                                     (dsa.SEMIGLOBAL, 12), (dsa.SEMIGLOBAL, 3), (dsa.SEMIGLOBAL, 10)])
 def test_long_pairs_banded_score_and_traceback(ctx, mode, fe):
     """Pairs of 2,000-6,000 bp (band pipeline across warps, checkpointed traceback)."""
     wl = W.long_pairs(seed=W.SEED_BASE + 30 + mode, n_pairs=5, lo=2000, hi=6000, mode=mode)
@@ -337,6 +337,37 @@ def test_long_pairs_banded_score_and_traceback(ctx, mode, fe):
     ctx.traceback(r)
     ctx.sync()
     check_traceback(r.hits(), r.cigar(), wl.queries, wl.db, wl.matrix, 5, 2, mode, fe)
+
+
+@pytest.mark.parametrize("mode,fe", [(dsa.GLOBAL, 15), (dsa.SEMIGLOBAL, 10)])
+def test_long_pair_traceback_diagonal_band(ctx, mode, fe):
+    """Long pairs whose paths start at (0, 0): related pairs (narrow diagonal
+    band from the score bound), an unrelated pair (band wider than the target:
+    whole rows), lengths not multiples of the 256-row bands, m != n."""
+    rng = np.random.default_rng(123 + fe)
+    S = W.dna_matrix(2, -3)
+    a = rng.integers(0, 4, 3001).astype(np.uint8)
+    b = rng.integers(0, 4, 2300).astype(np.uint8)
+    qs = W.SeqSet.from_list([a, b, a[:2900]])
+    db = W.SeqSet.from_list([W.mutate(rng, a, 0.05, 0.01), rng.integers(0, 4, 2100).astype(np.uint8),
+                             W.mutate(rng, a[150:], 0.02, 0.02)])
+    pairs = np.zeros(3, dtype=W.PAIR_DTYPE)
+    pairs["query_id"] = [0, 1, 2]
+    pairs["target_id"] = [0, 1, 2]
+    pairs["t_len"] = db.lengths
+    sc, qe, te = oracle.score_pairs(qs.codes, qs.offsets, db.codes, db.offsets, pairs["query_id"],
+                                    pairs["target_id"], S, 5, 2, mode, fe,
+                                    pair_toff=pairs["t_offset"], pair_tlen=pairs["t_len"])
+    d = ctx.load_set(db, 4)
+    q = ctx.load_set(qs, 4)
+    r = ctx.align(d, q, S, 5, 2, mode=mode, free_ends=fe, pairs=pairs)
+    ctx.sync()
+    h = r.hits()
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), f"long band mode={mode}")
+    assert r.phase_cells()["intra16"] == int((qs.lengths * db.lengths).sum())
+    ctx.traceback(r)
+    ctx.sync()
+    check_traceback(r.hits(), r.cigar(), qs, db, S, 5, 2, mode, fe)
 
 
 def test_long_and_short_pairs_mixed(ctx):
