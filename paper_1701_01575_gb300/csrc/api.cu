@@ -905,7 +905,9 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
       DevBuf d_pj;
       if ((rc = upload(ctx, d_pj, pj))) return fail(rc);
       phase_begin(res, PH_INTER);
-      if ((rc = launch_pairs16(ctx, db, qs, d_mat.as<int8_t>(), A, o, e, mode, fe, v.smax,
+      bool bytes = A <= 4;
+      for (int x = 0; x < A * A; ++x) bytes = bytes && matrix[x] + o >= -128 && matrix[x] + o <= 127;
+      if ((rc = launch_pairs16(ctx, db, qs, d_mat.as<int8_t>(), A, o, e, mode, fe, v.smax, bytes,
                                d_pj.as<Pair16Job>(), (uint32_t)pj.size(), max_n, sc)))
         return fail(rc);
       phase_end(res, PH_INTER);

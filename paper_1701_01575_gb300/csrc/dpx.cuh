@@ -25,6 +25,14 @@ __device__ __forceinline__ uint32_t max2_relu(uint32_t a, uint32_t b) {
 __device__ __forceinline__ uint32_t max3_2(uint32_t a, uint32_t b, uint32_t c) {
   return __vimax3_s16x2(a, b, c);
 }
+// Byte permute of {hi_tab, lo_tab} (bytes 0-3 from lo_tab, 4-7 from hi_tab):
+// each selector nibble picks a byte with its low 3 bits and, with bit 3 set,
+// replicates that byte's sign bit instead (PTX prmt, generic mode).
+__device__ __forceinline__ uint32_t prmt(uint32_t lo_tab, uint32_t hi_tab, uint32_t sel) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(lo_tab), "r"(hi_tab), "r"(sel));
+  return r;
+}
 // a + b per halfword (no carry between halves)
 __device__ __forceinline__ uint32_t add2(uint32_t a, uint32_t b) { return __vadd2(a, b); }
 

@@ -313,9 +313,10 @@ struct Pair16Job {
   uint32_t out_lo, out_hi;
   uint32_t pad;
 };
+// bytes: A <= 4 and every S + o in [-128, 127] (byte-permute substitution form)
 int launch_pairs16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix, int A,
-                   int o, int e, int mode, uint32_t fe, int smax, const Pair16Job* d_jobs,
-                   uint32_t n_jobs, uint32_t max_n, Scores out);
+                   int o, int e, int mode, uint32_t fe, int smax, bool bytes,
+                   const Pair16Job* d_jobs, uint32_t n_jobs, uint32_t max_n, Scores out);
 
 // Issue-rate probe; bounded-wait self-test.
 int run_issue_probe(dsa_ctx* ctx, int form, double* rate);

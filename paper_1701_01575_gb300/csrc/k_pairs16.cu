@@ -7,8 +7,12 @@
 // Per thread: the query rows in strips of ROWS rows held in registers, the
 // target windows scanned column by column, the strip's bottom row (H - o and
 // the next row's F) handed to the next strip through a per-thread boundary
-// row in global memory.  Substitution scores come from a shared-memory copy
-// of S + o (int16), two lookups per cell pair.
+// row in global memory.  Substitution scores (S + o): for alphabets of at most
+// four letters whose S + o fits a byte, each row keeps the four values of its
+// query residue as bytes, one register per pair, and one byte permute per
+// cell pair picks both and sign-extends them into the two halves (16-row
+// strips); otherwise two lookups per cell pair in a shared-memory copy of
+// S + o (int16, 16-row strips).
 //
 // Result cells (same rules as everywhere in the library): local = best cell
 // with the smallest (j, i) -- a column-maximum trigger parks the column in
@@ -26,8 +30,10 @@
 namespace dsa {
 namespace {
 
-constexpr int ROWS = 16;
 constexpr int NT = 128;
+constexpr int BLOCKS_PER_SM = 4;
+constexpr int ROWS_LDS = 16;     // strip rows, shared-memory substitution form
+constexpr int ROWS_BYTES = 16;   // strip rows, byte-permute form (two table registers per row)
 
 __device__ __forceinline__ int32_t h_row0(int mode, uint32_t fe, int64_t j, int o, int e) {
   if (j == 0 || mode == DSA_LOCAL || (mode == DSA_SEMIGLOBAL && (fe & DSA_FREE_T_BEGIN))) return 0;
@@ -49,16 +55,23 @@ struct C16 {
   }
 };
 
-template <bool LOCAL>
-__global__ void __launch_bounds__(NT, 4) k_pairs16(
+template <bool LOCAL, int ROWS, bool BYTES>
+__global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe, int T,
     const Pair16Job* __restrict__ jobs, uint32_t n_jobs, uint2* __restrict__ scratch,
     uint32_t scratch_cols, int32_t* __restrict__ o_score, int32_t* __restrict__ o_qend,
     int32_t* __restrict__ o_tend, uint8_t* __restrict__ o_flag) {
   __shared__ int16_t Sp[32 * 32];                       // S + o
+  __shared__ uint32_t Sb[4];                            // BYTES: row q of S + o as 4 bytes
   __shared__ uint32_t park[2][ROWS][NT];                // parked columns (local mode)
   for (int x = threadIdx.x; x < A * A; x += blockDim.x) Sp[x] = (int16_t)(Sg[x] + o);
+  if (BYTES && threadIdx.x < 4) {
+    uint32_t w = 0;
+    for (int a = 0; a < A; ++a)
+      if ((int)threadIdx.x < A) w |= (uint32_t)(uint8_t)(int8_t)(Sg[threadIdx.x * A + a] + o) << (8 * a);
+    Sb[threadIdx.x] = w;
+  }
   __syncthreads();
   const int tid = threadIdx.x;
   constexpr bool local = LOCAL;
@@ -93,14 +106,21 @@ __global__ void __launch_bounds__(NT, 4) k_pairs16(
     for (int32_t i0 = 0; i0 < m; i0 += ROWS) {
       const int rows = min(ROWS, m - i0);
       const bool last = i0 + rows == m;
-      uint32_t Ho[ROWS], E[ROWS], qa[ROWS];
+      // qa: LDS form, the two pairs' matrix row offsets; sb: BYTES form, the
+      // two pairs' S + o rows as bytes
+      uint32_t Ho[ROWS], E[ROWS], qa[ROWS], sb_lo[ROWS], sb_hi[ROWS];
 #pragma unroll
       for (int r = 0; r < ROWS; ++r) {
         const int32_t i = i0 + r + 1;
         const int32_t hc = h_col0(mode, fe, i, o, e) - o;
         Ho[r] = pack2(hc, hc);
         E[r] = NEG2;
-        qa[r] = r < rows ? ((uint32_t)qlo[i - 1] * A) | (((uint32_t)qhi[i - 1] * A) << 16) : 0u;
+        if (BYTES) {
+          sb_lo[r] = r < rows ? Sb[qlo[i - 1]] : 0u;
+          sb_hi[r] = r < rows ? Sb[qhi[i - 1]] : 0u;
+        } else {
+          qa[r] = r < rows ? ((uint32_t)qlo[i - 1] * A) | (((uint32_t)qhi[i - 1] * A) << 16) : 0u;
+        }
       }
       const int32_t hd = h_col0(mode, fe, i0, o, e) - o;
       uint32_t diag = pack2(hd, hd);
@@ -131,12 +151,16 @@ __global__ void __launch_bounds__(NT, 4) k_pairs16(
         }
         uint32_t d = diag;
         diag = topHo;
+        // BYTES: byte a_lo of the low row (sign-replicated into byte 1) and
+        // byte 4 + a_hi of the high row (sign-replicated into byte 3)
+        const uint32_t sel = (a_lo * 0x11u + 0x80u) | ((a_hi * 0x11u + 0xC4u) << 8);
         uint32_t cm = 0, hprev = 0, hlast = 0;
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
           if (r < rows) {
-            const uint32_t sp = (uint32_t)(uint16_t)Sp[(qa[r] & 0xFFFFu) + a_lo] |
-                                ((uint32_t)(uint16_t)Sp[(qa[r] >> 16) + a_hi] << 16);
+            const uint32_t sp = BYTES ? prmt(sb_lo[r], sb_hi[r], sel)
+                                      : (uint32_t)(uint16_t)Sp[(qa[r] & 0xFFFFu) + a_lo] |
+                                            ((uint32_t)(uint16_t)Sp[(qa[r] >> 16) + a_hi] << 16);
             const uint32_t old = Ho[r];
             E[r] = addmax2(E[r], neg_e2, old);
             const uint32_t t = addmax2(d, sp, E[r]);
@@ -233,14 +257,18 @@ __global__ void __launch_bounds__(NT, 4) k_pairs16(
 }  // namespace
 
 int launch_pairs16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix, int A,
-                   int o, int e, int mode, uint32_t fe, int smax, const Pair16Job* d_jobs,
-                   uint32_t n_jobs, uint32_t max_n, Scores out) {
+                   int o, int e, int mode, uint32_t fe, int smax, bool bytes,
+                   const Pair16Job* d_jobs, uint32_t n_jobs, uint32_t max_n, Scores out) {
   if (n_jobs == 0) return DSA_OK;
-  const uint64_t blocks = std::min<uint64_t>((n_jobs + NT - 1) / NT, (uint64_t)ctx->sm_count * 16);
+  // persistent: every block resident at once, jobs taken in a grid stride
+  const uint64_t blocks =
+      std::min<uint64_t>((n_jobs + NT - 1) / NT, (uint64_t)ctx->sm_count * BLOCKS_PER_SM);
   const size_t scr_bytes = (size_t)blocks * NT * max_n * sizeof(uint2);
   void* scr = nullptr;
   DSA_TRY(ctx->alloc(&scr, scr_bytes));
-  auto kern = mode == DSA_LOCAL ? k_pairs16<true> : k_pairs16<false>;
+  auto kern = mode == DSA_LOCAL
+                  ? (bytes ? k_pairs16<true, ROWS_BYTES, true> : k_pairs16<true, ROWS_LDS, false>)
+                  : (bytes ? k_pairs16<false, ROWS_BYTES, true> : k_pairs16<false, ROWS_LDS, false>);
   kern<<<(unsigned)blocks, NT, 0, ctx->stream>>>(
       qs->d_codes, db->d_codes, d_matrix, A, o, e, mode, fe, 32767 - std::max(0, smax), d_jobs,
       n_jobs, static_cast<uint2*>(scr), max_n, out.score, out.q_end, out.t_end, out.flag);

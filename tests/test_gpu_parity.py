@@ -534,3 +534,24 @@ def test_thread_traceback_reads_in_windows(ctx, mode, fe, uniform, monkeypatch):
     h = r.hits()
     check_traceback(h, r.cigar(), qs, db, S, 6, 1, mode, fe)
     assert (h["flags"] & dsa.HIT_HAS_TRACEBACK).sum() >= len(h) // 2
+
+
+@pytest.mark.parametrize("mode,fe", [(dsa.LOCAL, 15), (dsa.GLOBAL, 15), (dsa.SEMIGLOBAL, 9)])
+def test_packed_pairs_small_alphabet_asymmetric(ctx, mode, fe):
+    """Byte-permute substitution form: 3-letter alphabet, asymmetric matrix with
+    negative S + o entries (sign extension of each half), odd pair count."""
+    rng = np.random.default_rng(610 + mode)
+    S = np.array([[3, -4, 1], [-2, 2, -6], [0, -5, 4]], dtype=np.int8)
+    qs = W.SeqSet.from_list([rng.integers(0, 3, n).astype(np.uint8) for n in rng.integers(1, 90, 40)])
+    db = W.SeqSet.from_list([rng.integers(0, 3, n).astype(np.uint8) for n in rng.integers(1, 300, 30)])
+    pairs = _pairs_case(rng, qs, db, 333)
+    sc, qe, te = oracle.score_pairs(qs.codes, qs.offsets, db.codes, db.offsets, pairs["query_id"],
+                                    pairs["target_id"], S, 4, 1, mode, fe, pair_toff=pairs["t_offset"],
+                                    pair_tlen=pairs["t_len"])
+    d = ctx.load_set(db, 3)
+    q = ctx.load_set(qs, 3)
+    r = ctx.align(d, q, S, 4, 1, mode=mode, free_ends=fe, pairs=pairs)
+    ctx.sync()
+    h = r.hits()
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), f"3-letter pairs mode={mode}")
+    assert r.phase_cells()["inter16"] > 0
