@@ -12,6 +12,7 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <thread>
 
 namespace dsa {
 
@@ -27,6 +28,25 @@ void set_error(const char* fmt, ...) {
 }
 
 namespace {
+
+// Host threads for a loop of n items, at least `per` items each (1 .. 16).
+unsigned host_threads(size_t n, size_t per) {
+  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  return (unsigned)std::max<size_t>(1, std::min<size_t>(hw, n / std::max<size_t>(per, 1)));
+}
+
+// fn(t, begin, end) over T contiguous ranges of [0, n), on T host threads.
+template <class F>
+void parallel_for(size_t n, unsigned T, F&& fn) {
+  if (T <= 1) {
+    fn(0u, (size_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(T);
+  for (unsigned t = 0; t < T; ++t) th.emplace_back([&, t]() { fn(t, n * t / T, n * (t + 1) / T); });
+  for (std::thread& x : th) x.join();
+}
 
 // Stable ascending order of 64-bit keys: identity when they already are in
 // order, else an LSD radix sort on 11-bit digits (digits shared by every key
@@ -904,9 +924,9 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
       }
       DevBuf d_pj;
       if ((rc = upload(ctx, d_pj, pj))) return fail(rc);
-      phase_begin(res, PH_INTER);
-      bool bytes = A <= 4;
+      bool bytes = A <= 4;   // byte-permute substitution form
       for (int x = 0; x < A * A; ++x) bytes = bytes && matrix[x] + o >= -128 && matrix[x] + o <= 127;
+      phase_begin(res, PH_INTER);
       if ((rc = launch_pairs16(ctx, db, qs, d_mat.as<int8_t>(), A, o, e, mode, fe, v.smax, bytes,
                                d_pj.as<Pair16Job>(), (uint32_t)pj.size(), max_n, sc)))
         return fail(rc);
@@ -1094,7 +1114,34 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
                         (res->mode == DSA_SEMIGLOBAL &&
                          !(res->free_ends & (DSA_FREE_Q_BEGIN | DSA_FREE_T_BEGIN)))) &&
                        smax_pos + 2 * res->gap_extend > 0;
-  for (uint64_t h : sel) {
+  // hit h -> short job (false: the hit is skipped or is a long pair)
+  auto make_short = [&](uint64_t h, TbJob& j) -> bool {
+    const dsa_hit& hit = res->h_hits[h];
+    if (hit.flags & DSA_HIT_HAS_TRACEBACK) return false;
+    if (res->mode == DSA_LOCAL && (hit.q_end < 0 || hit.t_end < 0)) return false;
+    if (!res->long_bnd_off.empty() && res->long_bnd_off[h] != UINT64_MAX) return false;
+    j = TbJob{};
+    j.ie = hit.q_end + 1;
+    j.je = hit.t_end + 1;
+    j.hit = (uint32_t)h;
+    j.q_start = qs->h_off[hit.query_id];
+    j.t_start = db->h_off[hit.target_id] + hit.t_offset;
+    if (band_ok) {
+      // deletions on any path reaching the hit: score <= ie * max(S, 0) - (o + (k - 1) e)
+      const int64_t slack = (int64_t)j.ie * smax_pos - hit.score;
+      const int64_t kmax = slack < res->gap_open ? 0 : (slack - res->gap_open) / res->gap_extend + 1;
+      const int64_t jlo = (int64_t)j.je - j.ie - kmax;
+      if (jlo > 0) {
+        j.jlo = (int32_t)jlo;
+        j.t_start += (uint64_t)jlo;
+        j.je -= (int32_t)jlo;
+      }
+    }
+    j.wpr = (uint32_t)((j.je + 7) / 8);
+    return true;
+  };
+  // long pairs (few): serial
+  if (!res->long_bnd_off.empty()) for (uint64_t h : sel) {
     const dsa_hit& hit = res->h_hits[h];
     if (hit.flags & DSA_HIT_HAS_TRACEBACK) continue;
     if (res->mode == DSA_LOCAL && (hit.q_end < 0 || hit.t_end < 0)) continue;
@@ -1134,28 +1181,36 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
       lj.wpr = (uint32_t)((lj.wc + 7) / 8);
       ljobs.push_back(lj);
       cap_total += (uint64_t)lj.ie + lj.je + 1;
-      continue;
     }
-    TbJob j{};
-    j.ie = hit.q_end + 1;
-    j.je = hit.t_end + 1;
-    j.hit = (uint32_t)h;
-    j.q_start = qs->h_off[hit.query_id];
-    j.t_start = db->h_off[hit.target_id] + hit.t_offset;
-    if (band_ok) {
-      // deletions on any path reaching the hit: score <= ie * max(S, 0) - (o + (k - 1) e)
-      const int64_t slack = (int64_t)j.ie * smax_pos - hit.score;
-      const int64_t kmax = slack < res->gap_open ? 0 : (slack - res->gap_open) / res->gap_extend + 1;
-      const int64_t jlo = (int64_t)j.je - j.ie - kmax;
-      if (jlo > 0) {
-        j.jlo = (int32_t)jlo;
-        j.t_start += (uint64_t)jlo;
-        j.je -= (int32_t)jlo;
-      }
+  }
+  // short jobs: count per host thread, then fill in place (hit order kept)
+  {
+    const unsigned T = host_threads(sel.size(), 1u << 16);
+    std::vector<uint64_t> n_small(T + 1, 0), n_large(T + 1, 0), cap(T, 0);
+    parallel_for(sel.size(), T, [&](unsigned t, size_t b, size_t e) {
+      TbJob j;
+      for (size_t x = b; x < e; ++x)
+        if (make_short(sel[x], j)) {
+          ++(small(j) ? n_small : n_large)[t + 1];
+          cap[t] += (uint64_t)j.ie + j.je + 1;
+        }
+    });
+    for (unsigned t = 0; t < T; ++t) {
+      n_small[t + 1] += n_small[t];
+      n_large[t + 1] += n_large[t];
+      cap_total += cap[t];
     }
-    j.wpr = (uint32_t)((j.je + 7) / 8);
-    (small(j) ? tjobs : jobs).push_back(j);
-    cap_total += (uint64_t)j.ie + j.je + 1;
+    tjobs.resize(n_small[T]);
+    jobs.resize(n_large[T]);
+    parallel_for(sel.size(), T, [&](unsigned t, size_t b, size_t e) {
+      uint64_t ks = n_small[t], kl = n_large[t];
+      TbJob j;
+      for (size_t x = b; x < e; ++x)
+        if (make_short(sel[x], j)) {
+          if (small(j)) tjobs[ks++] = j;
+          else jobs[kl++] = j;
+        }
+    });
   }
   if (tjobs.size() < std::max<uint64_t>(thread_min, 1)) {
     jobs.insert(jobs.end(), tjobs.begin(), tjobs.end());
@@ -1206,8 +1261,11 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
         for (size_t x = 0; x < tjobs.size(); ++x)
           key[x] = ~(((uint64_t)(uint32_t)tjobs[x].ie << 32) | (uint32_t)tjobs[x].je);
         const std::vector<uint32_t> ord = radix_order(key);
-        std::vector<TbJob> sorted(tjobs.size());
-        for (size_t x = 0; x < ord.size(); ++x) sorted[x] = tjobs[ord[x]];
+        std::vector<TbJob>& sorted = ctx->h_tb2;
+        sorted.resize(tjobs.size());
+        parallel_for(ord.size(), host_threads(ord.size(), 1u << 16), [&](unsigned, size_t b, size_t e) {
+          for (size_t x = b; x < e; ++x) sorted[x] = tjobs[ord[x]];
+        });
         tjobs.swap(sorted);
       }
     }

@@ -62,7 +62,7 @@ struct dsa_ctx {
   // mapped (up to the budget) instead of returning it at every synchronize
   cudaMemPool_t pool = nullptr;
   // host staging reused across calls (large fresh vectors cost page faults)
-  std::vector<dsa::TbJob> h_tb;
+  std::vector<dsa::TbJob> h_tb, h_tb2;
   std::mutex mu;
 
   int alloc(void** p, size_t bytes, cudaStream_t on = nullptr);
