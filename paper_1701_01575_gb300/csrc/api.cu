@@ -50,7 +50,8 @@ void parallel_for(size_t n, unsigned T, F&& fn) {
 
 // Stable ascending order of 64-bit keys: identity when they already are in
 // order, else an LSD radix sort on 11-bit digits (digits shared by every key
-// are skipped).
+// are skipped); each pass counts per host thread, then scatters in parallel
+// (thread t's items of a digit follow those of threads < t: stable).
 std::vector<uint32_t> radix_order(const std::vector<uint64_t>& key) {
   const size_t n = key.size();
   std::vector<uint32_t> idx(n);
@@ -59,15 +60,36 @@ std::vector<uint32_t> radix_order(const std::vector<uint64_t>& key) {
   uint64_t all_or = 0, all_and = ~0ull;
   for (uint64_t k : key) { all_or |= k; all_and &= k; }
   const uint64_t varying = all_or ^ all_and;
+  const unsigned T = host_threads(n, 1u << 16);
+  constexpr size_t B = 2048;
   std::vector<uint32_t> tmp(n);
-  std::vector<uint32_t> cnt(2049);
+  std::vector<uint64_t> cur(n), nxt(n);   // keys in the current order
+  for (size_t x = 0; x < n; ++x) cur[x] = key[x];
+  std::vector<size_t> cnt((size_t)T * B);
   for (int shift = 0; shift < 64; shift += 11) {
     if (((varying >> shift) & 0x7FFull) == 0) continue;
-    std::fill(cnt.begin(), cnt.end(), 0u);
-    for (size_t x = 0; x < n; ++x) ++cnt[((key[idx[x]] >> shift) & 0x7FF) + 1];
-    for (size_t b = 1; b < cnt.size(); ++b) cnt[b] += cnt[b - 1];
-    for (size_t x = 0; x < n; ++x) tmp[cnt[(key[idx[x]] >> shift) & 0x7FF]++] = idx[x];
+    std::fill(cnt.begin(), cnt.end(), 0);
+    parallel_for(n, T, [&](unsigned t, size_t b, size_t e) {
+      size_t* c = cnt.data() + (size_t)t * B;
+      for (size_t x = b; x < e; ++x) ++c[(cur[x] >> shift) & 0x7FF];
+    });
+    size_t run = 0;   // exclusive offsets in (digit, thread) order
+    for (size_t d = 0; d < B; ++d)
+      for (unsigned t = 0; t < T; ++t) {
+        const size_t c = cnt[(size_t)t * B + d];
+        cnt[(size_t)t * B + d] = run;
+        run += c;
+      }
+    parallel_for(n, T, [&](unsigned t, size_t b, size_t e) {
+      size_t* c = cnt.data() + (size_t)t * B;
+      for (size_t x = b; x < e; ++x) {
+        const size_t dst = c[(cur[x] >> shift) & 0x7FF]++;
+        tmp[dst] = idx[x];
+        nxt[dst] = cur[x];
+      }
+    });
     idx.swap(tmp);
+    cur.swap(nxt);
   }
   return idx;
 }
@@ -1126,17 +1148,41 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
     j.hit = (uint32_t)h;
     j.q_start = qs->h_off[hit.query_id];
     j.t_start = db->h_off[hit.target_id] + hit.t_offset;
+    // diagonal window of the thread-per-hit kernel's 16-row strips:
+    // diagonals dlo .. dhi of every optimal path (default: whole rows)
+    int64_t dlo = -(int64_t)j.ie, dhi = j.je;
     if (band_ok) {
       // deletions on any path reaching the hit: score <= ie * max(S, 0) - (o + (k - 1) e)
+      const int64_t o = res->gap_open, e = res->gap_extend;
       const int64_t slack = (int64_t)j.ie * smax_pos - hit.score;
-      const int64_t kmax = slack < res->gap_open ? 0 : (slack - res->gap_open) / res->gap_extend + 1;
+      const int64_t kmax = slack < o ? 0 : (slack - o) / e + 1;
       const int64_t jlo = (int64_t)j.je - j.ie - kmax;
       if (jlo > 0) {
         j.jlo = (int32_t)jlo;
         j.t_start += (uint64_t)jlo;
         j.je -= (int32_t)jlo;
       }
+      // insertions: each one removes an M (at most max S) and costs at least e
+      // (the first o): score <= max(S, 0)(ie - k) - (o + (k - 1) e)
+      const int64_t imax = slack < o ? 0 : (slack - o + e) / (smax_pos + e);
+      // a cell (i, j) on the path: (je - j) - (ie - i) = D after - I after
+      const int64_t dn = (int64_t)j.je - j.ie;
+      dlo = dn - kmax;
+      dhi = dn + imax;
+    } else if (diag_ok) {
+      // paths from (0, 0): the total gap length g is bounded (see the long pairs)
+      const int64_t num = (int64_t)smax_pos * ((int64_t)j.ie + j.je) - 2 * (int64_t)hit.score -
+                          2 * ((int64_t)res->gap_open - res->gap_extend);
+      const int64_t gmax = num < 0 ? 0 : num / ((int64_t)smax_pos + 2 * (int64_t)res->gap_extend);
+      const int64_t dn = (int64_t)j.je - j.ie;
+      if (gmax >= std::llabs(dn)) {
+        const int64_t half = (gmax - std::llabs(dn)) / 2;
+        dlo = std::min<int64_t>(0, dn) - half;
+        dhi = std::max<int64_t>(0, dn) + half;
+      }
     }
+    j.dlo = (int32_t)std::max<int64_t>(dlo, -(int64_t)j.ie);
+    j.wc = (int32_t)std::min<int64_t>(j.je, 16 + dhi - j.dlo);
     j.wpr = (uint32_t)((j.je + 7) / 8);
     return true;
   };
@@ -1245,21 +1291,32 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
       // groups of 32 hits share a layout padded to their largest (ie, je):
       // keep the given order when that pads little, else order by (ie, je)
       // descending
-      uint64_t cells = 0, padded = 0;
-      for (size_t g = 0; g < tjobs.size(); g += 32) {
-        int32_t im = 0, jm = 0;
-        const size_t g1 = std::min(tjobs.size(), g + 32);
-        for (size_t x = g; x < g1; ++x) {
-          im = std::max(im, tjobs[x].ie);
-          jm = std::max(jm, tjobs[x].je);
-          cells += (uint64_t)tjobs[x].ie * tjobs[x].je;
+      const size_t n_groups = (tjobs.size() + 31) / 32;
+      const unsigned T = host_threads(tjobs.size(), 1u << 16);
+      std::vector<uint64_t> cells_t(T, 0), padded_t(T, 0);
+      parallel_for(n_groups, T, [&](unsigned t, size_t gb, size_t ge) {
+        for (size_t g = gb; g < ge; ++g) {
+          int32_t im = 0, jm = 0;
+          const size_t x1 = std::min(tjobs.size(), 32 * g + 32);
+          for (size_t x = 32 * g; x < x1; ++x) {
+            im = std::max(im, tjobs[x].ie);
+            jm = std::max(jm, tjobs[x].wc);
+            cells_t[t] += (uint64_t)tjobs[x].ie * tjobs[x].wc;
+          }
+          padded_t[t] += (uint64_t)im * jm * (x1 - 32 * g);
         }
-        padded += (uint64_t)im * jm * (g1 - g);
+      });
+      uint64_t cells = 0, padded = 0;
+      for (unsigned t = 0; t < T; ++t) {
+        cells += cells_t[t];
+        padded += padded_t[t];
       }
       if (padded > cells + cells / 4) {
         std::vector<uint64_t> key(tjobs.size());
-        for (size_t x = 0; x < tjobs.size(); ++x)
-          key[x] = ~(((uint64_t)(uint32_t)tjobs[x].ie << 32) | (uint32_t)tjobs[x].je);
+        parallel_for(tjobs.size(), T, [&](unsigned, size_t b, size_t e) {
+          for (size_t x = b; x < e; ++x)
+            key[x] = ~(((uint64_t)(uint32_t)tjobs[x].ie << 32) | (uint32_t)tjobs[x].wc);
+        });
         const std::vector<uint32_t> ord = radix_order(key);
         std::vector<TbJob>& sorted = ctx->h_tb2;
         sorted.resize(tjobs.size());
@@ -1277,18 +1334,19 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
       size_t k1 = k0;
       while (k1 < tjobs.size()) {
         const size_t g1 = std::min(tjobs.size(), k1 + 32);
-        int32_t ie_max = 1, je_max = 1;
+        int32_t ie_max = 1, je_max = 1, wc_max = 1;
         for (size_t x = k1; x < g1; ++x) {
           ie_max = std::max(ie_max, tjobs[x].ie);
           je_max = std::max(je_max, tjobs[x].je);
+          wc_max = std::max(wc_max, tjobs[x].wc);
         }
         const uint64_t strips = ((uint64_t)ie_max + 15) / 16;
-        const uint64_t w = strips * (uint64_t)je_max * 64;
+        const uint64_t w = strips * (uint64_t)wc_max * 64;
         if (k1 > k0 && dir + w > dir_limit) break;
         for (size_t x = k1; x < g1; ++x) {
           const uint32_t lane = (uint32_t)(x - k1);
           tjobs[x].dir_off = dir + lane;
-          tjobs[x].wpr = (uint32_t)je_max;
+          tjobs[x].wpr = (uint32_t)wc_max;
           tjobs[x].scr_off = scr + lane;
           tjobs[x].cig_off = cig;
           cig += (uint64_t)tjobs[x].ie + tjobs[x].je + 1;

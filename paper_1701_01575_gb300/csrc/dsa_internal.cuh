@@ -246,6 +246,10 @@ struct TbJob {
   uint32_t wpr;       // direction words per row
   int32_t jlo;        // first target column of the recomputed band (0 = whole rectangle);
                       // > 0: column jlo is a wall (H = -inf below row 0)
+  // thread-per-hit kernel: diagonal window of each 16-row strip (relative to
+  // the band): wc stored columns from clamp(i0 + 1 + dlo, 1, je - wc + 1)
+  int32_t dlo;
+  int32_t wc;
   uint32_t pad;
 };
 int launch_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,

@@ -212,12 +212,21 @@ __global__ void __launch_bounds__(128) k_traceback(
 // query rows held in registers, column by column, with the same 4-bit
 // decisions as above.  The decisions of a strip column (TROWS nibbles, two
 // words) go to a layout interleaved over the 32 hits of a warp,
-//   word (strip s, column j, half h) of lane l at
-//   dir_off + ((s * cols + j - 1) * 2 + h) * 32     (dir_off = group base + l),
+//   word (strip s, stored column c, half h) of lane l at
+//   dir_off + ((s * cols + c) * 2 + h) * 32        (dir_off = group base + l),
 // so every store of the warp is one 128-byte line; the strip's bottom row
-// (H, F) is handed to the next strip through an interleaved scratch row.
-// Each thread then walks its own hit back, so the 32 walks of a warp run side
-// by side instead of one after another.
+// (H, F) is handed to the next strip through an interleaved scratch row
+// indexed by target column.  Each thread then walks its own hit back, so the
+// 32 walks of a warp run side by side instead of one after another.
+//
+// Diagonal window: the host bounds the diagonals j - i of every optimal path
+// to dlo .. dlo + wc - TROWS (from the score: deletions, insertions or total
+// gaps are bounded as for the column band), so strip s keeps only the wc
+// columns from jlo_s = clamp(i0 + 1 + dlo, 1, je - wc + 1).  Cells left of
+// jlo_s and above-right of the previous strip's columns lie outside the
+// band and enter as -inf; a recomputed value is then at most the full DP's
+// and at least the band-restricted DP's, which agree on every cell of an
+// optimal path and on every candidate that ties there.
 constexpr int TROWS = 16;
 
 __global__ void __launch_bounds__(128) k_traceback_thread(
@@ -237,31 +246,41 @@ __global__ void __launch_bounds__(128) k_traceback_thread(
   const uint8_t* t = tcodes + jb.t_start;
   uint32_t* D = dir + jb.dir_off;
   int2* scr = scratch + jb.scr_off;
-  const uint64_t cols = jb.wpr;   // columns of the group's layout (>= je)
+  const uint64_t cols = jb.wpr;   // stored columns per strip in the group's layout (>= wc)
+  const int32_t wc = jb.wc;       // this hit's stored columns per strip (<= je)
+  auto strip_jlo = [&](int32_t i0) { return max(1, min(i0 + 1 + jb.dlo, je - wc + 1)); };
+  const int2 NEGP = make_int2(NEG32, NEG32);
 
   if (ie > 0 && je > 0) {
+    int32_t plo = 1, phi = je;   // columns the previous strip computed
     for (int32_t i0 = 0, s = 0; i0 < ie; i0 += TROWS, ++s) {
       const int rows = min(TROWS, ie - i0);
       const bool last = i0 + rows == ie;
+      const int32_t jlo = strip_jlo(i0), jhi = jlo + wc - 1;
+      const bool wall = jlo > 1 || jb.jlo > 0;   // column jlo - 1 is -inf below row 0
       int32_t H[TROWS], E[TROWS];
       int qa[TROWS];
 #pragma unroll
       for (int r = 0; r < TROWS; ++r) {
-        H[r] = jb.jlo > 0 ? NEG32 : h_col0(mode, fe, i0 + r + 1, o, e);
+        H[r] = wall ? NEG32 : h_col0(mode, fe, i0 + r + 1, o, e);
         E[r] = NEG32;
         qa[r] = r < rows ? q[i0 + r] * A : 0;
       }
-      int32_t diag = (jb.jlo > 0 && i0 > 0) ? NEG32 : h_col0(mode, fe, i0, o, e);
+      // H[i0][jlo - 1]
+      int32_t diag;
+      if (i0 == 0) diag = h_row0(mode, fe, jlo - 1, o, e);
+      else if (jlo == 1) diag = jb.jlo > 0 ? NEG32 : h_col0(mode, fe, i0, o, e);
+      else diag = (jlo - 1 >= plo && jlo - 1 <= phi) ? scr[(uint64_t)(jlo - 2) * 32].x : NEG32;
       uint32_t* Ds = D + (uint64_t)s * cols * 64;
       // loads run one column ahead of the arithmetic
-      int n_a = t[0];
-      int2 n_v = i0 > 0 ? scr[0] : make_int2(0, 0);
-      for (int32_t j = 1; j <= je; ++j) {
+      int n_a = t[jlo - 1];
+      int2 n_v = (i0 > 0 && jlo <= phi) ? scr[(uint64_t)(jlo - 1) * 32] : NEGP;
+      for (int32_t j = jlo; j <= jhi; ++j) {
         const int a = n_a;
         const int2 v = n_v;
-        if (j < je) {
+        if (j < jhi) {
           n_a = t[j];
-          if (i0 > 0) n_v = scr[(uint64_t)j * 32];
+          n_v = (i0 > 0 && j + 1 <= phi) ? scr[(uint64_t)j * 32] : NEGP;
         }
         int32_t Hp, F;
         if (i0 == 0) {
@@ -297,16 +316,24 @@ __global__ void __launch_bounds__(128) k_traceback_thread(
             Hp = v;
           }
         }
-        Ds[(uint64_t)(j - 1) * 64] = w0;
-        if (rows > 8) Ds[(uint64_t)(j - 1) * 64 + 32] = w1;
+        const uint64_t c = (uint64_t)(j - jlo);
+        Ds[c * 64] = w0;
+        if (rows > 8) Ds[c * 64 + 32] = w1;
         if (!last) scr[(uint64_t)(j - 1) * 32] = make_int2(Hp, F);
       }
+      plo = jlo;
+      phi = jhi;
     }
   }
-  auto nibble = [&](int32_t i, int32_t j) -> uint32_t {
+  // decision nibble of (i, j); false outside the stored window (only a
+  // corrupt decision could lead there)
+  auto nibble = [&](int32_t i, int32_t j, uint32_t& nib) -> bool {
     const uint32_t r = (uint32_t)(i - 1) % TROWS, s = (uint32_t)(i - 1) / TROWS;
-    const uint32_t w = D[(((uint64_t)s * cols + (uint32_t)(j - 1)) * 2 + (r >> 3)) * 32];
-    return (w >> (4 * (r & 7))) & 15u;
+    const int32_t c = j - strip_jlo((int32_t)s * TROWS);
+    if (c < 0 || c >= wc) return false;
+    const uint32_t w = D[(((uint64_t)s * cols + (uint32_t)c) * 2 + (r >> 3)) * 32];
+    nib = (w >> (4 * (r & 7))) & 15u;
+    return true;
   };
   RevCigar c;
   c.out = cig_tmp + jb.cig_off;
@@ -322,19 +349,21 @@ __global__ void __launch_bounds__(128) k_traceback_thread(
         while (i > 0) { c.emit(1); --i; }
         break;
       }
-      const uint32_t src = nibble(i, j) & 3u;
+      uint32_t nib;
+      if (!nibble(i, j, nib)) break;
+      const uint32_t src = nib & 3u;
       if (src == 3) break;
       if (src == 0) { c.emit(0); --i; --j; }
       else st = src == 1 ? 1 : 2;
     } else if (st == 1) {
-      if (i <= 0 || j <= 0) break;
-      const uint32_t nib = nibble(i, j);
+      uint32_t nib;
+      if (i <= 0 || j <= 0 || !nibble(i, j, nib)) break;
       c.emit(1);
       if (nib & 8u) st = 0;
       --i;
     } else {
-      if (i <= 0 || j <= 0) break;
-      const uint32_t nib = nibble(i, j);
+      uint32_t nib;
+      if (i <= 0 || j <= 0 || !nibble(i, j, nib)) break;
       c.emit(2);
       if (nib & 4u) st = 0;
       --j;
