@@ -824,7 +824,6 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
       return fail(rc);
   } else {
     std::vector<PairJob> jobs;
-    jobs.reserve(n_pairs);
     std::vector<LongJob> ljobs;
     std::vector<uint64_t> p16;   // pairs for the packed int16 kernel
     uint64_t scr = 0, cells = 0, lcells = 0, p16cells = 0;
@@ -835,17 +834,46 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
     const int64_t w16 = std::max<int64_t>({(int64_t)std::abs(v.smax), (int64_t)std::abs(v.smin), o, e});
     const bool local16 = mode == DSA_LOCAL && o >= 1 && o + e <= 4096 && v.smax + o < 8192 && v.smin > -8192;
     const bool packed_ok = !(flags & (DSA_FORCE_INT32 | DSA_PLAIN_FORM));
+    // classify on host threads: packed pairs (filled in place, pair order
+    // kept); long and int32 pairs are few or absent and follow serially
+    enum : uint8_t { C_P16, C_LONG, C_INT32 };
+    std::vector<uint8_t> cls(n_pairs);
+    {
+      const unsigned T = host_threads(n_pairs, 1u << 16);
+      std::vector<uint64_t> n16(T + 1, 0), cells_t(T, 0), c16_t(T, 0);
+      parallel_for(n_pairs, T, [&](unsigned t, size_t b, size_t x1) {
+        for (size_t k = b; k < x1; ++k) {
+          const dsa_pair& p = hp[k];
+          const uint64_t m = qs->h_len[p.query_id];
+          const uint64_t c = m * p.t_len;
+          cells_t[t] += c;
+          const bool fits16 = local16 || ((int64_t)(m + p.t_len) * w16 + o < 12000 && o + e < 4096);
+          if (packed_ok && fits16 && m >= 1 && p.t_len >= 1 && c < LONG_PAIR_CELLS) {
+            cls[k] = C_P16;
+            ++n16[t + 1];
+            c16_t[t] += c;
+          } else {
+            cls[k] = c >= LONG_PAIR_CELLS ? C_LONG : C_INT32;
+          }
+        }
+      });
+      for (unsigned t = 0; t < T; ++t) {
+        n16[t + 1] += n16[t];
+        cells += cells_t[t];
+        p16cells += c16_t[t];
+      }
+      p16.resize(n16[T]);
+      parallel_for(n_pairs, T, [&](unsigned t, size_t b, size_t x1) {
+        uint64_t pos = n16[t];
+        for (size_t k = b; k < x1; ++k)
+          if (cls[k] == C_P16) p16[pos++] = k;
+      });
+    }
     for (uint64_t k = 0; k < n_pairs; ++k) {
+      if (cls[k] == C_P16) continue;
       const dsa_pair& p = hp[k];
       const uint64_t m = qs->h_len[p.query_id];
-      cells += m * p.t_len;
-      const bool fits16 = local16 || ((int64_t)(m + p.t_len) * w16 + o < 12000 && o + e < 4096);
-      if (packed_ok && fits16 && m >= 1 && p.t_len >= 1 && m * p.t_len < LONG_PAIR_CELLS) {
-        p16.push_back(k);
-        p16cells += m * p.t_len;
-        continue;
-      }
-      if (m * p.t_len >= LONG_PAIR_CELLS) {
+      if (cls[k] == C_LONG) {
         const uint64_t nb = (m + band - 1) / band;
         LongJob lj{qs->h_off[p.query_id], db->h_off[p.target_id] + p.t_offset, bnd, prog, cand,
                    (int32_t)m, (int32_t)p.t_len, (uint32_t)k, 0};
@@ -904,46 +932,61 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
     }
     if (!p16.empty()) {
       // order by (query length, window length); two pairs of equal query length per thread
-      {
-        std::vector<uint64_t> key(p16.size());
-        for (size_t x = 0; x < p16.size(); ++x) {
+      const unsigned T = host_threads(p16.size(), 1u << 16);
+      std::vector<uint64_t> key(p16.size());
+      parallel_for(p16.size(), T, [&](unsigned, size_t b, size_t x1) {
+        for (size_t x = b; x < x1; ++x) {
           const dsa_pair& pp = hp[p16[x]];
           key[x] = ((uint64_t)qs->h_len[pp.query_id] << 32) | pp.t_len;
         }
+      });
+      {
         const std::vector<uint32_t> ord = radix_order(key);
-        std::vector<uint64_t> sorted(p16.size());
-        for (size_t x = 0; x < ord.size(); ++x) sorted[x] = p16[ord[x]];
+        std::vector<uint64_t> sorted(p16.size()), skey(p16.size());
+        parallel_for(ord.size(), T, [&](unsigned, size_t b, size_t x1) {
+          for (size_t x = b; x < x1; ++x) {
+            sorted[x] = p16[ord[x]];
+            skey[x] = key[ord[x]];
+          }
+        });
         p16.swap(sorted);
+        key.swap(skey);
       }
-      std::vector<Pair16Job> pj;
-      pj.reserve(p16.size() / 2 + 1);
+      // a job starts at every even offset inside a run of equal query length
+      std::vector<uint32_t> starts;
+      starts.reserve(p16.size() / 2 + 1);
       uint32_t max_n = 1;
-      for (size_t x = 0; x < p16.size();) {
-        const dsa_pair& a = hp[p16[x]];
-        Pair16Job j{};
-        j.m = (int32_t)qs->h_len[a.query_id];
-        j.q_lo = qs->h_off[a.query_id];
-        j.t_lo = db->h_off[a.target_id] + a.t_offset;
-        j.n_lo = (int32_t)a.t_len;
-        j.out_lo = (uint32_t)p16[x];
-        max_n = std::max(max_n, a.t_len);
-        if (x + 1 < p16.size() && qs->h_len[hp[p16[x + 1]].query_id] == (uint32_t)j.m) {
-          const dsa_pair& b = hp[p16[x + 1]];
-          j.q_hi = qs->h_off[b.query_id];
-          j.t_hi = db->h_off[b.target_id] + b.t_offset;
-          j.n_hi = (int32_t)b.t_len;
-          j.out_hi = (uint32_t)p16[x + 1];
-          max_n = std::max(max_n, b.t_len);
-          x += 2;
-        } else {
-          j.q_hi = j.q_lo;
-          j.t_hi = j.t_lo;
-          j.n_hi = 0;
-          j.out_hi = NONE;
-          x += 1;
-        }
-        pj.push_back(j);
+      for (size_t x = 0, run = 0; x < p16.size(); ++x) {
+        if (x > 0 && (key[x] >> 32) != (key[x - 1] >> 32)) run = x;
+        if (((x - run) & 1) == 0) starts.push_back((uint32_t)x);
+        max_n = std::max<uint32_t>(max_n, (uint32_t)key[x]);
       }
+      std::vector<Pair16Job> pj(starts.size());
+      parallel_for(starts.size(), T, [&](unsigned, size_t b, size_t x1) {
+        for (size_t k = b; k < x1; ++k) {
+          const size_t x = starts[k];
+          const dsa_pair& a = hp[p16[x]];
+          Pair16Job j{};
+          j.m = (int32_t)(key[x] >> 32);
+          j.q_lo = qs->h_off[a.query_id];
+          j.t_lo = db->h_off[a.target_id] + a.t_offset;
+          j.n_lo = (int32_t)a.t_len;
+          j.out_lo = (uint32_t)p16[x];
+          if (x + 1 < p16.size() && (key[x + 1] >> 32) == (key[x] >> 32)) {
+            const dsa_pair& bb = hp[p16[x + 1]];
+            j.q_hi = qs->h_off[bb.query_id];
+            j.t_hi = db->h_off[bb.target_id] + bb.t_offset;
+            j.n_hi = (int32_t)bb.t_len;
+            j.out_hi = (uint32_t)p16[x + 1];
+          } else {
+            j.q_hi = j.q_lo;
+            j.t_hi = j.t_lo;
+            j.n_hi = 0;
+            j.out_hi = NONE;
+          }
+          pj[k] = j;
+        }
+      });
       DevBuf d_pj;
       if ((rc = upload(ctx, d_pj, pj))) return fail(rc);
       bool bytes = A <= 4;   // byte-permute substitution form
