@@ -1174,11 +1174,33 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
   for (int8_t v : res->matrix) smax_pos = std::max<int>(smax_pos, v);
   const bool band_ok = res->mode == DSA_SEMIGLOBAL && (res->free_ends & DSA_FREE_T_BEGIN) &&
                        res->gap_extend > 0;
-  // diagonal band of long pairs whose paths start at (0, 0)
-  const bool diag_ok = (res->mode == DSA_GLOBAL ||
-                        (res->mode == DSA_SEMIGLOBAL &&
-                         !(res->free_ends & (DSA_FREE_Q_BEGIN | DSA_FREE_T_BEGIN)))) &&
-                       smax_pos + 2 * res->gap_extend > 0;
+  // Diagonal bands from the total gap length g of a path reaching (ie, je):
+  // it has at most (ie + je - g) / 2 M columns whatever its start, so
+  // 2 score <= max(S, 0)(ie + je) - g (max(S, 0) + 2e) - 2 (o - e) [g > 0].
+  // A cell (i, j) on it has |dn - d| <= g (gaps after it; d = j - i,
+  // dn = je - ie) and, for paths from (0, 0), |d| <= g as well (gaps before).
+  const bool diag_ok = smax_pos + 2 * res->gap_extend > 0;
+  const bool from_origin = res->mode == DSA_GLOBAL ||
+                           (res->mode == DSA_SEMIGLOBAL &&
+                            !(res->free_ends & (DSA_FREE_Q_BEGIN | DSA_FREE_T_BEGIN)));
+  // diagonals dlo..dhi of every optimal path reaching (ie, je) (false: none narrower)
+  auto diag_window = [&](int32_t ie, int32_t je, int32_t score, int64_t& dlo, int64_t& dhi) -> bool {
+    if (!diag_ok) return false;
+    const int64_t num = (int64_t)smax_pos * ((int64_t)ie + je) - 2 * (int64_t)score -
+                        2 * ((int64_t)res->gap_open - res->gap_extend);
+    const int64_t gmax = num < 0 ? 0 : num / ((int64_t)smax_pos + 2 * (int64_t)res->gap_extend);
+    const int64_t dn = (int64_t)je - ie;
+    if (!from_origin) {
+      dlo = dn - gmax;
+      dhi = dn + gmax;
+      return true;
+    }
+    if (gmax < std::llabs(dn)) return false;
+    const int64_t half = (gmax - std::llabs(dn)) / 2;
+    dlo = std::min<int64_t>(0, dn) - half;
+    dhi = std::max<int64_t>(0, dn) + half;
+    return true;
+  };
   // hit h -> short job (false: the hit is skipped or is a long pair)
   auto make_short = [&](uint64_t h, TbJob& j) -> bool {
     const dsa_hit& hit = res->h_hits[h];
@@ -1212,16 +1234,11 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
       const int64_t dn = (int64_t)j.je - j.ie;
       dlo = dn - kmax;
       dhi = dn + imax;
-    } else if (diag_ok) {
-      // paths from (0, 0): the total gap length g is bounded (see the long pairs)
-      const int64_t num = (int64_t)smax_pos * ((int64_t)j.ie + j.je) - 2 * (int64_t)hit.score -
-                          2 * ((int64_t)res->gap_open - res->gap_extend);
-      const int64_t gmax = num < 0 ? 0 : num / ((int64_t)smax_pos + 2 * (int64_t)res->gap_extend);
-      const int64_t dn = (int64_t)j.je - j.ie;
-      if (gmax >= std::llabs(dn)) {
-        const int64_t half = (gmax - std::llabs(dn)) / 2;
-        dlo = std::min<int64_t>(0, dn) - half;
-        dhi = std::max<int64_t>(0, dn) + half;
+    } else {
+      int64_t a, b;
+      if (diag_window(j.ie, j.je, hit.score, a, b)) {
+        dlo = a;
+        dhi = b;
       }
     }
     j.dlo = (int32_t)std::max<int64_t>(dlo, -(int64_t)j.ie);
@@ -1245,26 +1262,12 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
       lj.hit = (uint32_t)h;
       lj.dlo = 0;
       lj.wc = lj.je;
-      if (diag_ok && lj.ie > 0 && lj.je > 0) {
-        // A path from (0, 0) to (ie, je) with g gap columns has (ie + je - g) / 2
-        // M columns, so 2 score <= max(S, 0) (ie + je) - g (max(S, 0) + 2e)
-        // - 2 (o - e) [g > 0]; a cell (i, j) on it has |d| + |dn - d| <= g with
-        // d = j - i, dn = je - ie.  Every optimal path therefore stays in the
-        // diagonals dlo..dhi below.
-        const int64_t num = (int64_t)smax_pos * ((int64_t)lj.ie + lj.je) - 2 * (int64_t)hit.score -
-                            2 * ((int64_t)res->gap_open - res->gap_extend);
-        const int64_t den = (int64_t)smax_pos + 2 * (int64_t)res->gap_extend;
-        const int64_t gmax = num < 0 ? 0 : num / den;
-        const int64_t dn = (int64_t)lj.je - lj.ie;
-        if (gmax >= std::llabs(dn)) {
-          const int64_t half = (gmax - std::llabs(dn)) / 2;
-          const int64_t dlo = std::min<int64_t>(0, dn) - half;
-          const int64_t dhi = std::max<int64_t>(0, dn) + half;
-          const int64_t wc = (int64_t)band + dhi - dlo;
-          if (wc < lj.je) {
-            lj.dlo = (int32_t)dlo;
-            lj.wc = (int32_t)wc;
-          }
+      int64_t dlo, dhi;
+      if (lj.ie > 0 && lj.je > 0 && diag_window(lj.ie, lj.je, hit.score, dlo, dhi)) {
+        const int64_t wc = (int64_t)band + dhi - dlo;
+        if (wc < lj.je) {
+          lj.dlo = (int32_t)std::max<int64_t>(dlo, -(int64_t)lj.ie);
+          lj.wc = (int32_t)wc;
         }
       }
       lj.wpr = (uint32_t)((lj.wc + 7) / 8);

@@ -339,11 +339,13 @@ def test_long_pairs_banded_score_and_traceback(ctx, mode, fe):
     check_traceback(r.hits(), r.cigar(), wl.queries, wl.db, wl.matrix, 5, 2, mode, fe)
 
 
-@pytest.mark.parametrize("mode,fe", [(dsa.GLOBAL, 15), (dsa.SEMIGLOBAL, 10)])
+@pytest.mark.parametrize("mode,fe", [(dsa.GLOBAL, 15), (dsa.SEMIGLOBAL, 10), (dsa.LOCAL, 15),
+                                     (dsa.SEMIGLOBAL, 15), (dsa.SEMIGLOBAL, 3)])
 def test_long_pair_traceback_diagonal_band(ctx, mode, fe):
-    """Long pairs whose paths start at (0, 0): related pairs (narrow diagonal
-    band from the score bound), an unrelated pair (band wider than the target:
-    whole rows), lengths not multiples of the 256-row bands, m != n."""
+    """Diagonal bands of the long-pair traceback (two-sided for paths from
+    (0, 0), one-sided from the end cell otherwise): related pairs (narrow
+    band), an unrelated pair (band wider than the target: whole rows), lengths
+    not multiples of the 256-row bands, m != n."""
     rng = np.random.default_rng(123 + fe)
     S = W.dna_matrix(2, -3)
     a = rng.integers(0, 4, 3001).astype(np.uint8)
