@@ -842,20 +842,24 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
       const unsigned T = host_threads(n_pairs, 1u << 16);
       std::vector<uint64_t> n16(T + 1, 0), cells_t(T, 0), c16_t(T, 0);
       parallel_for(n_pairs, T, [&](unsigned t, size_t b, size_t x1) {
+        uint64_t n = 0, cl = 0, c16 = 0;   // thread-local: no shared cache lines in the loop
         for (size_t k = b; k < x1; ++k) {
           const dsa_pair& p = hp[k];
           const uint64_t m = qs->h_len[p.query_id];
           const uint64_t c = m * p.t_len;
-          cells_t[t] += c;
+          cl += c;
           const bool fits16 = local16 || ((int64_t)(m + p.t_len) * w16 + o < 12000 && o + e < 4096);
           if (packed_ok && fits16 && m >= 1 && p.t_len >= 1 && c < LONG_PAIR_CELLS) {
             cls[k] = C_P16;
-            ++n16[t + 1];
-            c16_t[t] += c;
+            ++n;
+            c16 += c;
           } else {
             cls[k] = c >= LONG_PAIR_CELLS ? C_LONG : C_INT32;
           }
         }
+        n16[t + 1] = n;
+        cells_t[t] = cl;
+        c16_t[t] = c16;
       });
       for (unsigned t = 0; t < T; ++t) {
         n16[t + 1] += n16[t];
@@ -1281,11 +1285,15 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
     std::vector<uint64_t> n_small(T + 1, 0), n_large(T + 1, 0), cap(T, 0);
     parallel_for(sel.size(), T, [&](unsigned t, size_t b, size_t e) {
       TbJob j;
+      uint64_t ns = 0, nl = 0, cp = 0;   // thread-local: no shared cache lines in the loop
       for (size_t x = b; x < e; ++x)
         if (make_short(sel[x], j)) {
-          ++(small(j) ? n_small : n_large)[t + 1];
-          cap[t] += (uint64_t)j.ie + j.je + 1;
+          ++(small(j) ? ns : nl);
+          cp += (uint64_t)j.ie + j.je + 1;
         }
+      n_small[t + 1] = ns;
+      n_large[t + 1] = nl;
+      cap[t] = cp;
     });
     for (unsigned t = 0; t < T; ++t) {
       n_small[t + 1] += n_small[t];
@@ -1341,16 +1349,19 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
       const unsigned T = host_threads(tjobs.size(), 1u << 16);
       std::vector<uint64_t> cells_t(T, 0), padded_t(T, 0);
       parallel_for(n_groups, T, [&](unsigned t, size_t gb, size_t ge) {
+        uint64_t cl = 0, pd = 0;
         for (size_t g = gb; g < ge; ++g) {
           int32_t im = 0, jm = 0;
           const size_t x1 = std::min(tjobs.size(), 32 * g + 32);
           for (size_t x = 32 * g; x < x1; ++x) {
             im = std::max(im, tjobs[x].ie);
             jm = std::max(jm, tjobs[x].wc);
-            cells_t[t] += (uint64_t)tjobs[x].ie * tjobs[x].wc;
+            cl += (uint64_t)tjobs[x].ie * tjobs[x].wc;
           }
-          padded_t[t] += (uint64_t)im * jm * (x1 - 32 * g);
+          pd += (uint64_t)im * jm * (x1 - 32 * g);
         }
+        cells_t[t] = cl;
+        padded_t[t] = pd;
       });
       uint64_t cells = 0, padded = 0;
       for (unsigned t = 0; t < T; ++t) {
