@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--targets", type=int, default=500_000)
     ap.add_argument("--queries", type=int, default=32)
+    ap.add_argument("--reads", type=int, default=1_000_000,
+                    help="reads_vs_windows: number of reads (profiling runs use a smaller case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -174,7 +176,7 @@ def make_workload(args, rank=0):
     if args.workload == "protein_vs_db":
         return W.protein_vs_db(seed=W.SEED_BASE + 0 + 1000 * rank)
     if args.workload == "reads_vs_windows":
-        return W.reads_vs_windows(seed=W.SEED_BASE + 2 + 1000 * rank)
+        return W.reads_vs_windows(seed=W.SEED_BASE + 2 + 1000 * rank, n_reads=args.reads)
     if args.workload in ("long_pairs", "long_pairs_local"):
         mode = W.MODE_LOCAL if args.workload == "long_pairs_local" else W.MODE_GLOBAL
         return W.long_pairs(seed=W.SEED_BASE + 3 + 1000 * rank, mode=mode)
@@ -283,6 +285,8 @@ def bench_ours(args):
     ms, total_cells, value = aggregate(world, ms_local, float(cells_per_step * args.steps))
 
     wtext = WORKLOAD if args.workload == "protein_search" else WORKLOAD_TEXT[args.workload]
+    if args.workload == "reads_vs_windows":
+        wtext = wtext.replace("1,000,000 reads", f"{args.reads:,} reads")
     out = {"metric": METRIC if args.workload == "protein_search" else
            f"GCUPS (bit-exact) {args.workload}", "value": round(value, 2), "unit": "GCUPS", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
