@@ -333,6 +333,7 @@ static void db_release(dsa_db* db) {
   rel(db->d_codes, db->n_res + 64);
   rel(db->d_off, (db->n + 1) * sizeof(uint64_t));
   rel(db->d_len, db->n * sizeof(uint32_t));
+  // the interleaved copy, when an all-vs-all search built it
   rel(db->d_perm, db->n * sizeof(uint32_t));
   rel(db->d_slen, db->n * sizeof(uint32_t));
   rel(db->d_gbase, db->n_groups * sizeof(uint64_t));
@@ -369,12 +370,23 @@ extern "C" int dsa_db_load(dsa_ctx* ctx, const uint8_t* codes, const uint64_t* o
   const uint64_t n_res = off[n_seqs];
   if (!codes) { set_error("codes is NULL"); return DSA_ERR_INVALID_ARG; }
   const uint8_t* src = codes + base;
-  for (uint64_t x = 0; x < n_res; ++x) {
-    if (src[x] >= (uint8_t)alphabet_size) {
-      set_error("residue code %u at position %llu is not below alphabet_size %d", src[x],
-                (unsigned long long)x, alphabet_size);
-      return DSA_ERR_INVALID_ARG;
-    }
+  {
+    // every code below the alphabet size (host threads; first offender reported)
+    const unsigned T = host_threads(n_res, 1u << 20);
+    std::vector<uint64_t> bad(T, UINT64_MAX);
+    parallel_for(n_res, T, [&](unsigned t, size_t b, size_t e) {
+      for (size_t x = b; x < e; ++x)
+        if (src[x] >= (uint8_t)alphabet_size) {
+          bad[t] = x;
+          return;
+        }
+    });
+    for (unsigned t = 0; t < T; ++t)
+      if (bad[t] != UINT64_MAX) {
+        set_error("residue code %u at position %llu is not below alphabet_size %d", src[bad[t]],
+                  (unsigned long long)bad[t], alphabet_size);
+        return DSA_ERR_INVALID_ARG;
+      }
   }
   dsa_db* db = new (std::nothrow) dsa_db;
   if (!db) { set_error("host allocation failed"); return DSA_ERR_OOM; }
@@ -384,24 +396,8 @@ extern "C" int dsa_db_load(dsa_ctx* ctx, const uint8_t* codes, const uint64_t* o
   db->A = alphabet_size;
   db->h_off = off;
   db->h_len = len;
-
-  // length-sorted order: longest first, ties by id
-  db->h_perm.resize(n_seqs);
-  std::iota(db->h_perm.begin(), db->h_perm.end(), 0u);
-  std::stable_sort(db->h_perm.begin(), db->h_perm.end(),
-                   [&](uint32_t a, uint32_t b) { return len[a] > len[b]; });
-  std::vector<uint32_t> slen(n_seqs);
-  for (uint32_t k = 0; k < n_seqs; ++k) slen[k] = len[db->h_perm[k]];
+  for (uint32_t L : len) db->max_len = std::max(db->max_len, L);
   db->n_groups = (n_seqs + GROUP - 1) / GROUP;
-  db->h_glen.resize(db->n_groups);
-  db->h_gbase.resize(db->n_groups);
-  uint64_t il = 0;
-  for (uint32_t g = 0; g < db->n_groups; ++g) {
-    db->h_glen[g] = slen[(size_t)g * GROUP];
-    db->h_gbase[g] = il;
-    il += (uint64_t)((db->h_glen[g] + CHUNK - 1) / CHUNK) * CHUNK * GROUP;
-  }
-  db->il_bytes = il;
 
   int rc = DSA_OK;
   auto fail = [&](int r) { db_release(db); delete db; return r; };
@@ -412,30 +408,15 @@ extern "C" int dsa_db_load(dsa_ctx* ctx, const uint8_t* codes, const uint64_t* o
   db->d_off = (uint64_t*)p;
   if ((rc = ctx->alloc(&p, n_seqs * sizeof(uint32_t)))) return fail(rc);
   db->d_len = (uint32_t*)p;
-  if ((rc = ctx->alloc(&p, n_seqs * sizeof(uint32_t)))) return fail(rc);
-  db->d_perm = (uint32_t*)p;
-  if ((rc = ctx->alloc(&p, n_seqs * sizeof(uint32_t)))) return fail(rc);
-  db->d_slen = (uint32_t*)p;
-  if ((rc = ctx->alloc(&p, db->n_groups * sizeof(uint64_t)))) return fail(rc);
-  db->d_gbase = (uint64_t*)p;
-  if ((rc = ctx->alloc(&p, db->n_groups * sizeof(uint32_t)))) return fail(rc);
-  db->d_glen = (uint32_t*)p;
-  if ((rc = ctx->alloc(&p, il ? il : 16))) return fail(rc);
-  db->d_il = (uint8_t*)p;
 
   cudaStream_t s = ctx->stream;
   if (cudaMemcpyAsync(db->d_codes, src, n_res, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(db->d_codes + n_res, 0, 64, s) != cudaSuccess ||
       cudaMemcpyAsync(db->d_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(db->d_len, len.data(), len.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(db->d_perm, db->h_perm.data(), n_seqs * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(db->d_slen, slen.data(), n_seqs * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(db->d_gbase, db->h_gbase.data(), db->n_groups * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(db->d_glen, db->h_glen.data(), db->n_groups * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      cudaMemcpyAsync(db->d_len, len.data(), len.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
     set_error("dsa_db_load: copy to device failed: %s", cudaGetErrorString(cudaGetLastError()));
     return fail(DSA_ERR_CUDA);
   }
-  if ((rc = launch_interleave(ctx, db))) return fail(rc);
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     set_error("dsa_db_load: %s", cudaGetErrorString(cudaGetLastError()));
     return fail(DSA_ERR_CUDA);
@@ -443,6 +424,69 @@ extern "C" int dsa_db_load(dsa_ctx* ctx, const uint8_t* codes, const uint64_t* o
   *out = db;
   return DSA_OK;
 }
+
+namespace dsa {
+
+int ensure_interleaved(dsa_ctx* ctx, const dsa_db* cdb) {
+  dsa_db* db = const_cast<dsa_db*>(cdb);
+  std::lock_guard<std::mutex> lk(db->il_mu);
+  if (db->il_ready) return DSA_OK;
+  const uint32_t n_seqs = db->n;
+  // length-sorted order: longest first, ties by id
+  std::vector<uint32_t> perm(n_seqs);
+  {
+    std::vector<uint64_t> key(n_seqs);
+    for (uint32_t k = 0; k < n_seqs; ++k) key[k] = ~(uint64_t)db->h_len[k] << 32 | k;
+    const std::vector<uint32_t> ord = radix_order(key);
+    for (uint32_t k = 0; k < n_seqs; ++k) perm[k] = ord[k];
+  }
+  std::vector<uint32_t> slen(n_seqs);
+  for (uint32_t k = 0; k < n_seqs; ++k) slen[k] = db->h_len[perm[k]];
+  std::vector<uint32_t> glen(db->n_groups);
+  std::vector<uint64_t> gbase(db->n_groups);
+  uint64_t il = 0;
+  for (uint32_t g = 0; g < db->n_groups; ++g) {
+    glen[g] = slen[(size_t)g * GROUP];
+    gbase[g] = il;
+    il += (uint64_t)((glen[g] + CHUNK - 1) / CHUNK) * CHUNK * GROUP;
+  }
+  // device arrays come from the owner's pool, ordered on the caller's stream
+  dsa_ctx* own = db->ctx;
+  cudaStream_t s = ctx->stream;
+  void* p[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  const size_t sz[5] = {n_seqs * sizeof(uint32_t), n_seqs * sizeof(uint32_t),
+                        db->n_groups * sizeof(uint64_t), db->n_groups * sizeof(uint32_t),
+                        il ? il : 16};
+  for (int k = 0; k < 5; ++k) {
+    int rc = own->alloc(&p[k], sz[k], s);
+    if (rc) {
+      for (int x = 0; x < k; ++x) own->release(p[x], sz[x], s);
+      return rc;
+    }
+  }
+  db->d_perm = (uint32_t*)p[0];
+  db->d_slen = (uint32_t*)p[1];
+  db->d_gbase = (uint64_t*)p[2];
+  db->d_glen = (uint32_t*)p[3];
+  db->d_il = (uint8_t*)p[4];
+  db->il_bytes = il;
+  db->h_perm.swap(perm);
+  db->h_glen.swap(glen);
+  db->h_gbase.swap(gbase);
+  if (cudaMemcpyAsync(db->d_perm, db->h_perm.data(), n_seqs * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(db->d_slen, slen.data(), n_seqs * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(db->d_gbase, db->h_gbase.data(), db->n_groups * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(db->d_glen, db->h_glen.data(), db->n_groups * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    set_error("interleave: copy to device failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return DSA_ERR_CUDA;
+  }
+  DSA_TRY(launch_interleave(ctx, db));
+  DSA_CUDA_TRY(cudaStreamSynchronize(s));   // usable from any stream from here on
+  db->il_ready = true;
+  return DSA_OK;
+}
+
+}  // namespace dsa
 
 extern "C" int dsa_db_free(dsa_db* db) {
   if (!db) return DSA_OK;
@@ -500,6 +544,7 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
   }
 
   // ---- packed path ----
+  DSA_TRY(ensure_interleaved(ctx, db));
   const int R = A + 1;
   std::vector<uint32_t> qorder(nq);
   std::iota(qorder.begin(), qorder.end(), 0u);

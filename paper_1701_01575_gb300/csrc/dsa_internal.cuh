@@ -81,7 +81,11 @@ struct dsa_db {
   uint32_t* d_len = nullptr;      // n
   std::vector<uint64_t> h_off;
   std::vector<uint32_t> h_len;
-  // length-sorted (descending, ties by id), lane-interleaved copy
+  uint32_t max_len = 0;
+  // length-sorted (descending, ties by id), lane-interleaved copy; built on
+  // first use by an all-vs-all search (ensure_interleaved), not at load
+  std::mutex il_mu;
+  bool il_ready = false;
   uint32_t* d_perm = nullptr;     // sorted position -> id
   uint32_t* d_slen = nullptr;     // sorted position -> length
   std::vector<uint32_t> h_perm;
@@ -94,6 +98,12 @@ struct dsa_db {
   uint64_t il_bytes = 0;
   size_t bytes_held = 0;
 };
+
+namespace dsa {
+// Builds the length-sorted, lane-interleaved copy of db (once; thread-safe),
+// on ctx's stream, and waits for it.
+int ensure_interleaved(dsa_ctx* ctx, const dsa_db* db);
+}  // namespace dsa
 
 struct dsa_res {
   dsa_ctx* ctx = nullptr;

@@ -95,7 +95,7 @@ size_t dsa_server::estimate(const std::vector<Req*>& batch) const {
   uint64_t bytes = 64ull << 20;   // profiles, job lists, small buffers
   if (batch[0]->r.kind == DSA_REQ_SEARCH) {
     const uint64_t nt = db->n;
-    const uint64_t glen = db->h_glen.empty() ? 0 : db->h_glen[0];
+    const uint64_t glen = db->max_len;
     bytes += nq * nt * 13;                                           // dense scores
     // boundary rows of the packed kernel: grid = min(items, 2 CTAs per SM),
     // items = units (<= query pairs) x blocks of 8 groups
