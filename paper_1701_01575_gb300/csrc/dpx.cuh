@@ -33,6 +33,15 @@ __device__ __forceinline__ uint32_t prmt(uint32_t lo_tab, uint32_t hi_tab, uint3
   asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(lo_tab), "r"(hi_tab), "r"(sel));
   return r;
 }
+// Offset-binary halfwords (sign bit flipped: v' = v + 0x8000 mod 2^16) order
+// like unsigned numbers; DPX add-max wraps mod 2^16 in each half, so adding a
+// two's-complement constant is the same in either form.
+__device__ __forceinline__ uint32_t addmax2u(uint32_t a, uint32_t b, uint32_t c) {
+  return __viaddmax_u16x2(a, b, c);
+}
+__device__ __forceinline__ uint32_t max3_2u(uint32_t a, uint32_t b, uint32_t c) {
+  return __vimax3_u16x2(a, b, c);
+}
 // a + b per halfword (no carry between halves)
 __device__ __forceinline__ uint32_t add2(uint32_t a, uint32_t b) { return __vadd2(a, b); }
 

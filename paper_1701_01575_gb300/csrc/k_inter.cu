@@ -24,12 +24,17 @@
 //     work queue ordered longest-first.
 //
 // Cell update for one row (Gotoh, local), with Ho = H - o and profile S + o:
-//   E  = max(E - e, Ho_left)            addmax2
-//   t  = max(Ho_diag + (S + o), E)      addmax2
-//   H  = max(t, F, 0)                   max2_relu
-//   Ho = H - o                          add2
-//   F' = max(F - e, Ho)                 addmax2   (F of the next row)
-// and the column maximum of H (max3_2 every two rows) for the end cell.
+//   E  = max(E - e, Ho_left)            addmax2u
+//   t  = max(Ho_diag + (S + o), E)      addmax2u
+//   H  = max(t, F, 0)                   max3_2u
+//   Ho = H - o                          32-bit subtract
+//   F' = max(F - e, Ho)                 addmax2u  (F of the next row)
+// and the column maximum of H (max3_2u every two rows) for the end cell.
+// Values are kept in offset binary (each half + 0x8000): the maxima are the
+// unsigned DPX forms, additions of constants wrap identically, and since
+// H >= 0, the low half of H + 0x8000 is at least 0x8000 > o, so H - o is a
+// plain 32-bit subtraction with no borrow between the halves -- an integer
+// add the compiler may issue outside the ALU pipe that carries the maxima.
 //
 // End cell (smallest target end j, then smallest query end i, among cells
 // holding the best score): the column maximum is compared with the running
@@ -121,8 +126,11 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
   // per-thread asynchronous copies two blocks ahead of the arithmetic
   uint2* const ring = reinterpret_cast<uint2*>(smem + 2 * bufbytes + 2 * W * NT * sizeof(int16_t)) + tid;
   const uint32_t strip_words = (uint32_t)A.R * PITCH;
-  const uint32_t neg_o2 = A.neg_o2, neg_e2 = A.neg_e2;
-  const uint32_t NEG2 = pack2(NEG16, NEG16);
+  constexpr uint32_t BIAS2 = 0x80008000u;                  // offset-binary 0 in both halves
+  const uint32_t neg_e2 = A.neg_e2;                         // -e, added mod 2^16
+  const uint32_t mo2 = A.neg_o2 ^ BIAS2;                    // -o (offset binary)
+  const uint32_t o2 = ((uint32_t)A.o << 16) | (uint32_t)A.o;
+  const uint32_t NEG2 = pack2(NEG16, NEG16) ^ BIAS2;
 
   if (tid == 0) {
     mbar_init(&bars[0], 1);
@@ -184,10 +192,10 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
       uint32_t Ho[W], E[W];
 #pragma unroll
       for (int r = 0; r < W; ++r) {
-        Ho[r] = neg_o2;
+        Ho[r] = mo2;
         E[r] = NEG2;
       }
-      uint32_t diag = neg_o2;
+      uint32_t diag = mo2;
       uint2* scr = scr_base;
       uint4 rv = make_uint4(0, 0, 0, 0);
       // Packed trigger threshold per half, tested as cm > thr with
@@ -195,7 +203,7 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
       // (or is the first positive one) triggers; the exact rule (strictly
       // better, or equal at a smaller column) is applied in the trigger path.
       uint32_t thr2 = 0;
-      auto set_thr = [&]() { thr2 = pack2(max(best_lo - 1, 0), max(best_hi - 1, 0)); };
+      auto set_thr = [&]() { thr2 = pack2(max(best_lo - 1, 0), max(best_hi - 1, 0)) ^ BIAS2; };
       set_thr();
       int pend = 0;   // bit 0 / 1: low / high half improved in this strip
 
@@ -226,13 +234,13 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
           if (keep != 0xFFFFFFFFu) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              top[k].x = (top[k].x & keep) | (neg_o2 & ~keep);
-              top[k].y = (top[k].y & keep) | (neg_o2 & ~keep);
+              top[k].x = (top[k].x & keep) | (mo2 & ~keep);
+              top[k].y = (top[k].y & keep) | (mo2 & ~keep);
             }
           }
         } else {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) top[k] = make_uint2(neg_o2, neg_o2);
+          for (int k = 0; k < 4; ++k) top[k] = make_uint2(mo2, mo2);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -241,7 +249,7 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
           uint32_t F = top[k].y;
           uint32_t d = diag;
           diag = top[k].x;
-          uint32_t cm = 0, hprev = 0;
+          uint32_t cm = BIAS2, hprev = BIAS2;
 #pragma unroll
           for (int q4 = 0; q4 < W / 4; ++q4) {
             const uint4 pv = prow[q4];
@@ -250,21 +258,21 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
             for (int u = 0; u < 4; ++u) {
               const int r = q4 * 4 + u;
               const uint32_t old = Ho[r];
-              E[r] = addmax2(E[r], neg_e2, old);
-              const uint32_t t = addmax2(d, pr[u], E[r]);
-              const uint32_t h = max2_relu(t, F);
-              Ho[r] = add2(h, neg_o2);
-              F = addmax2(F, neg_e2, Ho[r]);
+              E[r] = addmax2u(E[r], neg_e2, old);
+              const uint32_t t = addmax2u(d, pr[u], E[r]);
+              const uint32_t h = max3_2u(t, F, BIAS2);
+              Ho[r] = h - o2;
+              F = addmax2u(F, neg_e2, Ho[r]);
               d = old;
-              if (r & 1) cm = max3_2(cm, hprev, h);
+              if (r & 1) cm = max3_2u(cm, hprev, h);
               else hprev = h;
             }
           }
           scr[(uint64_t)(c4 + k) * NT] = make_uint2(Ho[W - 1], F);
           // end-cell tracking for column j: trigger when cm > thr (per half)
           const int j = (int)c4 + k + 1;
-          if (__vmaxs2(cm, thr2) != thr2) {   // some half has cm > thr
-            const int cl = lo16(cm), ch = hi16(cm);
+          if (__vmaxu2(cm, thr2) != thr2) {   // some half has cm > thr
+            const int cl = lo16(cm ^ BIAS2), ch = hi16(cm ^ BIAS2);
             const int thr_lo = best_lo - (j < bj_lo ? 1 : 0);
             const int thr_hi = best_hi - (j < bj_hi ? 1 : 0);
             // rare: a half improved.  Park the column in that half's area of
@@ -273,12 +281,12 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
             // supersedes this one)
             if (cl > thr_lo) {
 #pragma unroll
-              for (int r = 0; r < W; ++r) park_lo[r * NT + tid] = (int16_t)lo16(Ho[r]);
+              for (int r = 0; r < W; ++r) park_lo[r * NT + tid] = (int16_t)lo16(Ho[r] ^ BIAS2);
               best_lo = cl; bj_lo = j; pend |= 1;
             }
             if (ch > thr_hi) {
 #pragma unroll
-              for (int r = 0; r < W; ++r) park_hi[r * NT + tid] = (int16_t)hi16(Ho[r]);
+              for (int r = 0; r < W; ++r) park_hi[r * NT + tid] = (int16_t)hi16(Ho[r] ^ BIAS2);
               best_hi = ch; bj_hi = j; pend |= 2;
             }
             set_thr();
