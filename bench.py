@@ -35,7 +35,7 @@ METRIC = "GCUPS (bit-exact) batched protein database search"
 # profiles/k_inter_local16_protein_8q_350k.md (416.4 GB read + written for
 # 1.194 T cells); traffic grows with the cells (boundary rows per column and
 # strip), so a launch's traffic is this figure times its cells.
-INTER_DRAM_BYTES_PER_CELL = 416.35e9 / 1.194104e12
+INTER_DRAM_BYTES_PER_CELL = 416.40e9 / 1.194104e12
 
 WORKLOAD = ("protein_search: 32 queries (log-uniform 64..5000) x 500,000 targets "
             "(lognormal median 300, sigma 0.7, cap 35,000), BLOSUM62 11/1, local, "
@@ -302,13 +302,17 @@ def bench_ours(args):
     inter_ms = statistics.mean(phase["inter16"]) if phase["inter16"] else None
     if args.workload != "protein_search":
         inter_ms = None
-    rate = ctx.probe_issue_rate(0)     # DPX s16x2 add-max, warp-instr / SM / clk
+    rate = ctx.probe_issue_rate(0)      # DPX s16x2 add-max, warp-instr / SM / clk
+    rate_add = ctx.probe_issue_rate(3)  # 32-bit integer add, warp-instr / SM / clk
     sm_mhz = clk.get("sm_mhz") or (props.clock_rate / 1e3 if hasattr(props, "clock_rate") else None)
     if inter_ms and sm_mhz:
         achieved = pcells["inter16"] / (inter_ms / 1e3) / 1e9
-        # 6 algorithmic int32 ops per cell (H-o, E, F, max with diagonal, max with F/0,
-        # running best); in packed 16x2 form one instruction covers 2 cells
-        peak = props.multi_processor_count * sm_mhz * 1e6 * rate * 32 * 2 / 6 / 1e9
+        # 6 algorithmic ops per cell (H-o, E, F, max with diagonal, max with F/0, running
+        # best), each at the measured rate of the form the kernel uses: five maxima as
+        # DPX s16x2 instructions, H - o as one 32-bit add over both offset-binary halves;
+        # every instruction covers 2 cells of 32 lanes
+        peak = (props.multi_processor_count * sm_mhz * 1e6 * 32 * 2 / (5 / rate + 1 / rate_add)
+                / 1e9)
         out["roofline"] = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
                            "unit": "GCUPS", "frac": round(achieved / peak, 4),
                            "traffic": round(INTER_DRAM_BYTES_PER_CELL * pcells["inter16"]),
@@ -316,8 +320,9 @@ def bench_ours(args):
                                             "capture, scaled by cells to this launch",
                            "kernel": "k_inter_local16", "kernel_ms": round(inter_ms, 3),
                            "peak_basis": f"{props.multi_processor_count} SMs x {sm_mhz:.0f} MHz x "
-                                         f"{rate:.3f} DPX warp-instr/SM/clk (measured) x 32 lanes "
-                                         "x 2 cells / 6 ops"}
+                                         "32 lanes x 2 cells / (5 DPX ops / "
+                                         f"{rate:.3f} + 1 add / {rate_add:.3f} warp-instr/SM/clk, "
+                                         "both measured)"}
     out["phases_ms"] = {k: round(statistics.mean(v), 3) for k, v in phase.items() if v}
     out["phase_gcups"] = {k: round(pcells[k] / (statistics.mean(v) / 1e3) / 1e9, 1)
                           for k, v in phase.items() if v and pcells.get(k)}
