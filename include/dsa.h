@@ -129,9 +129,11 @@ uint64_t dsa_kernel_launches(const dsa_ctx* ctx);
 /* Load `n_seqs` sequences to the device (the paper's map phase reading the
  * reference set, Sec. II.B.1).  `codes` holds all residues concatenated;
  * sequence k is codes[offsets[k] .. offsets[k+1]).  Every code must be below
- * `alphabet_size` (1..31); every sequence must be non-empty.  The loader also
- * builds the length-sorted, lane-interleaved copy the batched kernels read.
- * The same call loads query sets. */
+ * `alphabet_size` (1..31); every sequence must be non-empty.  The same call
+ * loads query sets.  The length-sorted, lane-interleaved copy that the
+ * batched all-vs-all kernels read is built on the set's first all-vs-all use
+ * (charged to the loading context), so query sets and pair windows never pay
+ * for it.  The codes are copied; the caller keeps its arrays. */
 int dsa_db_load(dsa_ctx* ctx, const uint8_t* codes, const uint64_t* offsets, uint32_t n_seqs,
                 int alphabet_size, dsa_db** out);
 int dsa_db_free(dsa_db* db);
@@ -165,7 +167,11 @@ int dsa_align_batch(dsa_ctx* ctx, const dsa_db* db, const uint8_t* q_codes,
 
 /* Begin coordinates and CIGAR for hits of `res` (the paper's location +
  * CIGAR, Sec. I and II.B.1).  `which` lists hit indices (host array), NULL =
- * every hit.  Hits with a local score of 0 get no CIGAR. */
+ * every hit.  Hits with a local score of 0 get no CIGAR.  The DP of each hit
+ * is recomputed over the part of its rectangle that every optimal path must
+ * cross (bounded from the hit's score), storing 4-bit decisions, and walked
+ * back with the tie rules stop > M > I > D, gap opening preferred; results
+ * are identical to a walk over the full rectangle. */
 int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, uint64_t n);
 
 /* Access results.  Without DSA_RESULTS_ON_DEVICE the arrays are host copies

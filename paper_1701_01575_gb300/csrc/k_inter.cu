@@ -411,12 +411,9 @@ int launch_inter_local16(dsa_ctx* ctx, const dsa_db* db, const PackedPlan& plan,
   A.status = ctx->d_status;
   const size_t smem = 2ull * NCOPY * replica_stride(plan.R) + 2ull * W * NT * sizeof(int16_t) +
                       (size_t)RING * 4 * NT * sizeof(uint2);
-  static size_t attr_bytes = 0;   // largest dynamic shared memory requested so far
-  if (smem > attr_bytes) {
-    DSA_CUDA_TRY(cudaFuncSetAttribute(k_inter_local16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-    attr_bytes = smem;
-  }
+  // the attribute belongs to the current device: set it on every launch (cheap)
+  DSA_CUDA_TRY(cudaFuncSetAttribute(k_inter_local16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
   DSA_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), ctx->stream));
   k_inter_local16<<<grid, NT, smem, ctx->stream>>>(A);
   ++ctx->launches;
