@@ -4,6 +4,8 @@ Scores, end cells, begin cells and CIGARs are integers: the bar is bit-exact.
 Sizes span several strips (32 query rows), interleave chunks (16 residues),
 warp groups (32 targets) and CTA blocks (8 groups), with ragged tails.
 """
+import zlib
+
 import numpy as np
 import pytest
 
@@ -557,3 +559,72 @@ def test_packed_pairs_small_alphabet_asymmetric(ctx, mode, fe):
     h = r.hits()
     assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), f"3-letter pairs mode={mode}")
     assert r.phase_cells()["inter16"] > 0
+
+
+BAND_PARAMS = [
+    ("dna_1_-4_6_1", W.dna_matrix(1, -4), 6, 1),
+    ("o_eq_e", W.dna_matrix(2, -3), 3, 3),
+    ("e_zero", W.dna_matrix(2, -3), 4, 0),
+    ("smax_zero", np.array([[0, -3, -3, -3], [-3, 0, -3, -3], [-3, -3, 0, -3], [-3, -3, -3, 0]], np.int8), 2, 1),
+    ("smax_neg", np.array([[-1, -4, -4, -4], [-4, -1, -4, -4], [-4, -4, -1, -4], [-4, -4, -4, -1]], np.int8), 2, 1),
+    ("big_match", W.dna_matrix(9, -2), 10, 1),
+]
+
+
+@pytest.mark.parametrize("name,S,o,e", BAND_PARAMS, ids=[p[0] for p in BAND_PARAMS])
+@pytest.mark.parametrize("mode,fe", [(dsa.SEMIGLOBAL, 12), (dsa.GLOBAL, 15), (dsa.LOCAL, 15),
+                                     (dsa.SEMIGLOBAL, 3)])
+def test_traceback_band_parameter_sweep(ctx, name, S, o, e, mode, fe, monkeypatch):
+    """Score-derived traceback windows under unusual scoring (no extension
+    penalty, o = e, largest entry 0 or negative, large matches) and heavy
+    indels: thread-per-hit path against the oracle's full-rectangle walk."""
+    monkeypatch.setenv("DSA_TB_THREAD_MIN", "1")
+    rng = np.random.default_rng(zlib.crc32(name.encode()) % 1000 + 7 * mode + fe)
+    genome = rng.integers(0, 4, 8000).astype(np.uint8)
+    db = W.SeqSet.from_list([genome])
+    reads, starts = [], []
+    for n in rng.integers(5, 60, 120):
+        st = int(rng.integers(0, 8000 - 150))
+        reads.append(W.mutate(rng, genome[st + 15: st + 15 + n], 0.06, 0.08))
+        starts.append(st)
+    reads = [x if len(x) else np.zeros(1, np.uint8) for x in reads]
+    qs = W.SeqSet.from_list(reads)
+    pairs = np.zeros(qs.n, dtype=W.PAIR_DTYPE)
+    pairs["query_id"] = np.arange(qs.n)
+    pairs["t_offset"] = starts
+    pairs["t_len"] = 40 + rng.integers(0, 100, qs.n)
+    d = ctx.load_set(db, 4)
+    q = ctx.load_set(qs, 4)
+    r = ctx.align(d, q, S, o, e, mode=mode, free_ends=fe, pairs=pairs)
+    ctx.traceback(r)
+    h = r.hits()
+    sc, qe, te = oracle.score_pairs(qs.codes, qs.offsets, db.codes, db.offsets, pairs["query_id"],
+                                    pairs["target_id"], S, o, e, mode, fe,
+                                    pair_toff=pairs["t_offset"], pair_tlen=pairs["t_len"])
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), f"band sweep {name}")
+    check_traceback(h, r.cigar(), qs, db, S, o, e, mode, fe)
+
+
+@pytest.mark.parametrize("name,S,o,e", BAND_PARAMS[:4], ids=[p[0] for p in BAND_PARAMS[:4]])
+@pytest.mark.parametrize("mode,fe", [(dsa.GLOBAL, 15), (dsa.LOCAL, 15)])
+def test_long_pair_band_parameter_sweep(ctx, name, S, o, e, mode, fe):
+    """The same scoring corner cases on pairs above the long-pair threshold."""
+    rng = np.random.default_rng(zlib.crc32(name.encode()) % 1000 + 31 * mode)
+    a = rng.integers(0, 4, 2300).astype(np.uint8)
+    qs = W.SeqSet.from_list([a, rng.integers(0, 4, 2100).astype(np.uint8)])
+    db = W.SeqSet.from_list([W.mutate(rng, a, 0.04, 0.03), rng.integers(0, 4, 2050).astype(np.uint8)])
+    pairs = np.zeros(2, dtype=W.PAIR_DTYPE)
+    pairs["query_id"] = [0, 1]
+    pairs["target_id"] = [0, 1]
+    pairs["t_len"] = db.lengths
+    d = ctx.load_set(db, 4)
+    q = ctx.load_set(qs, 4)
+    r = ctx.align(d, q, S, o, e, mode=mode, free_ends=fe, pairs=pairs)
+    ctx.traceback(r)
+    h = r.hits()
+    sc, qe, te = oracle.score_pairs(qs.codes, qs.offsets, db.codes, db.offsets, pairs["query_id"],
+                                    pairs["target_id"], S, o, e, mode, fe,
+                                    pair_toff=pairs["t_offset"], pair_tlen=pairs["t_len"])
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), f"long band sweep {name}")
+    assert r.phase_cells()["intra16"] > 0
+    check_traceback(h, r.cigar(), qs, db, S, o, e, mode, fe)
