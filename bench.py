@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--queries", type=int, default=32)
     ap.add_argument("--reads", type=int, default=1_000_000,
                     help="reads_vs_windows: number of reads (profiling runs use a smaller case)")
+    ap.add_argument("--long-pairs", type=int, default=64,
+                    help="long_pairs*: number of pairs (profiling runs use a smaller case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -179,7 +181,7 @@ def make_workload(args, rank=0):
         return W.reads_vs_windows(seed=W.SEED_BASE + 2 + 1000 * rank, n_reads=args.reads)
     if args.workload in ("long_pairs", "long_pairs_local"):
         mode = W.MODE_LOCAL if args.workload == "long_pairs_local" else W.MODE_GLOBAL
-        return W.long_pairs(seed=W.SEED_BASE + 3 + 1000 * rank, mode=mode)
+        return W.long_pairs(seed=W.SEED_BASE + 3 + 1000 * rank, mode=mode, n_pairs=args.long_pairs)
     return W.protein_search(seed=W.SEED_BASE + 1 + 1000 * rank, n_queries=args.queries,
                             n_targets=args.targets)
 
@@ -287,6 +289,8 @@ def bench_ours(args):
     wtext = WORKLOAD if args.workload == "protein_search" else WORKLOAD_TEXT[args.workload]
     if args.workload == "reads_vs_windows":
         wtext = wtext.replace("1,000,000 reads", f"{args.reads:,} reads")
+    if args.workload.startswith("long_pairs"):
+        wtext = wtext.replace("64 DNA pairs", f"{args.long_pairs} DNA pairs")
     out = {"metric": METRIC if args.workload == "protein_search" else
            f"GCUPS (bit-exact) {args.workload}", "value": round(value, 2), "unit": "GCUPS", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),

@@ -57,6 +57,13 @@ __device__ __forceinline__ bool cand_better(const Cand& a, const Cand& b) {
 }
 
 
+// Column inputs of the wavefront: lane 0 takes column j = s at step s; the
+// boundary row of the band above and the target residues are fetched by the
+// whole warp 32 columns at a time (lane k holds column blk + k + 1), one
+// block ahead, and handed to lane 0 by shuffle; residues then travel lane to
+// lane with H and F.  The wait on the band above is bounded and covers a
+// whole block.
+template <bool LOCAL, bool BYTES>
 __global__ void __launch_bounds__(WARPS * 32) k_long_score(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
@@ -64,17 +71,24 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
     uint32_t* __restrict__ counter, int2* __restrict__ bnd, uint32_t* __restrict__ prog,
     Cand* __restrict__ cands, int32_t* __restrict__ status) {
   __shared__ int8_t S[32 * 32];
+  __shared__ uint32_t Sb[4];   // BYTES: row q of S as 4 bytes
   for (int x = threadIdx.x; x < A * A; x += blockDim.x) S[x] = Sg[x];
+  if (BYTES && threadIdx.x < 4) {
+    uint32_t w = 0;
+    for (int a = 0; a < A; ++a)
+      if ((int)threadIdx.x < A) w |= (uint32_t)(uint8_t)Sg[threadIdx.x * A + a] << (8 * a);
+    Sb[threadIdx.x] = w;
+  }
   __syncthreads();
+  constexpr unsigned FULL = 0xFFFFFFFFu;
   const int lane = threadIdx.x & 31;
-  const bool local = mode == DSA_LOCAL;
   const bool sg = mode == DSA_SEMIGLOBAL;
   const bool q_end_free = sg && (fe & DSA_FREE_Q_END);
   const bool t_end_free = sg && (fe & DSA_FREE_T_END);
   for (;;) {
     uint32_t it = 0;
     if (lane == 0) it = atomicAdd(counter, 1u);
-    it = __shfl_sync(0xFFFFFFFFu, it, 0);
+    it = __shfl_sync(FULL, it, 0);
     if (it >= n_items) break;
     const LongJob jb = jobs[items[2 * it]];
     const uint32_t b = items[2 * it + 1];
@@ -92,73 +106,127 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
     // the lane that holds the band's bottom row publishes it
     const int32_t bottom = min(m, i0 + BAND);
     const int bot_lane = (bottom - 1 - i0) / ROWS;
+    const bool owns_m = r0 < m && m <= r0 + ROWS;
 
     int32_t H[ROWS], E[ROWS];
-    int qc[ROWS];
+    uint32_t qv[ROWS];   // BYTES: S row of the query residue as bytes; else its matrix offset
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
       const int32_t i = r0 + r + 1;
       H[r] = h_col0(mode, fe, i, o, e);
       E[r] = NEG32;
-      qc[r] = i <= m ? q[i - 1] * A : 0;
+      qv[r] = i <= m ? (BYTES ? Sb[q[i - 1]] : (uint32_t)q[i - 1] * A) : 0u;
     }
     Cand c = {0, 0, 0, 0};
-    if (t_end_free && r0 < m && m <= r0 + ROWS) {   // H[m][0] on row m
+    if (t_end_free && owns_m) {   // H[m][0] on row m
       c = {H[m - r0 - 1], m, 0, 1};
     }
     int32_t diag = h_col0(mode, fe, r0, o, e);
     int32_t sendH = 0, sendF = NEG32;
-    uint32_t seen = 0;    // columns of the band above known to be complete
+    int sendA = 0;
     bool timed_out = false;
-    const int32_t steps = n + 31;
-    for (int32_t s = 1; s <= steps; ++s) {
-      int32_t Hup = __shfl_up_sync(0xFFFFFFFFu, sendH, 1);
-      int32_t Fup = __shfl_up_sync(0xFFFFFFFFu, sendF, 1);
-      const int32_t j = s - lane;
-      if (lane == 0 && j >= 1 && j <= n) {
-        if (b == 0) {
-          Hup = h_row0(mode, fe, j, o, e);
-          Fup = NEG32;
-        } else {
-          if (seen < (uint32_t)j && !timed_out) {
-            const uint64_t t0 = global_ns();
-            for (;;) {
-              seen = ld_acquire_u32(up_prog);
-              if (seen >= (uint32_t)j) break;
-              if (global_ns() - t0 > WAIT_LIMIT_NS) {
-                timed_out = true;
-                atomicExch(status, DSA_ERR_DEVICE_TIMEOUT);
-                break;
-              }
-            }
+    // boundary row of the band above for columns blk+1 .. blk+32 (lane k: blk+k+1)
+    auto fetch_bnd = [&](int32_t blk) -> int2 {
+      if (b == 0 || blk >= n) return make_int2(NEG32, NEG32);
+      const uint32_t need = (uint32_t)min(blk + 32, n);
+      bool late = false;
+      if (!timed_out) {
+        const uint64_t t0 = global_ns();
+        for (;;) {
+          if (ld_acquire_u32(up_prog) >= need) break;
+          if (global_ns() - t0 > WAIT_LIMIT_NS) {
+            late = true;
+            break;
           }
-          const int2 v = up_bnd[j - 1];
-          Hup = v.x;
-          Fup = v.y;
         }
       }
+      if (__any_sync(FULL, late)) {
+        if (!timed_out && lane == 0) atomicExch(status, DSA_ERR_DEVICE_TIMEOUT);
+        timed_out = true;
+      }
+      const int32_t jj = blk + lane + 1;
+      return jj <= n ? up_bnd[jj - 1] : make_int2(NEG32, NEG32);
+    };
+    auto fetch_res = [&](int32_t blk) -> int {
+      const int32_t jj = blk + lane;
+      return jj < n ? (int)t[jj] : 0;
+    };
+    int2 bcur = fetch_bnd(0), bnxt = fetch_bnd(32);
+    int tcur = fetch_res(0), tnxt = fetch_res(32);
+    const int32_t steps = n + 31;
+    for (int32_t s = 1; s <= steps; ++s) {
+      const int k = (s - 1) & 31;
+      const int32_t bx = __shfl_sync(FULL, bcur.x, k);
+      const int32_t by = __shfl_sync(FULL, bcur.y, k);
+      const int ta = __shfl_sync(FULL, tcur, k);
+      int32_t Hup = __shfl_up_sync(FULL, sendH, 1);
+      int32_t Fup = __shfl_up_sync(FULL, sendF, 1);
+      int a = __shfl_up_sync(FULL, sendA, 1);
+      if (lane == 0) {
+        a = ta;
+        if (b == 0) {
+          Hup = h_row0(mode, fe, s, o, e);
+          Fup = NEG32;
+        } else {
+          Hup = bx;
+          Fup = by;
+        }
+      }
+      if (k == 31) {   // block consumed: rotate, fetch the block after the next
+        bcur = bnxt;
+        tcur = tnxt;
+        const int32_t blk = (s - 1 - k) + 64;
+        bnxt = fetch_bnd(blk);
+        tnxt = fetch_res(blk);
+      }
+      sendA = a;
+      const int32_t j = s - lane;
       if (j >= 1 && j <= n && r0 < m) {
-        const int a = t[j - 1];
         int32_t d = diag;
         diag = Hup;
         int32_t F = Fup, Hp = Hup;
+        // BYTES: byte a of the row table, sign-replicated into bytes 1-3
+        const uint32_t sel = (uint32_t)a + ((uint32_t)a | 8u) * 0x1110u;
+        int32_t cm = 0;
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
           const int32_t i = r0 + r + 1;
           if (i <= m) {
             F = max(F - e, Hp - o);
             E[r] = max(E[r] - e, H[r] - o);
-            int32_t h = max(d + S[qc[r] + a], max(E[r], F));
-            if (local) h = max(h, 0);
+            const int32_t sv = BYTES ? (int32_t)prmt(qv[r], 0u, sel) : (int32_t)S[qv[r] + a];
+            int32_t h = max(d + sv, max(E[r], F));
+            if (LOCAL) {
+              h = max(h, 0);
+              cm = max(cm, h);
+            }
             d = H[r];
             H[r] = h;
             Hp = h;
-            if (local) {
-              if (h > 0 && (!c.has || h > c.s)) c = {h, i, j, 1};
-            } else if ((j == n && (q_end_free || i == m)) || (t_end_free && i == m)) {
-              if (!c.has || h > c.s) c = {h, i, j, 1};
-            }
           }
+        }
+        if (LOCAL) {
+          // first strictly better cell of this lane in (j, i) order
+          if (cm > c.s) {
+            int rr = 0;
+#pragma unroll
+            for (int r = ROWS - 1; r >= 0; --r)
+              if (H[r] == cm) rr = r;
+            c = {cm, r0 + rr + 1, j, 1};
+          }
+        } else if (j == n) {
+          // column n (query end free) or the corner (m, n), rows in order
+#pragma unroll
+          for (int r = 0; r < ROWS; ++r) {
+            const int32_t i = r0 + r + 1;
+            if (i <= m && (q_end_free || i == m) && (!c.has || H[r] > c.s)) c = {H[r], i, j, 1};
+          }
+        } else if (t_end_free && owns_m) {
+          int32_t hm = H[0];
+#pragma unroll
+          for (int r = 1; r < ROWS; ++r)
+            if (r == m - r0 - 1) hm = H[r];
+          if (!c.has || hm > c.s) c = {hm, m, j, 1};
         }
         sendH = Hp;
         sendF = F;
@@ -175,10 +243,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       Cand x;
-      x.s = __shfl_xor_sync(0xFFFFFFFFu, c.s, off);
-      x.i = __shfl_xor_sync(0xFFFFFFFFu, c.i, off);
-      x.j = __shfl_xor_sync(0xFFFFFFFFu, c.j, off);
-      x.has = __shfl_xor_sync(0xFFFFFFFFu, c.has, off);
+      x.s = __shfl_xor_sync(FULL, c.s, off);
+      x.i = __shfl_xor_sync(FULL, c.i, off);
+      x.j = __shfl_xor_sync(FULL, c.j, off);
+      x.has = __shfl_xor_sync(FULL, c.has, off);
       if (cand_better(x, c)) c = x;
     }
     if (lane == 0) cands[jb.cand_off + b] = c;
@@ -404,13 +472,17 @@ int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const in
   if (n_items == 0) return DSA_OK;
   // every warp must be resident at once (bands wait on their predecessors):
   // the grid never exceeds what the device holds simultaneously
+  // alphabets of up to 4 letters: substitution scores by byte permute
+  const bool bytes = A <= 4;
+  auto kern = mode == DSA_LOCAL ? (bytes ? k_long_score<true, true> : k_long_score<true, false>)
+                                : (bytes ? k_long_score<false, true> : k_long_score<false, false>);
   int per_sm = 0;
-  DSA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_long_score, WARPS * 32, 0));
+  DSA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, 0));
   const uint64_t resident = (uint64_t)std::max(1, per_sm) * ctx->sm_count;
   const unsigned grid = (unsigned)std::min<uint64_t>(resident, (n_items + WARPS - 1) / WARPS);
   uint32_t* counter = ctx->d_counters + 3;
   DSA_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(uint32_t), ctx->stream));
-  k_long_score<<<grid, WARPS * 32, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e,
+  kern<<<grid, WARPS * 32, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e,
                                                       mode, fe, d_jobs, d_items, n_items, counter,
                                                       d_bnd, d_prog, static_cast<Cand*>(d_cands),
                                                       ctx->d_status);
