@@ -21,8 +21,9 @@
 // Traceback.  The checkpoints make every band independent: all bands of all
 // hits are recomputed at once (one warp each) over the rectangle up to the
 // end cell, storing the 4-bit decision of every cell (as in the short-hit
-// traceback), then one thread per hit walks back.  Decision memory is half a
-// byte per cell of the rectangle, handled in chunks of bounded size.
+// traceback), then one warp per hit walks back through a shared-memory window
+// of the decisions.  Decision memory is half a byte per cell of the
+// rectangle (or of its diagonal band), handled in chunks of bounded size.
 #include "dsa_internal.cuh"
 #include "dpx.cuh"
 
@@ -401,65 +402,106 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
   }
 }
 
-// Checkpointed traceback, part 2: one thread per hit walks the stored
-// decisions from the end cell (stop > M > I > D, open preferred on ties).
-__global__ void k_long_tb_walk(const LongTbJob* __restrict__ jobs, uint32_t n_jobs, int mode,
-                               uint32_t fe, const uint32_t* __restrict__ dir,
-                               uint32_t* __restrict__ cig_tmp, dsa_hit* __restrict__ hits) {
+// Checkpointed traceback, part 2: one warp per hit.  Lane 0 walks the stored
+// decisions from the end cell (stop > M > I > D, open preferred on ties); the
+// warp keeps a window of them in shared memory -- the rows of the current
+// 256-row band up to the walk's row, WIN_WORDS words (8 cells each) ending at
+// the walk's column -- and reloads it with coalesced row loads whenever the
+// walk leaves it (the walk only moves up and left), so each step reads shared
+// memory instead of waiting on a global load.
+constexpr int WIN_WORDS = 32;
+
+__global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict__ jobs,
+                                                     uint32_t n_jobs, int mode, uint32_t fe,
+                                                     const uint32_t* __restrict__ dir,
+                                                     uint32_t* __restrict__ cig_tmp,
+                                                     dsa_hit* __restrict__ hits) {
+  __shared__ uint32_t win[BAND * WIN_WORDS];
+  constexpr unsigned FULL = 0xFFFFFFFFu;
+  const int lane = threadIdx.x;
   const bool local = mode == DSA_LOCAL;
   const bool sg = mode == DSA_SEMIGLOBAL;
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_jobs; k += gridDim.x * blockDim.x) {
+  for (uint32_t k = blockIdx.x; k < n_jobs; k += gridDim.x) {
     const LongTbJob jb = jobs[k];
     const uint32_t* D = dir + jb.dir_off;
     const uint32_t wpr = jb.wpr;
-    // decision nibble of (i, j); false when (i, j) lies outside the stored
-    // band (only a corrupt decision could lead there)
-    auto nibble = [&](int32_t i, int32_t j, uint32_t& nib) -> bool {
-      const int32_t jlo = band_jlo(jb, (i - 1) / BAND);
-      if (j < jlo || j >= jlo + jb.wc) return false;
-      const uint32_t jc = (uint32_t)(j - jlo);
-      nib = (D[(uint64_t)(i - 1) * wpr + jc / 8u] >> (4 * (jc & 7))) & 15u;
-      return true;
+    int32_t wb = -1, wlo = 0, wrows = 0;   // window: band, first word, rows loaded
+    // lane 0: 0 = decision of (ii, jj) in nib, 1 = outside the window,
+    // 2 = outside the stored band (only a corrupt decision leads there)
+    auto look = [&](int32_t ii, int32_t jj, uint32_t& nib) -> int {
+      const int32_t b = (ii - 1) / BAND;
+      const int32_t jlo = band_jlo(jb, b);
+      if (jj < jlo || jj >= jlo + jb.wc) return 2;
+      const int32_t jc = jj - jlo, wi = jc >> 3, rr = ii - 1 - b * BAND;
+      if (b != wb || wi < wlo || wi >= wlo + WIN_WORDS || rr >= wrows) return 1;
+      nib = (win[rr * WIN_WORDS + (wi - wlo)] >> (4 * (jc & 7))) & 15u;
+      return 0;
     };
     RevCigar c;
     c.out = cig_tmp + jb.cig_off;
     int32_t i = jb.ie, j = jb.je;
     int st = 0;
-    for (int64_t guard = 2 * ((int64_t)jb.ie + jb.je) + 2; guard > 0; --guard) {
-      if (st == 0) {
-        if (sg && ((i == 0 && (fe & DSA_FREE_T_BEGIN)) || (j == 0 && (fe & DSA_FREE_Q_BEGIN)))) break;
-        if (i == 0 || j == 0) {
-          if (local) break;
-          while (j > 0) { c.emit(2); --j; }
-          while (i > 0) { c.emit(1); --i; }
-          break;
+    int64_t guard = 2 * ((int64_t)jb.ie + jb.je) + 2;
+    for (;;) {
+      int need = 2;   // 1: reload the window around (i, j); 2: finished
+      if (lane == 0) {
+        for (; guard > 0; --guard) {
+          uint32_t nib = 0;
+          int lk;
+          if (st == 0) {
+            if (sg && ((i == 0 && (fe & DSA_FREE_T_BEGIN)) || (j == 0 && (fe & DSA_FREE_Q_BEGIN)))) break;
+            if (i == 0 || j == 0) {
+              if (!local) {
+                while (j > 0) { c.emit(2); --j; }
+                while (i > 0) { c.emit(1); --i; }
+              }
+              break;
+            }
+            if ((lk = look(i, j, nib)) != 0) { need = lk; break; }
+            const uint32_t src = nib & 3u;
+            if (src == 3) break;
+            if (src == 0) { c.emit(0); --i; --j; }
+            else st = src == 1 ? 1 : 2;
+          } else {
+            if (i <= 0 || j <= 0) break;
+            if ((lk = look(i, j, nib)) != 0) { need = lk; break; }
+            if (st == 1) {
+              c.emit(1);
+              if (nib & 8u) st = 0;
+              --i;
+            } else {
+              c.emit(2);
+              if (nib & 4u) st = 0;
+              --j;
+            }
+          }
         }
-        uint32_t nib;
-        if (!nibble(i, j, nib)) break;
-        const uint32_t src = nib & 3u;
-        if (src == 3) break;
-        if (src == 0) { c.emit(0); --i; --j; }
-        else st = src == 1 ? 1 : 2;
-      } else if (st == 1) {
-        uint32_t nib;
-        if (i <= 0 || j <= 0 || !nibble(i, j, nib)) break;
-        c.emit(1);
-        if (nib & 8u) st = 0;
-        --i;
-      } else {
-        uint32_t nib;
-        if (i <= 0 || j <= 0 || !nibble(i, j, nib)) break;
-        c.emit(2);
-        if (nib & 4u) st = 0;
-        --j;
       }
+      need = __shfl_sync(FULL, need, 0);
+      if (need != 1) break;
+      // reload: rows of (i, j)'s band up to row i, words ending at j's word
+      const int32_t ci = __shfl_sync(FULL, i, 0), cj = __shfl_sync(FULL, j, 0);
+      wb = (ci - 1) / BAND;
+      const int32_t wi = (cj - band_jlo(jb, wb)) >> 3;
+      wlo = max(0, wi - (WIN_WORDS - 1));
+      wrows = ci - wb * BAND;
+      __syncwarp();
+      const int32_t w = wlo + lane;
+#pragma unroll 8
+      for (int rr = 0; rr < wrows; ++rr)
+        win[rr * WIN_WORDS + lane] =
+            w < (int32_t)wpr ? D[(uint64_t)(wb * BAND + rr) * wpr + (uint32_t)w] : 0u;
+      __syncwarp();
     }
-    c.flush();
-    dsa_hit* h = hits + jb.hit;
-    h->q_begin = i;
-    h->t_begin = j;
-    h->cigar_len = c.n;
-    h->flags |= DSA_HIT_HAS_TRACEBACK;
+    if (lane == 0) {
+      c.flush();
+      dsa_hit* h = hits + jb.hit;
+      h->q_begin = i;
+      h->t_begin = j;
+      h->cigar_len = c.n;
+      h->flags |= DSA_HIT_HAS_TRACEBACK;
+    }
+    __syncwarp();
   }
 }
 
@@ -513,8 +555,8 @@ int launch_long_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
                                                         d_dir);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
-  k_long_tb_walk<<<(n_jobs + 63) / 64, 64, 0, ctx->stream>>>(d_jobs, n_jobs, mode, fe, d_dir,
-                                                             d_cig_tmp, d_hits);
+  k_long_tb_walk<<<n_jobs, 32, 0, ctx->stream>>>(d_jobs, n_jobs, mode, fe, d_dir, d_cig_tmp,
+                                                 d_hits);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   return DSA_OK;
