@@ -308,21 +308,30 @@ __device__ __forceinline__ int32_t band_jlo(const LongTbJob& jb, int32_t b) {
   return max(1, min(want, jb.je - jb.wc + 1));
 }
 
+template <bool BYTES>
 __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
     const LongTbJob* __restrict__ jobs, const uint32_t* __restrict__ items, uint32_t n_items,
     const int2* __restrict__ bnd, uint32_t* __restrict__ dir) {
   __shared__ int8_t S[32 * 32];
+  __shared__ uint32_t Sb[4];   // BYTES: row q of S as 4 bytes
   for (int x = threadIdx.x; x < A * A; x += blockDim.x) S[x] = Sg[x];
+  if (BYTES && threadIdx.x < 4) {
+    uint32_t w = 0;
+    for (int a = 0; a < A; ++a)
+      if ((int)threadIdx.x < A) w |= (uint32_t)(uint8_t)Sg[threadIdx.x * A + a] << (8 * a);
+    Sb[threadIdx.x] = w;
+  }
   __syncthreads();
+  constexpr unsigned FULL = 0xFFFFFFFFu;
   const int lane = threadIdx.x & 31;
   const bool local = mode == DSA_LOCAL;
   const uint32_t warps = gridDim.x * WARPS;
   for (uint32_t it = blockIdx.x * WARPS + (threadIdx.x >> 5); it < n_items; it += warps) {
     const LongTbJob jb = jobs[items[2 * it]];
     const int32_t b = (int32_t)items[2 * it + 1];
-    const int32_t ie = jb.ie, je = jb.je;
+    const int32_t ie = jb.ie;
     const uint8_t* q = qcodes + jb.q_start;
     const uint8_t* t = tcodes + jb.t_start;
     uint32_t* D = dir + jb.dir_off;
@@ -335,36 +344,62 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
     const bool wall = jlo > 1;
     int32_t H[ROWS], E[ROWS];
     uint32_t nbw[ROWS];
-    int qc[ROWS];
+    uint32_t qv[ROWS];   // BYTES: S row of the query residue as bytes; else its matrix offset
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
       const int32_t ii = r0 + r + 1;
       H[r] = wall ? NEG32 : h_col0(mode, fe, ii, o, e);
       E[r] = NEG32;
       nbw[r] = 0;
-      qc[r] = ii <= ie ? q[ii - 1] * A : 0;
+      qv[r] = ii <= ie ? (BYTES ? Sb[q[ii - 1]] : (uint32_t)q[ii - 1] * A) : 0u;
     }
     int32_t diag = wall ? NEG32 : h_col0(mode, fe, r0, o, e);
     int32_t sendH = 0, sendF = NEG32;
+    int sendA = 0;
+    // checkpoint row above and target residues for columns jlo + blk .. + 31
+    // (lane k: column jlo + blk + k), fetched by the warp one block ahead
+    auto fetch_up = [&](int32_t blk) -> int2 {
+      const int32_t jj = jlo + blk + lane;
+      return (b > 0 && jj <= jhi) ? up[jj - 1] : make_int2(NEG32, NEG32);
+    };
+    auto fetch_res = [&](int32_t blk) -> int {
+      const int32_t jj = jlo + blk + lane;
+      return jj <= jhi ? (int)t[jj - 1] : 0;
+    };
+    int2 ucur = fetch_up(0), unxt = fetch_up(32);
+    int tcur = fetch_res(0), tnxt = fetch_res(32);
     for (int32_t s = 1; s <= jb.wc + 31; ++s) {
-      int32_t Hup = __shfl_up_sync(0xFFFFFFFFu, sendH, 1);
-      int32_t Fup = __shfl_up_sync(0xFFFFFFFFu, sendF, 1);
+      const int k = (s - 1) & 31;
+      const int32_t ux = __shfl_sync(FULL, ucur.x, k);
+      const int32_t uy = __shfl_sync(FULL, ucur.y, k);
+      const int ta = __shfl_sync(FULL, tcur, k);
+      int32_t Hup = __shfl_up_sync(FULL, sendH, 1);
+      int32_t Fup = __shfl_up_sync(FULL, sendF, 1);
+      int a = __shfl_up_sync(FULL, sendA, 1);
       const int32_t jj = jlo - 1 + s - lane;
-      if (jj >= jlo && jj <= jhi && r0 < ie) {
-        if (lane == 0) {
-          if (b == 0) {
-            Hup = h_row0(mode, fe, jj, o, e);
-            Fup = NEG32;
-          } else {
-            const int2 v = up[jj - 1];
-            Hup = v.x;
-            Fup = v.y;
-          }
+      if (lane == 0) {
+        a = ta;
+        if (b == 0) {
+          Hup = h_row0(mode, fe, jj, o, e);
+          Fup = NEG32;
+        } else {
+          Hup = ux;
+          Fup = uy;
         }
-        const int a = t[jj - 1];
+      }
+      if (k == 31) {   // block consumed: rotate, fetch the block after the next
+        ucur = unxt;
+        tcur = tnxt;
+        const int32_t blk = (s - 1 - k) + 64;
+        unxt = fetch_up(blk);
+        tnxt = fetch_res(blk);
+      }
+      sendA = a;
+      if (jj >= jlo && jj <= jhi && r0 < ie) {
         int32_t d = diag;
         diag = Hup;
         int32_t F = Fup, Hp = Hup;
+        const uint32_t sel = (uint32_t)a + ((uint32_t)a | 8u) * 0x1110u;
         const int32_t jc = jj - jlo;   // stored column
         const int sh = 4 * (jc & 7);
         const bool flushw = ((jc & 7) == 7) || jj == jhi;
@@ -376,7 +411,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
             F = max(fx, fo);
             const int32_t eo = H[r] - o, ex = E[r] - e;
             E[r] = max(ex, eo);
-            const int32_t mm = d + S[qc[r] + a];
+            const int32_t sv = BYTES ? (int32_t)prmt(qv[r], 0u, sel) : (int32_t)S[qv[r] + a];
+            const int32_t mm = d + sv;
             int32_t v = max(mm, max(E[r], F));
             if (local) v = max(v, 0);
             uint32_t src;
@@ -524,10 +560,9 @@ int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const in
   const unsigned grid = (unsigned)std::min<uint64_t>(resident, (n_items + WARPS - 1) / WARPS);
   uint32_t* counter = ctx->d_counters + 3;
   DSA_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(uint32_t), ctx->stream));
-  kern<<<grid, WARPS * 32, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e,
-                                                      mode, fe, d_jobs, d_items, n_items, counter,
-                                                      d_bnd, d_prog, static_cast<Cand*>(d_cands),
-                                                      ctx->d_status);
+  kern<<<grid, WARPS * 32, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e, mode, fe,
+                                              d_jobs, d_items, n_items, counter, d_bnd, d_prog,
+                                              static_cast<Cand*>(d_cands), ctx->d_status);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   const unsigned rb = (unsigned)std::min<uint64_t>((n_jobs + 127) / 128, 1024);
@@ -550,9 +585,9 @@ int launch_long_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
   if (n_jobs == 0) return DSA_OK;
   const unsigned grid = (unsigned)std::min<uint64_t>((n_items + WARPS - 1) / WARPS,
                                                      (uint64_t)ctx->sm_count * 16);
-  k_long_tb_fill<<<grid, WARPS * 32, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e,
-                                                        mode, fe, d_jobs, d_items, n_items, d_bnd,
-                                                        d_dir);
+  auto fill = A <= 4 ? k_long_tb_fill<true> : k_long_tb_fill<false>;
+  fill<<<grid, WARPS * 32, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e, mode, fe,
+                                              d_jobs, d_items, n_items, d_bnd, d_dir);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   k_long_tb_walk<<<n_jobs, 32, 0, ctx->stream>>>(d_jobs, n_jobs, mode, fe, d_dir, d_cig_tmp,
