@@ -1361,7 +1361,53 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
     jobs.insert(jobs.end(), tjobs.begin(), tjobs.end());
     tjobs.clear();
   }
-  if (jobs.empty() && tjobs.empty() && ljobs.empty()) return DSA_OK;
+  // Big rectangles of hits without score-pass checkpoints (1 M cells or more
+  // over at least two 256-row bands): a checkpointed score pass over the
+  // hit's rectangle (the band pipeline of the long pairs), then the long-pair
+  // traceback (parallel band fill, windowed walk) instead of one warp working
+  // through the bands one after another.
+  std::vector<LongJob> bscore;
+  std::vector<LongTbJob> bjobs;
+  uint64_t b_bnd = 0, b_bands = 0;
+  {
+    std::vector<TbJob> keep;
+    for (const TbJob& j : jobs) {
+      const dsa_hit& hit = res->h_hits[j.hit];
+      const int32_t ie = hit.q_end + 1, je = hit.t_end + 1;   // the whole rectangle
+      if ((uint64_t)ie * (uint64_t)je < (1u << 18) || ie <= band) {
+        keep.push_back(j);
+        continue;
+      }
+      const uint64_t nb = ((uint64_t)ie + band - 1) / band;
+      const uint64_t q0 = qs->h_off[hit.query_id], t0 = db->h_off[hit.target_id] + hit.t_offset;
+      bscore.push_back({q0, t0, b_bnd, b_bands, b_bands, ie, je, (uint32_t)bscore.size(), 0});
+      LongTbJob lj{};
+      lj.q_start = q0;
+      lj.t_start = t0;
+      lj.bnd_off = b_bnd;
+      lj.n = je;
+      lj.ie = ie;
+      lj.je = je;
+      lj.hit = j.hit;
+      lj.dlo = 0;
+      lj.wc = je;
+      int64_t dlo, dhi;
+      if (diag_window(ie, je, hit.score, dlo, dhi)) {
+        const int64_t wc = (int64_t)band + dhi - dlo;
+        if (wc < je) {
+          lj.dlo = (int32_t)std::max<int64_t>(dlo, -(int64_t)ie);
+          lj.wc = (int32_t)wc;
+        }
+      }
+      lj.wpr = (uint32_t)((lj.wc + 7) / 8);
+      bjobs.push_back(lj);
+      cap_total += (uint64_t)je - j.je;   // CIGAR capacity of the whole rectangle
+      b_bnd += nb * (uint64_t)je;
+      b_bands += nb;
+    }
+    jobs.swap(keep);
+  }
+  if (jobs.empty() && tjobs.empty() && ljobs.empty() && bjobs.empty()) return DSA_OK;
 
   // grow the result's CIGAR array by the capacity bound
   const uint64_t old_n = res->n_cigar;
@@ -1510,16 +1556,17 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
     DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     k0 = k1;
   }
-  if (!ljobs.empty()) {
-    // decision matrices of whole rectangles, in chunks of at most 32 GiB
+  // decision matrices of the rectangles (or their diagonal bands), in chunks
+  // of at most 32 GiB; bnd_rows: the score pass's checkpoint rows
+  auto run_long = [&](std::vector<LongTbJob>& list, const int2* bnd_rows) -> int {
     const uint64_t limit = 8ull << 30;   // words
     size_t k0 = 0;
-    while (k0 < ljobs.size()) {
+    while (k0 < list.size()) {
       uint64_t dir = 0, cig = 0;
       size_t k1 = k0;
       std::vector<uint32_t> items;
-      while (k1 < ljobs.size()) {
-        LongTbJob& lj = ljobs[k1];
+      while (k1 < list.size()) {
+        LongTbJob& lj = list[k1];
         const uint64_t w = (uint64_t)lj.ie * lj.wpr;
         if (k1 > k0 && dir + w > limit) break;
         lj.dir_off = dir;
@@ -1530,7 +1577,7 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
         for (uint32_t b = 0; b < nb; ++b) { items.push_back((uint32_t)(k1 - k0)); items.push_back(b); }
         ++k1;
       }
-      std::vector<LongTbJob> chunk(ljobs.begin() + k0, ljobs.begin() + k1);
+      std::vector<LongTbJob> chunk(list.begin() + k0, list.begin() + k1);
       std::vector<TbJob> shim(chunk.size());   // the CIGAR packer reads hit and cig_off
       for (size_t k = 0; k < chunk.size(); ++k) {
         shim[k].hit = chunk[k].hit;
@@ -1546,7 +1593,7 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
                                     res->gap_extend, res->mode, res->free_ends,
                                     d_lj.as<LongTbJob>(), (uint32_t)chunk.size(),
                                     d_items.as<uint32_t>(), (uint32_t)(items.size() / 2),
-                                    res->d_bnd, d_dir.as<uint32_t>(), d_cig.as<uint32_t>(),
+                                    bnd_rows, d_dir.as<uint32_t>(), d_cig.as<uint32_t>(),
                                     res->d_hits));
       DSA_TRY(launch_cigar_compact(ctx, res->d_hits, d_shim.as<TbJob>(), (uint32_t)shim.size(),
                                    d_cig.as<uint32_t>(), res->d_cigar, total,
@@ -1556,6 +1603,40 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
       DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
       k0 = k1;
     }
+    return DSA_OK;
+  };
+  if (!ljobs.empty()) DSA_TRY(run_long(ljobs, res->d_bnd));
+  if (!bscore.empty()) {
+    // checkpointed score pass over the big rectangles: largest first, bands in order
+    std::vector<uint32_t> order(bscore.size());
+    std::iota(order.begin(), order.end(), 0u);
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+      return (uint64_t)bscore[a].m * bscore[a].n > (uint64_t)bscore[b].m * bscore[b].n;
+    });
+    std::vector<uint32_t> items;
+    for (uint32_t x : order) {
+      const uint32_t nb = (uint32_t)((bscore[x].m + band - 1) / band);
+      for (uint32_t b = 0; b < nb; ++b) { items.push_back(x); items.push_back(b); }
+    }
+    const size_t nj = bscore.size();
+    DevBuf d_bs, d_bitems, d_bbnd, d_bprog, d_bcand, d_bout;
+    DSA_TRY(upload(ctx, d_bs, bscore));
+    DSA_TRY(upload(ctx, d_bitems, items));
+    DSA_TRY(d_bbnd.alloc(ctx, b_bnd * sizeof(int2)));
+    DSA_TRY(d_bprog.alloc(ctx, b_bands * sizeof(uint32_t)));
+    DSA_TRY(d_bcand.alloc(ctx, b_bands * long_cand_size()));
+    DSA_TRY(d_bout.alloc(ctx, nj * 13));
+    DSA_CUDA_TRY(cudaMemsetAsync(d_bprog.p, 0, b_bands * sizeof(uint32_t), ctx->stream));
+    Scores bsc;   // the rerun's scores are not needed: only its checkpoint rows
+    bsc.score = d_bout.as<int32_t>();
+    bsc.q_end = bsc.score + nj;
+    bsc.t_end = bsc.q_end + nj;
+    bsc.flag = reinterpret_cast<uint8_t*>(bsc.t_end + nj);
+    DSA_TRY(launch_long_score(ctx, db, qs, d_mat.as<int8_t>(), res->A, res->gap_open,
+                              res->gap_extend, res->mode, res->free_ends, d_bs.as<LongJob>(),
+                              (uint32_t)nj, d_bitems.as<uint32_t>(), (uint32_t)(items.size() / 2),
+                              d_bbnd.as<int2>(), d_bprog.as<uint32_t>(), d_bcand.p, bsc));
+    DSA_TRY(run_long(bjobs, d_bbnd.as<int2>()));
   }
   phase_end(res, PH_TRACE);
   res->n_cigar = total;

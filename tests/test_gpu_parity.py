@@ -628,3 +628,33 @@ def test_long_pair_band_parameter_sweep(ctx, name, S, o, e, mode, fe):
     assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), f"long band sweep {name}")
     assert r.phase_cells()["intra16"] > 0
     check_traceback(h, r.cigar(), qs, db, S, o, e, mode, fe)
+
+
+@pytest.mark.parametrize("mode,fe", [(dsa.LOCAL, 15), (dsa.GLOBAL, 15), (dsa.SEMIGLOBAL, 15)])
+def test_big_all_vs_all_hits_checkpointed_traceback(ctx, mode, fe):
+    """All-vs-all hits of 4 M cells or more: a checkpointed score pass over each
+    hit's rectangle, then the parallel band traceback (no checkpoints from the
+    search itself)."""
+    rng = np.random.default_rng(900 + mode * 16 + fe)
+    if mode == dsa.LOCAL:
+        bg = W.protein_background()
+        q0 = rng.choice(20, 2600, p=bg).astype(np.uint8)
+        targets = [W.mutate(rng, q0, 0.15, 0.02, alphabet=20) for _ in range(3)]
+        targets += [rng.choice(20, n, p=bg).astype(np.uint8) for n in rng.integers(50, 3000, 40)]
+        queries = W.SeqSet.from_list([q0, rng.choice(20, 300, p=bg).astype(np.uint8)])
+        S, o, e, A, top_k = W.blosum62(), 11, 1, 24, 5
+    else:
+        S, o, e, A, top_k = W.dna_matrix(2, -3), 5, 2, 4, 0
+        q0 = rng.integers(0, 4, 2400).astype(np.uint8)
+        targets = [W.mutate(rng, q0, 0.05, 0.01), rng.integers(0, 4, 2200).astype(np.uint8),
+                   rng.integers(0, 4, 300).astype(np.uint8)]
+        queries = W.SeqSet.from_list([q0, rng.integers(0, 4, 1900).astype(np.uint8)])
+    db = W.SeqSet.from_list(targets)
+    d = ctx.load_set(db, A)
+    q = ctx.load_set(queries, A)
+    r = ctx.align(d, q, S, o, e, mode=mode, free_ends=fe, top_k=top_k)
+    ctx.traceback(r)
+    h = r.hits()
+    big = (h["q_end"].astype(np.int64) + 1) * (h["t_end"].astype(np.int64) + 1) >= (1 << 22)
+    assert big.any()
+    check_traceback(h, r.cigar(), queries, db, S, o, e, mode, fe)
