@@ -1434,7 +1434,7 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
   {
     if (!tjobs.empty()) {
       // groups of 32 hits share a layout padded to their largest (ie, je):
-      // keep the given order when that pads little, else order by (ie, je)
+      // keep the given order unless it would double the work, else order by (ie, wc)
       // descending
       const size_t n_groups = (tjobs.size() + 31) / 32;
       const unsigned T = host_threads(tjobs.size(), 1u << 16);
@@ -1459,7 +1459,7 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
         cells += cells_t[t];
         padded += padded_t[t];
       }
-      if (padded > cells + cells / 4) {
+      if (padded > 2 * cells) {
         std::vector<uint64_t> key(tjobs.size());
         parallel_for(tjobs.size(), T, [&](unsigned, size_t b, size_t e) {
           for (size_t x = b; x < e; ++x)

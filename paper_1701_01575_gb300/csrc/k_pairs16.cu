@@ -27,6 +27,8 @@
 #include "dsa_internal.cuh"
 #include "dpx.cuh"
 
+#include <type_traits>
+
 namespace dsa {
 namespace {
 
@@ -126,96 +128,113 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
       uint32_t diag = pack2(hd, hd);
       int pend = 0;
       uint32_t thr2 = pack2(max(best_lo - 1, 0), max(best_hi - 1, 0));
-      // loads run one column ahead of the arithmetic (target residues and the
-      // boundary row handed down by the previous strip)
-      uint32_t n_alo = tlo[0], n_ahi = nhi > 0 ? thi[0] : 0u;
-      uint2 n_v = i0 > 0 ? scr[0] : make_uint2(0u, 0u);
-      for (int32_t j = 1; j <= nmax; ++j) {
-        const uint32_t a_lo = j <= nlo ? n_alo : 0u;
-        const uint32_t a_hi = j <= nhi ? n_ahi : 0u;
-        const uint2 v = n_v;
-        if (j < nmax) {
-          n_alo = j < nlo ? tlo[j] : 0u;
-          n_ahi = j < nhi ? thi[j] : 0u;
-          if (i0 > 0) n_v = scr[(uint64_t)j * stride];
-        }
-        uint32_t topHo, F;
-        if (i0 == 0) {
-          const int32_t h0l = h_row0(mode, fe, min(j, nlo), o, e) - o;
-          const int32_t h0h = h_row0(mode, fe, min(j, nhi), o, e) - o;
-          topHo = pack2(h0l, h0h);
-          F = topHo;   // F of row 1 = H[0][j] - o
-        } else {
-          topHo = v.x;
-          F = v.y;
-        }
-        uint32_t d = diag;
-        diag = topHo;
-        // BYTES: byte a_lo of the low row (sign-replicated into byte 1) and
-        // byte 4 + a_hi of the high row (sign-replicated into byte 3)
-        const uint32_t sel = (a_lo * 0x11u + 0x80u) | ((a_hi * 0x11u + 0xC4u) << 8);
-        uint32_t cm = 0, hprev = 0, hlast = 0;
+      // The column loop in four forms (first strip: top row from the boundary
+      // of the matrix; last strip: result candidates, no boundary row to hand
+      // down), so that no per-column branch depends on the strip.
+      auto columns = [&](auto first_c, auto last_c) {
+        constexpr bool FIRST = decltype(first_c)::value;
+        constexpr bool LAST = decltype(last_c)::value;
+        const bool col_n = LAST || q_end_free;   // column-n candidates in this strip
+        // loads run one column ahead of the arithmetic (target residues and
+        // the boundary row handed down by the previous strip); the last
+        // iteration re-reads a valid column instead of branching
+        uint32_t n_alo = tlo[0], n_ahi = thi[0];
+        uint2 n_v = FIRST ? make_uint2(0u, 0u) : scr[0];
+        for (int32_t j = 1; j <= nmax; ++j) {
+          const uint32_t a_lo = j <= nlo ? n_alo : 0u;
+          const uint32_t a_hi = j <= nhi ? n_ahi : 0u;
+          const uint2 v = n_v;
+          const int32_t jn = min(j, nmax - 1);
+          n_alo = tlo[min(jn, max(nlo - 1, 0))];
+          n_ahi = thi[min(jn, max(nhi - 1, 0))];
+          if (!FIRST) n_v = scr[(uint64_t)jn * stride];
+          uint32_t topHo, F;
+          if (FIRST) {
+            const int32_t h0l = h_row0(mode, fe, min(j, nlo), o, e) - o;
+            const int32_t h0h = h_row0(mode, fe, min(j, nhi), o, e) - o;
+            topHo = pack2(h0l, h0h);
+            F = topHo;   // F of row 1 = H[0][j] - o
+          } else {
+            topHo = v.x;
+            F = v.y;
+          }
+          uint32_t d = diag;
+          diag = topHo;
+          // BYTES: byte a_lo of the low row (sign-replicated into byte 1) and
+          // byte 4 + a_hi of the high row (sign-replicated into byte 3)
+          const uint32_t sel = (a_lo * 0x11u + 0x80u) | ((a_hi * 0x11u + 0xC4u) << 8);
+          uint32_t cm = 0, hprev = 0, hlast = 0;
 #pragma unroll
-        for (int r = 0; r < ROWS; ++r) {
-          if (r < rows) {
-            const uint32_t sp = BYTES ? prmt(sb_lo[r], sb_hi[r], sel)
-                                      : (uint32_t)(uint16_t)Sp[(qa[r] & 0xFFFFu) + a_lo] |
-                                            ((uint32_t)(uint16_t)Sp[(qa[r] >> 16) + a_hi] << 16);
-            const uint32_t old = Ho[r];
-            E[r] = addmax2(E[r], neg_e2, old);
-            const uint32_t t = addmax2(d, sp, E[r]);
-            const uint32_t h = local ? max2_relu(t, F) : __vmaxs2(t, F);
-            Ho[r] = add2(h, neg_o2);
-            F = addmax2(F, neg_e2, Ho[r]);
-            d = old;
-            hlast = h;
-            if (local) {
-              if (r & 1) cm = max3_2(cm, hprev, h);
-              else hprev = h;
+          for (int r = 0; r < ROWS; ++r) {
+            if (LAST ? r < rows : true) {
+              const uint32_t sp = BYTES ? prmt(sb_lo[r], sb_hi[r], sel)
+                                        : (uint32_t)(uint16_t)Sp[(qa[r] & 0xFFFFu) + a_lo] |
+                                              ((uint32_t)(uint16_t)Sp[(qa[r] >> 16) + a_hi] << 16);
+              const uint32_t old = Ho[r];
+              E[r] = addmax2(E[r], neg_e2, old);
+              const uint32_t t = addmax2(d, sp, E[r]);
+              const uint32_t h = local ? max2_relu(t, F) : __vmaxs2(t, F);
+              Ho[r] = add2(h, neg_o2);
+              F = addmax2(F, neg_e2, Ho[r]);
+              d = old;
+              hlast = h;
+              if (local) {
+                if (r & 1) cm = max3_2(cm, hprev, h);
+                else hprev = h;
+              }
+            }
+          }
+          if (local && LAST && (rows & 1)) cm = __vmaxs2(cm, hprev);
+          if (!LAST) scr[(uint64_t)(j - 1) * stride] = make_uint2(Ho[ROWS - 1], F);
+          if (local) {
+            if (__vmaxs2(cm, thr2) != thr2) {
+              const int cl = lo16(cm), ch = hi16(cm);
+              const int thr_lo = best_lo - (j < bj_lo ? 1 : 0);
+              const int thr_hi = best_hi - (j < bj_hi ? 1 : 0);
+              if (cl > thr_lo && j <= nlo) {
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) park[0][r][tid] = Ho[r];
+                best_lo = cl; bj_lo = j; pend |= 1;
+              }
+              if (ch > thr_hi && j <= nhi) {
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) park[1][r][tid] = Ho[r];
+                best_hi = ch; bj_hi = j; pend |= 2;
+              }
+              thr2 = pack2(max(best_lo - 1, 0), max(best_hi - 1, 0));
+            }
+          } else {
+            // row m (last strip) and column n
+            if (LAST && t_end_free) {
+              if (j <= nlo) clo.offer(lo16(hlast), m, j);
+              if (j <= nhi) chi.offer(hi16(hlast), m, j);
+            }
+            if (col_n && j == nlo) {
+              // column n of the low pair: first row of this strip holding its maximum
+              int bs = -32768, br = 0;
+#pragma unroll
+              for (int r = ROWS - 1; r >= 0; --r)
+                if (r < rows && (q_end_free || r == rows - 1) && lo16(Ho[r]) + o >= bs) { bs = lo16(Ho[r]) + o; br = r; }
+              clo.offer(bs, i0 + br + 1, j);
+            }
+            if (col_n && j == nhi) {
+              int bs = -32768, br = 0;
+#pragma unroll
+              for (int r = ROWS - 1; r >= 0; --r)
+                if (r < rows && (q_end_free || r == rows - 1) && hi16(Ho[r]) + o >= bs) { bs = hi16(Ho[r]) + o; br = r; }
+              chi.offer(bs, i0 + br + 1, j);
             }
           }
         }
-        if (local && (rows & 1)) cm = __vmaxs2(cm, hprev);
-        if (!last) scr[(uint64_t)(j - 1) * stride] = make_uint2(Ho[ROWS - 1], F);   // !last => rows == ROWS
-        if (local) {
-          if (__vmaxs2(cm, thr2) != thr2) {
-            const int cl = lo16(cm), ch = hi16(cm);
-            const int thr_lo = best_lo - (j < bj_lo ? 1 : 0);
-            const int thr_hi = best_hi - (j < bj_hi ? 1 : 0);
-            if (cl > thr_lo && j <= nlo) {
-#pragma unroll
-              for (int r = 0; r < ROWS; ++r) park[0][r][tid] = Ho[r];
-              best_lo = cl; bj_lo = j; pend |= 1;
-            }
-            if (ch > thr_hi && j <= nhi) {
-#pragma unroll
-              for (int r = 0; r < ROWS; ++r) park[1][r][tid] = Ho[r];
-              best_hi = ch; bj_hi = j; pend |= 2;
-            }
-            thr2 = pack2(max(best_lo - 1, 0), max(best_hi - 1, 0));
-          }
-        } else {
-          // row m (last strip) and column n
-          if (last && t_end_free) {
-            if (j <= nlo) clo.offer(lo16(hlast), m, j);
-            if (j <= nhi) chi.offer(hi16(hlast), m, j);
-          }
-          if (j == nlo && (q_end_free || last)) {
-            // column n of the low pair: first row of this strip holding its maximum
-            int bs = -32768, br = 0;
-#pragma unroll
-            for (int r = ROWS - 1; r >= 0; --r)
-              if (r < rows && (q_end_free || r == rows - 1) && lo16(Ho[r]) + o >= bs) { bs = lo16(Ho[r]) + o; br = r; }
-            clo.offer(bs, i0 + br + 1, j);
-          }
-          if (j == nhi && (q_end_free || last)) {
-            int bs = -32768, br = 0;
-#pragma unroll
-            for (int r = ROWS - 1; r >= 0; --r)
-              if (r < rows && (q_end_free || r == rows - 1) && hi16(Ho[r]) + o >= bs) { bs = hi16(Ho[r]) + o; br = r; }
-            chi.offer(bs, i0 + br + 1, j);
-          }
-        }
+      };
+      using T_ = std::true_type;
+      using F_ = std::false_type;
+      if (i0 == 0) {
+        if (last) columns(T_{}, T_{});
+        else columns(T_{}, F_{});
+      } else {
+        if (last) columns(F_{}, T_{});
+        else columns(F_{}, F_{});
       }
       if (pend & 1) {
         const int want = best_lo - o;
