@@ -16,6 +16,9 @@
 // run-length CIGAR words in reverse order; a second kernel packs them
 // forward into the result's CIGAR array.
 #include "dsa_internal.cuh"
+#include "dpx.cuh"
+
+#include <type_traits>
 
 namespace dsa {
 namespace {
@@ -229,17 +232,25 @@ __global__ void __launch_bounds__(128) k_traceback(
 // optimal path and on every candidate that ties there.
 constexpr int TROWS = 16;
 
-__global__ void __launch_bounds__(128) k_traceback_thread(
+template <bool LOCAL, bool BYTES>
+__global__ void __launch_bounds__(128, 4) k_traceback_thread(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
     const TbJob* __restrict__ jobs, uint32_t n_jobs, uint32_t* __restrict__ dir,
     uint32_t* __restrict__ cig_tmp, int2* __restrict__ scratch, dsa_hit* __restrict__ hits) {
   __shared__ int32_t S[32 * 32];
+  __shared__ uint32_t Sb[4];   // BYTES: row q of S as 4 bytes
   for (int x = threadIdx.x; x < A * A; x += blockDim.x) S[x] = Sg[x];
+  if (BYTES && threadIdx.x < 4) {
+    uint32_t w = 0;
+    for (int a = 0; a < A; ++a)
+      if ((int)threadIdx.x < A) w |= (uint32_t)(uint8_t)Sg[threadIdx.x * A + a] << (8 * a);
+    Sb[threadIdx.x] = w;
+  }
   __syncthreads();
   const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_jobs) return;
-  const bool local = mode == DSA_LOCAL;
+  constexpr bool local = LOCAL;
   const TbJob jb = jobs[k];
   const int32_t ie = jb.ie, je = jb.je;
   const uint8_t* q = qcodes + jb.q_start;
@@ -259,12 +270,12 @@ __global__ void __launch_bounds__(128) k_traceback_thread(
       const int32_t jlo = strip_jlo(i0), jhi = jlo + wc - 1;
       const bool wall = jlo > 1 || jb.jlo > 0;   // column jlo - 1 is -inf below row 0
       int32_t H[TROWS], E[TROWS];
-      int qa[TROWS];
+      uint32_t qv[TROWS];   // BYTES: S row of the query residue as bytes; else its matrix offset
 #pragma unroll
       for (int r = 0; r < TROWS; ++r) {
         H[r] = wall ? NEG32 : h_col0(mode, fe, i0 + r + 1, o, e);
         E[r] = NEG32;
-        qa[r] = r < rows ? q[i0 + r] * A : 0;
+        qv[r] = r < rows ? (BYTES ? Sb[q[i0 + r]] : (uint32_t)q[i0 + r] * A) : 0u;
       }
       // H[i0][jlo - 1]
       int32_t diag;
@@ -272,54 +283,75 @@ __global__ void __launch_bounds__(128) k_traceback_thread(
       else if (jlo == 1) diag = jb.jlo > 0 ? NEG32 : h_col0(mode, fe, i0, o, e);
       else diag = (jlo - 1 >= plo && jlo - 1 <= phi) ? scr[(uint64_t)(jlo - 2) * 32].x : NEG32;
       uint32_t* Ds = D + (uint64_t)s * cols * 64;
-      // loads run one column ahead of the arithmetic
-      int n_a = t[jlo - 1];
-      int2 n_v = (i0 > 0 && jlo <= phi) ? scr[(uint64_t)(jlo - 1) * 32] : NEGP;
-      for (int32_t j = jlo; j <= jhi; ++j) {
-        const int a = n_a;
-        const int2 v = n_v;
-        if (j < jhi) {
-          n_a = t[j];
-          n_v = (i0 > 0 && j + 1 <= phi) ? scr[(uint64_t)j * 32] : NEGP;
-        }
-        int32_t Hp, F;
-        if (i0 == 0) {
-          Hp = h_row0(mode, fe, j, o, e);
-          F = NEG32;
-        } else {
-          Hp = v.x;
-          F = v.y;
-        }
-        int32_t d = diag;
-        diag = Hp;
-        uint32_t w0 = 0, w1 = 0;
-#pragma unroll
-        for (int r = 0; r < TROWS; ++r) {
-          if (r < rows) {
-            const int32_t fo = Hp - o, fx = F - e;
-            F = max(fx, fo);
-            const int32_t eo = H[r] - o, ex = E[r] - e;
-            E[r] = max(ex, eo);
-            const int32_t m = d + S[qa[r] + a];
-            int32_t v = max(m, max(E[r], F));
-            if (local) v = max(v, 0);
-            uint32_t src;
-            if (local && v == 0) src = 3;
-            else if (v == m) src = 0;
-            else if (v == F) src = 1;
-            else src = 2;
-            const uint32_t nib = src | ((eo >= ex) ? 4u : 0u) | ((fo >= fx) ? 8u : 0u);
-            if (r < 8) w0 |= nib << (4 * r);
-            else w1 |= nib << (4 * (r - 8));
-            d = H[r];
-            H[r] = v;
-            Hp = v;
+      // the column loop in four forms (first strip: top row from the boundary
+      // of the matrix; last strip: nothing to hand down), with no per-column
+      // branch that depends on the strip
+      auto columns = [&](auto first_c, auto last_c) {
+        constexpr bool FIRST = decltype(first_c)::value;
+        constexpr bool LAST = decltype(last_c)::value;
+        // loads run one column ahead of the arithmetic; the last iteration
+        // re-reads a valid column instead of branching
+        int n_a = t[jlo - 1];
+        int2 n_v = (!FIRST && jlo <= phi) ? scr[(uint64_t)(jlo - 1) * 32] : NEGP;
+        for (int32_t j = jlo; j <= jhi; ++j) {
+          const int a = n_a;
+          const int2 v = n_v;
+          n_a = t[min(j, jhi - 1)];
+          if (!FIRST) {
+            const int2 nv = scr[(uint64_t)min(j, phi - 1) * 32];
+            n_v = j + 1 <= phi ? nv : NEGP;
           }
+          int32_t Hp, F;
+          if (FIRST) {
+            Hp = h_row0(mode, fe, j, o, e);
+            F = NEG32;
+          } else {
+            Hp = v.x;
+            F = v.y;
+          }
+          int32_t d = diag;
+          diag = Hp;
+          // BYTES: byte a of the row table, sign-replicated into bytes 1-3
+          const uint32_t sel = (uint32_t)a + ((uint32_t)a | 8u) * 0x1110u;
+          uint32_t w0 = 0, w1 = 0;
+#pragma unroll
+          for (int r = 0; r < TROWS; ++r) {
+            if (LAST ? r < rows : true) {
+              const int32_t fo = Hp - o, fx = F - e;
+              F = max(fx, fo);
+              const int32_t eo = H[r] - o, ex = E[r] - e;
+              E[r] = max(ex, eo);
+              const int32_t sv = BYTES ? (int32_t)prmt(qv[r], 0u, sel) : S[qv[r] + a];
+              const int32_t m = d + sv;
+              int32_t v = max(m, max(E[r], F));
+              if (local) v = max(v, 0);
+              uint32_t src;
+              if (local && v == 0) src = 3;
+              else if (v == m) src = 0;
+              else if (v == F) src = 1;
+              else src = 2;
+              const uint32_t nib = src | ((eo >= ex) ? 4u : 0u) | ((fo >= fx) ? 8u : 0u);
+              if (r < 8) w0 |= nib << (4 * r);
+              else w1 |= nib << (4 * (r - 8));
+              d = H[r];
+              H[r] = v;
+              Hp = v;
+            }
+          }
+          const uint64_t c = (uint64_t)(j - jlo);
+          Ds[c * 64] = w0;
+          if (!LAST || rows > 8) Ds[c * 64 + 32] = w1;
+          if (!LAST) scr[(uint64_t)(j - 1) * 32] = make_int2(Hp, F);
         }
-        const uint64_t c = (uint64_t)(j - jlo);
-        Ds[c * 64] = w0;
-        if (rows > 8) Ds[c * 64 + 32] = w1;
-        if (!last) scr[(uint64_t)(j - 1) * 32] = make_int2(Hp, F);
+      };
+      using T_ = std::true_type;
+      using F_ = std::false_type;
+      if (i0 == 0) {
+        if (last) columns(T_{}, T_{});
+        else columns(T_{}, F_{});
+      } else {
+        if (last) columns(F_{}, T_{});
+        else columns(F_{}, F_{});
       }
       plo = jlo;
       phi = jhi;
@@ -440,9 +472,12 @@ int launch_traceback_thread(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
                             uint32_t* d_cig_tmp, int2* d_scr, dsa_hit* d_hits) {
   if (n_jobs == 0) return DSA_OK;
   const unsigned blocks = (n_jobs + 127) / 128;
-  k_traceback_thread<<<blocks, 128, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e,
-                                                      mode, fe, d_jobs, n_jobs, d_dir, d_cig_tmp,
-                                                      d_scr, d_hits);
+  const bool bytes = A <= 4;   // substitution scores by byte permute
+  auto kern = mode == DSA_LOCAL
+                  ? (bytes ? k_traceback_thread<true, true> : k_traceback_thread<true, false>)
+                  : (bytes ? k_traceback_thread<false, true> : k_traceback_thread<false, false>);
+  kern<<<blocks, 128, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e, mode, fe, d_jobs,
+                                        n_jobs, d_dir, d_cig_tmp, d_scr, d_hits);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   return DSA_OK;
