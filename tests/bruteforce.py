@@ -41,35 +41,38 @@ def alignments(a: int, b: int):
 
 
 @functools.lru_cache(maxsize=None)
-def _tables(a: int, b: int, o: int, e: int):
-    """Per op string: gap cost and the (x, y) M-column incidence over an a x b grid."""
+def _shape_tables(a: int, b: int):
+    """Per op string over an a x b grid: the (x, y) M-column incidence, the
+    number of gap runs and the total gap length (a run of k gap columns costs
+    o + (k-1)e = (o - e) + k e, so the gaps of an op string cost
+    runs (o - e) + length e)."""
     ops = alignments(a, b)
-    inc = np.zeros((len(ops), max(1, a * b)), dtype=np.int64)
-    gap = np.zeros(len(ops), dtype=np.int64)
+    inc = np.zeros((len(ops), max(1, a * b)), dtype=np.int32)
+    runs = np.zeros(len(ops), dtype=np.int64)
+    glen = np.zeros(len(ops), dtype=np.int64)
     for k, s in enumerate(ops):
         x = y = 0
         prev = None
-        run = 0
-        cost = 0
         for op in s:
             if op == M:
                 inc[k, x * b + y] = 1
                 x += 1; y += 1
-            elif op == I:
-                x += 1
             else:
-                y += 1
-            if op != M and op == prev:
-                run += 1
-            else:
-                if prev is not None and prev != M:
-                    cost += o + (run - 1) * e
-                run = 1
+                if op == I:
+                    x += 1
+                else:
+                    y += 1
+                glen[k] += 1
+                if op != prev:
+                    runs[k] += 1
             prev = op
-        if prev is not None and prev != M:
-            cost += o + (run - 1) * e
-        gap[k] = cost
-    return ops, inc, gap
+    return ops, inc, runs, glen
+
+
+def _tables(a: int, b: int, o: int, e: int):
+    """Op strings, M-column incidence and gap cost of every alignment of a x b."""
+    ops, inc, runs, glen = _shape_tables(a, b)
+    return ops, inc, runs * (o - e) + glen * e
 
 
 def _allowed(m, n, mode, fe):
@@ -112,8 +115,8 @@ def brute(q, t, S, o, e, mode, fe=15):
         a, b = i - a0, j - b0
         ops, inc, gap = _tables(a, b, o, e)
         if a * b:
-            sub = S[np.ix_(q[a0:i], t[b0:j])].reshape(-1)
-            scores = inc @ sub - gap
+            sub = S[np.ix_(q[a0:i], t[b0:j])].reshape(-1).astype(np.int32)
+            scores = (inc @ sub).astype(np.int64) - gap
         else:
             scores = -gap
         top = int(scores.max())
