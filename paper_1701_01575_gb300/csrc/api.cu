@@ -12,6 +12,9 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <unistd.h>
+#include <sys/stat.h>
+#include <map>
 #include <thread>
 
 namespace dsa {
@@ -509,42 +512,102 @@ extern "C" int dsa_db_info(const dsa_db* db, uint32_t* n_seqs, uint64_t* n_resid
 
 namespace {
 
-// Score pass for all queries x all targets.
-int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs, int mode,
-                     uint32_t fe, const int8_t* d_mat, int A, int o, int e, const Validated& v,
-                     uint32_t flags, Scores out, uint64_t* n_rerun) {
-  const uint32_t nq = qs->n, nt = db->n;
-  const bool packed = mode == DSA_LOCAL && !(flags & (DSA_FORCE_INT32 | DSA_PLAIN_FORM)) &&
-                      o >= 1 && o + e <= 4096 && v.smax + o < 8192 && v.smin > -8192;
-  *n_rerun = 0;
-  if (!packed) {
-    // exact int32: one launch per query over every target (input order)
-    std::vector<uint64_t> poff(nq);
-    uint64_t words = 0;
-    for (uint32_t q = 0; q < nq; ++q) {
-      poff[q] = words;
-      words += (uint64_t)A * ((qs->h_len[q] + 7u) & ~7u);
-    }
-    DevBuf d_prof, d_poff, d_scr;
-    DSA_TRY(d_prof.alloc(ctx, words * sizeof(int32_t)));
-    DSA_TRY(upload(ctx, d_poff, poff));
-    DSA_TRY(launch_profile_int32(ctx, qs, d_mat, A, d_prof.as<int32_t>(), d_poff.as<uint64_t>()));
-    DSA_TRY(d_scr.alloc(ctx, db->n_res * sizeof(int2)));
-    if (res) {
-      uint64_t qsum = 0;
-      for (uint32_t x : qs->h_len) qsum += x;
-      res->phase_cells[PH_INT32] += qsum * db->n_res;
-    }
-    phase_begin(res, PH_INT32);
-    for (uint32_t q = 0; q < nq; ++q)
-      DSA_TRY(launch_generic_int32(ctx, db, qs, d_prof.as<int32_t>(), d_poff.as<uint64_t>(),
-                                   nullptr, nt, q, d_scr.as<int2>(), mode, fe, o, e, 0, out));
-    phase_end(res, PH_INT32);
-    return DSA_OK;
-  }
+// ---- autotuner: the long-target threshold of the packed path ----
+//
+// Which targets go to the wavefront kernel (long) and which to the
+// inter-sequence kernel is a speed choice only (both are exact).  For a
+// workload shape (GPU, alphabet, and log2 bins of the query count, query
+// residues, target count, database residues and longest target) the first
+// call times a small local search of thresholds -- starting at 4096, then
+// lower or higher by factors of 4 while it keeps improving by 3% or more --
+// and keeps the best in a JSON cache file.  DSA_AUTOTUNE=off (fixed 4096) | cache (default:
+// tune on a miss) | retune (always tune); DSA_AUTOTUNE_CACHE names the file
+// (default $XDG_CACHE_HOME/dsa/autotune.json or ~/.cache/dsa/autotune.json);
+// DSA_LONG_THRESHOLD overrides everything.
+struct Tuner {
+  std::mutex mu;
+  bool loaded = false;
+  std::string path;
+  std::map<std::string, uint32_t> cache;
+};
+Tuner& tuner() {
+  static Tuner t;
+  return t;
+}
 
-  // ---- packed path ----
-  DSA_TRY(ensure_interleaved(ctx, db));
+std::string tune_cache_path() {
+  if (const char* p = getenv("DSA_AUTOTUNE_CACHE")) return p;
+  std::string dir;
+  if (const char* x = getenv("XDG_CACHE_HOME")) dir = x;
+  else if (const char* h = getenv("HOME")) dir = std::string(h) + "/.cache";
+  else return "";
+  return dir + "/dsa/autotune.json";
+}
+
+// flat JSON object of "key": unsigned integer
+void tune_load(Tuner& t, const std::string& path) {
+  t.loaded = true;
+  t.path = path;
+  t.cache.clear();
+  if (t.path.empty()) return;
+  FILE* f = fopen(t.path.c_str(), "rb");
+  if (!f) return;
+  std::string txt;
+  char buf[4096];
+  size_t n;
+  while ((n = fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, n);
+  fclose(f);
+  size_t pos = 0;
+  for (;;) {
+    const size_t k0 = txt.find('"', pos);
+    if (k0 == std::string::npos) break;
+    const size_t k1 = txt.find('"', k0 + 1);
+    if (k1 == std::string::npos) break;
+    const size_t c = txt.find(':', k1);
+    if (c == std::string::npos) break;
+    char* endp = nullptr;
+    const unsigned long long val = strtoull(txt.c_str() + c + 1, &endp, 10);
+    if (endp == txt.c_str() + c + 1) break;
+    t.cache[txt.substr(k0 + 1, k1 - k0 - 1)] =
+        (uint32_t)std::min<unsigned long long>(val, UINT32_MAX);
+    pos = (size_t)(endp - txt.c_str());
+  }
+}
+
+void tune_store(Tuner& t) {
+  if (t.path.empty()) return;
+  const size_t slash = t.path.rfind('/');
+  if (slash != std::string::npos) {
+    // create the directory chain (failures are ignored: the cache is optional)
+    const std::string d = t.path.substr(0, slash);
+    for (size_t k = 1; k <= d.size(); ++k)
+      if (k == d.size() || d[k] == '/') mkdir(d.substr(0, k).c_str(), 0755);
+  }
+  const std::string tmp = t.path + ".tmp" + std::to_string((long long)getpid());
+  FILE* f = fopen(tmp.c_str(), "wb");
+  if (!f) return;
+  fputs("{\n", f);
+  size_t k = 0;
+  for (const auto& kv : t.cache)
+    fprintf(f, "  \"%s\": %u%s\n", kv.first.c_str(), kv.second, ++k < t.cache.size() ? "," : "");
+  fputs("}\n", f);
+  fclose(f);
+  rename(tmp.c_str(), t.path.c_str());
+}
+
+int ilog2_bin(uint64_t x) {
+  int b = 0;
+  while (x > 1) { x >>= 1; ++b; }
+  return b;
+}
+
+// Packed score pass (local, int16x2): targets of groups longer than
+// `long_thr` go to the wavefront kernel on the side stream, the rest to the
+// inter-sequence kernel.  The results do not depend on long_thr, only the time.
+int packed_score(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
+                 const int8_t* d_mat, int A, int o, int e, const Validated& v, Scores out,
+                 uint32_t long_thr) {
+  const uint32_t nq = qs->n, nt = db->n;
   const int R = A + 1;
   std::vector<uint32_t> qorder(nq);
   std::iota(qorder.begin(), qorder.end(), 0u);
@@ -553,8 +616,6 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
   auto strips_of = [&](uint32_t q) { return (qs->h_len[q] + INTER_ROWS - 1) / INTER_ROWS; };
 
   // groups whose longest target exceeds the threshold go to the wavefront kernel
-  uint32_t long_thr = 4096;
-  if (const char* env = getenv("DSA_LONG_THRESHOLD")) long_thr = (uint32_t)strtoul(env, nullptr, 10);
   uint32_t g_long = 0;
   while (g_long < db->n_groups && db->h_glen[g_long] > long_thr) ++g_long;
   const uint32_t n_long = std::min<uint32_t>(nt, g_long * GROUP);
@@ -723,6 +784,145 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
   DSA_TRY(launch_inter_local16(ctx, db, spl, iw, o, e, v.smax, out, nt));
   phase_end(res, PH_INTER);
   if (n_long) DSA_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->join_ev, 0));
+  return DSA_OK;
+}
+
+// The packed pass with the autotuned long-target threshold.
+int run_packed_tuned(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
+                     const int8_t* d_mat, int A, int o, int e, const Validated& v, Scores out) {
+  if (const char* env = getenv("DSA_LONG_THRESHOLD"))
+    return packed_score(ctx, res, db, qs, d_mat, A, o, e, v, out,
+                        (uint32_t)strtoul(env, nullptr, 10));
+  const char* mode_env = getenv("DSA_AUTOTUNE");
+  const std::string mode = mode_env ? mode_env : "cache";
+  constexpr uint32_t DEFAULT_THR = 4096;
+  if (mode == "off") return packed_score(ctx, res, db, qs, d_mat, A, o, e, v, out, DEFAULT_THR);
+  // workload shape key
+  uint64_t qres = 0;
+  for (uint32_t x : qs->h_len) qres += x;
+  cudaDeviceProp prop;
+  DSA_CUDA_TRY(cudaGetDeviceProperties(&prop, ctx->device));
+  int drv = 0;
+  cudaDriverGetVersion(&drv);
+  char key[512];
+  snprintf(key, sizeof key, "%s|sm%d|drv%d|A%d|q%d|qr%d|t%d|tr%d|L%d", prop.name, ctx->sm_count,
+           drv, A, ilog2_bin(qs->n), ilog2_bin(qres), ilog2_bin(db->n), ilog2_bin(db->n_res),
+           ilog2_bin(db->max_len));
+  Tuner& t = tuner();
+  {
+    std::lock_guard<std::mutex> lk(t.mu);
+    const std::string path = tune_cache_path();
+    if (!t.loaded || path != t.path) tune_load(t, path);   // first use, or another file
+    auto it = t.cache.find(key);
+    if (mode != "retune" && it != t.cache.end())
+      return packed_score(ctx, res, db, qs, d_mat, A, o, e, v, out, it->second);
+  }
+  if (!ctx->tune)   // contexts that must not spend calls on tuning (serving workers)
+    return packed_score(ctx, res, db, qs, d_mat, A, o, e, v, out, DEFAULT_THR);
+  // thresholds are compared by the number of target groups they move
+  auto groups_over = [&](uint32_t thr) {
+    uint32_t g = 0;
+    while (g < db->n_groups && db->h_glen[g] > thr) ++g;
+    return g;
+  };
+  std::map<uint32_t, double> timed;   // long groups -> ms
+  cudaEvent_t ev0, ev1;
+  DSA_CUDA_TRY(cudaEventCreate(&ev0));
+  DSA_CUDA_TRY(cudaEventCreate(&ev1));
+  int rc = DSA_OK;
+  auto measure = [&](uint32_t thr) -> double {
+    const uint32_t g = groups_over(thr);
+    auto it = timed.find(g);
+    if (it != timed.end()) return it->second;
+    float ms = 0.f;
+    if (rc == DSA_OK && cudaEventRecord(ev0, ctx->stream) != cudaSuccess) rc = DSA_ERR_CUDA;
+    if (rc == DSA_OK) rc = packed_score(ctx, nullptr, db, qs, d_mat, A, o, e, v, out, thr);
+    if (rc == DSA_OK && cudaEventRecord(ev1, ctx->stream) != cudaSuccess) rc = DSA_ERR_CUDA;
+    if (rc == DSA_OK && cudaEventSynchronize(ev1) != cudaSuccess) rc = DSA_ERR_CUDA;
+    if (rc == DSA_OK) cudaEventElapsedTime(&ms, ev0, ev1);
+    timed[g] = ms;
+    return ms;
+  };
+  // local search from the default by factors of 4, in each direction while it
+  // improves; thresholds that move the same groups as the last one are
+  // skipped, and a switch needs a gain of at least 3% (single timings)
+  uint32_t best = DEFAULT_THR;
+  double best_ms = measure(best);
+  for (int dir = -1; dir <= 1 && rc == DSA_OK; dir += 2) {
+    uint64_t cur = DEFAULT_THR;
+    uint32_t last_g = groups_over(DEFAULT_THR);
+    for (int step = 0; step < 12 && rc == DSA_OK; ++step) {
+      const uint64_t nx = dir < 0 ? cur / 4 : cur * 4;
+      const uint32_t thr = (dir > 0 && nx >= db->max_len) ? UINT32_MAX : (uint32_t)nx;
+      cur = nx;
+      const uint32_t g = groups_over(thr);
+      if (g == last_g) {
+        if (thr == 0 || thr == UINT32_MAX) break;
+        continue;
+      }
+      last_g = g;
+      const double ms = measure(thr);
+      if (ms < 0.97 * best_ms) {
+        best_ms = ms;
+        best = thr;
+      } else {
+        break;
+      }
+      if (thr == 0 || thr == UINT32_MAX) break;
+    }
+  }
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (rc) {
+    set_error("autotune: %s", cudaGetErrorString(cudaGetLastError()));
+    return rc;
+  }
+  {
+    std::lock_guard<std::mutex> lk(t.mu);
+    t.cache[key] = best;
+    tune_store(t);
+  }
+  // the final pass with the chosen threshold records the phase timings and cells
+  return packed_score(ctx, res, db, qs, d_mat, A, o, e, v, out, best);
+}
+
+// Score pass for all queries x all targets.
+int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs, int mode,
+                     uint32_t fe, const int8_t* d_mat, int A, int o, int e, const Validated& v,
+                     uint32_t flags, Scores out, uint64_t* n_rerun) {
+  const uint32_t nq = qs->n, nt = db->n;
+  const bool packed = mode == DSA_LOCAL && !(flags & (DSA_FORCE_INT32 | DSA_PLAIN_FORM)) &&
+                      o >= 1 && o + e <= 4096 && v.smax + o < 8192 && v.smin > -8192;
+  *n_rerun = 0;
+  if (!packed) {
+    // exact int32: one launch per query over every target (input order)
+    std::vector<uint64_t> poff(nq);
+    uint64_t words = 0;
+    for (uint32_t q = 0; q < nq; ++q) {
+      poff[q] = words;
+      words += (uint64_t)A * ((qs->h_len[q] + 7u) & ~7u);
+    }
+    DevBuf d_prof, d_poff, d_scr;
+    DSA_TRY(d_prof.alloc(ctx, words * sizeof(int32_t)));
+    DSA_TRY(upload(ctx, d_poff, poff));
+    DSA_TRY(launch_profile_int32(ctx, qs, d_mat, A, d_prof.as<int32_t>(), d_poff.as<uint64_t>()));
+    DSA_TRY(d_scr.alloc(ctx, db->n_res * sizeof(int2)));
+    if (res) {
+      uint64_t qsum = 0;
+      for (uint32_t x : qs->h_len) qsum += x;
+      res->phase_cells[PH_INT32] += qsum * db->n_res;
+    }
+    phase_begin(res, PH_INT32);
+    for (uint32_t q = 0; q < nq; ++q)
+      DSA_TRY(launch_generic_int32(ctx, db, qs, d_prof.as<int32_t>(), d_poff.as<uint64_t>(),
+                                   nullptr, nt, q, d_scr.as<int2>(), mode, fe, o, e, 0, out));
+    phase_end(res, PH_INT32);
+    return DSA_OK;
+  }
+
+  // ---- packed path ----
+  DSA_TRY(ensure_interleaved(ctx, db));
+  DSA_TRY(run_packed_tuned(ctx, res, db, qs, d_mat, A, o, e, v, out));
 
   // ---- exact int32 rerun of saturated pairs ----
   const uint64_t n_out = (uint64_t)nq * nt;

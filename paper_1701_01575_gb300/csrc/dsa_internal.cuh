@@ -58,6 +58,7 @@ struct dsa_ctx {
   int32_t* d_status = nullptr;   // device status word written by kernels
   uint32_t* d_counters = nullptr;  // work-queue counters (reset per launch)
   uint64_t launches = 0;         // kernels launched through this context
+  bool tune = true;              // may spend calls on autotuning (off for serving workers)
   // the context's own stream-ordered memory pool; it keeps freed memory
   // mapped (up to the budget) instead of returning it at every synchronize
   cudaMemPool_t pool = nullptr;

@@ -287,6 +287,7 @@ extern "C" int dsa_server_create(int device, const dsa_server_config* cfg, dsa_s
       delete s;
       return rc;
     }
+    c->tune = false;   // requests use cached tuning decisions only: no tuning passes in a request
     s->slots.push_back(c);
   }
   s->sm_count = s->slots[0]->sm_count;

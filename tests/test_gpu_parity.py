@@ -658,3 +658,36 @@ def test_big_all_vs_all_hits_checkpointed_traceback(ctx, mode, fe):
     big = (h["q_end"].astype(np.int64) + 1) * (h["t_end"].astype(np.int64) + 1) >= (1 << 22)
     assert big.any()
     check_traceback(h, r.cigar(), queries, db, S, o, e, mode, fe)
+
+
+def test_autotuned_long_threshold(ctx, tmp_path, monkeypatch):
+    """The packed path's long-target threshold is tuned on the first call of a
+    workload shape, stored in the cache file and reused; results stay exact."""
+    cache = tmp_path / "autotune.json"
+    monkeypatch.setenv("DSA_AUTOTUNE_CACHE", str(cache))
+    monkeypatch.delenv("DSA_LONG_THRESHOLD", raising=False)
+    rng = np.random.default_rng(77)
+    bg = W.protein_background()
+    queries = W.SeqSet.from_list([rng.choice(20, n, p=bg).astype(np.uint8) for n in (90, 140, 300)])
+    db = W.SeqSet.from_list([rng.choice(20, n, p=bg).astype(np.uint8)
+                             for n in np.concatenate([rng.integers(20, 400, 300), [5000, 9000, 20000]])])
+    S = W.blosum62()
+    sc, qe, te = oracle.score_all_vs_all(queries, db, S, 11, 1, oracle.LOCAL, 15)
+    d = ctx.load_set(db, 24)
+    q = ctx.load_set(queries, 24)
+    for mode in ("retune", "cache", "off"):
+        monkeypatch.setenv("DSA_AUTOTUNE", mode)
+        before = ctx.kernel_launches()
+        r = ctx.align(d, q, S, 11, 1)
+        ctx.sync()
+        launches = ctx.kernel_launches() - before
+        h = r.hits()
+        assert_same((h["score"], h["q_end"], h["t_end"]),
+                    (sc.reshape(-1), qe.reshape(-1), te.reshape(-1)), f"autotune {mode}")
+        if mode == "retune":
+            tuned_launches = launches
+            text = cache.read_text()
+            assert "|A24|" in text and ":" in text
+        elif mode == "cache":
+            assert launches < tuned_launches   # no tuning passes on a cache hit
+        r.free()
