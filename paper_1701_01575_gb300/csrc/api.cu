@@ -1387,12 +1387,115 @@ static int fetch_hits(dsa_res* res) {
   return DSA_OK;
 }
 
+namespace dsa {
+
+int traceback_device_staged(dsa_ctx* ctx, dsa_res* res, const TbBounds& B) {
+  const uint64_t n = res->n_hits;
+  const dsa_db* db = res->db;
+  const dsa_db* qs = res->queries;
+  DevBuf d_full, d_valid, d_cnt;
+  DSA_TRY(d_full.alloc(ctx, n * sizeof(TbJob)));
+  DSA_TRY(d_valid.alloc(ctx, n * sizeof(uint64_t)));
+  DSA_TRY(d_cnt.alloc(ctx, 8 * sizeof(uint64_t)));
+  uint64_t* cnt = d_cnt.as<uint64_t>();   // [0] valid jobs, [1..3] layout totals, [4] not small
+  DSA_CUDA_TRY(cudaMemsetAsync(cnt, 0, 8 * sizeof(uint64_t), ctx->stream));
+  phase_begin(res, PH_TRACE);   // the phase includes the staging
+  DSA_TRY(launch_tb_stage(ctx, res->d_hits, n, qs->d_off, db->d_off, B, d_full.as<TbJob>(),
+                          d_valid.as<uint64_t>(), reinterpret_cast<uint32_t*>(cnt + 4)));
+  DSA_TRY(launch_scan_u64(ctx, d_valid.as<uint64_t>(), n, cnt + 0));
+  uint64_t h_cnt[8];
+  DSA_CUDA_TRY(cudaMemcpyAsync(h_cnt, cnt, sizeof h_cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if ((uint32_t)h_cnt[4] != 0) return TB_STAGE_FALLBACK;   // a hit needs another path
+  const uint64_t nv = h_cnt[0];
+  if (nv == 0) return DSA_OK;
+  DevBuf d_jobs, d_gdir, d_gscr, d_jcig;
+  const uint64_t n_groups = (nv + 31) / 32;
+  DSA_TRY(d_jobs.alloc(ctx, nv * sizeof(TbJob)));
+  DSA_TRY(launch_tb_compact(ctx, d_full.as<TbJob>(), d_valid.as<uint64_t>(), cnt + 0, n,
+                            d_jobs.as<TbJob>()));
+  d_full.reset();
+  d_valid.reset();
+  DSA_TRY(d_gdir.alloc(ctx, n_groups * sizeof(uint64_t)));
+  DSA_TRY(d_gscr.alloc(ctx, n_groups * sizeof(uint64_t)));
+  DSA_TRY(d_jcig.alloc(ctx, nv * sizeof(uint64_t)));
+  DSA_TRY(launch_tb_layout(ctx, d_jobs.as<TbJob>(), nv, d_gdir.as<uint64_t>(), d_gscr.as<uint64_t>(),
+                           d_jcig.as<uint64_t>(), cnt + 1));
+  DSA_CUDA_TRY(cudaMemcpyAsync(h_cnt, cnt, sizeof h_cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  const uint64_t dir = h_cnt[1], scr = h_cnt[2], cap = h_cnt[3];
+  d_gdir.reset();
+  d_gscr.reset();
+  d_jcig.reset();
+  // grow the result's CIGAR array by the capacity bound
+  const uint64_t old_n = res->n_cigar;
+  void* newp = nullptr;
+  DSA_TRY(ctx->alloc(&newp, (old_n + cap) * sizeof(uint32_t)));
+  if (old_n)
+    DSA_CUDA_TRY(cudaMemcpyAsync(newp, res->d_cigar, old_n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (res->d_cigar) ctx->release(res->d_cigar, res->cigar_bytes);
+  res->d_cigar = (uint32_t*)newp;
+  res->cigar_bytes = (old_n + cap) * sizeof(uint32_t);
+  DevBuf d_mat, d_dir, d_cig, d_scr;
+  DSA_TRY(d_mat.alloc(ctx, res->A * res->A));
+  DSA_CUDA_TRY(cudaMemcpyAsync(d_mat.p, res->matrix.data(), res->A * res->A, cudaMemcpyHostToDevice,
+                               ctx->stream));
+  DSA_TRY(d_dir.alloc(ctx, dir * 4));
+  DSA_TRY(d_cig.alloc(ctx, cap * 4));
+  DSA_TRY(d_scr.alloc(ctx, scr * sizeof(int2)));
+  DSA_CUDA_TRY(cudaMemcpyAsync(cnt, &old_n, sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
+  DSA_TRY(launch_traceback_thread(ctx, db, qs, d_mat.as<int8_t>(), res->A, res->gap_open,
+                                  res->gap_extend, res->mode, res->free_ends, d_jobs.as<TbJob>(),
+                                  (uint32_t)nv, d_dir.as<uint32_t>(), d_cig.as<uint32_t>(),
+                                  d_scr.as<int2>(), res->d_hits));
+  DSA_TRY(launch_cigar_compact(ctx, res->d_hits, d_jobs.as<TbJob>(), (uint32_t)nv,
+                               d_cig.as<uint32_t>(), res->d_cigar, old_n, cnt));
+  phase_end(res, PH_TRACE);
+  uint64_t total = 0;
+  DSA_CUDA_TRY(cudaMemcpyAsync(&total, cnt, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  res->n_cigar = total;
+  res->host_valid = false;
+  return DSA_OK;
+}
+
+}  // namespace dsa
+
 extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, uint64_t n) {
   if (!ctx || !res || res->ctx != ctx) {
     set_error("bad ctx / res (results handed out by a server are host-only)");
     return DSA_ERR_INVALID_ARG;
   }
   DSA_TRY(set_device(ctx));
+  // Many small rectangles: one thread per hit (groups of 32 hits of similar
+  // size share an interleaved decision layout).  Few or large ones: one warp
+  // per hit.
+  uint64_t thread_min = 16384;
+  if (const char* env = getenv("DSA_TB_THREAD_MIN")) thread_min = strtoull(env, nullptr, 10);
+  // exact column band for a free target begin (see k_traceback.cu); needs e > 0
+  int smax_pos = 0;
+  for (int8_t v : res->matrix) smax_pos = std::max<int>(smax_pos, v);
+  const bool band_ok = res->mode == DSA_SEMIGLOBAL && (res->free_ends & DSA_FREE_T_BEGIN) &&
+                       res->gap_extend > 0;
+  // Diagonal bands from the total gap length g of a path reaching (ie, je)
+  // (tb_diag_window): it has at most (ie + je - g) / 2 M columns whatever its
+  // start, so 2 score <= max(S, 0)(ie + je) - g (max(S, 0) + 2e) - 2 (o - e);
+  // a cell (i, j) on it has |dn - d| <= g (gaps after it; d = j - i,
+  // dn = je - ie) and, for paths from (0, 0), |d| <= g as well (gaps before).
+  const bool diag_ok = smax_pos + 2 * res->gap_extend > 0;
+  const bool from_origin = res->mode == DSA_GLOBAL ||
+                           (res->mode == DSA_SEMIGLOBAL &&
+                            !(res->free_ends & (DSA_FREE_Q_BEGIN | DSA_FREE_T_BEGIN)));
+  const TbBounds bounds{res->mode, res->free_ends, res->gap_open, res->gap_extend, smax_pos,
+                        band_ok, diag_ok, from_origin};
+  // every hit of a large result on the thread path: staged on the device
+  // (DSA_TB_HOST_STAGING=1 keeps the host staging below)
+  const char* host_staging = getenv("DSA_TB_HOST_STAGING");
+  if (!which && res->long_bnd_off.empty() && res->n_hits >= std::max<uint64_t>(thread_min, 1) &&
+      !(host_staging && host_staging[0] == '1')) {
+    const int rc = traceback_device_staged(ctx, res, bounds);
+    if (rc != TB_STAGE_FALLBACK) return rc;
+  }
   DSA_TRY(fetch_hits(res));
   std::vector<uint64_t> sel;
   if (which) {
@@ -1406,11 +1509,6 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
   }
   const dsa_db* db = res->db;
   const dsa_db* qs = res->queries;
-  // Many small rectangles: one thread per hit (groups of 32 hits of similar
-  // size share an interleaved decision layout).  Few or large ones: one warp
-  // per hit.
-  uint64_t thread_min = 16384;
-  if (const char* env = getenv("DSA_TB_THREAD_MIN")) thread_min = strtoull(env, nullptr, 10);
   auto small = [](const TbJob& j) { return j.ie <= 4096 && (uint64_t)j.ie * j.je <= (1u << 20); };
   std::vector<TbJob>& tjobs = ctx->h_tb;   // thread-per-hit candidates
   tjobs.clear();
@@ -1418,37 +1516,8 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
   std::vector<LongTbJob> ljobs;
   uint64_t cap_total = 0;
   const int band = long_band_rows();
-  // exact column band for a free target begin (see k_traceback.cu); needs e > 0
-  int smax_pos = 0;
-  for (int8_t v : res->matrix) smax_pos = std::max<int>(smax_pos, v);
-  const bool band_ok = res->mode == DSA_SEMIGLOBAL && (res->free_ends & DSA_FREE_T_BEGIN) &&
-                       res->gap_extend > 0;
-  // Diagonal bands from the total gap length g of a path reaching (ie, je):
-  // it has at most (ie + je - g) / 2 M columns whatever its start, so
-  // 2 score <= max(S, 0)(ie + je) - g (max(S, 0) + 2e) - 2 (o - e) [g > 0].
-  // A cell (i, j) on it has |dn - d| <= g (gaps after it; d = j - i,
-  // dn = je - ie) and, for paths from (0, 0), |d| <= g as well (gaps before).
-  const bool diag_ok = smax_pos + 2 * res->gap_extend > 0;
-  const bool from_origin = res->mode == DSA_GLOBAL ||
-                           (res->mode == DSA_SEMIGLOBAL &&
-                            !(res->free_ends & (DSA_FREE_Q_BEGIN | DSA_FREE_T_BEGIN)));
-  // diagonals dlo..dhi of every optimal path reaching (ie, je) (false: none narrower)
-  auto diag_window = [&](int32_t ie, int32_t je, int32_t score, int64_t& dlo, int64_t& dhi) -> bool {
-    if (!diag_ok) return false;
-    const int64_t num = (int64_t)smax_pos * ((int64_t)ie + je) - 2 * (int64_t)score -
-                        2 * ((int64_t)res->gap_open - res->gap_extend);
-    const int64_t gmax = num < 0 ? 0 : num / ((int64_t)smax_pos + 2 * (int64_t)res->gap_extend);
-    const int64_t dn = (int64_t)je - ie;
-    if (!from_origin) {
-      dlo = dn - gmax;
-      dhi = dn + gmax;
-      return true;
-    }
-    if (gmax < std::llabs(dn)) return false;
-    const int64_t half = (gmax - std::llabs(dn)) / 2;
-    dlo = std::min<int64_t>(0, dn) - half;
-    dhi = std::max<int64_t>(0, dn) + half;
-    return true;
+  auto diag_window = [&](int32_t ie, int32_t je, int32_t score, int64_t& dlo, int64_t& dhi) {
+    return tb_diag_window(bounds, ie, je, score, dlo, dhi);
   };
   // hit h -> short job (false: the hit is skipped or is a long pair)
   auto make_short = [&](uint64_t h, TbJob& j) -> bool {
@@ -1456,43 +1525,8 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
     if (hit.flags & DSA_HIT_HAS_TRACEBACK) return false;
     if (res->mode == DSA_LOCAL && (hit.q_end < 0 || hit.t_end < 0)) return false;
     if (!res->long_bnd_off.empty() && res->long_bnd_off[h] != UINT64_MAX) return false;
-    j = TbJob{};
-    j.ie = hit.q_end + 1;
-    j.je = hit.t_end + 1;
-    j.hit = (uint32_t)h;
-    j.q_start = qs->h_off[hit.query_id];
-    j.t_start = db->h_off[hit.target_id] + hit.t_offset;
-    // diagonal window of the thread-per-hit kernel's 16-row strips:
-    // diagonals dlo .. dhi of every optimal path (default: whole rows)
-    int64_t dlo = -(int64_t)j.ie, dhi = j.je;
-    if (band_ok) {
-      // deletions on any path reaching the hit: score <= ie * max(S, 0) - (o + (k - 1) e)
-      const int64_t o = res->gap_open, e = res->gap_extend;
-      const int64_t slack = (int64_t)j.ie * smax_pos - hit.score;
-      const int64_t kmax = slack < o ? 0 : (slack - o) / e + 1;
-      const int64_t jlo = (int64_t)j.je - j.ie - kmax;
-      if (jlo > 0) {
-        j.jlo = (int32_t)jlo;
-        j.t_start += (uint64_t)jlo;
-        j.je -= (int32_t)jlo;
-      }
-      // insertions: each one removes an M (at most max S) and costs at least e
-      // (the first o): score <= max(S, 0)(ie - k) - (o + (k - 1) e)
-      const int64_t imax = slack < o ? 0 : (slack - o + e) / (smax_pos + e);
-      // a cell (i, j) on the path: (je - j) - (ie - i) = D after - I after
-      const int64_t dn = (int64_t)j.je - j.ie;
-      dlo = dn - kmax;
-      dhi = dn + imax;
-    } else {
-      int64_t a, b;
-      if (diag_window(j.ie, j.je, hit.score, a, b)) {
-        dlo = a;
-        dhi = b;
-      }
-    }
-    j.dlo = (int32_t)std::max<int64_t>(dlo, -(int64_t)j.ie);
-    j.wc = (int32_t)std::min<int64_t>(j.je, 16 + dhi - j.dlo);
-    j.wpr = (uint32_t)((j.je + 7) / 8);
+    tb_short_job(bounds, hit.q_end + 1, hit.t_end + 1, hit.score, qs->h_off[hit.query_id],
+                 db->h_off[hit.target_id] + hit.t_offset, (uint32_t)h, j);
     return true;
   };
   // long pairs (few): serial

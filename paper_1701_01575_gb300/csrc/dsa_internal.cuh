@@ -263,6 +263,102 @@ struct TbJob {
   int32_t wc;
   uint32_t pad;
 };
+// Score-derived traceback windows, shared by the host staging and the
+// device staging of the traceback (see k_traceback.cu for the argument).
+struct TbBounds {
+  int mode;
+  uint32_t fe;
+  int o, e;
+  int smax_pos;      // max(S, 0)
+  bool band_ok;      // semi-global with a free target begin and e > 0: column band
+  bool diag_ok;      // max(S, 0) + 2e > 0: total-gap bound
+  bool from_origin;  // paths start at (0, 0): two-sided diagonal window
+};
+
+// Diagonals dlo..dhi of every optimal path reaching (ie, je); false: none narrower.
+__host__ __device__ inline bool tb_diag_window(const TbBounds& B, int32_t ie, int32_t je,
+                                               int32_t score, int64_t& dlo, int64_t& dhi) {
+  if (!B.diag_ok) return false;
+  // at most (ie + je - g) / 2 M columns, each scoring at most max(S, 0), and
+  // gap runs costing at least g e + (o - e) when g > 0
+  const int64_t num = (int64_t)B.smax_pos * ((int64_t)ie + je) - 2 * (int64_t)score -
+                      2 * ((int64_t)B.o - B.e);
+  const int64_t gmax = num < 0 ? 0 : num / ((int64_t)B.smax_pos + 2 * (int64_t)B.e);
+  const int64_t dn = (int64_t)je - ie;
+  if (!B.from_origin) {   // gaps after the cell only
+    dlo = dn - gmax;
+    dhi = dn + gmax;
+    return true;
+  }
+  const int64_t adn = dn < 0 ? -dn : dn;
+  if (gmax < adn) return false;
+  const int64_t half = (gmax - adn) / 2;
+  dlo = (dn < 0 ? dn : 0) - half;
+  dhi = (dn > 0 ? dn : 0) + half;
+  return true;
+}
+
+// The thread-per-hit job of a hit with end cell (ie, je) (1-based) and score:
+// column band (free target begin) and the diagonal window of its 16-row strips.
+__host__ __device__ inline void tb_short_job(const TbBounds& B, int32_t ie, int32_t je,
+                                             int32_t score, uint64_t q_start, uint64_t t_start,
+                                             uint32_t hit, TbJob& j) {
+  j = TbJob{};
+  j.ie = ie;
+  j.je = je;
+  j.hit = hit;
+  j.q_start = q_start;
+  j.t_start = t_start;
+  int64_t dlo = -(int64_t)ie, dhi = je;   // default: whole rows
+  if (B.band_ok) {
+    // deletions on any path reaching the hit: score <= ie max(S, 0) - (o + (k - 1) e)
+    const int64_t o = B.o, e = B.e;
+    const int64_t slack = (int64_t)ie * B.smax_pos - score;
+    const int64_t kmax = slack < o ? 0 : (slack - o) / e + 1;
+    const int64_t jlo = (int64_t)je - ie - kmax;
+    if (jlo > 0) {
+      j.jlo = (int32_t)jlo;
+      j.t_start += (uint64_t)jlo;
+      j.je -= (int32_t)jlo;
+    }
+    // insertions: each one removes an M (at most max S) and costs at least e
+    // (the first o): score <= max(S, 0)(ie - k) - (o + (k - 1) e)
+    const int64_t imax = slack < o ? 0 : (slack - o + e) / (B.smax_pos + e);
+    // a cell (i, j) on the path: (je - j) - (ie - i) = D after - I after
+    const int64_t dn = (int64_t)j.je - ie;
+    dlo = dn - kmax;
+    dhi = dn + imax;
+  } else {
+    int64_t a, b;
+    if (tb_diag_window(B, ie, je, score, a, b)) {
+      dlo = a;
+      dhi = b;
+    }
+  }
+  j.dlo = (int32_t)(dlo > -(int64_t)ie ? dlo : -(int64_t)ie);
+  const int64_t wc = 16 + dhi - j.dlo;
+  j.wc = (int32_t)(wc < j.je ? wc : j.je);
+  j.wpr = (uint32_t)((j.je + 7) / 8);
+}
+
+// Device-side staging kernels (k_tbstage.cu).
+int launch_scan_u64(dsa_ctx* ctx, uint64_t* d_data, uint64_t n, uint64_t* d_total);
+int launch_tb_stage(dsa_ctx* ctx, const dsa_hit* d_hits, uint64_t n, const uint64_t* d_q_off,
+                    const uint64_t* d_t_off, const TbBounds& B, TbJob* d_full, uint64_t* d_valid,
+                    uint32_t* d_not_small);
+int launch_tb_compact(dsa_ctx* ctx, const TbJob* d_full, const uint64_t* d_pos,
+                      const uint64_t* d_total, uint64_t n, TbJob* d_jobs);
+int launch_tb_layout(dsa_ctx* ctx, TbJob* d_jobs, uint64_t n, uint64_t* d_gdir, uint64_t* d_gscr,
+                     uint64_t* d_jcig, uint64_t* d_totals);
+int launch_cigar_offsets_scan(dsa_ctx* ctx, dsa_hit* d_hits, const TbJob* d_jobs, uint64_t n,
+                              uint64_t* d_base);
+
+// Device staging of the traceback of every hit of a result on the thread path
+// (jobs built, compacted and laid out on the device).  Returns DSA_OK, or
+// TB_STAGE_FALLBACK when some hit needs another path (nothing was changed).
+constexpr int TB_STAGE_FALLBACK = 1;
+int traceback_device_staged(dsa_ctx* ctx, dsa_res* res, const TbBounds& B, const int8_t* d_matrix);
+
 int launch_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,
                      int A, int o, int e, int mode, uint32_t fe, const TbJob* d_jobs,
                      uint32_t n_jobs, uint32_t* d_dir, uint32_t* d_cig_tmp, int2* d_scr,

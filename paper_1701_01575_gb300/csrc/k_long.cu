@@ -353,7 +353,14 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
       nbw[r] = 0;
       qv[r] = ii <= ie ? (BYTES ? Sb[q[ii - 1]] : (uint32_t)q[ii - 1] * A) : 0u;
     }
-    int32_t diag = wall ? NEG32 : h_col0(mode, fe, r0, o, e);
+    // H[r0][jlo - 1]: for lane 0 the corner (i0, jlo - 1) lies on the window's
+    // edge diagonal, inside the band -- the boundary row (band 0) or the
+    // checkpoint row gives it; for the other lanes it lies left of the band
+    int32_t diag;
+    if (!wall) diag = h_col0(mode, fe, r0, o, e);
+    else if (lane != 0) diag = NEG32;
+    else if (b == 0) diag = h_row0(mode, fe, jlo - 1, o, e);
+    else diag = up[jlo - 2].x;
     int32_t sendH = 0, sendF = NEG32;
     int sendA = 0;
     // checkpoint row above and target residues for columns jlo + blk .. + 31

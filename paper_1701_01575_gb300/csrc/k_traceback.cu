@@ -487,9 +487,14 @@ int launch_cigar_compact(dsa_ctx* ctx, dsa_hit* d_hits, const TbJob* d_jobs, uin
                          const uint32_t* d_cig_tmp, uint32_t* d_cigar, uint64_t base,
                          uint64_t* d_total) {
   if (n_jobs == 0) return DSA_OK;
-  k_cigar_offsets<<<1, 1024, 0, ctx->stream>>>(d_hits, d_jobs, n_jobs, base, d_total);
-  DSA_CUDA_TRY(cudaGetLastError());
-  ++ctx->launches;
+  if (n_jobs >= 8192) {
+    // many jobs: offsets from a device scan (the base is *d_total, which equals `base`)
+    DSA_TRY(launch_cigar_offsets_scan(ctx, d_hits, d_jobs, n_jobs, d_total));
+  } else {
+    k_cigar_offsets<<<1, 1024, 0, ctx->stream>>>(d_hits, d_jobs, n_jobs, base, d_total);
+    DSA_CUDA_TRY(cudaGetLastError());
+    ++ctx->launches;
+  }
   uint64_t blocks = ((uint64_t)n_jobs * 32 + 255) / 256;
   if (blocks > (uint64_t)ctx->sm_count * 16) blocks = (uint64_t)ctx->sm_count * 16;
   k_cigar_copy<<<(unsigned)blocks, 256, 0, ctx->stream>>>(d_hits, d_jobs, n_jobs, d_cig_tmp,

@@ -374,6 +374,35 @@ def test_long_pair_traceback_diagonal_band(ctx, mode, fe):
     check_traceback(r.hits(), r.cigar(), qs, db, S, 5, 2, mode, fe)
 
 
+@pytest.mark.parametrize("mode,fe", [(dsa.GLOBAL, 15), (dsa.SEMIGLOBAL, 12), (dsa.LOCAL, 15)])
+def test_long_pair_traceback_exact_match_edge(ctx, mode, fe):
+    """Error-free long pairs: the score leaves no slack, so the diagonal band
+    is the path's own diagonal and the path runs along the edge of every
+    band's column window, through the corner cell each band takes from the
+    row above it (the boundary row for the first band, a checkpoint row
+    after that)."""
+    rng = np.random.default_rng(77 + fe)
+    S = W.dna_matrix(1, -4)
+    g = rng.integers(0, 4, 6000).astype(np.uint8)
+    qs = W.SeqSet.from_list([g[100:2200], g[1000:3700], g[3000:5100]])
+    db = W.SeqSet.from_list([g[90:2200], g[1000:3700], g[2990:5110]])
+    pairs = np.zeros(3, dtype=W.PAIR_DTYPE)
+    pairs["query_id"] = [0, 1, 2]
+    pairs["target_id"] = [0, 1, 2]
+    pairs["t_len"] = db.lengths
+    sc, qe, te = oracle.score_pairs(qs.codes, qs.offsets, db.codes, db.offsets, pairs["query_id"],
+                                    pairs["target_id"], S, 6, 1, mode, fe,
+                                    pair_toff=pairs["t_offset"], pair_tlen=pairs["t_len"])
+    d = ctx.load_set(db, 4)
+    q = ctx.load_set(qs, 4)
+    r = ctx.align(d, q, S, 6, 1, mode=mode, free_ends=fe, pairs=pairs)
+    ctx.traceback(r)
+    ctx.sync()
+    h = r.hits()
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), f"exact long mode={mode}")
+    check_traceback(h, r.cigar(), qs, db, S, 6, 1, mode, fe)
+
+
 def test_long_and_short_pairs_mixed(ctx):
     """One call with pairs on both sides of the banded-path threshold."""
     rng = np.random.default_rng(99)
@@ -507,14 +536,17 @@ def test_packed_pairs_saturation_rerun(ctx):
     assert r.stats()[1] >= 2
 
 
+@pytest.mark.parametrize("staging", ["device", "host"])
 @pytest.mark.parametrize("uniform", [False, True])
 @pytest.mark.parametrize("mode,fe", [(dsa.SEMIGLOBAL, 12), (dsa.GLOBAL, 15), (dsa.LOCAL, 15),
                                      (dsa.SEMIGLOBAL, 15)])
-def test_thread_traceback_reads_in_windows(ctx, mode, fe, uniform, monkeypatch):
+def test_thread_traceback_reads_in_windows(ctx, mode, fe, uniform, staging, monkeypatch):
     """Thread-per-hit traceback on read/window pairs: 1..70-row reads (one strip,
     several strips, ragged last strip, fewer than 9 rows), partial last group;
-    uniform = equal read and window lengths (hits keep their given order)."""
+    uniform = equal read and window lengths; jobs staged on the device or on
+    the host."""
     monkeypatch.setenv("DSA_TB_THREAD_MIN", "1")
+    monkeypatch.setenv("DSA_TB_HOST_STAGING", "1" if staging == "host" else "0")
     rng = np.random.default_rng(70 + mode * 16 + fe + 7 * uniform)
     genome = rng.integers(0, 4, 20000).astype(np.uint8)
     db = W.SeqSet.from_list([genome])
@@ -690,4 +722,42 @@ def test_autotuned_long_threshold(ctx, tmp_path, monkeypatch):
             assert "|A24|" in text and ":" in text
         elif mode == "cache":
             assert launches < tuned_launches   # no tuning passes on a cache hit
+        r.free()
+
+
+
+def test_device_staged_traceback_twice_and_fallback(ctx, monkeypatch):
+    """Device staging: a second traceback call leaves traced hits alone (their
+    CIGAR offsets stay valid); a result with a hit too big for the thread path
+    falls back to the host staging."""
+    monkeypatch.setenv("DSA_TB_THREAD_MIN", "1")
+    monkeypatch.delenv("DSA_TB_HOST_STAGING", raising=False)
+    rng = np.random.default_rng(5)
+    genome = rng.integers(0, 4, 30000).astype(np.uint8)
+    db = W.SeqSet.from_list([genome])
+    reads, starts = [], []
+    for n in rng.integers(20, 90, 64):
+        st = int(rng.integers(0, 30000 - 3000))
+        reads.append(W.mutate(rng, genome[st + 10: st + 10 + n], 0.03, 0.02))
+        starts.append(st)
+    reads.append(genome[100:2200].copy())   # 2,100 x 2,200 cells: above the thread path's bound
+    starts.append(90)
+    qs = W.SeqSet.from_list([x if len(x) else np.zeros(1, np.uint8) for x in reads])
+    pairs = np.zeros(qs.n, dtype=W.PAIR_DTYPE)
+    pairs["query_id"] = np.arange(qs.n)
+    pairs["t_offset"] = starts
+    pairs["t_len"] = 150
+    pairs["t_len"][-1] = 2200
+    S = W.dna_matrix(1, -4)
+    d = ctx.load_set(db, 4)
+    q = ctx.load_set(qs, 4)
+    for with_big in (False, True):
+        p = pairs if with_big else pairs[:-1]
+        r = ctx.align(d, q, S, 6, 1, mode=dsa.SEMIGLOBAL, free_ends=12, pairs=p)
+        ctx.traceback(r)
+        first = r.hits().copy()
+        ctx.traceback(r)   # nothing left to trace: unchanged
+        h = r.hits()
+        assert (h["cigar_off"] == first["cigar_off"]).all()
+        check_traceback(h, r.cigar(), qs, db, S, 6, 1, dsa.SEMIGLOBAL, 12)
         r.free()
