@@ -97,28 +97,6 @@ std::vector<uint32_t> radix_order(const std::vector<uint64_t>& key) {
   return idx;
 }
 
-// Stream-ordered device buffer charged against the context's budget.
-struct DevBuf {
-  dsa_ctx* ctx = nullptr;
-  void* p = nullptr;
-  size_t bytes = 0;
-  DevBuf() = default;
-  DevBuf(const DevBuf&) = delete;
-  DevBuf& operator=(const DevBuf&) = delete;
-  ~DevBuf() { reset(); }
-  int alloc(dsa_ctx* c, size_t n) {
-    reset();
-    ctx = c;
-    bytes = n ? n : 16;
-    return ctx->alloc(&p, bytes);
-  }
-  void reset() {
-    if (p && ctx) ctx->release(p, bytes);
-    p = nullptr;
-    bytes = 0;
-  }
-  template <class T> T* as() const { return static_cast<T*>(p); }
-};
 
 template <class T>
 int upload(dsa_ctx* ctx, DevBuf& buf, const T* p, size_t n) {
@@ -1000,35 +978,67 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
     set_error("top_k applies to all-vs-all searches only");
     return DSA_ERR_UNSUPPORTED;
   }
-  // host copy of explicit pairs (validation and planning)
-  std::vector<dsa_pair> hp;
+  // int16 eligibility: local with the saturation flag, or any mode whose
+  // scores provably stay inside int16: (m + n) * w + o well below 2^14
+  const int64_t w16 = std::max<int64_t>({(int64_t)std::abs(v.smax), (int64_t)std::abs(v.smin), o, e});
+  const bool local16 = mode == DSA_LOCAL && o >= 1 && o + e <= 4096 && v.smax + o < 8192 && v.smin > -8192;
+  const bool packed_ok = !(flags & (DSA_FORCE_INT32 | DSA_PLAIN_FORM));
+  // explicit pairs: a device copy (the caller's own when they are on the
+  // device), checked and classified there; the host sees only the totals
+  DevBuf d_pairs_buf, d_key, d_idx, d_hist, d_jcnt, d_stats;
+  const dsa_pair* d_pairs = nullptr;
+  PairPlanStats pst{};
+  const uint64_t L = (uint64_t)qs->max_len + 2;
   if (!all) {
+    if (flags & DSA_PAIRS_ON_DEVICE) {
+      d_pairs = pairs;
+    } else {
+      DSA_TRY(upload(ctx, d_pairs_buf, pairs, n_pairs));
+      d_pairs = d_pairs_buf.as<dsa_pair>();
+    }
+    DSA_TRY(d_key.alloc(ctx, n_pairs * sizeof(uint64_t)));
+    DSA_TRY(d_idx.alloc(ctx, n_pairs * sizeof(uint32_t)));
+    DSA_TRY(d_hist.alloc(ctx, L * sizeof(uint64_t)));
+    DSA_TRY(d_jcnt.alloc(ctx, L * sizeof(uint64_t)));
+    DSA_TRY(d_stats.alloc(ctx, sizeof(PairPlanStats)));
+    PairPlanStats* st = d_stats.as<PairPlanStats>();
+    DSA_CUDA_TRY(cudaMemsetAsync(d_hist.p, 0, L * sizeof(uint64_t), ctx->stream));
+    DSA_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(PairPlanStats), ctx->stream));
+    DSA_CUDA_TRY(cudaMemsetAsync(&st->first_bad, 0xFF, sizeof(uint64_t), ctx->stream));
+    const PairPlanParams P{qs->n, db->n, w16, o, e, local16, packed_ok};
+    DSA_TRY(launch_pair_classify(ctx, d_pairs, n_pairs, qs, db, P, d_key.as<uint64_t>(),
+                                 d_idx.as<uint32_t>(), d_hist.as<uint64_t>(), L,
+                                 d_jcnt.as<uint64_t>(), st));
+    DSA_CUDA_TRY(cudaMemcpyAsync(&pst, st, sizeof pst, cudaMemcpyDeviceToHost, ctx->stream));
+    DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (pst.first_bad != UINT64_MAX) {
+      set_error("pair %llu is out of range", (unsigned long long)pst.first_bad);
+      return DSA_ERR_INVALID_ARG;
+    }
+  }
+  // host copy of the pairs, made only when the host planner needs it
+  std::vector<dsa_pair> hp;
+  bool hp_ready = all;
+  auto need_hp = [&]() -> int {
+    if (hp_ready) return DSA_OK;
     hp.resize(n_pairs);
     if (flags & DSA_PAIRS_ON_DEVICE) {
-      DSA_CUDA_TRY(cudaMemcpyAsync(hp.data(), pairs, n_pairs * sizeof(dsa_pair),
-                                   cudaMemcpyDeviceToHost, ctx->stream));
+      if (n_pairs)
+        DSA_CUDA_TRY(cudaMemcpyAsync(hp.data(), pairs, n_pairs * sizeof(dsa_pair),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
       DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     } else if (n_pairs) {
       memcpy(hp.data(), pairs, n_pairs * sizeof(dsa_pair));
     }
-    for (uint64_t k = 0; k < n_pairs; ++k) {
-      const dsa_pair& p = hp[k];
-      if (p.query_id >= qs->n || p.target_id >= db->n || p.t_len == 0 ||
-          p.t_offset + p.t_len > db->h_len[p.target_id]) {
-        set_error("pair %llu is out of range", (unsigned long long)k);
-        return DSA_ERR_INVALID_ARG;
-      }
-    }
-  }
+    hp_ready = true;
+    return DSA_OK;
+  };
   // int32 range: (m + n) * max|value step| must stay far from 2^31
-  uint32_t max_m = 0, max_n = 0;
-  for (uint32_t x : qs->h_len) max_m = std::max(max_m, x);
-  if (all) for (uint32_t x : db->h_len) max_n = std::max(max_n, x);
-  else for (const dsa_pair& p : hp) max_n = std::max(max_n, p.t_len);
-  const int64_t w = std::max<int64_t>({(int64_t)std::abs(v.smax), (int64_t)std::abs(v.smin), o, e});
-  if (((int64_t)max_m + max_n + 2) * (w + 1) >= (1ll << 29)) {
+  const uint32_t max_m = qs->max_len;
+  const uint32_t max_n = all ? db->max_len : pst.max_t_len;
+  if (((int64_t)max_m + max_n + 2) * (w16 + 1) >= (1ll << 29)) {
     set_error("scores could leave the int32 range (lengths %u + %u, weight %lld)", max_m, max_n,
-              (long long)w);
+              (long long)w16);
     return DSA_ERR_UNSUPPORTED;
   }
 
@@ -1074,16 +1084,18 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
     uint64_t scr = 0, cells = 0, lcells = 0, p16cells = 0;
     uint64_t bnd = 0, prog = 0, cand = 0;
     const int band = long_band_rows();
-    // int16 eligibility: local with the saturation flag, or any mode whose
-    // scores provably stay inside int16: (m + n) * w + o well below 2^14
-    const int64_t w16 = std::max<int64_t>({(int64_t)std::abs(v.smax), (int64_t)std::abs(v.smin), o, e});
-    const bool local16 = mode == DSA_LOCAL && o >= 1 && o + e <= 4096 && v.smax + o < 8192 && v.smin > -8192;
-    const bool packed_ok = !(flags & (DSA_FORCE_INT32 | DSA_PLAIN_FORM));
-    // classify on host threads: packed pairs (filled in place, pair order
-    // kept); long and int32 pairs are few or absent and follow serially
+    // every pair packed: the device planner lays out the jobs
+    const bool dev_plan = n_pairs > 0 && pst.n_other == 0;
+    // host planner: classify on host threads: packed pairs (filled in place,
+    // pair order kept); long and int32 pairs are few and follow serially
     enum : uint8_t { C_P16, C_LONG, C_INT32 };
-    std::vector<uint8_t> cls(n_pairs);
-    {
+    std::vector<uint8_t> cls;
+    if (dev_plan) {
+      cells = pst.cells;
+      p16cells = pst.cells16;
+    } else {
+      if ((rc = need_hp())) return fail(rc);
+      cls.resize(n_pairs);
       const unsigned T = host_threads(n_pairs, 1u << 16);
       std::vector<uint64_t> n16(T + 1, 0), cells_t(T, 0), c16_t(T, 0);
       parallel_for(n_pairs, T, [&](unsigned t, size_t b, size_t x1) {
@@ -1118,7 +1130,7 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
           if (cls[k] == C_P16) p16[pos++] = k;
       });
     }
-    for (uint64_t k = 0; k < n_pairs; ++k) {
+    for (uint64_t k = 0; k < cls.size(); ++k) {
       if (cls[k] == C_P16) continue;
       const dsa_pair& p = hp[k];
       const uint64_t m = qs->h_len[p.query_id];
@@ -1179,70 +1191,93 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
       res->phase_cells[PH_INTRA] = lcells;
       res->phase_cells[PH_INT32] = cells - lcells;
     }
-    if (!p16.empty()) {
-      // order by (query length, window length); two pairs of equal query length per thread
-      const unsigned T = host_threads(p16.size(), 1u << 16);
-      std::vector<uint64_t> key(p16.size());
-      parallel_for(p16.size(), T, [&](unsigned, size_t b, size_t x1) {
-        for (size_t x = b; x < x1; ++x) {
-          const dsa_pair& pp = hp[p16[x]];
-          key[x] = ((uint64_t)qs->h_len[pp.query_id] << 32) | pp.t_len;
-        }
-      });
-      {
-        const std::vector<uint32_t> ord = radix_order(key);
-        std::vector<uint64_t> sorted(p16.size()), skey(p16.size());
-        parallel_for(ord.size(), T, [&](unsigned, size_t b, size_t x1) {
+    if (dev_plan || !p16.empty()) {
+      DevBuf d_pj;
+      uint32_t n_pj = 0, max_n = 1;
+      if (dev_plan) {
+        // device planner: stable sort by (query length, window length), jobs
+        // from the runs of equal query length
+        DevBuf d_key2, d_idx2;
+        if ((rc = d_key2.alloc(ctx, n_pairs * sizeof(uint64_t))) ||
+            (rc = d_idx2.alloc(ctx, n_pairs * sizeof(uint32_t))) ||
+            (rc = d_pj.alloc(ctx, pst.n_jobs * sizeof(Pair16Job))))
+          return fail(rc);
+        uint64_t* kk = d_key.as<uint64_t>();
+        uint32_t* vv = d_idx.as<uint32_t>();
+        if ((rc = launch_pair_sort(ctx, kk, vv, d_key2.as<uint64_t>(), d_idx2.as<uint32_t>(), n_pairs,
+                                   qs->max_len, pst.max_t_len)) ||
+            (rc = launch_pair_build_jobs(ctx, kk, vv, n_pairs, d_hist.as<uint64_t>(),
+                                         d_jcnt.as<uint64_t>(), L, d_pairs, qs, db,
+                                         d_pj.as<Pair16Job>())))
+          return fail(rc);
+        n_pj = (uint32_t)pst.n_jobs;
+        max_n = std::max<uint32_t>(1, pst.max_t_len);
+      } else {
+        // order by (query length, window length); two pairs of equal query length per thread
+        const unsigned T = host_threads(p16.size(), 1u << 16);
+        std::vector<uint64_t> key(p16.size());
+        parallel_for(p16.size(), T, [&](unsigned, size_t b, size_t x1) {
           for (size_t x = b; x < x1; ++x) {
-            sorted[x] = p16[ord[x]];
-            skey[x] = key[ord[x]];
+            const dsa_pair& pp = hp[p16[x]];
+            key[x] = ((uint64_t)qs->h_len[pp.query_id] << 32) | pp.t_len;
           }
         });
-        p16.swap(sorted);
-        key.swap(skey);
-      }
-      // a job starts at every even offset inside a run of equal query length
-      std::vector<uint32_t> starts;
-      starts.reserve(p16.size() / 2 + 1);
-      uint32_t max_n = 1;
-      for (size_t x = 0, run = 0; x < p16.size(); ++x) {
-        if (x > 0 && (key[x] >> 32) != (key[x - 1] >> 32)) run = x;
-        if (((x - run) & 1) == 0) starts.push_back((uint32_t)x);
-        max_n = std::max<uint32_t>(max_n, (uint32_t)key[x]);
-      }
-      std::vector<Pair16Job> pj(starts.size());
-      parallel_for(starts.size(), T, [&](unsigned, size_t b, size_t x1) {
-        for (size_t k = b; k < x1; ++k) {
-          const size_t x = starts[k];
-          const dsa_pair& a = hp[p16[x]];
-          Pair16Job j{};
-          j.m = (int32_t)(key[x] >> 32);
-          j.q_lo = qs->h_off[a.query_id];
-          j.t_lo = db->h_off[a.target_id] + a.t_offset;
-          j.n_lo = (int32_t)a.t_len;
-          j.out_lo = (uint32_t)p16[x];
-          if (x + 1 < p16.size() && (key[x + 1] >> 32) == (key[x] >> 32)) {
-            const dsa_pair& bb = hp[p16[x + 1]];
-            j.q_hi = qs->h_off[bb.query_id];
-            j.t_hi = db->h_off[bb.target_id] + bb.t_offset;
-            j.n_hi = (int32_t)bb.t_len;
-            j.out_hi = (uint32_t)p16[x + 1];
-          } else {
-            j.q_hi = j.q_lo;
-            j.t_hi = j.t_lo;
-            j.n_hi = 0;
-            j.out_hi = NONE;
-          }
-          pj[k] = j;
+        {
+          const std::vector<uint32_t> ord = radix_order(key);
+          std::vector<uint64_t> sorted(p16.size()), skey(p16.size());
+          parallel_for(ord.size(), T, [&](unsigned, size_t b, size_t x1) {
+            for (size_t x = b; x < x1; ++x) {
+              sorted[x] = p16[ord[x]];
+              skey[x] = key[ord[x]];
+            }
+          });
+          p16.swap(sorted);
+          key.swap(skey);
         }
-      });
-      DevBuf d_pj;
-      if ((rc = upload(ctx, d_pj, pj))) return fail(rc);
+        // a job starts at every even offset inside a run of equal query length
+        std::vector<uint32_t> starts;
+        starts.reserve(p16.size() / 2 + 1);
+        uint32_t max_n16 = 1;
+        for (size_t x = 0, run = 0; x < p16.size(); ++x) {
+          if (x > 0 && (key[x] >> 32) != (key[x - 1] >> 32)) run = x;
+          if (((x - run) & 1) == 0) starts.push_back((uint32_t)x);
+          max_n16 = std::max<uint32_t>(max_n16, (uint32_t)key[x]);
+        }
+        std::vector<Pair16Job> pj(starts.size());
+        parallel_for(starts.size(), T, [&](unsigned, size_t b, size_t x1) {
+          for (size_t k = b; k < x1; ++k) {
+            const size_t x = starts[k];
+            const dsa_pair& a = hp[p16[x]];
+            Pair16Job j{};
+            j.m = (int32_t)(key[x] >> 32);
+            j.q_lo = qs->h_off[a.query_id];
+            j.t_lo = db->h_off[a.target_id] + a.t_offset;
+            j.n_lo = (int32_t)a.t_len;
+            j.out_lo = (uint32_t)p16[x];
+            if (x + 1 < p16.size() && (key[x + 1] >> 32) == (key[x] >> 32)) {
+              const dsa_pair& bb = hp[p16[x + 1]];
+              j.q_hi = qs->h_off[bb.query_id];
+              j.t_hi = db->h_off[bb.target_id] + bb.t_offset;
+              j.n_hi = (int32_t)bb.t_len;
+              j.out_hi = (uint32_t)p16[x + 1];
+            } else {
+              j.q_hi = j.q_lo;
+              j.t_hi = j.t_lo;
+              j.n_hi = 0;
+              j.out_hi = NONE;
+            }
+            pj[k] = j;
+          }
+        });
+        if ((rc = upload(ctx, d_pj, pj))) return fail(rc);
+        n_pj = (uint32_t)pj.size();
+        max_n = max_n16;
+      }
       bool bytes = A <= 4;   // byte-permute substitution form
       for (int x = 0; x < A * A; ++x) bytes = bytes && matrix[x] + o >= -128 && matrix[x] + o <= 127;
       phase_begin(res, PH_INTER);
       if ((rc = launch_pairs16(ctx, db, qs, d_mat.as<int8_t>(), A, o, e, mode, fe, v.smax, bytes,
-                               d_pj.as<Pair16Job>(), (uint32_t)pj.size(), max_n, sc)))
+                               d_pj.as<Pair16Job>(), n_pj, max_n, sc)))
         return fail(rc);
       phase_end(res, PH_INTER);
       res->phase_cells[PH_INTER] = p16cells;
@@ -1267,6 +1302,7 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
         res->n_rerun = count;
         if (count > cap) { set_error("too many saturated pairs (%u)", count); return fail(DSA_ERR_UNSUPPORTED); }
         if (count) {
+          if ((rc = need_hp())) return fail(rc);
           std::vector<uint32_t> list(count);
           if (cudaMemcpy(list.data(), d_list.p, count * sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
             return fail(DSA_ERR_CUDA);
@@ -1316,27 +1352,8 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
     void* p;
     if ((rc = ctx->alloc(&p, std::max<uint64_t>(1, res->n_hits) * sizeof(dsa_hit)))) return fail(rc);
     res->d_hits = (dsa_hit*)p;
-    DevBuf d_pq, d_pt, d_po;
-    if (!all) {
-      std::vector<uint32_t> pq(n_pairs), pt(n_pairs);
-      std::vector<uint64_t> po(n_pairs);
-      for (uint64_t k = 0; k < n_pairs; ++k) {
-        pq[k] = hp[k].query_id; pt[k] = hp[k].target_id; po[k] = hp[k].t_offset;
-      }
-      if ((rc = upload(ctx, d_pq, pq)) || (rc = upload(ctx, d_pt, pt)) || (rc = upload(ctx, d_po, po)))
-        return fail(rc);
-      if ((rc = launch_fill_hits(ctx, sc, d_pq.as<uint32_t>(), d_pt.as<uint32_t>(),
-                                 d_po.as<uint64_t>(), n_out, db->n, res->d_hits)))
-        return fail(rc);
-      // keep host-side pair vectors alive until the copies have been consumed
-      if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
-        set_error("%s", cudaGetErrorString(cudaGetLastError()));
-        return fail(DSA_ERR_CUDA);
-      }
-    } else {
-      if ((rc = launch_fill_hits(ctx, sc, nullptr, nullptr, nullptr, n_out, db->n, res->d_hits)))
-        return fail(rc);
-    }
+    if ((rc = launch_fill_hits(ctx, sc, all ? nullptr : d_pairs, n_out, db->n, res->d_hits)))
+      return fail(rc);
   }
   phase_end(res, PH_HITS);
   if (cudaGetLastError() != cudaSuccess) { set_error("kernel launch failed"); return fail(DSA_ERR_CUDA); }

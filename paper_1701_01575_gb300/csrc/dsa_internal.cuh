@@ -101,6 +101,29 @@ struct dsa_db {
 };
 
 namespace dsa {
+// Stream-ordered device buffer charged against the context's budget.
+struct DevBuf {
+  dsa_ctx* ctx = nullptr;
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { reset(); }
+  int alloc(dsa_ctx* c, size_t n) {
+    reset();
+    ctx = c;
+    bytes = n ? n : 16;
+    return ctx->alloc(&p, bytes);
+  }
+  void reset() {
+    if (p && ctx) ctx->release(p, bytes);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
 // Builds the length-sorted, lane-interleaved copy of db (once; thread-safe),
 // on ctx's stream, and waits for it.
 int ensure_interleaved(dsa_ctx* ctx, const dsa_db* db);
@@ -241,8 +264,8 @@ int launch_intra_local16(dsa_ctx* ctx, cudaStream_t stream, const dsa_db* db,
 int launch_topk(dsa_ctx* ctx, const Scores& s, uint32_t n_queries, uint32_t n_targets,
                 uint32_t k, dsa_hit* d_hits);
 // Dense pair results -> hit array.
-int launch_fill_hits(dsa_ctx* ctx, const Scores& s, const uint32_t* d_pair_q,
-                     const uint32_t* d_pair_t, const uint64_t* d_pair_off, uint64_t n,
+// d_pairs: the explicit pairs (device), or nullptr for an all-vs-all matrix.
+int launch_fill_hits(dsa_ctx* ctx, const Scores& s, const dsa_pair* d_pairs, uint64_t n,
                      uint32_t n_targets, dsa_hit* d_hits);
 
 // Traceback of hits.
@@ -428,6 +451,39 @@ struct Pair16Job {
 int launch_pairs16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix, int A,
                    int o, int e, int mode, uint32_t fe, int smax, bool bytes,
                    const Pair16Job* d_jobs, uint32_t n_jobs, uint32_t max_n, Scores out);
+
+// Device planning of explicit pairs (k_pairplan.cu).
+struct PairPlanParams {
+  uint32_t n_queries, n_targets;
+  int64_t w16;          // largest |S|, o, e: int16 range bound (m + n) * w16 + o
+  int32_t o, e;
+  bool local16;         // local mode with the saturation flag: every size fits
+  bool packed_ok;       // the packed int16 form is allowed
+};
+struct PairPlanStats {   // field order is used by the kernels' atomics
+  uint64_t cells;        // cells of all valid pairs
+  uint64_t cells16;      // cells of the packed pairs
+  uint64_t n_other;      // valid pairs for the long or int32 paths
+  uint64_t first_bad;    // smallest index of an out-of-range pair, or UINT64_MAX
+  uint64_t n_jobs;       // packed jobs (two pairs of equal query length each)
+  uint32_t max_t_len;    // longest window of a valid pair
+  uint32_t pad;
+};
+// Range check, class, sort key ((m << 32) | t_len) and value (pair index) of
+// every packed pair; hist[m] = packed pairs of query length m, jcnt[m] = their
+// jobs; L = longest query + 2 entries (the last stays 0).
+int launch_pair_classify(dsa_ctx* ctx, const dsa_pair* d_pairs, uint64_t n, const dsa_db* qs,
+                         const dsa_db* db, const PairPlanParams& P, uint64_t* d_key,
+                         uint32_t* d_idx, uint64_t* d_hist, uint64_t L, uint64_t* d_jcnt,
+                         PairPlanStats* d_stats);
+// Stable sort of (key, value) by key; d_key / d_val are set to the buffer
+// pair that holds the result (the input pair or the *2 pair).
+int launch_pair_sort(dsa_ctx* ctx, uint64_t*& d_key, uint32_t*& d_val, uint64_t* d_key2,
+                     uint32_t* d_val2, uint64_t n, uint32_t max_m, uint32_t max_t);
+// Job list from the sorted packed pairs (hist and jcnt are scanned in place).
+int launch_pair_build_jobs(dsa_ctx* ctx, const uint64_t* d_key, const uint32_t* d_val, uint64_t n,
+                           uint64_t* d_hist, uint64_t* d_jcnt, uint64_t L, const dsa_pair* d_pairs,
+                           const dsa_db* qs, const dsa_db* db, Pair16Job* d_jobs);
 
 // Issue-rate probe; bounded-wait self-test.
 int run_issue_probe(dsa_ctx* ctx, int form, double* rate);

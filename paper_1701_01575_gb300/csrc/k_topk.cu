@@ -88,16 +88,16 @@ __global__ void __launch_bounds__(TK_THREADS) k_topk(const int32_t* __restrict__
 
 __global__ void k_fill_hits(const int32_t* __restrict__ score, const int32_t* __restrict__ qend,
                             const int32_t* __restrict__ tend, const uint8_t* __restrict__ flag,
-                            const uint32_t* __restrict__ pair_q, const uint32_t* __restrict__ pair_t,
-                            const uint64_t* __restrict__ pair_off, uint64_t n, uint32_t n_targets,
+                            const dsa_pair* __restrict__ pairs, uint64_t n, uint32_t n_targets,
                             dsa_hit* __restrict__ hits) {
   for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n;
        x += (uint64_t)gridDim.x * blockDim.x) {
     dsa_hit h;
     h.score = score[x]; h.q_end = qend[x]; h.t_end = tend[x];
     h.q_begin = -1; h.t_begin = -1;
-    if (pair_q) {
-      h.query_id = pair_q[x]; h.target_id = pair_t[x]; h.t_offset = pair_off[x];
+    if (pairs) {
+      const dsa_pair p = pairs[x];
+      h.query_id = p.query_id; h.target_id = p.target_id; h.t_offset = p.t_offset;
     } else {
       h.query_id = (uint32_t)(x / n_targets); h.target_id = (uint32_t)(x % n_targets); h.t_offset = 0;
     }
@@ -127,15 +127,13 @@ int launch_topk(dsa_ctx* ctx, const Scores& s, uint32_t n_queries, uint32_t n_ta
   return DSA_OK;
 }
 
-int launch_fill_hits(dsa_ctx* ctx, const Scores& s, const uint32_t* d_pair_q,
-                     const uint32_t* d_pair_t, const uint64_t* d_pair_off, uint64_t n,
+int launch_fill_hits(dsa_ctx* ctx, const Scores& s, const dsa_pair* d_pairs, uint64_t n,
                      uint32_t n_targets, dsa_hit* d_hits) {
   if (n == 0) return DSA_OK;
   uint64_t blocks = (n + 255) / 256;
   if (blocks > (uint64_t)ctx->sm_count * 32) blocks = (uint64_t)ctx->sm_count * 32;
   k_fill_hits<<<(unsigned)blocks, 256, 0, ctx->stream>>>(s.score, s.q_end, s.t_end, s.flag,
-                                                         d_pair_q, d_pair_t, d_pair_off, n,
-                                                         n_targets, d_hits);
+                                                         d_pairs, n, n_targets, d_hits);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   return DSA_OK;

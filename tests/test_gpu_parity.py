@@ -489,6 +489,67 @@ def test_packed_pairs_all_modes(ctx, mode, fe):
         check_traceback(r.hits()[:200], r.cigar(), qs, db, S, 5, 2, mode, fe)
 
 
+def test_packed_pairs_device_plan_multi_digit(ctx):
+    """Device planning of a pair list with query and window lengths above 255
+    (two sort digits each) over several sort tiles: pairs given from host
+    memory and from device memory give the oracle's results."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(2024)
+    S = W.dna_matrix(2, -3)
+    n_q, n_pairs = 900, 6000
+    qlen = np.where(rng.random(n_q) < 0.8, rng.integers(1, 81, n_q), rng.integers(250, 651, n_q))
+    qs = W.SeqSet.from_list([rng.integers(0, 4, int(n)).astype(np.uint8) for n in qlen])
+    db = W.random_dna(rng, 50, 1200, 1400)
+    pairs = np.zeros(n_pairs, dtype=W.PAIR_DTYPE)
+    pairs["query_id"] = rng.integers(0, n_q, n_pairs)
+    pairs["target_id"] = rng.integers(0, db.n, n_pairs)
+    tl = np.where(rng.random(n_pairs) < 0.8, rng.integers(1, 121, n_pairs), rng.integers(260, 1101, n_pairs))
+    room = db.lengths[pairs["target_id"]] - tl
+    pairs["t_offset"] = (rng.random(n_pairs) * (room + 1)).astype(np.uint64)
+    pairs["t_len"] = tl
+    sc, qe, te = oracle.score_pairs(qs.codes, qs.offsets, db.codes, db.offsets, pairs["query_id"],
+                                    pairs["target_id"], S, 5, 2, dsa.SEMIGLOBAL, 12,
+                                    pair_toff=pairs["t_offset"], pair_tlen=pairs["t_len"])
+    d = ctx.load_set(db, 4)
+    q = ctx.load_set(qs, 4)
+    dev = torch.as_tensor(pairs.view(np.uint8), device="cuda")
+    for p_arg in (pairs, dev):
+        r = ctx.align(d, q, S, 5, 2, mode=dsa.SEMIGLOBAL, free_ends=12, pairs=p_arg)
+        ctx.sync()
+        h = r.hits()
+        assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), "device-planned pairs")
+        assert (h["query_id"] == pairs["query_id"]).all() and (h["t_offset"] == pairs["t_offset"]).all()
+        assert r.phase_cells()["inter16"] == int((qs.lengths[pairs["query_id"]] * tl).sum())
+        r.free()
+
+
+def test_pair_range_errors(ctx):
+    """Out-of-range pairs are refused with the smallest bad index, whether the
+    pairs are in host or device memory; nothing is aligned."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(8)
+    qs = W.SeqSet.from_list([rng.integers(0, 4, 30).astype(np.uint8) for _ in range(5)])
+    db = W.random_dna(rng, 4, 100, 100)
+    d = ctx.load_set(db, 4)
+    q = ctx.load_set(qs, 4)
+    S = W.dna_matrix(1, -4)
+    good = np.zeros(5000, dtype=W.PAIR_DTYPE)
+    good["query_id"] = rng.integers(0, 5, 5000)
+    good["target_id"] = rng.integers(0, 4, 5000)
+    good["t_len"] = 50
+    bad_cases = [("query_id", 5), ("target_id", 4), ("t_len", 0), ("t_len", 101),
+                 ("t_offset", 2 ** 63), ("t_offset", 51)]
+    for field, value in bad_cases:
+        p = good.copy()
+        p[field][4321] = value
+        p[field][4999] = value
+        for p_arg in (p, torch.as_tensor(p.view(np.uint8), device="cuda")):
+            with pytest.raises(dsa.DsaError) as ex:
+                ctx.align(d, q, S, 6, 1, mode=dsa.SEMIGLOBAL, free_ends=12, pairs=p_arg)
+            assert ex.value.code == dsa.ERR_INVALID_ARG
+            assert "pair 4321 is out of range" in str(ex.value), (field, value)
+
+
 def test_packed_pairs_protein_local(ctx):
     rng = np.random.default_rng(42)
     bg = W.protein_background()
