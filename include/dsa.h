@@ -202,7 +202,11 @@ int dsa_sync(dsa_ctx* ctx);
  * returns warp-instructions per SM per clock.  form: 0 = s16x2 add-max
  * (DPX), 1 = s16x2 max with ReLU (DPX), 2 = s16x2 three-way max (DPX),
  * 3 = int32 add, 4 = int32 max, 5 = s16x2 add (SIMD video), 6 = int32
- * add-max (DPX), 7 = the packed local cell update mix. */
+ * add-max (DPX), 7 = the packed local cell update mix (5 instructions per
+ * two cells), 8 = u8x4 max, 9 = u8x4 saturating add, 10 = u8x4 saturating
+ * subtract (the packed-byte SIMD intrinsics), 11 = an 8-bit biased unsigned
+ * local cell update (10 intrinsics per four cells), counted per intrinsic
+ * call.  Returns DSA_ERR_INVALID_ARG for another form. */
 int dsa_probe_issue_rate(dsa_ctx* ctx, int form, double* warp_instr_per_sm_per_clk);
 
 /* Self-test of the device-side failure path (no fault is raised): enqueues a
@@ -309,6 +313,72 @@ int dsa_score_pairs_noalloc(const uint8_t* d_q_codes, const uint64_t* d_q_offset
                             uint32_t free_ends, const int8_t* d_matrix, int alphabet_size,
                             int gap_open, int gap_extend, uint32_t max_t_len, int32_t* d_score,
                             int32_t* d_q_end, int32_t* d_t_end, void* cuda_stream);
+
+/* ---- sequence ingest: FASTA / FASTQ text to residue codes (host) ----
+ *
+ * The paper's data-format API converts the common sequence file formats to
+ * its internal representation before alignment (Sec. II.C.1); these calls do
+ * that for FASTA and FASTQ (the paper's third format, ADAM, belongs to its
+ * JVM ecosystem and is not read), streaming, on the host, and produce exactly the
+ * (codes, offsets) arrays dsa_db_load and dsa_align_batch take.
+ *
+ * Format: each record starts at a line whose first character is '>' (FASTA)
+ * or '@' (FASTQ); the rest of that line is the record's name.  FASTA
+ * sequence lines run to the next '>' line; FASTQ sequence lines run to a
+ * line starting with '+', followed by quality lines of exactly as many
+ * characters as the sequence (so a quality line may itself start with '@'
+ * or '+'); qualities are checked for length only and not kept.  Lines end
+ * in "\n" or "\r\n"; blank lines between records and spaces or tabs inside
+ * sequence lines are ignored; residues are case-insensitive.
+ *
+ * Alphabets (code = position in the string):
+ *   DSA_ALPHABET_DNA4    "ACGT"   (U reads as T)
+ *   DSA_ALPHABET_DNA5    "ACGTN"  (U reads as T; the IUPAC ambiguity codes
+ *                                  R Y S W K M B D H V read as N)
+ *   DSA_ALPHABET_PROTEIN "ARNDCQEGHILKMFPSTWYVBZX*" (the NCBI BLOSUM62
+ *                                  order; U, O and J read as X)
+ * Any other character in a sequence line is an error (DSA_ERR_INVALID_ARG,
+ * message with the line number) unless DSA_READ_MAP_UNKNOWN is given, which
+ * reads it as the alphabet's catch-all code: N for DNA5, X for protein, and
+ * A (code 0) for DNA4, which has none.
+ * A record with no residues is kept as an empty sequence (dsa_db_load
+ * refuses empty sequences) unless DSA_READ_SKIP_EMPTY is given. */
+#define DSA_ALPHABET_DNA4 1
+#define DSA_ALPHABET_DNA5 2
+#define DSA_ALPHABET_PROTEIN 3
+#define DSA_READ_MAP_UNKNOWN 1u
+#define DSA_READ_SKIP_EMPTY 2u
+
+typedef struct dsa_reader dsa_reader;
+typedef struct dsa_seqs dsa_seqs;
+
+/* Open a reader over the file at `path` (read in chunks of `chunk_bytes`,
+ * 0 = 4 MiB) or over `len` bytes of text at `data` (not copied: the buffer
+ * must stay valid until dsa_reader_close).  `alphabet` is a
+ * DSA_ALPHABET_* value, `flags` DSA_READ_* bits. */
+int dsa_reader_open(const char* path, int alphabet, uint32_t flags, uint64_t chunk_bytes,
+                    dsa_reader** out);
+int dsa_reader_open_mem(const char* data, uint64_t len, int alphabet, uint32_t flags,
+                        dsa_reader** out);
+/* Parse the next batch of whole records: records are added while the batch
+ * holds at most `max_residues` residues and `max_seqs` records (0 = no
+ * limit), and a batch holds at least one record even if that record alone
+ * is larger.  *out = NULL at the end of the input.  After an error the
+ * reader stays at the failing record and every later call returns the same
+ * error. */
+int dsa_reader_next(dsa_reader* r, uint64_t max_residues, uint32_t max_seqs, dsa_seqs** out);
+int dsa_reader_close(dsa_reader* r);
+
+/* The arrays of a parsed batch, owned by it: `codes` (offsets[n_seqs]
+ * residues), `offsets` (n_seqs + 1 entries, record k = codes[offsets[k] ..
+ * offsets[k+1])), the names concatenated in `names` with `name_offsets`
+ * (n_seqs + 1 entries; names are not NUL-terminated), and the 1-based line
+ * number of each record's header in `lines` (n_seqs entries).  Any output
+ * pointer may be NULL. */
+int dsa_seqs_get(const dsa_seqs* s, const uint8_t** codes, const uint64_t** offsets,
+                 uint32_t* n_seqs, const char** names, const uint64_t** name_offsets,
+                 const uint64_t** lines);
+int dsa_seqs_free(dsa_seqs* s);
 
 #ifdef __cplusplus
 }

@@ -29,6 +29,15 @@ __device__ __forceinline__ uint32_t step(uint32_t x, uint32_t a, uint32_t b) {
   }
   if (FORM == 5) return __vadd2(x, a);
   if (FORM == 6) return (uint32_t)__viaddmax_s32((int)x, (int)a, (int)b);
+  if (FORM >= 8 && FORM <= 10) {
+    // the empty asm hides the operand's value: a max or saturating chain
+    // over known operands could otherwise be folded
+    uint32_t y = a;
+    asm volatile("" : "+r"(y));
+    if (FORM == 8) return __vmaxu4(x, y);
+    if (FORM == 9) return __vaddus4(x, y);
+    return __vsubus4(x, y);
+  }
   return x;
 }
 
@@ -94,6 +103,45 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_cell(uint32_t neg_o2, u
   if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// An 8-bit packed local cell update (four cells per register, unsigned
+// saturating bytes with a bias, the form of 8-bit striped SIMD
+// Smith-Waterman): 10 instructions per update of four cells.
+__global__ void __launch_bounds__(PROBE_THREADS) k_probe_cell8(uint32_t o4, uint32_t e4,
+                                                               uint32_t bias4, int iters,
+                                                               uint32_t* sink, long long* cycles) {
+  uint32_t H[CHAINS], E[CHAINS], F[CHAINS], best[CHAINS];
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) { H[c] = threadIdx.x + c; E[c] = c; F[c] = 3 * c; best[c] = 0; }
+  __syncthreads();
+  const long long t0 = clock64();
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+#pragma unroll
+      for (int c = 0; c < CHAINS; ++c) {
+        uint32_t h = __vaddus4(H[(c + 1) % CHAINS], 0x05030705u + c);   // diagonal + S + bias
+        h = __vsubus4(h, bias4);
+        h = __vmaxu4(h, E[c]);
+        h = __vmaxu4(h, F[c]);
+        best[c] = __vmaxu4(best[c], h);
+        const uint32_t ho = __vsubus4(h, o4);
+        E[c] = __vmaxu4(__vsubus4(E[c], e4), ho);
+        F[c] = __vmaxu4(__vsubus4(F[c], e4), ho);
+        H[c] = h;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) asm volatile("" ::"r"(H[c]), "r"(F[c]), "r"(E[c]), "r"(best[c]));
+  __syncthreads();
+  const long long t1 = clock64();
+  uint32_t acc = 0;
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) acc ^= H[c] ^ F[c] ^ best[c];
+  if (acc == 0x12345678u) sink[threadIdx.x] = acc;
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 // Self-test of the bounded waits: a wait that nothing will ever satisfy must
 // give up after `limit_ns`, record DSA_ERR_DEVICE_TIMEOUT in the status word
 // and let the kernel return normally.
@@ -150,7 +198,7 @@ int run_selftest_wait(dsa_ctx* ctx, int kind, uint64_t limit_ns) {
 }
 
 int run_issue_probe(dsa_ctx* ctx, int form, double* rate) {
-  if (form < 0 || form > 7) {
+  if (form < 0 || form > 11) {
     set_error("unknown probe form %d", form);
     return DSA_ERR_INVALID_ARG;
   }
@@ -175,6 +223,11 @@ int run_issue_probe(dsa_ctx* ctx, int form, double* rate) {
       case 6: k_probe<6><<<blocks, PROBE_THREADS, 0, ctx->stream>>>(a, b, iters, s, c); break;
       case 7: k_probe_cell<<<blocks, PROBE_THREADS, 0, ctx->stream>>>(0xFFF5FFF5u, 0xFFFFFFFFu,
                                                                     iters, s, c); break;
+      case 8: k_probe<8><<<blocks, PROBE_THREADS, 0, ctx->stream>>>(a, b, iters, s, c); break;
+      case 9: k_probe<9><<<blocks, PROBE_THREADS, 0, ctx->stream>>>(a, b, iters, s, c); break;
+      case 10: k_probe<10><<<blocks, PROBE_THREADS, 0, ctx->stream>>>(a, b, iters, s, c); break;
+      case 11: k_probe_cell8<<<blocks, PROBE_THREADS, 0, ctx->stream>>>(0x0B0B0B0Bu, 0x01010101u,
+                                                                     0x04040404u, iters, s, c); break;
     }
   }
   ctx->launches += 2;
@@ -192,7 +245,8 @@ int run_issue_probe(dsa_ctx* ctx, int form, double* rate) {
   }
   std::sort(h.begin(), h.end());
   const double mean = (double)h[h.size() / 2];   // median CTA
-  const double instr_per_thread = (double)iters * 16 * CHAINS * (form == 7 ? 5 : 1);
+  const double instr_per_thread =
+      (double)iters * 16 * CHAINS * (form == 7 ? 5 : form == 11 ? 10 : 1);
   const double warp_instr_per_sm =
       instr_per_thread * PROBE_THREADS / 32.0 * PROBE_BLOCKS_PER_SM;
   *rate = warp_instr_per_sm / mean;

@@ -40,7 +40,11 @@ SYMBOLS = ["dsa_create", "dsa_destroy", "dsa_last_error", "dsa_mem_in_use", "dsa
            "dsa_res_timing", "dsa_kernel_launches", "dsa_score_pairs_noalloc",
            "dsa_res_phase_cells", "dsa_server_create", "dsa_submit", "dsa_poll",
            "dsa_server_drain", "dsa_server_now", "dsa_server_destroy",
-           "dsa_selftest_wait_timeout"]
+           "dsa_selftest_wait_timeout", "dsa_reader_open", "dsa_reader_open_mem",
+           "dsa_reader_next", "dsa_reader_close", "dsa_seqs_get", "dsa_seqs_free"]
+ALPHABET_DNA4, ALPHABET_DNA5, ALPHABET_PROTEIN = 1, 2, 3
+READ_MAP_UNKNOWN, READ_SKIP_EMPTY = 1, 2
+ALPHABET_SIZE = {ALPHABET_DNA4: 4, ALPHABET_DNA5: 5, ALPHABET_PROTEIN: 24}
 REQ_SEARCH, REQ_PAIRS = 0, 1
 
 
@@ -121,6 +125,13 @@ def load_library(path: str = LIB_PATH):
     lib.dsa_score_pairs_noalloc.argtypes = [_vp, _vp, _u32, _vp, _vp, _u32, _vp, _u64, ctypes.c_int,
                                             _u32, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             _u32, _vp, _vp, _vp, _vp]
+    lib.dsa_reader_open.argtypes = [ctypes.c_char_p, ctypes.c_int, _u32, _u64, ctypes.POINTER(_vp)]
+    lib.dsa_reader_open_mem.argtypes = [_vp, _u64, ctypes.c_int, _u32, ctypes.POINTER(_vp)]
+    lib.dsa_reader_next.argtypes = [_vp, _u64, _u32, ctypes.POINTER(_vp)]
+    lib.dsa_reader_close.argtypes = [_vp]
+    lib.dsa_seqs_get.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_u32),
+                                 ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]
+    lib.dsa_seqs_free.argtypes = [_vp]
     _lib = lib
     return lib
 
@@ -443,3 +454,87 @@ class Server:
 def cigar_of(hit, cigar: np.ndarray) -> np.ndarray:
     off, n = int(hit["cigar_off"]), int(hit["cigar_len"])
     return cigar[off:off + n]
+
+
+class Reader:
+    """Streaming FASTA / FASTQ reader (``dsa_reader_*``): batches of whole
+    records as (codes, offsets, names, header lines) -- the arrays
+    ``Context.load`` takes.  Give ``path`` (a file, read in ``chunk_bytes``
+    pieces) or ``data`` (bytes held for the reader's lifetime)."""
+
+    def __init__(self, path=None, data=None, alphabet: int = ALPHABET_DNA4, flags: int = 0,
+                 chunk_bytes: int = 0):
+        if _lib is None:
+            load_library()
+        if (path is None) == (data is None):
+            raise ValueError("give exactly one of path and data")
+        self.alphabet_size = ALPHABET_SIZE.get(alphabet, 0)
+        h = _vp()
+        self._data = None
+        if path is not None:
+            _check(_lib.dsa_reader_open(os.fsencode(path), alphabet, flags, chunk_bytes, ctypes.byref(h)))
+        else:
+            self._data = ctypes.create_string_buffer(bytes(data), len(data))
+            _check(_lib.dsa_reader_open_mem(ctypes.addressof(self._data), len(data), alphabet, flags,
+                                            ctypes.byref(h)))
+        self.handle = h.value
+
+    def next_batch(self, max_residues: int = 0, max_seqs: int = 0):
+        """The next batch, or None at the end of the input."""
+        b = _vp()
+        _check(_lib.dsa_reader_next(self.handle, max_residues, max_seqs, ctypes.byref(b)))
+        if not b.value:
+            return None
+        try:
+            c, o, n, nm, no, ln = _vp(), _vp(), _u32(), _vp(), _vp(), _vp()
+            _check(_lib.dsa_seqs_get(b.value, ctypes.byref(c), ctypes.byref(o), ctypes.byref(n),
+                                     ctypes.byref(nm), ctypes.byref(no), ctypes.byref(ln)))
+            k = n.value
+            offsets = np.ctypeslib.as_array(ctypes.cast(o, ctypes.POINTER(_u64)), (k + 1,)).copy()
+            total = int(offsets[-1])
+            codes = (np.ctypeslib.as_array(ctypes.cast(c, ctypes.POINTER(ctypes.c_uint8)), (total,)).copy()
+                     if total else np.zeros(0, np.uint8))
+            name_off = np.ctypeslib.as_array(ctypes.cast(no, ctypes.POINTER(_u64)), (k + 1,)).copy()
+            raw = ctypes.string_at(nm, int(name_off[-1])) if name_off[-1] else b""
+            names = [raw[name_off[x]:name_off[x + 1]].decode(errors="replace") for x in range(k)]
+            lines = np.ctypeslib.as_array(ctypes.cast(ln, ctypes.POINTER(_u64)), (k,)).copy()
+            return codes, offsets, names, lines
+        finally:
+            _lib.dsa_seqs_free(b.value)
+
+    def batches(self, max_residues: int = 0, max_seqs: int = 0):
+        """Every remaining batch under the given limits (0 = no limit)."""
+        while True:
+            b = self.next_batch(max_residues, max_seqs)
+            if b is None:
+                return
+            yield b
+
+    def __iter__(self):
+        return self.batches()
+
+    def close(self):
+        if self.handle:
+            _lib.dsa_reader_close(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def read_sequences(path=None, data=None, alphabet: int = ALPHABET_DNA4, flags: int = 0):
+    """Whole input as one (codes, offsets, names, lines) batch."""
+    with Reader(path=path, data=data, alphabet=alphabet, flags=flags) as r:
+        b = r.next_batch()
+        if b is None:
+            return np.zeros(0, np.uint8), np.zeros(1, np.uint64), [], np.zeros(0, np.uint64)
+        return b

@@ -290,9 +290,12 @@ def test_traceback_topk_protein_long_hits(ctx):
 
 
 def test_issue_probe(ctx):
-    for form in range(8):
+    for form in range(12):
         rate = ctx.probe_issue_rate(form)
         assert 0.05 < rate < 16, (form, rate)
+    with pytest.raises(dsa.DsaError) as ex:
+        ctx.probe_issue_rate(12)
+    assert ex.value.code == dsa.ERR_INVALID_ARG
 
 
 def test_memory_budget_enforced():
@@ -521,6 +524,50 @@ def test_packed_pairs_device_plan_multi_digit(ctx):
         assert (h["query_id"] == pairs["query_id"]).all() and (h["t_offset"] == pairs["t_offset"]).all()
         assert r.phase_cells()["inter16"] == int((qs.lengths[pairs["query_id"]] * tl).sum())
         r.free()
+
+
+def test_fasta_fastq_ingest_to_alignment(ctx, tmp_path):
+    """A FASTA database and FASTQ reads go through the streaming reader, the
+    device load and a semi-global search of each read in its window; the
+    oracle scores the codes the generator wrote."""
+    rng = np.random.default_rng(31)
+    genome = [rng.integers(0, 4, int(n)).astype(np.uint8) for n in (5000, 3000)]
+    fa = tmp_path / "g.fa"
+    with open(fa, "w") as f:
+        for k, g in enumerate(genome):
+            f.write(f">chr{k}\n")
+            text = "".join("ACGT"[c] for c in g)
+            for x in range(0, len(text), 61):
+                f.write(text[x:x + 61] + "\n")
+    reads, pairs = [], np.zeros(40, dtype=W.PAIR_DTYPE)
+    for k in range(40):
+        t = k % 2
+        st = int(rng.integers(0, len(genome[t]) - 300))
+        reads.append(W.mutate(rng, genome[t][st + 20: st + 20 + int(rng.integers(50, 150))], 0.02, 0.01))
+        pairs[k] = (k, t, st, 250, 0)
+    fq = tmp_path / "r.fq"
+    with open(fq, "w") as f:
+        for k, rd in enumerate(reads):
+            f.write(f"@read{k}\n{''.join('ACGT'[c] for c in rd)}\n+\n{'I' * len(rd)}\n")
+    with dsa.Reader(path=str(fa), alphabet=dsa.ALPHABET_DNA4, chunk_bytes=1000) as r:
+        dcodes, doffs, dnames, _ = r.next_batch()
+    qcodes, qoffs, qnames, _ = dsa.read_sequences(path=str(fq), alphabet=dsa.ALPHABET_DNA4)
+    db = W.SeqSet.from_list(genome)
+    qs = W.SeqSet.from_list(reads)
+    assert np.array_equal(dcodes, db.codes) and np.array_equal(qcodes, qs.codes)
+    assert dnames == ["chr0", "chr1"] and qnames[7] == "read7"
+    d = ctx.load(dcodes, doffs, 4)
+    q = ctx.load(qcodes, qoffs, 4)
+    S = W.dna_matrix(1, -4)
+    r = ctx.align(d, q, S, 6, 1, mode=dsa.SEMIGLOBAL, free_ends=12, pairs=pairs)
+    ctx.traceback(r)
+    ctx.sync()
+    h = r.hits()
+    sc, qe, te = oracle.score_pairs(qs.codes, qs.offsets, db.codes, db.offsets, pairs["query_id"],
+                                    pairs["target_id"], S, 6, 1, dsa.SEMIGLOBAL, 12,
+                                    pair_toff=pairs["t_offset"], pair_tlen=pairs["t_len"])
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), "ingested reads")
+    check_traceback(h, r.cigar(), qs, db, S, 6, 1, dsa.SEMIGLOBAL, 12)
 
 
 def test_pair_range_errors(ctx):
