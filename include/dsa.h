@@ -314,6 +314,51 @@ int dsa_score_pairs_noalloc(const uint8_t* d_q_codes, const uint64_t* d_q_offset
                             int gap_open, int gap_extend, uint32_t max_t_len, int32_t* d_score,
                             int32_t* d_q_end, int32_t* d_t_end, void* cuda_stream);
 
+/* ---- partition + reduce of top-K searches (Sec. II.B.2) ----
+ *
+ * The paper keeps the top K of every database partition and reduces those
+ * lists to the top K of the whole database.  Under the library's total order
+ * (score descending, then target id ascending) the reduce of exact
+ * per-partition lists equals one search of the whole database, so a
+ * database larger than the device or the context's budget can be searched
+ * one partition at a time, and lists from several devices merge the same
+ * way. */
+
+/* Merge `n_parts` top-K hit lists (host arrays) of the same `n_queries`
+ * queries against consecutive partitions of one database.  part_hits[p]
+ * holds part_n_hits[p] hits, query-major, part_n_hits[p] / n_queries per
+ * query in rank order (the layout dsa_res_get gives for a top-K search);
+ * their target ids are partition-local and target_base[p], the global id of
+ * the partition's first target, is added.  part_cigar[p] holds the
+ * partition's CIGAR words (may be NULL when no hit of it is traced).
+ * Output: out_hits (caller-allocated, n_queries * k entries) receives per
+ * query the best min(k, sum of the per-query list lengths) hits in rank
+ * order with global target ids; out_cigar (caller-allocated, at least the
+ * sum of the inputs' cigar_len, or NULL when nothing is traced) receives
+ * their CIGAR words, re-indexed by cigar_off.  Lists out of order, hits of
+ * the wrong query, or traced hits without CIGAR arrays are
+ * DSA_ERR_INVALID_ARG. */
+int dsa_merge_topk(const dsa_hit* const* part_hits, const uint64_t* part_n_hits,
+                   const uint32_t* const* part_cigar, const uint32_t* target_base,
+                   uint32_t n_parts, uint32_t n_queries, uint32_t k, dsa_hit* out_hits,
+                   uint64_t* out_n_hits, uint32_t* out_cigar, uint64_t* out_n_cigar);
+
+/* Top-K search of device-resident `queries` against a host database
+ * (`codes`, `offsets`, `n_seqs` sequences as for dsa_db_load) too large to
+ * hold at once: consecutive targets are loaded `partition_residues` residues
+ * at a time (at least one target per partition; 0 = one partition), each
+ * partition is searched (and, if `traceback` is non-zero, traced) on the
+ * context's stream and freed, and the lists are merged with dsa_merge_topk.
+ * The result is host-only (dsa_res_get gives host arrays; it cannot be
+ * traced further) and holds the same hits and CIGARs as one dsa_align +
+ * dsa_traceback over the whole database; dsa_res_stats gives the summed
+ * cells and reruns. */
+int dsa_search_partitioned(dsa_ctx* ctx, const uint8_t* codes, const uint64_t* offsets,
+                           uint32_t n_seqs, int alphabet_size, uint64_t partition_residues,
+                           const dsa_db* queries, int mode, uint32_t free_ends,
+                           const int8_t* matrix, int gap_open, int gap_extend, uint32_t top_k,
+                           int traceback, dsa_res** out);
+
 /* ---- sequence ingest: FASTA / FASTQ text to residue codes (host) ----
  *
  * The paper's data-format API converts the common sequence file formats to

@@ -41,7 +41,8 @@ SYMBOLS = ["dsa_create", "dsa_destroy", "dsa_last_error", "dsa_mem_in_use", "dsa
            "dsa_res_phase_cells", "dsa_server_create", "dsa_submit", "dsa_poll",
            "dsa_server_drain", "dsa_server_now", "dsa_server_destroy",
            "dsa_selftest_wait_timeout", "dsa_reader_open", "dsa_reader_open_mem",
-           "dsa_reader_next", "dsa_reader_close", "dsa_seqs_get", "dsa_seqs_free"]
+           "dsa_reader_next", "dsa_reader_close", "dsa_seqs_get", "dsa_seqs_free",
+           "dsa_merge_topk", "dsa_search_partitioned"]
 ALPHABET_DNA4, ALPHABET_DNA5, ALPHABET_PROTEIN = 1, 2, 3
 READ_MAP_UNKNOWN, READ_SKIP_EMPTY = 1, 2
 ALPHABET_SIZE = {ALPHABET_DNA4: 4, ALPHABET_DNA5: 5, ALPHABET_PROTEIN: 24}
@@ -132,6 +133,11 @@ def load_library(path: str = LIB_PATH):
     lib.dsa_seqs_get.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_u32),
                                  ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]
     lib.dsa_seqs_free.argtypes = [_vp]
+    lib.dsa_merge_topk.argtypes = [_vp, _vp, _vp, _vp, _u32, _u32, _u32, _vp, ctypes.POINTER(_u64), _vp,
+                                   ctypes.POINTER(_u64)]
+    lib.dsa_search_partitioned.argtypes = [_vp, _vp, _vp, _u32, ctypes.c_int, _u64, _vp, ctypes.c_int,
+                                           _u32, _vp, ctypes.c_int, ctypes.c_int, _u32, ctypes.c_int,
+                                           ctypes.POINTER(_vp)]
     _lib = lib
     return lib
 
@@ -307,6 +313,22 @@ class Context:
         if arr.dtype != PAIR_DTYPE:
             arr = arr.astype(PAIR_DTYPE)
         return _ptr(arr), len(arr), 0, arr
+
+    def search_partitioned(self, codes: np.ndarray, offsets: np.ndarray, alphabet_size: int,
+                           queries: Database, matrix: np.ndarray, gap_open: int, gap_extend: int,
+                           top_k: int, partition_residues: int, mode: int = LOCAL,
+                           free_ends: int = 15, traceback: bool = True) -> Result:
+        """``dsa_search_partitioned``: a host database searched one partition at
+        a time; the result is host-only."""
+        codes = np.ascontiguousarray(codes, dtype=np.uint8)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        mat = np.ascontiguousarray(matrix, dtype=np.int8)
+        h = _vp()
+        _check(_lib.dsa_search_partitioned(self.handle, _ptr(codes), _ptr(offsets), len(offsets) - 1,
+                                           alphabet_size, partition_residues, queries.handle, mode,
+                                           free_ends, _ptr(mat), gap_open, gap_extend, top_k,
+                                           1 if traceback else 0, ctypes.byref(h)))
+        return Result(self, h.value, False, keep=(queries,))
 
     def align(self, db: Database, queries: Database, matrix: np.ndarray, gap_open: int,
               gap_extend: int, mode: int = LOCAL, free_ends: int = 15, pairs=None, top_k: int = 0,
@@ -538,3 +560,25 @@ def read_sequences(path=None, data=None, alphabet: int = ALPHABET_DNA4, flags: i
         if b is None:
             return np.zeros(0, np.uint8), np.zeros(1, np.uint64), [], np.zeros(0, np.uint64)
         return b
+
+
+def merge_topk(parts, target_base, n_queries: int, k: int):
+    """``dsa_merge_topk`` over host arrays: ``parts`` is a list of (hits,
+    cigar or None) per partition (hits as HIT_DTYPE arrays, query-major);
+    returns the merged (hits, cigar) with global target ids."""
+    if _lib is None:
+        load_library()
+    hs = [np.ascontiguousarray(h, dtype=HIT_DTYPE) for h, _ in parts]
+    cs = [None if c is None else np.ascontiguousarray(c, dtype=np.uint32) for _, c in parts]
+    n = len(parts)
+    hp = (_vp * max(n, 1))(*[h.ctypes.data if len(h) else None for h in hs])
+    cp = (_vp * max(n, 1))(*[None if c is None or not len(c) else c.ctypes.data for c in cs])
+    nh = np.array([len(h) for h in hs] or [0], dtype=np.uint64)
+    base = np.ascontiguousarray(target_base, dtype=np.uint32)
+    out = np.zeros(max(1, n_queries * k), dtype=HIT_DTYPE)
+    cig_cap = sum(int(h["cigar_len"].sum()) for h in hs)
+    out_c = np.zeros(max(1, cig_cap), dtype=np.uint32)
+    on, oc = _u64(), _u64()
+    _check(_lib.dsa_merge_topk(hp, _ptr(nh), cp, _ptr(base), n, n_queries, k, _ptr(out),
+                               ctypes.byref(on), _ptr(out_c), ctypes.byref(oc)))
+    return out[:on.value].copy(), out_c[:oc.value].copy()

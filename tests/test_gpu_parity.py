@@ -570,6 +570,36 @@ def test_fasta_fastq_ingest_to_alignment(ctx, tmp_path):
     check_traceback(h, r.cigar(), qs, db, S, 6, 1, dsa.SEMIGLOBAL, 12)
 
 
+@pytest.mark.parametrize("part_res", [0, 9_000, 700, 1])
+def test_partitioned_search_equals_whole_database(ctx, part_res):
+    """Sec. II.B.2's partition + reduce on one device: the database is loaded
+    and searched a partition at a time (top 10, traceback) and the lists are
+    merged; hits, coordinates and CIGARs equal one search of the whole
+    database (partitions of one target each at the smallest size)."""
+    rng = np.random.default_rng(404)
+    bg = W.protein_background()
+    db = W.SeqSet.from_list([rng.choice(20, int(n), p=bg).astype(np.uint8)
+                             for n in rng.integers(30, 400, 120)])
+    qs = W.SeqSet.from_list([rng.choice(20, int(n), p=bg).astype(np.uint8) for n in (60, 150, 333)])
+    S = W.blosum62()
+    d = ctx.load_set(db, 24)
+    q = ctx.load_set(qs, 24)
+    whole = ctx.align(d, q, S, 11, 1, top_k=10)
+    ctx.traceback(whole)
+    want, wcig = whole.hits(), whole.cigar()
+    part = ctx.search_partitioned(db.codes, db.offsets, 24, q, S, 11, 1, top_k=10,
+                                  partition_residues=part_res)
+    got, gcig = part.hits(), part.cigar()
+    for f in ("score", "q_begin", "q_end", "t_begin", "t_end", "query_id", "target_id"):
+        assert np.array_equal(got[f], want[f]), f
+    for a, b in zip(got, want):
+        assert np.array_equal(gcig[a["cigar_off"]:a["cigar_off"] + a["cigar_len"]],
+                              wcig[b["cigar_off"]:b["cigar_off"] + b["cigar_len"]])
+    assert part.stats()[0] == whole.stats()[0]
+    with pytest.raises(dsa.DsaError):
+        ctx.traceback(part)   # host-only result
+
+
 def test_pair_range_errors(ctx):
     """Out-of-range pairs are refused with the smallest bad index, whether the
     pairs are in host or device memory; nothing is aligned."""
