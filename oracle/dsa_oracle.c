@@ -33,6 +33,11 @@
  * when (m+n)*max(|S|, o, e) could reach 2^29.
  *
  * Rows of S are query residues, columns target residues: S[q*A + t].
+ *
+ * Position-specific form (the user-defined scoring of Sec. II.C.2): a query
+ * may instead be given as a profile P of m rows of A scores, and the
+ * substitution term of cell (i, j) is P[i-1][t_j] in place of S[q_i][t_j];
+ * everything else is unchanged (oracle_score_pssm, oracle_score_pairs_pssm).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -87,16 +92,31 @@ static void offer(int32_t h, int64_t i, int64_t j, int32_t* best, int64_t* bi, i
   }
 }
 
+/* Largest |value| of a position-specific score profile (m rows of A). */
+static int check_pssm(int64_t m, int64_t n, const int8_t* P, int A, int32_t o, int32_t e,
+                      int mode) {
+  if (m < 1 || n < 1 || A < 1 || A > 256 || o < 0 || e < 0 || e > o) return ORC_EINVAL;
+  if (mode < 0 || mode > 2) return ORC_EINVAL;
+  int32_t smax = 0;
+  for (int64_t k = 0; k < m * A; ++k) {
+    int32_t v = P[k] < 0 ? -P[k] : P[k];
+    if (v > smax) smax = v;
+  }
+  int64_t w = smax > o ? smax : o;
+  if (e > w) w = e;
+  if ((m + n + 2) * (w + 1) >= ((int64_t)1 << 29)) return ORC_EINVAL;
+  return ORC_OK;
+}
+
 /*
- * Score pass: optimal score and result cell of one pair.
- * Outputs 0-based inclusive ends (q_end = i-1, t_end = j-1 of the 1-based
- * result cell); local alignments with score 0 report ends -1.
+ * Score pass of one pair, the DP shared by the matrix and the profile forms:
+ * the substitution row of query position i is S[q_i] (P == NULL) or the
+ * profile's row i, P[i] (the position-specific scores of the user-defined
+ * scoring extension, Sec. II.C.2).
  */
-int oracle_score(const uint8_t* q, int64_t m, const uint8_t* t, int64_t n,
-                 const int8_t* S, int A, int32_t o, int32_t e, int mode, uint32_t fe,
-                 int32_t* score, int32_t* q_end, int32_t* t_end) {
-  int rc = check_args(m, n, S, A, o, e, mode);
-  if (rc) return rc;
+static int score_core(const uint8_t* q, const int8_t* S, const int8_t* P, int64_t m,
+                      const uint8_t* t, int64_t n, int A, int32_t o, int32_t e, int mode,
+                      uint32_t fe, int32_t* score, int32_t* q_end, int32_t* t_end) {
   int32_t* H = (int32_t*)malloc((size_t)(n + 1) * sizeof(int32_t));
   int32_t* F = (int32_t*)malloc((size_t)(n + 1) * sizeof(int32_t));
   if (!H || !F) { free(H); free(F); return ORC_ENOMEM; }
@@ -112,7 +132,7 @@ int oracle_score(const uint8_t* q, int64_t m, const uint8_t* t, int64_t n,
     int32_t diag = H[0];                 /* H[i-1][0] */
     H[0] = h_col0(mode, fe, i, o, e);    /* H[i][0]   */
     int32_t E = ORC_NEG_INF;             /* E[i][0]   */
-    const int8_t* Srow = S + (size_t)q[i - 1] * A;
+    const int8_t* Srow = P ? P + (size_t)(i - 1) * A : S + (size_t)q[i - 1] * A;
     for (int64_t j = 1; j <= n; ++j) {
       E = imax(E - e, H[j - 1] - o);              /* H[j-1] holds H[i][j-1] */
       int32_t f = imax(F[j] - e, H[j] - o);       /* H[j] still holds H[i-1][j] */
@@ -137,6 +157,32 @@ int oracle_score(const uint8_t* q, int64_t m, const uint8_t* t, int64_t n,
   if (mode == ORC_LOCAL && !have) { *score = 0; *q_end = -1; *t_end = -1; return ORC_OK; }
   *score = best; *q_end = (int32_t)(bi - 1); *t_end = (int32_t)(bj - 1);
   return ORC_OK;
+}
+
+/*
+ * Score pass: optimal score and result cell of one pair.
+ * Outputs 0-based inclusive ends (q_end = i-1, t_end = j-1 of the 1-based
+ * result cell); local alignments with score 0 report ends -1.
+ */
+int oracle_score(const uint8_t* q, int64_t m, const uint8_t* t, int64_t n,
+                 const int8_t* S, int A, int32_t o, int32_t e, int mode, uint32_t fe,
+                 int32_t* score, int32_t* q_end, int32_t* t_end) {
+  int rc = check_args(m, n, S, A, o, e, mode);
+  if (rc) return rc;
+  return score_core(q, S, NULL, m, t, n, A, o, e, mode, fe, score, q_end, t_end);
+}
+
+/*
+ * Score pass of a query given as a position-specific profile: P holds m rows
+ * of A int8 scores, P[i * A + a] for query position i against target residue
+ * a.  Same outputs as oracle_score.
+ */
+int oracle_score_pssm(const int8_t* P, int64_t m, const uint8_t* t, int64_t n, int A,
+                      int32_t o, int32_t e, int mode, uint32_t fe, int32_t* score,
+                      int32_t* q_end, int32_t* t_end) {
+  int rc = check_pssm(m, n, P, A, o, e, mode);
+  if (rc) return rc;
+  return score_core(NULL, NULL, P, m, t, n, A, o, e, mode, fe, score, q_end, t_end);
 }
 
 /*
@@ -235,6 +281,7 @@ typedef struct {
   const uint32_t* pair_tlen;
   int64_t n_pairs;
   const int8_t* S; int A; int32_t o, e; int mode; uint32_t fe;
+  const int8_t* pssm;          /* NULL: matrix S; else rows of every query residue */
   int32_t* score; int32_t* q_end; int32_t* t_end;
   int64_t next; pthread_mutex_t mu; int rc;
 } batch_job;
@@ -252,12 +299,25 @@ static void* batch_worker(void* arg) {
     const uint8_t* ts = J->t_codes + J->t_off[ti];
     int64_t n = (int64_t)(J->t_off[ti + 1] - J->t_off[ti]);
     if (J->pair_toff) { ts += J->pair_toff[p]; n = J->pair_tlen[p]; }
-    int rc = oracle_score(qs, m, ts, n, J->S, J->A, J->o, J->e, J->mode, J->fe,
-                          &J->score[p], &J->q_end[p], &J->t_end[p]);
+    int rc = J->pssm
+                 ? oracle_score_pssm(J->pssm + J->q_off[qi] * (uint64_t)J->A, m, ts, n, J->A,
+                                     J->o, J->e, J->mode, J->fe, &J->score[p], &J->q_end[p],
+                                     &J->t_end[p])
+                 : oracle_score(qs, m, ts, n, J->S, J->A, J->o, J->e, J->mode, J->fe,
+                                &J->score[p], &J->q_end[p], &J->t_end[p]);
     if (rc) { pthread_mutex_lock(&J->mu); J->rc = rc; pthread_mutex_unlock(&J->mu); }
   }
   return NULL;
 }
+
+static int run_batch(batch_job* J, int n_threads);
+int oracle_score_pairs_pssm(const uint8_t* q_codes, const uint64_t* q_off,
+                            const uint8_t* t_codes, const uint64_t* t_off,
+                            const uint32_t* pair_q, const uint32_t* pair_t,
+                            const uint64_t* pair_toff, const uint32_t* pair_tlen,
+                            int64_t n_pairs, const int8_t* S, const int8_t* pssm, int A,
+                            int32_t o, int32_t e, int mode, uint32_t fe, int n_threads,
+                            int32_t* score, int32_t* q_end, int32_t* t_end);
 
 int oracle_score_pairs(const uint8_t* q_codes, const uint64_t* q_off,
                        const uint8_t* t_codes, const uint64_t* t_off,
@@ -265,12 +325,33 @@ int oracle_score_pairs(const uint8_t* q_codes, const uint64_t* q_off,
                        const uint64_t* pair_toff, const uint32_t* pair_tlen, int64_t n_pairs,
                        const int8_t* S, int A, int32_t o, int32_t e, int mode, uint32_t fe,
                        int n_threads, int32_t* score, int32_t* q_end, int32_t* t_end) {
+  return oracle_score_pairs_pssm(q_codes, q_off, t_codes, t_off, pair_q, pair_t, pair_toff,
+                                 pair_tlen, n_pairs, S, NULL, A, o, e, mode, fe, n_threads,
+                                 score, q_end, t_end);
+}
+
+/* As oracle_score_pairs; with pssm != NULL the queries are position-specific
+ * profiles: query residue k of the query set (offsets q_off) has the score
+ * row pssm[k * A .. k * A + A - 1], and q_codes is not read. */
+int oracle_score_pairs_pssm(const uint8_t* q_codes, const uint64_t* q_off,
+                            const uint8_t* t_codes, const uint64_t* t_off,
+                            const uint32_t* pair_q, const uint32_t* pair_t,
+                            const uint64_t* pair_toff, const uint32_t* pair_tlen,
+                            int64_t n_pairs, const int8_t* S, const int8_t* pssm, int A,
+                            int32_t o, int32_t e, int mode, uint32_t fe, int n_threads,
+                            int32_t* score, int32_t* q_end, int32_t* t_end) {
   batch_job J;
   memset(&J, 0, sizeof(J));
+  J.pssm = pssm;
   J.q_codes = q_codes; J.q_off = q_off; J.t_codes = t_codes; J.t_off = t_off;
   J.pair_q = pair_q; J.pair_t = pair_t; J.pair_toff = pair_toff; J.pair_tlen = pair_tlen;
   J.n_pairs = n_pairs; J.S = S; J.A = A; J.o = o; J.e = e; J.mode = mode; J.fe = fe;
   J.score = score; J.q_end = q_end; J.t_end = t_end;
+  return run_batch(&J, n_threads);
+}
+
+static int run_batch(batch_job* Jp, int n_threads) {
+  batch_job J = *Jp;
   pthread_mutex_init(&J.mu, NULL);
   if (n_threads < 1) n_threads = 1;
   if (n_threads > 512) n_threads = 512;

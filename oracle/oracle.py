@@ -69,6 +69,14 @@ def _load():
                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
                                                ctypes.c_uint32, ctypes.c_int, _i32p, _i32p,
                                                _i32p]
+            lib.oracle_score_pssm.argtypes = [_i8p, ctypes.c_int64, _u8p, ctypes.c_int64,
+                                              ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int, ctypes.c_uint32, _i32p, _i32p, _i32p]
+            lib.oracle_score_pairs_pssm.argtypes = [_u8p, _u64p, _u8p, _u64p, _u32p, _u32p,
+                                                    _u64p, _u32p, ctypes.c_int64, _i8p, _i8p,
+                                                    ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
+                                                    ctypes.c_int, ctypes.c_uint32, ctypes.c_int,
+                                                    _i32p, _i32p, _i32p]
             _lib = lib
     return _lib
 
@@ -117,9 +125,31 @@ def traceback(q, t, S, gap_open: int, gap_extend: int, mode: int, free_ends: int
     return int(qb.value), int(tb.value), cig[:nops.value].copy()
 
 
+def score_pssm(P, t, gap_open: int, gap_extend: int, mode: int = LOCAL, free_ends: int = 15):
+    """(score, q_end, t_end) of a query given as a position-specific profile:
+    P is an (m, A) int8 array, P[i, a] the score of query position i against
+    target residue a (Sec. II.C.2's user-defined scoring)."""
+    lib = _load()
+    P = np.ascontiguousarray(np.asarray(P, dtype=np.int8))
+    assert P.ndim == 2
+    t = _u8(t)
+    sc = ctypes.c_int32(); qe = ctypes.c_int32(); te = ctypes.c_int32()
+    rc = lib.oracle_score_pssm(_p(P, _i8p), P.shape[0], _p(t, _u8p), len(t), P.shape[1],
+                               gap_open, gap_extend, mode, free_ends,
+                               ctypes.byref(sc), ctypes.byref(qe), ctypes.byref(te))
+    if rc:
+        raise ValueError(f"oracle_score_pssm failed ({rc})")
+    return int(sc.value), int(qe.value), int(te.value)
+
+
 def score_pairs(q_codes, q_off, t_codes, t_off, pair_q, pair_t, S, gap_open, gap_extend,
-                mode=LOCAL, free_ends=15, pair_toff=None, pair_tlen=None, threads=None):
-    """Score many (query, target) pairs on host threads.  Returns (score, q_end, t_end)."""
+                mode=LOCAL, free_ends=15, pair_toff=None, pair_tlen=None, threads=None,
+                pssm=None):
+    """Score many (query, target) pairs on host threads.  Returns (score, q_end, t_end).
+
+    With ``pssm`` (an (total query residues, A) int8 array, one row per query
+    residue in q_codes order) the queries are position-specific profiles and
+    ``S`` only gives the alphabet size A."""
     lib = _load()
     q_codes = _u8(q_codes); t_codes = _u8(t_codes); S = _mat(S)
     q_off = np.ascontiguousarray(q_off, dtype=np.uint64)
@@ -136,18 +166,22 @@ def score_pairs(q_codes, q_off, t_codes, t_off, pair_q, pair_t, S, gap_open, gap
         toff_p, tlen_p = None, None
     if threads is None:
         threads = os.cpu_count() or 1
-    rc = lib.oracle_score_pairs(_p(q_codes, _u8p), _p(q_off, _u64p), _p(t_codes, _u8p),
-                                _p(t_off, _u64p), _p(pair_q, _u32p), _p(pair_t, _u32p),
-                                toff_p, tlen_p, n, _p(S, _i8p), S.shape[0], gap_open,
-                                gap_extend, mode, free_ends, threads, _p(sc, _i32p),
-                                _p(qe, _i32p), _p(te, _i32p))
+    if pssm is not None:
+        pssm = np.ascontiguousarray(np.asarray(pssm, dtype=np.int8))
+        assert pssm.shape == (int(q_off[-1]), S.shape[0])
+    rc = lib.oracle_score_pairs_pssm(_p(q_codes, _u8p), _p(q_off, _u64p), _p(t_codes, _u8p),
+                                     _p(t_off, _u64p), _p(pair_q, _u32p), _p(pair_t, _u32p),
+                                     toff_p, tlen_p, n, _p(S, _i8p),
+                                     None if pssm is None else _p(pssm, _i8p), S.shape[0],
+                                     gap_open, gap_extend, mode, free_ends, threads,
+                                     _p(sc, _i32p), _p(qe, _i32p), _p(te, _i32p))
     if rc:
         raise ValueError(f"oracle_score_pairs failed ({rc})")
     return sc, qe, te
 
 
 def score_all_vs_all(queries, db, S, gap_open, gap_extend, mode=LOCAL, free_ends=15,
-                     targets=None, threads=None):
+                     targets=None, threads=None, pssm=None):
     """Score every query against every target (or the given target ids).
 
     ``queries``/``db`` are objects with ``codes`` and ``offsets``.  Returns
@@ -157,7 +191,7 @@ def score_all_vs_all(queries, db, S, gap_open, gap_extend, mode=LOCAL, free_ends
     pq = np.repeat(np.arange(nq, dtype=np.uint32), len(tids))
     pt = np.tile(tids, nq)
     sc, qe, te = score_pairs(queries.codes, queries.offsets, db.codes, db.offsets, pq, pt, S,
-                             gap_open, gap_extend, mode, free_ends, threads=threads)
+                             gap_open, gap_extend, mode, free_ends, threads=threads, pssm=pssm)
     shape = (nq, len(tids))
     return sc.reshape(shape), qe.reshape(shape), te.reshape(shape)
 

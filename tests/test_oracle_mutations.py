@@ -27,6 +27,7 @@ MUTANTS = {
     "traceback_extend_before_open": ("if (AT(Fm, i, j) == AT(H, i - 1, j) - o) state = 0;",
                                      "if (AT(Fm, i, j) != AT(Fm, i - 1, j) - e) state = 0;"),
     "local_floor_missing": ("if (mode == ORC_LOCAL && h < 0) h = 0;\n      diag", "diag"),
+    "profile_row_stride_dropped": ("P ? P + (size_t)(i - 1) * A", "P ? P + (size_t)(i - 1)"),
 }
 
 
@@ -42,7 +43,8 @@ def test_pins_catch_mutant(name, tmp_path):
                     str(so_path)], check=True)
     env = dict(os.environ, DSA_ORACLE_LIB=str(so_path))
     tests = [os.path.join(ROOT, "tests", "test_oracle_bruteforce.py"),
-             os.path.join(ROOT, "tests", "test_oracle_golden.py")]
+             os.path.join(ROOT, "tests", "test_oracle_golden.py"),
+             os.path.join(ROOT, "tests", "test_oracle_pssm.py")]
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] + tests,
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
