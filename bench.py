@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--partition-residues", type=int, default=0,
                     help="protein_search: stream the host database through the device this many "
                          "residues at a time (partition + top-K reduce) instead of keeping it resident")
+    ap.add_argument("--pssm", action="store_true",
+                    help="protein_search: score against position-specific profiles (the queries' "
+                         "BLOSUM62 rows perturbed by -2..+2) instead of the matrix; top-10 without "
+                         "traceback (profile results carry scores and ends only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -248,7 +252,17 @@ def bench_ours(args):
     if wl.pairs is not None:
         pairs_dev = torch.as_tensor(wl.pairs.view(np.uint8), device="cuda")
 
+    pssm = None
+    if args.pssm:
+        from paper_1701_01575_gb300 import workloads as W
+        prng = np.random.default_rng(W.SEED_BASE + 77)
+        pssm = np.clip(S[wl.queries.codes].astype(np.int16) + prng.integers(-2, 3, (len(wl.queries.codes), A)),
+                       -128, 127).astype(np.int8)
+
     def step():
+        if pssm is not None:
+            return ctx.align_pssm(db, qs, pssm, o, e, mode=wl.mode, free_ends=wl.free_ends,
+                                  top_k=wl.top_k, flags=flags)
         if args.partition_residues:
             # every step loads each partition from host memory, searches and
             # traces it, and merges the per-partition top-K lists
@@ -300,6 +314,9 @@ def bench_ours(args):
         wtext = wtext.replace("1,000,000 reads", f"{args.reads:,} reads")
     if args.workload.startswith("long_pairs"):
         wtext = wtext.replace("64 DNA pairs", f"{args.long_pairs} DNA pairs")
+    if args.pssm:
+        wtext = wtext.replace("BLOSUM62 11/1", "position-specific profiles (BLOSUM62 rows of each "
+                              "query residue + uniform -2..2), 11/1").replace(" + traceback", "")
     if args.partition_residues:
         wtext += (f"; database streamed from host memory in partitions of {args.partition_residues:,} "
                   "residues, per-partition top-K merged")

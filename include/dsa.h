@@ -165,6 +165,22 @@ int dsa_align_batch(dsa_ctx* ctx, const dsa_db* db, const uint8_t* q_codes,
                     int alphabet_size, int gap_open, int gap_extend, uint32_t top_k,
                     uint32_t flags, dsa_res** out);
 
+/* All-vs-all search with position-specific scores (the user-defined scoring
+ * extension of Sec. II.C.2, e.g. a PSSM built from a query family): query
+ * residue i of query q scores against target residue a with
+ * pssm[(o_q + i) * alphabet_size + a], where o_q is the query's offset in
+ * the set `queries` was loaded from (so the rows follow the query codes;
+ * the codes themselves are not read).  `pssm` is host memory of
+ * n_residues(queries) x alphabet_size int8 values, copied during the call.
+ * Everything else is as for dsa_align without pairs (modes, free ends, top
+ * K, flags; local mode runs the packed int16 kernels with the exact int32
+ * rerun, whose range check uses the profile's extreme values).  The result
+ * holds scores and end cells only: dsa_traceback on it returns
+ * DSA_ERR_UNSUPPORTED. */
+int dsa_align_pssm(dsa_ctx* ctx, const dsa_db* db, const dsa_db* queries, const int8_t* pssm,
+                   int alphabet_size, int mode, uint32_t free_ends, int gap_open, int gap_extend,
+                   uint32_t top_k, uint32_t flags, dsa_res** out);
+
 /* Begin coordinates and CIGAR for hits of `res` (the paper's location +
  * CIGAR, Sec. I and II.B.1).  `which` lists hit indices (host array), NULL =
  * every hit.  Hits with a local score of 0 get no CIGAR.  The DP of each hit

@@ -153,6 +153,23 @@ int check_matrix(const int8_t* matrix, int A, int o, int e, Validated* v) {
   return DSA_OK;
 }
 
+// Position-specific profile: the value range of its `n` entries.
+int check_pssm(const int8_t* pssm, uint64_t n, int o, int e, Validated* v) {
+  if (!pssm) { set_error("pssm is NULL"); return DSA_ERR_INVALID_ARG; }
+  if (o < 0 || e < 0 || e > o) {
+    set_error("gap penalties must satisfy 0 <= gap_extend <= gap_open (got %d, %d)", o, e);
+    return DSA_ERR_INVALID_ARG;
+  }
+  int smax = -128, smin = 127;
+  for (uint64_t k = 0; k < n; ++k) {
+    smax = std::max<int>(smax, pssm[k]);
+    smin = std::min<int>(smin, pssm[k]);
+  }
+  v->smax = smax;
+  v->smin = smin;
+  return DSA_OK;
+}
+
 }  // namespace
 
 void phase_begin(dsa_res* res, Phase p, cudaStream_t on) {
@@ -583,7 +600,7 @@ int ilog2_bin(uint64_t x) {
 // `long_thr` go to the wavefront kernel on the side stream, the rest to the
 // inter-sequence kernel.  The results do not depend on long_thr, only the time.
 int packed_score(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
-                 const int8_t* d_mat, int A, int o, int e, const Validated& v, Scores out,
+                 const int8_t* d_mat, const int8_t* d_pssm, int A, int o, int e, const Validated& v, Scores out,
                  uint32_t long_thr) {
   const uint32_t nq = qs->n, nt = db->n;
   const int R = A + 1;
@@ -734,7 +751,7 @@ int packed_score(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
   spl.d_ns = d_sns.as<uint32_t>();
   spl.d_prof = d_sprof.as<uint32_t>();
   iw.d_items = d_items.as<uint32_t>();
-  DSA_TRY(launch_strip_profile(ctx, qs, d_mat, A, o, spl));
+  DSA_TRY(launch_strip_profile(ctx, qs, d_mat, d_pssm, A, o, spl));
   if (n_long) {
     DSA_TRY(upload(ctx, d_pmeta, pmeta));
     DSA_TRY(upload(ctx, d_pbase, p_sbase));
@@ -748,7 +765,7 @@ int packed_score(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
     ppl.d_prof = d_pprof.as<uint32_t>();
     xw.d_long_ids = d_long.as<uint32_t>();
     xw.d_items = d_litems.as<uint32_t>();
-    DSA_TRY(launch_strip_profile(ctx, qs, d_mat, A, o, ppl));
+    DSA_TRY(launch_strip_profile(ctx, qs, d_mat, d_pssm, A, o, ppl));
     // long targets on the side stream, overlapping the inter-sequence kernel:
     // the two kernels write disjoint targets' results
     DSA_CUDA_TRY(cudaEventRecord(ctx->fork_ev, ctx->stream));
@@ -767,14 +784,14 @@ int packed_score(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
 
 // The packed pass with the autotuned long-target threshold.
 int run_packed_tuned(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
-                     const int8_t* d_mat, int A, int o, int e, const Validated& v, Scores out) {
+                     const int8_t* d_mat, const int8_t* d_pssm, int A, int o, int e, const Validated& v, Scores out) {
   if (const char* env = getenv("DSA_LONG_THRESHOLD"))
-    return packed_score(ctx, res, db, qs, d_mat, A, o, e, v, out,
+    return packed_score(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out,
                         (uint32_t)strtoul(env, nullptr, 10));
   const char* mode_env = getenv("DSA_AUTOTUNE");
   const std::string mode = mode_env ? mode_env : "cache";
   constexpr uint32_t DEFAULT_THR = 4096;
-  if (mode == "off") return packed_score(ctx, res, db, qs, d_mat, A, o, e, v, out, DEFAULT_THR);
+  if (mode == "off") return packed_score(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out, DEFAULT_THR);
   // workload shape key
   uint64_t qres = 0;
   for (uint32_t x : qs->h_len) qres += x;
@@ -793,10 +810,10 @@ int run_packed_tuned(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
     if (!t.loaded || path != t.path) tune_load(t, path);   // first use, or another file
     auto it = t.cache.find(key);
     if (mode != "retune" && it != t.cache.end())
-      return packed_score(ctx, res, db, qs, d_mat, A, o, e, v, out, it->second);
+      return packed_score(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out, it->second);
   }
   if (!ctx->tune)   // contexts that must not spend calls on tuning (serving workers)
-    return packed_score(ctx, res, db, qs, d_mat, A, o, e, v, out, DEFAULT_THR);
+    return packed_score(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out, DEFAULT_THR);
   // thresholds are compared by the number of target groups they move
   auto groups_over = [&](uint32_t thr) {
     uint32_t g = 0;
@@ -814,7 +831,7 @@ int run_packed_tuned(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
     if (it != timed.end()) return it->second;
     float ms = 0.f;
     if (rc == DSA_OK && cudaEventRecord(ev0, ctx->stream) != cudaSuccess) rc = DSA_ERR_CUDA;
-    if (rc == DSA_OK) rc = packed_score(ctx, nullptr, db, qs, d_mat, A, o, e, v, out, thr);
+    if (rc == DSA_OK) rc = packed_score(ctx, nullptr, db, qs, d_mat, d_pssm, A, o, e, v, out, thr);
     if (rc == DSA_OK && cudaEventRecord(ev1, ctx->stream) != cudaSuccess) rc = DSA_ERR_CUDA;
     if (rc == DSA_OK && cudaEventSynchronize(ev1) != cudaSuccess) rc = DSA_ERR_CUDA;
     if (rc == DSA_OK) cudaEventElapsedTime(&ms, ev0, ev1);
@@ -861,12 +878,12 @@ int run_packed_tuned(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
     tune_store(t);
   }
   // the final pass with the chosen threshold records the phase timings and cells
-  return packed_score(ctx, res, db, qs, d_mat, A, o, e, v, out, best);
+  return packed_score(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out, best);
 }
 
 // Score pass for all queries x all targets.
 int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs, int mode,
-                     uint32_t fe, const int8_t* d_mat, int A, int o, int e, const Validated& v,
+                     uint32_t fe, const int8_t* d_mat, const int8_t* d_pssm, int A, int o, int e, const Validated& v,
                      uint32_t flags, Scores out, uint64_t* n_rerun) {
   const uint32_t nq = qs->n, nt = db->n;
   const bool packed = mode == DSA_LOCAL && !(flags & (DSA_FORCE_INT32 | DSA_PLAIN_FORM)) &&
@@ -883,7 +900,7 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
     DevBuf d_prof, d_poff, d_scr;
     DSA_TRY(d_prof.alloc(ctx, words * sizeof(int32_t)));
     DSA_TRY(upload(ctx, d_poff, poff));
-    DSA_TRY(launch_profile_int32(ctx, qs, d_mat, A, d_prof.as<int32_t>(), d_poff.as<uint64_t>()));
+    DSA_TRY(launch_profile_int32(ctx, qs, d_mat, d_pssm, A, d_prof.as<int32_t>(), d_poff.as<uint64_t>()));
     DSA_TRY(d_scr.alloc(ctx, db->n_res * sizeof(int2)));
     if (res) {
       uint64_t qsum = 0;
@@ -900,7 +917,7 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
 
   // ---- packed path ----
   DSA_TRY(ensure_interleaved(ctx, db));
-  DSA_TRY(run_packed_tuned(ctx, res, db, qs, d_mat, A, o, e, v, out));
+  DSA_TRY(run_packed_tuned(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out));
 
   // ---- exact int32 rerun of saturated pairs ----
   const uint64_t n_out = (uint64_t)nq * nt;
@@ -924,7 +941,7 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
   std::vector<PairJob> jobs;
   if (count > cap) {
     // too many to list: rerun everything in int32
-    return score_all_vs_all(ctx, res, db, qs, mode, fe, d_mat, A, o, e, v, flags | DSA_FORCE_INT32,
+    return score_all_vs_all(ctx, res, db, qs, mode, fe, d_mat, d_pssm, A, o, e, v, flags | DSA_FORCE_INT32,
                             out, n_rerun);
   }
   std::vector<uint32_t> list(count);
@@ -948,7 +965,7 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
   DevBuf d_prof32, d_poff32, d_jobs, d_scr;
   DSA_TRY(d_prof32.alloc(ctx, pw * sizeof(int32_t)));
   DSA_TRY(upload(ctx, d_poff32, poff));
-  DSA_TRY(launch_profile_int32(ctx, qs, d_mat, A, d_prof32.as<int32_t>(), d_poff32.as<uint64_t>()));
+  DSA_TRY(launch_profile_int32(ctx, qs, d_mat, d_pssm, A, d_prof32.as<int32_t>(), d_poff32.as<uint64_t>()));
   DSA_TRY(upload(ctx, d_jobs, jobs));
   DSA_TRY(d_scr.alloc(ctx, scr * sizeof(int2)));
   phase_begin(res, PH_INT32);
@@ -959,9 +976,11 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
   return DSA_OK;
 }
 
+// pssm (host, optional): position-specific rows, one per query residue of
+// the set (qs->n_res x A), used instead of `matrix` by an all-vs-all search.
 int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair* pairs,
                uint64_t n_pairs, int mode, uint32_t fe, const int8_t* matrix, int A, int o, int e,
-               uint32_t top_k, uint32_t flags, dsa_res** out) {
+               uint32_t top_k, uint32_t flags, dsa_res** out, const int8_t* pssm = nullptr) {
   if (!ctx || !db || !qs || !out) { set_error("NULL argument"); return DSA_ERR_INVALID_ARG; }
   *out = nullptr;
   if (mode < DSA_LOCAL || mode > DSA_SEMIGLOBAL) { set_error("bad mode %d", mode); return DSA_ERR_INVALID_ARG; }
@@ -971,7 +990,15 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
     return DSA_ERR_INVALID_ARG;
   }
   Validated v;
-  DSA_TRY(check_matrix(matrix, A, o, e, &v));
+  if (pssm) {
+    if (pairs) {
+      set_error("position-specific profiles apply to all-vs-all searches only");
+      return DSA_ERR_UNSUPPORTED;
+    }
+    DSA_TRY(check_pssm(pssm, qs->n_res * (uint64_t)A, o, e, &v));
+  } else {
+    DSA_TRY(check_matrix(matrix, A, o, e, &v));
+  }
   DSA_TRY(set_device(ctx));
   const bool all = pairs == nullptr;
   if (!all && top_k) {
@@ -1046,7 +1073,8 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
   if (!res) { set_error("host allocation failed"); return DSA_ERR_OOM; }
   res->ctx = ctx; res->db = db; res->queries = qs; res->mode = mode; res->free_ends = fe;
   res->A = A; res->gap_open = o; res->gap_extend = e;
-  res->matrix.assign(matrix, matrix + A * A);
+  if (matrix) res->matrix.assign(matrix, matrix + A * A);
+  res->pssm = pssm != nullptr;
   res->flags = flags;
   auto fail = [&](int rc) {
     if (res->d_hits) ctx->release(res->d_hits, std::max<uint64_t>(1, res->n_hits) * sizeof(dsa_hit));
@@ -1055,11 +1083,16 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
     return rc;
   };
 
-  DevBuf d_mat;
-  if (int rc = d_mat.alloc(ctx, A * A)) return fail(rc);
-  if (cudaMemcpyAsync(d_mat.p, matrix, A * A, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
-    set_error("matrix upload failed");
-    return fail(DSA_ERR_CUDA);
+  DevBuf d_mat, d_pssm;
+  if (matrix) {
+    if (int rc = d_mat.alloc(ctx, A * A)) return fail(rc);
+    if (cudaMemcpyAsync(d_mat.p, matrix, A * A, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+      set_error("matrix upload failed");
+      return fail(DSA_ERR_CUDA);
+    }
+  }
+  if (pssm) {
+    if (int rc = upload(ctx, d_pssm, pssm, qs->n_res * (uint64_t)A)) return fail(rc);
   }
 
   const uint64_t n_out = all ? (uint64_t)qs->n * db->n : n_pairs;
@@ -1074,7 +1107,8 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
     uint64_t sq = 0;
     for (uint32_t x : qs->h_len) sq += x;
     res->cells = sq * db->n_res;
-    if ((rc = score_all_vs_all(ctx, res, db, qs, mode, fe, d_mat.as<int8_t>(), A, o, e, v, flags,
+    if ((rc = score_all_vs_all(ctx, res, db, qs, mode, fe, d_mat.as<int8_t>(), d_pssm.as<int8_t>(),
+                               A, o, e, v, flags,
                                sc, &res->n_rerun)))
       return fail(rc);
   } else {
@@ -1326,7 +1360,7 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
       if ((rc = d_prof.alloc(ctx, pw * 4)) || (rc = upload(ctx, d_poff, poff)) ||
           (rc = upload(ctx, d_jobs, jobs)) || (rc = d_scr.alloc(ctx, scr * sizeof(int2))))
         return fail(rc);
-      if ((rc = launch_profile_int32(ctx, qs, d_mat.as<int8_t>(), A, d_prof.as<int32_t>(),
+      if ((rc = launch_profile_int32(ctx, qs, d_mat.as<int8_t>(), nullptr, A, d_prof.as<int32_t>(),
                                      d_poff.as<uint64_t>())))
         return fail(rc);
       phase_begin(res, PH_INT32);
@@ -1384,6 +1418,19 @@ extern "C" int dsa_align_batch(dsa_ctx* ctx, const dsa_db* db, const uint8_t* q_
   if (rc) { dsa_db_free(qs); return rc; }
   (*out)->owned_queries = qs;
   return DSA_OK;
+}
+
+extern "C" int dsa_align_pssm(dsa_ctx* ctx, const dsa_db* db, const dsa_db* queries,
+                              const int8_t* pssm, int alphabet_size, int mode, uint32_t free_ends,
+                              int gap_open, int gap_extend, uint32_t top_k, uint32_t flags,
+                              dsa_res** out) {
+  if (!pssm) { set_error("pssm is NULL"); return DSA_ERR_INVALID_ARG; }
+  if (flags & DSA_PAIRS_ON_DEVICE) {
+    set_error("position-specific profiles apply to all-vs-all searches only");
+    return DSA_ERR_UNSUPPORTED;
+  }
+  return align_impl(ctx, db, queries, nullptr, 0, mode, free_ends, nullptr, alphabet_size,
+                    gap_open, gap_extend, top_k, flags, out, pssm);
 }
 
 // ---------------------------------------------------------------- traceback --
@@ -1482,6 +1529,10 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
   if (!ctx || !res || res->ctx != ctx) {
     set_error("bad ctx / res (results handed out by a server are host-only)");
     return DSA_ERR_INVALID_ARG;
+  }
+  if (res->pssm) {
+    set_error("results scored with position-specific profiles carry scores and ends only");
+    return DSA_ERR_UNSUPPORTED;
   }
   DSA_TRY(set_device(ctx));
   // Many small rectangles: one thread per hit (groups of 32 hits of similar

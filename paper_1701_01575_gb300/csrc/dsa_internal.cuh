@@ -138,6 +138,7 @@ struct dsa_res {
   uint32_t free_ends = 15;
   int A = 0, gap_open = 0, gap_extend = 0;
   std::vector<int8_t> matrix;
+  bool pssm = false;   // scored with position-specific profiles: no traceback
   uint32_t flags = 0;
   uint64_t n_hits = 0;
   dsa_hit* d_hits = nullptr;
@@ -197,9 +198,10 @@ int launch_generic_int32(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const
                          uint32_t fixed_q, int2* d_scratch, int mode, uint32_t fe, int o, int e,
                          uint8_t flag_value, Scores out);
 
-// Per-query int32 profile P[a][i] = S[q_i][a] (rows a = 0..A-1, row stride = m).
-int launch_profile_int32(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix, int A,
-                         int32_t* d_prof, const uint64_t* d_prof_off);
+// Per-query int32 profile P[a][i] = S[q_i][a] (rows a = 0..A-1, row stride = m),
+// or the position-specific row d_pssm[q_off + i][a] when d_pssm is given.
+int launch_profile_int32(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix,
+                         const int8_t* d_pssm, int A, int32_t* d_prof, const uint64_t* d_prof_off);
 
 // Interleaved DB build (dsa_db_load).
 int launch_interleave(dsa_ctx* ctx, dsa_db* db);
@@ -244,8 +246,9 @@ struct IntraWork {
   uint32_t max_long_len = 0;
 };
 
-int launch_strip_profile(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix, int A, int o,
-                         const PackedPlan& plan);
+// d_pssm: position-specific rows (one per query residue of the set) or NULL.
+int launch_strip_profile(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix,
+                         const int8_t* d_pssm, int A, int o, const PackedPlan& plan);
 int launch_inter_local16(dsa_ctx* ctx, const dsa_db* db, const PackedPlan& plan,
                          const InterWork& work, int o, int e, int smax, Scores out,
                          uint32_t n_targets_out);

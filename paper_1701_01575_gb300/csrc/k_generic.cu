@@ -139,11 +139,13 @@ __global__ void __launch_bounds__(128) k_generic_int32(
   }
 }
 
-// P[q][a][i] = S[q_i][a] for a < A, rows padded to a multiple of 8 with 0.
+// P[q][a][i] = S[q_i][a] for a < A, rows padded to a multiple of 8 with 0;
+// with a position-specific profile Pq (one row per query residue of the set)
+// P[q][a][i] = Pq[qoff[q] + i][a].
 __global__ void k_profile_int32(const uint8_t* __restrict__ qcodes, const uint64_t* __restrict__ qoff,
                                 const uint32_t* __restrict__ qlen, uint32_t nq,
-                                const int8_t* __restrict__ S, int A, int32_t* __restrict__ prof,
-                                const uint64_t* __restrict__ prof_off) {
+                                const int8_t* __restrict__ S, const int8_t* __restrict__ Pq, int A,
+                                int32_t* __restrict__ prof, const uint64_t* __restrict__ prof_off) {
   for (uint32_t q = blockIdx.y; q < nq; q += gridDim.y) {
     const int32_t m = (int32_t)qlen[q];
     const int32_t mpad = (m + 7) & ~7;
@@ -153,7 +155,9 @@ __global__ void k_profile_int32(const uint8_t* __restrict__ qcodes, const uint64
          x += (int64_t)gridDim.x * blockDim.x) {
       const int a = (int)(x / mpad);
       const int i = (int)(x % mpad);
-      P[x] = i < m ? (int32_t)S[qs[i] * A + a] : 0;
+      P[x] = i >= m ? 0
+             : Pq   ? (int32_t)Pq[(qoff[q] + (uint64_t)i) * A + a]
+                    : (int32_t)S[qs[i] * A + a];
     }
   }
 }
@@ -210,12 +214,12 @@ int launch_generic_int32(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const
   return DSA_OK;
 }
 
-int launch_profile_int32(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix, int A,
-                         int32_t* d_prof, const uint64_t* d_prof_off) {
+int launch_profile_int32(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix,
+                         const int8_t* d_pssm, int A, int32_t* d_prof, const uint64_t* d_prof_off) {
   if (qs->n == 0) return DSA_OK;
   dim3 grid(qs->n > 4096 ? 1 : 64, std::min<uint32_t>(qs->n, 65535));
   k_profile_int32<<<grid, 256, 0, ctx->stream>>>(qs->d_codes, qs->d_off, qs->d_len, qs->n,
-                                                 d_matrix, A, d_prof, d_prof_off);
+                                                 d_matrix, d_pssm, A, d_prof, d_prof_off);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   return DSA_OK;

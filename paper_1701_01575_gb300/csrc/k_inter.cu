@@ -338,12 +338,17 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
 // Packed profile of every strip: [strip][residue a][row r] int16x2 =
 // (S[qa_i][a] + o, S[qb_i][a] + o) with i = rows * (strip index in the query) + r;
 // rows past a query's end, absent queries and the padding residue a = A get
-// NEG16.
+// NEG16.  With a position-specific profile P (row per query residue of the
+// set, Sec. II.C.2's user-defined scoring) the score is P[qoff + i][a].
 __global__ void k_strip_profile(const uint8_t* __restrict__ qcodes,
                                 const uint64_t* __restrict__ qoff, const uint32_t* __restrict__ qlen,
                                 const StripMeta* __restrict__ meta, uint32_t n_strips,
-                                const int8_t* __restrict__ S, int A, int R, int rows, int pitch,
-                                int o, uint32_t* __restrict__ prof) {
+                                const int8_t* __restrict__ S, const int8_t* __restrict__ P, int A,
+                                int R, int rows, int pitch, int o, uint32_t* __restrict__ prof) {
+  auto sub = [&](uint32_t q, int i, int a) -> int {
+    const uint64_t k = qoff[q] + (uint64_t)i;
+    return P ? (int)P[k * A + a] : (int)S[qcodes[k] * A + a];
+  };
   const uint64_t total = (uint64_t)n_strips * R * pitch;
   for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < total;
        x += (uint64_t)gridDim.x * blockDim.x) {
@@ -356,11 +361,11 @@ __global__ void k_strip_profile(const uint8_t* __restrict__ qcodes,
       // row padding, never read
     } else if (a < A && md.qa != NONE) {
       const int i = (int)(md.ka & ~LAST) * rows + r;
-      if (i < (int)qlen[md.qa]) lo = (int)S[qcodes[qoff[md.qa] + i] * A + a] + o;
+      if (i < (int)qlen[md.qa]) lo = sub(md.qa, i, a) + o;
     }
     if (r < rows && a < A && md.qb != NONE) {
       const int i = (int)(md.kb & ~LAST) * rows + r;
-      if (i < (int)qlen[md.qb]) hi = (int)S[qcodes[qoff[md.qb] + i] * A + a] + o;
+      if (i < (int)qlen[md.qb]) hi = sub(md.qb, i, a) + o;
     }
     prof[x] = pack2(lo, hi);
   }
@@ -370,15 +375,15 @@ __global__ void k_strip_profile(const uint8_t* __restrict__ qcodes,
 
 int inter_blocks_per_sm() { return 2; }
 
-int launch_strip_profile(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix, int A, int o,
-                         const PackedPlan& plan) {
+int launch_strip_profile(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix,
+                         const int8_t* d_pssm, int A, int o, const PackedPlan& plan) {
   if (plan.n_strips == 0) return DSA_OK;
   const uint64_t total = (uint64_t)plan.n_strips * plan.R * plan.pitch;
   uint64_t blocks = std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->sm_count * 8);
   k_strip_profile<<<(unsigned)blocks, 256, 0, ctx->stream>>>(qs->d_codes, qs->d_off, qs->d_len,
                                                             plan.d_meta, plan.n_strips, d_matrix,
-                                                            A, plan.R, plan.rows, plan.pitch, o,
-                                                            plan.d_prof);
+                                                            d_pssm, A, plan.R, plan.rows,
+                                                            plan.pitch, o, plan.d_prof);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   return DSA_OK;

@@ -42,7 +42,7 @@ SYMBOLS = ["dsa_create", "dsa_destroy", "dsa_last_error", "dsa_mem_in_use", "dsa
            "dsa_server_drain", "dsa_server_now", "dsa_server_destroy",
            "dsa_selftest_wait_timeout", "dsa_reader_open", "dsa_reader_open_mem",
            "dsa_reader_next", "dsa_reader_close", "dsa_seqs_get", "dsa_seqs_free",
-           "dsa_merge_topk", "dsa_search_partitioned"]
+           "dsa_merge_topk", "dsa_search_partitioned", "dsa_align_pssm"]
 ALPHABET_DNA4, ALPHABET_DNA5, ALPHABET_PROTEIN = 1, 2, 3
 READ_MAP_UNKNOWN, READ_SKIP_EMPTY = 1, 2
 ALPHABET_SIZE = {ALPHABET_DNA4: 4, ALPHABET_DNA5: 5, ALPHABET_PROTEIN: 24}
@@ -133,6 +133,8 @@ def load_library(path: str = LIB_PATH):
     lib.dsa_seqs_get.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_u32),
                                  ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]
     lib.dsa_seqs_free.argtypes = [_vp]
+    lib.dsa_align_pssm.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _u32, ctypes.c_int,
+                                   ctypes.c_int, _u32, _u32, ctypes.POINTER(_vp)]
     lib.dsa_merge_topk.argtypes = [_vp, _vp, _vp, _vp, _u32, _u32, _u32, _vp, ctypes.POINTER(_u64), _vp,
                                    ctypes.POINTER(_u64)]
     lib.dsa_search_partitioned.argtypes = [_vp, _vp, _vp, _u32, ctypes.c_int, _u64, _vp, ctypes.c_int,
@@ -313,6 +315,20 @@ class Context:
         if arr.dtype != PAIR_DTYPE:
             arr = arr.astype(PAIR_DTYPE)
         return _ptr(arr), len(arr), 0, arr
+
+    def align_pssm(self, db: Database, queries: Database, pssm: np.ndarray, gap_open: int,
+                   gap_extend: int, mode: int = LOCAL, free_ends: int = 15, top_k: int = 0,
+                   flags: int = 0) -> Result:
+        """``dsa_align_pssm``: ``pssm`` is an (n_residues(queries), A) int8 array,
+        one row per query residue in the order the queries were loaded."""
+        P = np.ascontiguousarray(pssm, dtype=np.int8)
+        if P.ndim != 2 or P.shape != (queries.n_res, queries.alphabet_size):
+            raise ValueError(f"pssm must have shape (query residues, alphabet) = "
+                             f"{(queries.n_res, queries.alphabet_size)}, not {P.shape}")
+        h = _vp()
+        _check(_lib.dsa_align_pssm(self.handle, db.handle, queries.handle, _ptr(P), P.shape[1], mode,
+                                   free_ends, gap_open, gap_extend, top_k, flags, ctypes.byref(h)))
+        return Result(self, h.value, bool(flags & RESULTS_ON_DEVICE), keep=(db, queries))
 
     def search_partitioned(self, codes: np.ndarray, offsets: np.ndarray, alphabet_size: int,
                            queries: Database, matrix: np.ndarray, gap_open: int, gap_extend: int,

@@ -600,6 +600,100 @@ def test_partitioned_search_equals_whole_database(ctx, part_res):
         ctx.traceback(part)   # host-only result
 
 
+def _pssm_case(rng, n_q=5, n_t=150, lo=-8, hi=10):
+    bg = W.protein_background()
+    qs = W.SeqSet.from_list([rng.choice(20, int(n), p=bg).astype(np.uint8)
+                             for n in rng.integers(20, 260, n_q)])
+    db = W.SeqSet.from_list([rng.choice(20, int(n), p=bg).astype(np.uint8)
+                             for n in rng.integers(10, 700, n_t)])
+    P = rng.integers(lo, hi + 1, size=(int(qs.offsets[-1]), 24)).astype(np.int8)
+    return qs, db, P
+
+
+@pytest.mark.parametrize("thr", ["4096", "300"])
+def test_pssm_search_local_matches_oracle(ctx, thr, monkeypatch):
+    """Position-specific scores (Sec. II.C.2 user-defined scoring) on the packed
+    local kernels: with a long-target threshold of 300 part of the database
+    takes the wavefront kernel; every score and end of the dense matrix equals
+    the oracle's."""
+    monkeypatch.setenv("DSA_LONG_THRESHOLD", thr)
+    rng = np.random.default_rng(600 + int(thr))
+    qs, db, P = _pssm_case(rng)
+    d = ctx.load_set(db, 24)
+    q = ctx.load_set(qs, 24)
+    r = ctx.align_pssm(d, q, P, 11, 1)
+    ctx.sync()
+    h = r.hits()
+    sc, qe, te = oracle.score_all_vs_all(qs, db, W.blosum62(), 11, 1, pssm=P)
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc.ravel(), qe.ravel(), te.ravel()), "pssm local")
+    if thr == "300":
+        assert r.phase_cells()["intra16"] > 0
+    with pytest.raises(dsa.DsaError) as ex:
+        ctx.traceback(r)
+    assert ex.value.code == dsa.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("mode,fe", [(dsa.GLOBAL, 15), (dsa.SEMIGLOBAL, 12), (dsa.SEMIGLOBAL, 3)])
+def test_pssm_search_global_modes_match_oracle(ctx, mode, fe):
+    rng = np.random.default_rng(610 + mode + fe)
+    qs, db, P = _pssm_case(rng, n_q=3, n_t=60)
+    d = ctx.load_set(db, 24)
+    q = ctx.load_set(qs, 24)
+    r = ctx.align_pssm(d, q, P, 11, 1, mode=mode, free_ends=fe)
+    ctx.sync()
+    h = r.hits()
+    sc, qe, te = oracle.score_all_vs_all(qs, db, W.blosum62(), 11, 1, mode=mode, free_ends=fe, pssm=P)
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc.ravel(), qe.ravel(), te.ravel()), "pssm global")
+
+
+def test_pssm_saturation_rerun_and_top_k(ctx):
+    """A profile that rewards one target's residues with +100 drives the
+    packed pass past int16: those pairs are rerun in int32 from the same
+    profile.  Top-K follows (score desc, target id asc)."""
+    rng = np.random.default_rng(620)
+    bg = W.protein_background()
+    qs = W.SeqSet.from_list([rng.choice(20, int(n), p=bg).astype(np.uint8) for n in (400, 90, 150, 33)])
+    db = W.SeqSet.from_list([rng.choice(20, int(n), p=bg).astype(np.uint8)
+                             for n in [500 if k == 7 else int(rng.integers(10, 600)) for k in range(80)]])
+    P = rng.integers(-3, 4, size=(int(qs.offsets[-1]), 24)).astype(np.int8)
+    target = db.seq(7)
+    P[np.arange(400), target[:400]] = 100   # query 0 position i likes target 7's residue i
+    d = ctx.load_set(db, 24)
+    q = ctx.load_set(qs, 24)
+    r = ctx.align_pssm(d, q, P, 11, 1)
+    ctx.sync()
+    h = r.hits()
+    sc, qe, te = oracle.score_all_vs_all(qs, db, W.blosum62(), 11, 1, pssm=P)
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc.ravel(), qe.ravel(), te.ravel()), "pssm rerun")
+    assert sc[0, 7] > 32767 and r.stats()[1] >= 1
+    k = 6
+    rk = ctx.align_pssm(d, q, P, 11, 1, top_k=k)
+    hk = rk.hits()
+    for qi in range(qs.n):
+        order = np.lexsort((np.arange(db.n), -sc[qi]))[:k]
+        got = hk[qi * k:(qi + 1) * k]
+        assert got["target_id"].tolist() == order.tolist()
+        assert got["score"].tolist() == sc[qi, order].tolist()
+
+
+def test_pssm_of_the_matrix_equals_matrix_search(ctx):
+    """The profile whose row i is S[q_i] gives the matrix search's results
+    bit for bit (scores, ends, rerun flags), locally and globally."""
+    rng = np.random.default_rng(630)
+    qs, db, _ = _pssm_case(rng, n_q=6, n_t=120)
+    S = W.blosum62()
+    P = S[qs.codes]
+    d = ctx.load_set(db, 24)
+    q = ctx.load_set(qs, 24)
+    for mode in (dsa.LOCAL, dsa.GLOBAL):
+        a = ctx.align(d, q, S, 11, 1, mode=mode).hits()
+        b = ctx.align_pssm(d, q, P, 11, 1, mode=mode).hits()
+        for f in ("score", "q_end", "t_end", "flags", "target_id", "query_id"):
+            assert np.array_equal(a[f], b[f]), (mode, f)
+    with pytest.raises(ValueError):
+        ctx.align_pssm(d, q, P[:-1], 11, 1)
+
+
 def test_pair_range_errors(ctx):
     """Out-of-range pairs are refused with the smallest bad index, whether the
     pairs are in host or device memory; nothing is aligned."""
