@@ -153,6 +153,37 @@ int check_matrix(const int8_t* matrix, int A, int o, int e, Validated* v) {
   return DSA_OK;
 }
 
+// Band items (pair, band) of a band-pipelined score pass, in latest-start
+// order.  Band b of a pair trails its predecessor, so it can start about
+// b * LAG steps after the pair's first band, and the pair needs about
+// n + bands * LAG steps in all; sorting the items by b * LAG - (n + bands *
+// LAG) starts the longest chains first without parking warps on bands that
+// are far behind their predecessors.  Inside a pair the key grows with b, so
+// a band's predecessor is always taken earlier (the bounded waits rely on
+// that: a warp waits only on a band some running warp holds).
+std::vector<uint32_t> band_items(const std::vector<std::pair<uint32_t, uint32_t>>& mn, int band) {
+  constexpr int64_t LAG = 128;
+  struct It { int64_t key; uint32_t p, b; };
+  std::vector<It> its;
+  for (uint32_t p = 0; p < mn.size(); ++p) {
+    const uint32_t nb = (mn[p].first + band - 1) / band;
+    const int64_t cp = (int64_t)mn[p].second + (int64_t)nb * LAG;
+    for (uint32_t b = 0; b < nb; ++b) its.push_back({(int64_t)b * LAG - cp, p, b});
+  }
+  std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) { return x.key < y.key; });
+  std::vector<uint32_t> items;
+  items.reserve(2 * its.size());
+  for (const It& it : its) { items.push_back(it.p); items.push_back(it.b); }
+  return items;
+}
+
+// Every S + o of the matrix fits int8 (the byte-permute substitution tables).
+bool s_plus_o_fits_int8(const int8_t* matrix, int A, int o) {
+  for (int x = 0; x < A * A; ++x)
+    if (matrix[x] + o < -128 || matrix[x] + o > 127) return false;
+  return true;
+}
+
 // Position-specific profile: the value range of its `n` entries.
 int check_pssm(const int8_t* pssm, uint64_t n, int o, int e, Validated* v) {
   if (!pssm) { set_error("pssm is NULL"); return DSA_ERR_INVALID_ARG; }
@@ -1185,17 +1216,10 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
     res->cells = cells;
     res->phase_cells[PH_INT32] = cells;
     if (!ljobs.empty()) {
-      // band items, largest pairs first, bands in order inside a pair
-      std::vector<uint32_t> jorder(ljobs.size());
-      std::iota(jorder.begin(), jorder.end(), 0u);
-      std::stable_sort(jorder.begin(), jorder.end(), [&](uint32_t a, uint32_t b) {
-        return (uint64_t)ljobs[a].m * ljobs[a].n > (uint64_t)ljobs[b].m * ljobs[b].n;
-      });
-      std::vector<uint32_t> items;
-      for (uint32_t jx : jorder) {
-        const uint32_t nb = (ljobs[jx].m + band - 1) / band;
-        for (uint32_t b = 0; b < nb; ++b) { items.push_back(jx); items.push_back(b); }
-      }
+      // band items in latest-start order (bands in order inside a pair)
+      std::vector<std::pair<uint32_t, uint32_t>> mn(ljobs.size());
+      for (size_t k = 0; k < ljobs.size(); ++k) mn[k] = {(uint32_t)ljobs[k].m, (uint32_t)ljobs[k].n};
+      const std::vector<uint32_t> items = band_items(mn, band);
       DevBuf d_ljobs, d_items, d_prog, d_cands;
       void* pb = nullptr;
       if ((rc = upload(ctx, d_ljobs, ljobs)) || (rc = upload(ctx, d_items, items)) ||
@@ -1217,7 +1241,7 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
       }
       phase_begin(res, PH_INTRA);
       if ((rc = launch_long_score(ctx, db, qs, d_mat.as<int8_t>(), A, o, e, mode, fe,
-                                  d_ljobs.as<LongJob>(), (uint32_t)ljobs.size(), d_items.as<uint32_t>(),
+                                  s_plus_o_fits_int8(matrix, A, o), d_ljobs.as<LongJob>(), (uint32_t)ljobs.size(), d_items.as<uint32_t>(),
                                   (uint32_t)(items.size() / 2), res->d_bnd, d_prog.as<uint32_t>(),
                                   d_cands.p, sc)))
         return fail(rc);
@@ -1909,17 +1933,10 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
   };
   if (!ljobs.empty()) DSA_TRY(run_long(ljobs, res->d_bnd));
   if (!bscore.empty()) {
-    // checkpointed score pass over the big rectangles: largest first, bands in order
-    std::vector<uint32_t> order(bscore.size());
-    std::iota(order.begin(), order.end(), 0u);
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
-      return (uint64_t)bscore[a].m * bscore[a].n > (uint64_t)bscore[b].m * bscore[b].n;
-    });
-    std::vector<uint32_t> items;
-    for (uint32_t x : order) {
-      const uint32_t nb = (uint32_t)((bscore[x].m + band - 1) / band);
-      for (uint32_t b = 0; b < nb; ++b) { items.push_back(x); items.push_back(b); }
-    }
+    // checkpointed score pass over the big rectangles, bands in latest-start order
+    std::vector<std::pair<uint32_t, uint32_t>> mn(bscore.size());
+    for (size_t k = 0; k < bscore.size(); ++k) mn[k] = {(uint32_t)bscore[k].m, (uint32_t)bscore[k].n};
+    const std::vector<uint32_t> items = band_items(mn, band);
     const size_t nj = bscore.size();
     DevBuf d_bs, d_bitems, d_bbnd, d_bprog, d_bcand, d_bout;
     DSA_TRY(upload(ctx, d_bs, bscore));
@@ -1935,7 +1952,9 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
     bsc.t_end = bsc.q_end + nj;
     bsc.flag = reinterpret_cast<uint8_t*>(bsc.t_end + nj);
     DSA_TRY(launch_long_score(ctx, db, qs, d_mat.as<int8_t>(), res->A, res->gap_open,
-                              res->gap_extend, res->mode, res->free_ends, d_bs.as<LongJob>(),
+                              res->gap_extend, res->mode, res->free_ends,
+                              s_plus_o_fits_int8(res->matrix.data(), res->A, res->gap_open),
+                              d_bs.as<LongJob>(),
                               (uint32_t)nj, d_bitems.as<uint32_t>(), (uint32_t)(items.size() / 2),
                               d_bbnd.as<int2>(), d_bprog.as<uint32_t>(), d_bcand.p, bsc));
     DSA_TRY(run_long(bjobs, d_bbnd.as<int2>()));

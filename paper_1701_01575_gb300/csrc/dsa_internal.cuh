@@ -427,10 +427,11 @@ struct LongTbJob {
   int32_t wc;
   uint32_t pad;
 };
+// bytes_ok: every S + o fits int8 (with A <= 4 the byte-permute form is used)
 int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,
-                      int A, int o, int e, int mode, uint32_t fe, const LongJob* d_jobs,
-                      uint32_t n_jobs, const uint32_t* d_items, uint32_t n_items, int2* d_bnd,
-                      uint32_t* d_prog, void* d_cands, Scores out);
+                      int A, int o, int e, int mode, uint32_t fe, bool bytes_ok,
+                      const LongJob* d_jobs, uint32_t n_jobs, const uint32_t* d_items,
+                      uint32_t n_items, int2* d_bnd, uint32_t* d_prog, void* d_cands, Scores out);
 // items: 2 words (job, band) per band of every job
 int launch_long_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
                           const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,

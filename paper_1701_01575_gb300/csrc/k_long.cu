@@ -71,13 +71,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
     const LongJob* __restrict__ jobs, const uint32_t* __restrict__ items, uint32_t n_items,
     uint32_t* __restrict__ counter, int2* __restrict__ bnd, uint32_t* __restrict__ prog,
     Cand* __restrict__ cands, int32_t* __restrict__ status) {
-  __shared__ int8_t S[32 * 32];
-  __shared__ uint32_t Sb[4];   // BYTES: row q of S as 4 bytes
-  for (int x = threadIdx.x; x < A * A; x += blockDim.x) S[x] = Sg[x];
+  // substitution scores with o added: the diagonal term H[i-1][j-1] + S is
+  // taken as (H[i-1][j-1] - o) + (S + o), from the stored H - o
+  __shared__ int16_t So[32 * 32];
+  __shared__ uint32_t Sb[4];   // BYTES: row q of S + o as 4 bytes (each fits int8)
+  for (int x = threadIdx.x; x < A * A; x += blockDim.x) So[x] = (int16_t)(Sg[x] + o);
   if (BYTES && threadIdx.x < 4) {
     uint32_t w = 0;
     for (int a = 0; a < A; ++a)
-      if ((int)threadIdx.x < A) w |= (uint32_t)(uint8_t)Sg[threadIdx.x * A + a] << (8 * a);
+      if ((int)threadIdx.x < A) w |= (uint32_t)(uint8_t)(int8_t)(Sg[threadIdx.x * A + a] + o) << (8 * a);
     Sb[threadIdx.x] = w;
   }
   __syncthreads();
@@ -109,21 +111,23 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
     const int bot_lane = (bottom - 1 - i0) / ROWS;
     const bool owns_m = r0 < m && m <= r0 + ROWS;
 
-    int32_t H[ROWS], E[ROWS];
-    uint32_t qv[ROWS];   // BYTES: S row of the query residue as bytes; else its matrix offset
+    // Ho = H - o of the lane's rows in the previous column (the operand both
+    // gap recurrences extend), E of those rows
+    int32_t Ho[ROWS], E[ROWS];
+    uint32_t qv[ROWS];   // BYTES: S + o row of the query residue as bytes; else its matrix offset
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
       const int32_t i = r0 + r + 1;
-      H[r] = h_col0(mode, fe, i, o, e);
+      Ho[r] = h_col0(mode, fe, i, o, e) - o;
       E[r] = NEG32;
       qv[r] = i <= m ? (BYTES ? Sb[q[i - 1]] : (uint32_t)q[i - 1] * A) : 0u;
     }
     Cand c = {0, 0, 0, 0};
     if (t_end_free && owns_m) {   // H[m][0] on row m
-      c = {H[m - r0 - 1], m, 0, 1};
+      c = {Ho[m - r0 - 1] + o, m, 0, 1};
     }
-    int32_t diag = h_col0(mode, fe, r0, o, e);
-    int32_t sendH = 0, sendF = NEG32;
+    int32_t diag = h_col0(mode, fe, r0, o, e) - o;   // H - o above-left of the lane's first row
+    int32_t sendH = 0, sendF = NEG32;                  // H - o and F of the lane's last row
     int sendA = 0;
     bool timed_out = false;
     // boundary row of the band above for columns blk+1 .. blk+32 (lane k: blk+k+1)
@@ -133,12 +137,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
       bool late = false;
       if (!timed_out) {
         const uint64_t t0 = global_ns();
+        uint32_t nap = 32;   // back off: a waiting warp leaves the issue slots to working ones
         for (;;) {
           if (ld_acquire_u32(up_prog) >= need) break;
           if (global_ns() - t0 > WAIT_LIMIT_NS) {
             late = true;
             break;
           }
+          __nanosleep(nap);
+          nap = min(nap * 2, 1024u);
         }
       }
       if (__any_sync(FULL, late)) {
@@ -160,16 +167,16 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
       const int32_t bx = __shfl_sync(FULL, bcur.x, k);
       const int32_t by = __shfl_sync(FULL, bcur.y, k);
       const int ta = __shfl_sync(FULL, tcur, k);
-      int32_t Hup = __shfl_up_sync(FULL, sendH, 1);
+      int32_t Hup = __shfl_up_sync(FULL, sendH, 1);   // H - o of the cell above the lane
       int32_t Fup = __shfl_up_sync(FULL, sendF, 1);
       int a = __shfl_up_sync(FULL, sendA, 1);
       if (lane == 0) {
         a = ta;
         if (b == 0) {
-          Hup = h_row0(mode, fe, s, o, e);
+          Hup = h_row0(mode, fe, s, o, e) - o;
           Fup = NEG32;
         } else {
-          Hup = bx;
+          Hup = bx - o;
           Fup = by;
         }
       }
@@ -183,9 +190,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
       sendA = a;
       const int32_t j = s - lane;
       if (j >= 1 && j <= n && r0 < m) {
-        int32_t d = diag;
+        int32_t d = diag;   // H - o above-left
         diag = Hup;
-        int32_t F = Fup, Hp = Hup;
+        int32_t F = Fup, hoa = Hup;   // F and H - o of the cell above
         // BYTES: byte a of the row table, sign-replicated into bytes 1-3
         const uint32_t sel = (uint32_t)a + ((uint32_t)a | 8u) * 0x1110u;
         int32_t cm = 0;
@@ -193,17 +200,20 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
         for (int r = 0; r < ROWS; ++r) {
           const int32_t i = r0 + r + 1;
           if (i <= m) {
-            F = max(F - e, Hp - o);
-            E[r] = max(E[r] - e, H[r] - o);
-            const int32_t sv = BYTES ? (int32_t)prmt(qv[r], 0u, sel) : (int32_t)S[qv[r] + a];
-            int32_t h = max(d + sv, max(E[r], F));
+            F = __viaddmax_s32(F, -e, hoa);                  // F = max(F - e, H_above - o)
+            E[r] = __viaddmax_s32(E[r], -e, Ho[r]);          // E = max(E - e, H_left - o)
+            const int32_t sv = BYTES ? (int32_t)prmt(qv[r], 0u, sel) : (int32_t)So[qv[r] + a];
+            const int32_t t = __viaddmax_s32(d, sv, E[r]);   // max(H_diag + S, E)
+            int32_t h;
             if (LOCAL) {
-              h = max(h, 0);
+              h = __vimax_s32_relu(t, F);
               cm = max(cm, h);
+            } else {
+              h = max(t, F);
             }
-            d = H[r];
-            H[r] = h;
-            Hp = h;
+            d = Ho[r];
+            Ho[r] = h - o;
+            hoa = Ho[r];
           }
         }
         if (LOCAL) {
@@ -212,7 +222,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
             int rr = 0;
 #pragma unroll
             for (int r = ROWS - 1; r >= 0; --r)
-              if (H[r] == cm) rr = r;
+              if (Ho[r] == cm - o) rr = r;
             c = {cm, r0 + rr + 1, j, 1};
           }
         } else if (j == n) {
@@ -220,19 +230,19 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
 #pragma unroll
           for (int r = 0; r < ROWS; ++r) {
             const int32_t i = r0 + r + 1;
-            if (i <= m && (q_end_free || i == m) && (!c.has || H[r] > c.s)) c = {H[r], i, j, 1};
+            if (i <= m && (q_end_free || i == m) && (!c.has || Ho[r] + o > c.s)) c = {Ho[r] + o, i, j, 1};
           }
         } else if (t_end_free && owns_m) {
-          int32_t hm = H[0];
+          int32_t hm = Ho[0] + o;
 #pragma unroll
           for (int r = 1; r < ROWS; ++r)
-            if (r == m - r0 - 1) hm = H[r];
+            if (r == m - r0 - 1) hm = Ho[r] + o;
           if (!c.has || hm > c.s) c = {hm, m, j, 1};
         }
-        sendH = Hp;
+        sendH = hoa;
         sendF = F;
         if (!last_band && lane == bot_lane) {
-          my_bnd[j - 1] = make_int2(Hp, F);
+          my_bnd[j - 1] = make_int2(hoa + o, F);
           if ((uint32_t)j % PUBLISH == 0 || j == n) {
             __threadfence();
             st_release_u32(my_prog, (uint32_t)j);
@@ -551,14 +561,15 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
 }  // namespace
 
 int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,
-                      int A, int o, int e, int mode, uint32_t fe, const LongJob* d_jobs,
-                      uint32_t n_jobs, const uint32_t* d_items, uint32_t n_items, int2* d_bnd,
-                      uint32_t* d_prog, void* d_cands, Scores out) {
+                      int A, int o, int e, int mode, uint32_t fe, bool bytes_ok,
+                      const LongJob* d_jobs, uint32_t n_jobs, const uint32_t* d_items,
+                      uint32_t n_items, int2* d_bnd, uint32_t* d_prog, void* d_cands, Scores out) {
   if (n_items == 0) return DSA_OK;
   // every warp must be resident at once (bands wait on their predecessors):
   // the grid never exceeds what the device holds simultaneously
-  // alphabets of up to 4 letters: substitution scores by byte permute
-  const bool bytes = A <= 4;
+  // alphabets of up to 4 letters with every S + o in int8: substitution
+  // scores by byte permute
+  const bool bytes = A <= 4 && bytes_ok;
   auto kern = mode == DSA_LOCAL ? (bytes ? k_long_score<true, true> : k_long_score<true, false>)
                                 : (bytes ? k_long_score<false, true> : k_long_score<false, false>);
   int per_sm = 0;
