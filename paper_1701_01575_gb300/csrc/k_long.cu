@@ -30,7 +30,7 @@
 namespace dsa {
 namespace {
 
-constexpr int ROWS = 8;
+constexpr int ROWS = 16;
 constexpr int BAND = 32 * ROWS;
 constexpr int WARPS = 4;
 constexpr uint32_t PUBLISH = 32;   // columns between progress updates
@@ -457,19 +457,20 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
 
 // Checkpointed traceback, part 2: one warp per hit.  Lane 0 walks the stored
 // decisions from the end cell (stop > M > I > D, open preferred on ties); the
-// warp keeps a window of them in shared memory -- the rows of the current
-// 256-row band up to the walk's row, WIN_WORDS words (8 cells each) ending at
-// the walk's column -- and reloads it with coalesced row loads whenever the
-// walk leaves it (the walk only moves up and left), so each step reads shared
-// memory instead of waiting on a global load.
+// warp keeps a window of them in shared memory -- up to WIN_ROWS rows of the
+// current band ending at the walk's row, WIN_WORDS words (8 cells each)
+// ending at the walk's column -- and reloads it with coalesced row loads
+// whenever the walk leaves it (the walk only moves up and left), so each step
+// reads shared memory instead of waiting on a global load.
 constexpr int WIN_WORDS = 32;
+constexpr int WIN_ROWS = 256;
 
 __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict__ jobs,
                                                      uint32_t n_jobs, int mode, uint32_t fe,
                                                      const uint32_t* __restrict__ dir,
                                                      uint32_t* __restrict__ cig_tmp,
                                                      dsa_hit* __restrict__ hits) {
-  __shared__ uint32_t win[BAND * WIN_WORDS];
+  __shared__ uint32_t win[WIN_ROWS * WIN_WORDS];
   constexpr unsigned FULL = 0xFFFFFFFFu;
   const int lane = threadIdx.x;
   const bool local = mode == DSA_LOCAL;
@@ -478,7 +479,7 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
     const LongTbJob jb = jobs[k];
     const uint32_t* D = dir + jb.dir_off;
     const uint32_t wpr = jb.wpr;
-    int32_t wb = -1, wlo = 0, wrows = 0;   // window: band, first word, rows loaded
+    int32_t wb = -1, wlo = 0, wr0 = 0, wr1 = 0;   // window: band, first word, rows [wr0, wr1)
     // lane 0: 0 = decision of (ii, jj) in nib, 1 = outside the window,
     // 2 = outside the stored band (only a corrupt decision leads there)
     auto look = [&](int32_t ii, int32_t jj, uint32_t& nib) -> int {
@@ -486,8 +487,8 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
       const int32_t jlo = band_jlo(jb, b);
       if (jj < jlo || jj >= jlo + jb.wc) return 2;
       const int32_t jc = jj - jlo, wi = jc >> 3, rr = ii - 1 - b * BAND;
-      if (b != wb || wi < wlo || wi >= wlo + WIN_WORDS || rr >= wrows) return 1;
-      nib = (win[rr * WIN_WORDS + (wi - wlo)] >> (4 * (jc & 7))) & 15u;
+      if (b != wb || wi < wlo || wi >= wlo + WIN_WORDS || rr < wr0 || rr >= wr1) return 1;
+      nib = (win[(rr - wr0) * WIN_WORDS + (wi - wlo)] >> (4 * (jc & 7))) & 15u;
       return 0;
     };
     RevCigar c;
@@ -532,17 +533,18 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
       }
       need = __shfl_sync(FULL, need, 0);
       if (need != 1) break;
-      // reload: rows of (i, j)'s band up to row i, words ending at j's word
+      // reload: rows of (i, j)'s band ending at row i, words ending at j's word
       const int32_t ci = __shfl_sync(FULL, i, 0), cj = __shfl_sync(FULL, j, 0);
       wb = (ci - 1) / BAND;
       const int32_t wi = (cj - band_jlo(jb, wb)) >> 3;
       wlo = max(0, wi - (WIN_WORDS - 1));
-      wrows = ci - wb * BAND;
+      wr1 = ci - wb * BAND;
+      wr0 = max(0, wr1 - WIN_ROWS);
       __syncwarp();
       const int32_t w = wlo + lane;
 #pragma unroll 8
-      for (int rr = 0; rr < wrows; ++rr)
-        win[rr * WIN_WORDS + lane] =
+      for (int rr = wr0; rr < wr1; ++rr)
+        win[(rr - wr0) * WIN_WORDS + lane] =
             w < (int32_t)wpr ? D[(uint64_t)(wb * BAND + rr) * wpr + (uint32_t)w] : 0u;
       __syncwarp();
     }
