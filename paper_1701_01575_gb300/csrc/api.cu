@@ -1533,7 +1533,9 @@ int traceback_device_staged(dsa_ctx* ctx, dsa_res* res, const TbBounds& B) {
   DSA_TRY(d_scr.alloc(ctx, scr * sizeof(int2)));
   DSA_CUDA_TRY(cudaMemcpyAsync(cnt, &old_n, sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
   DSA_TRY(launch_traceback_thread(ctx, db, qs, d_mat.as<int8_t>(), res->A, res->gap_open,
-                                  res->gap_extend, res->mode, res->free_ends, d_jobs.as<TbJob>(),
+                                  res->gap_extend, res->mode, res->free_ends,
+                                  s_plus_o_fits_int8(res->matrix.data(), res->A, res->gap_open),
+                                  d_jobs.as<TbJob>(),
                                   (uint32_t)nv, d_dir.as<uint32_t>(), d_cig.as<uint32_t>(),
                                   d_scr.as<int2>(), res->d_hits));
   DSA_TRY(launch_cigar_compact(ctx, res->d_hits, d_jobs.as<TbJob>(), (uint32_t)nv,
@@ -1837,6 +1839,7 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
       DSA_TRY(d_scr.alloc(ctx, scr * sizeof(int2)));
       DSA_TRY(launch_traceback_thread(ctx, db, qs, d_mat.as<int8_t>(), res->A, res->gap_open,
                                       res->gap_extend, res->mode, res->free_ends,
+                                      s_plus_o_fits_int8(res->matrix.data(), res->A, res->gap_open),
                                       d_jobs.as<TbJob>(), (uint32_t)n_chunk,
                                       d_dir.as<uint32_t>(), d_cig.as<uint32_t>(), d_scr.as<int2>(),
                                       res->d_hits));

@@ -393,9 +393,10 @@ int launch_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int
 // job order; total words written are added to *d_total.
 // One thread per hit; TbJob.dir_off = group base + lane, .wpr = the group's
 // column count, .scr_off = group scratch base + lane (layouts interleaved by 32).
+// bytes_ok: every S + o fits int8 (with A <= 4 the byte-permute form is used)
 int launch_traceback_thread(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
                             const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
-                            const TbJob* d_jobs, uint32_t n_jobs, uint32_t* d_dir,
+                            bool bytes_ok, const TbJob* d_jobs, uint32_t n_jobs, uint32_t* d_dir,
                             uint32_t* d_cig_tmp, int2* d_scr, dsa_hit* d_hits);
 int launch_cigar_compact(dsa_ctx* ctx, dsa_hit* d_hits, const TbJob* d_jobs, uint32_t n_jobs,
                          const uint32_t* d_cig_tmp, uint32_t* d_cigar, uint64_t base,

@@ -238,13 +238,15 @@ __global__ void __launch_bounds__(128, 4) k_traceback_thread(
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
     const TbJob* __restrict__ jobs, uint32_t n_jobs, uint32_t* __restrict__ dir,
     uint32_t* __restrict__ cig_tmp, int2* __restrict__ scratch, dsa_hit* __restrict__ hits) {
-  __shared__ int32_t S[32 * 32];
-  __shared__ uint32_t Sb[4];   // BYTES: row q of S as 4 bytes
-  for (int x = threadIdx.x; x < A * A; x += blockDim.x) S[x] = Sg[x];
+  // substitution scores with o added: the diagonal term H + S is taken as
+  // (H - o) + (S + o) from the stored H - o
+  __shared__ int32_t So[32 * 32];
+  __shared__ uint32_t Sb[4];   // BYTES: row q of S + o as 4 bytes (each fits int8)
+  for (int x = threadIdx.x; x < A * A; x += blockDim.x) So[x] = Sg[x] + o;
   if (BYTES && threadIdx.x < 4) {
     uint32_t w = 0;
     for (int a = 0; a < A; ++a)
-      if ((int)threadIdx.x < A) w |= (uint32_t)(uint8_t)Sg[threadIdx.x * A + a] << (8 * a);
+      if ((int)threadIdx.x < A) w |= (uint32_t)(uint8_t)(int8_t)(Sg[threadIdx.x * A + a] + o) << (8 * a);
     Sb[threadIdx.x] = w;
   }
   __syncthreads();
@@ -269,19 +271,21 @@ __global__ void __launch_bounds__(128, 4) k_traceback_thread(
       const bool last = i0 + rows == ie;
       const int32_t jlo = strip_jlo(i0), jhi = jlo + wc - 1;
       const bool wall = jlo > 1 || jb.jlo > 0;   // column jlo - 1 is -inf below row 0
-      int32_t H[TROWS], E[TROWS];
-      uint32_t qv[TROWS];   // BYTES: S row of the query residue as bytes; else its matrix offset
+      // Ho = H - o of the strip's rows in the previous column, E of those rows
+      int32_t Ho[TROWS], E[TROWS];
+      uint32_t qv[TROWS];   // BYTES: S + o row of the query residue as bytes; else its matrix offset
 #pragma unroll
       for (int r = 0; r < TROWS; ++r) {
-        H[r] = wall ? NEG32 : h_col0(mode, fe, i0 + r + 1, o, e);
+        Ho[r] = (wall ? NEG32 : h_col0(mode, fe, i0 + r + 1, o, e)) - o;
         E[r] = NEG32;
         qv[r] = r < rows ? (BYTES ? Sb[q[i0 + r]] : (uint32_t)q[i0 + r] * A) : 0u;
       }
-      // H[i0][jlo - 1]
+      // H[i0][jlo - 1] - o
       int32_t diag;
       if (i0 == 0) diag = h_row0(mode, fe, jlo - 1, o, e);
       else if (jlo == 1) diag = jb.jlo > 0 ? NEG32 : h_col0(mode, fe, i0, o, e);
       else diag = (jlo - 1 >= plo && jlo - 1 <= phi) ? scr[(uint64_t)(jlo - 2) * 32].x : NEG32;
+      diag -= o;
       uint32_t* Ds = D + (uint64_t)s * cols * 64;
       // the column loop in four forms (first strip: top row from the boundary
       // of the matrix; last strip: nothing to hand down), with no per-column
@@ -301,47 +305,48 @@ __global__ void __launch_bounds__(128, 4) k_traceback_thread(
             const int2 nv = scr[(uint64_t)min(j, phi - 1) * 32];
             n_v = j + 1 <= phi ? nv : NEGP;
           }
-          int32_t Hp, F;
+          int32_t hoa, F;   // H - o and F of the cell above
           if (FIRST) {
-            Hp = h_row0(mode, fe, j, o, e);
+            hoa = h_row0(mode, fe, j, o, e) - o;
             F = NEG32;
           } else {
-            Hp = v.x;
+            hoa = v.x - o;
             F = v.y;
           }
-          int32_t d = diag;
-          diag = Hp;
+          int32_t d = diag;   // H - o above-left
+          diag = hoa;
           // BYTES: byte a of the row table, sign-replicated into bytes 1-3
           const uint32_t sel = (uint32_t)a + ((uint32_t)a | 8u) * 0x1110u;
           uint32_t w0 = 0, w1 = 0;
 #pragma unroll
           for (int r = 0; r < TROWS; ++r) {
             if (LAST ? r < rows : true) {
-              const int32_t fo = Hp - o, fx = F - e;
-              F = max(fx, fo);
-              const int32_t eo = H[r] - o, ex = E[r] - e;
-              E[r] = max(ex, eo);
-              const int32_t sv = BYTES ? (int32_t)prmt(qv[r], 0u, sel) : S[qv[r] + a];
-              const int32_t m = d + sv;
-              int32_t v = max(m, max(E[r], F));
-              if (local) v = max(v, 0);
+              // a gap is opened here exactly when the opening term wins or ties:
+              // max(F - e, H_above - o) == H_above - o  <=>  H_above - o >= F - e
+              F = __viaddmax_s32(F, -e, hoa);
+              const uint32_t fbit = F == hoa ? 8u : 0u;
+              E[r] = __viaddmax_s32(E[r], -e, Ho[r]);
+              const uint32_t ebit = E[r] == Ho[r] ? 4u : 0u;
+              const int32_t sv = BYTES ? (int32_t)prmt(qv[r], 0u, sel) : So[qv[r] + a];
+              const int32_t m = d + sv;   // H_diag + S
+              const int32_t v = local ? __vimax_s32_relu(m, max(E[r], F)) : __vimax3_s32(m, E[r], F);
               uint32_t src;
               if (local && v == 0) src = 3;
               else if (v == m) src = 0;
               else if (v == F) src = 1;
               else src = 2;
-              const uint32_t nib = src | ((eo >= ex) ? 4u : 0u) | ((fo >= fx) ? 8u : 0u);
+              const uint32_t nib = src | ebit | fbit;
               if (r < 8) w0 |= nib << (4 * r);
               else w1 |= nib << (4 * (r - 8));
-              d = H[r];
-              H[r] = v;
-              Hp = v;
+              d = Ho[r];
+              Ho[r] = v - o;
+              hoa = Ho[r];
             }
           }
           const uint64_t c = (uint64_t)(j - jlo);
           Ds[c * 64] = w0;
           if (!LAST || rows > 8) Ds[c * 64 + 32] = w1;
-          if (!LAST) scr[(uint64_t)(j - 1) * 32] = make_int2(Hp, F);
+          if (!LAST) scr[(uint64_t)(j - 1) * 32] = make_int2(hoa + o, F);
         }
       };
       using T_ = std::true_type;
@@ -468,11 +473,12 @@ int launch_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int
 
 int launch_traceback_thread(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
                             const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
-                            const TbJob* d_jobs, uint32_t n_jobs, uint32_t* d_dir,
+                            bool bytes_ok, const TbJob* d_jobs, uint32_t n_jobs, uint32_t* d_dir,
                             uint32_t* d_cig_tmp, int2* d_scr, dsa_hit* d_hits) {
   if (n_jobs == 0) return DSA_OK;
   const unsigned blocks = (n_jobs + 127) / 128;
-  const bool bytes = A <= 4;   // substitution scores by byte permute
+  // substitution scores (S + o) by byte permute
+  const bool bytes = A <= 4 && bytes_ok;
   auto kern = mode == DSA_LOCAL
                   ? (bytes ? k_traceback_thread<true, true> : k_traceback_thread<true, false>)
                   : (bytes ? k_traceback_thread<false, true> : k_traceback_thread<false, false>);
