@@ -480,28 +480,20 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
     const uint32_t* D = dir + jb.dir_off;
     const uint32_t wpr = jb.wpr;
     int32_t wb = -1, wlo = 0, wr0 = 0, wr1 = 0;   // window: band, first word, rows [wr0, wr1)
-    // lane 0: 0 = decision of (ii, jj) in nib, 1 = outside the window,
-    // 2 = outside the stored band (only a corrupt decision leads there)
-    auto look = [&](int32_t ii, int32_t jj, uint32_t& nib) -> int {
-      const int32_t b = (ii - 1) / BAND;
-      const int32_t jlo = band_jlo(jb, b);
-      if (jj < jlo || jj >= jlo + jb.wc) return 2;
-      const int32_t jc = jj - jlo, wi = jc >> 3, rr = ii - 1 - b * BAND;
-      if (b != wb || wi < wlo || wi >= wlo + WIN_WORDS || rr < wr0 || rr >= wr1) return 1;
-      nib = (win[(rr - wr0) * WIN_WORDS + (wi - wlo)] >> (4 * (jc & 7))) & 15u;
-      return 0;
-    };
     RevCigar c;
     c.out = cig_tmp + jb.cig_off;
     int32_t i = jb.ie, j = jb.je;
     int st = 0;
     int64_t guard = 2 * ((int64_t)jb.ie + jb.je) + 2;
+    // lane 0: the walk's cell as (row in band wb, stored column of that band),
+    // valid once a reload has placed the window around it.  The walk only
+    // moves up and left, so only the window's lower bounds can be crossed;
+    // crossing one (a new band included: its rows start at 0) reloads.
+    int32_t rr = -1, jc = -1;
     for (;;) {
       int need = 2;   // 1: reload the window around (i, j); 2: finished
       if (lane == 0) {
         for (; guard > 0; --guard) {
-          uint32_t nib = 0;
-          int lk;
           if (st == 0) {
             if (sg && ((i == 0 && (fe & DSA_FREE_T_BEGIN)) || (j == 0 && (fe & DSA_FREE_Q_BEGIN)))) break;
             if (i == 0 || j == 0) {
@@ -511,41 +503,52 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
               }
               break;
             }
-            if ((lk = look(i, j, nib)) != 0) { need = lk; break; }
+          } else if (i <= 0 || j <= 0) {
+            break;
+          }
+          if (rr < wr0 || (jc >> 3) < wlo) { need = 1; break; }
+          const uint32_t nib = (win[(rr - wr0) * WIN_WORDS + ((jc >> 3) - wlo)] >> (4 * (jc & 7))) & 15u;
+          if (st == 0) {
             const uint32_t src = nib & 3u;
             if (src == 3) break;
-            if (src == 0) { c.emit(0); --i; --j; }
+            if (src == 0) { c.emit(0); --i; --j; --rr; --jc; }
             else st = src == 1 ? 1 : 2;
+          } else if (st == 1) {
+            c.emit(1);
+            if (nib & 8u) st = 0;
+            --i;
+            --rr;
           } else {
-            if (i <= 0 || j <= 0) break;
-            if ((lk = look(i, j, nib)) != 0) { need = lk; break; }
-            if (st == 1) {
-              c.emit(1);
-              if (nib & 8u) st = 0;
-              --i;
-            } else {
-              c.emit(2);
-              if (nib & 4u) st = 0;
-              --j;
-            }
+            c.emit(2);
+            if (nib & 4u) st = 0;
+            --j;
+            --jc;
           }
         }
       }
       need = __shfl_sync(FULL, need, 0);
       if (need != 1) break;
-      // reload: rows of (i, j)'s band ending at row i, words ending at j's word
+      // reload: rows of (i, j)'s band ending at row i, words ending at j's word;
+      // a cell left of the band's stored columns ends the walk (only a corrupt
+      // decision leads there)
       const int32_t ci = __shfl_sync(FULL, i, 0), cj = __shfl_sync(FULL, j, 0);
       wb = (ci - 1) / BAND;
-      const int32_t wi = (cj - band_jlo(jb, wb)) >> 3;
+      const int32_t jlo = band_jlo(jb, wb);
+      if (cj < jlo || cj >= jlo + jb.wc) break;
+      const int32_t wi = (cj - jlo) >> 3;
       wlo = max(0, wi - (WIN_WORDS - 1));
       wr1 = ci - wb * BAND;
       wr0 = max(0, wr1 - WIN_ROWS);
+      rr = wr1 - 1;
+      jc = cj - jlo;
       __syncwarp();
       const int32_t w = wlo + lane;
-#pragma unroll 8
-      for (int rr = wr0; rr < wr1; ++rr)
-        win[(rr - wr0) * WIN_WORDS + lane] =
-            w < (int32_t)wpr ? D[(uint64_t)(wb * BAND + rr) * wpr + (uint32_t)w] : 0u;
+      // 32 independent row loads in flight per lane: a reload costs a few
+      // memory latencies, not one per 8 rows
+#pragma unroll 32
+      for (int r = wr0; r < wr1; ++r)
+        win[(r - wr0) * WIN_WORDS + lane] =
+            w < (int32_t)wpr ? D[(uint64_t)(wb * BAND + r) * wpr + (uint32_t)w] : 0u;
       __syncwarp();
     }
     if (lane == 0) {
