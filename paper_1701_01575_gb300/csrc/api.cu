@@ -1148,7 +1148,7 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
     std::vector<uint64_t> p16;   // pairs for the packed int16 kernel
     uint64_t scr = 0, cells = 0, lcells = 0, p16cells = 0;
     uint64_t bnd = 0, prog = 0, cand = 0;
-    const int band = long_band_rows();
+    const int band = long_band_rows(), ckpt = long_ckpt_rows();
     // every pair packed: the device planner lays out the jobs
     const bool dev_plan = n_pairs > 0 && pst.n_other == 0;
     // host planner: classify on host threads: packed pairs (filled in place,
@@ -1201,10 +1201,11 @@ int align_impl(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const dsa_pair*
       const uint64_t m = qs->h_len[p.query_id];
       if (cls[k] == C_LONG) {
         const uint64_t nb = (m + band - 1) / band;
+        const uint64_t nck = (m + ckpt - 1) / ckpt;   // checkpoint rows
         LongJob lj{qs->h_off[p.query_id], db->h_off[p.target_id] + p.t_offset, bnd, prog, cand,
                    (int32_t)m, (int32_t)p.t_len, (uint32_t)k, 0};
         ljobs.push_back(lj);
-        bnd += nb * p.t_len;
+        bnd += nck * p.t_len;
         prog += nb;
         cand += nb;
         lcells += m * p.t_len;
@@ -1609,7 +1610,7 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
   std::vector<TbJob> jobs;                 // warp-per-hit
   std::vector<LongTbJob> ljobs;
   uint64_t cap_total = 0;
-  const int band = long_band_rows();
+  const int band = long_band_rows(), ckpt = long_ckpt_rows();
   auto diag_window = [&](int32_t ie, int32_t je, int32_t score, int64_t& dlo, int64_t& dhi) {
     return tb_diag_window(bounds, ie, je, score, dlo, dhi);
   };
@@ -1641,7 +1642,7 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
       lj.wc = lj.je;
       int64_t dlo, dhi;
       if (lj.ie > 0 && lj.je > 0 && diag_window(lj.ie, lj.je, hit.score, dlo, dhi)) {
-        const int64_t wc = (int64_t)band + dhi - dlo;
+        const int64_t wc = (int64_t)ckpt + dhi - dlo;   // a traceback band's window
         if (wc < lj.je) {
           lj.dlo = (int32_t)std::max<int64_t>(dlo, -(int64_t)lj.ie);
           lj.wc = (int32_t)wc;
@@ -1721,7 +1722,7 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
       lj.wc = je;
       int64_t dlo, dhi;
       if (diag_window(ie, je, hit.score, dlo, dhi)) {
-        const int64_t wc = (int64_t)band + dhi - dlo;
+        const int64_t wc = (int64_t)ckpt + dhi - dlo;   // a traceback band's window
         if (wc < je) {
           lj.dlo = (int32_t)std::max<int64_t>(dlo, -(int64_t)ie);
           lj.wc = (int32_t)wc;
@@ -1730,7 +1731,7 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
       lj.wpr = (uint32_t)((lj.wc + 7) / 8);
       bjobs.push_back(lj);
       cap_total += (uint64_t)je - j.je;   // CIGAR capacity of the whole rectangle
-      b_bnd += nb * (uint64_t)je;
+      b_bnd += ((uint64_t)ie + ckpt - 1) / ckpt * (uint64_t)je;   // checkpoint rows
       b_bands += nb;
     }
     jobs.swap(keep);
@@ -1902,7 +1903,7 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
         lj.cig_off = cig;
         dir += w;
         cig += (uint64_t)lj.ie + lj.je + 1;
-        const uint32_t nb = (uint32_t)((lj.ie + band - 1) / band);
+        const uint32_t nb = (uint32_t)((lj.ie + ckpt - 1) / ckpt);   // traceback bands
         for (uint32_t b = 0; b < nb; ++b) { items.push_back((uint32_t)(k1 - k0)); items.push_back(b); }
         ++k1;
       }

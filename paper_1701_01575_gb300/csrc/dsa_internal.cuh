@@ -440,7 +440,8 @@ int launch_long_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
                           uint32_t n_items, const int2* d_bnd, uint32_t* d_dir,
                           uint32_t* d_cig_tmp, dsa_hit* d_hits);
 size_t long_cand_size();
-int long_band_rows();
+int long_band_rows();   // rows of a score-pass band
+int long_ckpt_rows();   // rows between traceback checkpoints (a traceback band)
 constexpr uint64_t LONG_PAIR_CELLS = 1ull << 22;   // explicit pairs at least this big run banded
 
 // Packed int16x2 kernel for explicit short pairs: two pairs of equal query

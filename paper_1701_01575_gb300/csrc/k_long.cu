@@ -11,15 +11,18 @@
 // waits on that counter with a bounded wait before it needs a column.  Work
 // items (pair, band) are taken in order from one counter by persistent
 // warps, so every band's predecessor was taken earlier by a warp that is
-// already running: the pipeline always advances.  The boundary rows are kept
-// as checkpoints for the traceback.
+// already running: the pipeline always advances.  Checkpoint rows (H, F)
+// for the traceback are kept every TB_BAND = BAND / 2 rows: a band's bottom
+// row (also the next band's input) and its middle row.  Checkpoint c holds
+// row (c + 1) TB_BAND.
 //
 // Result cell.  Inside a lane, cells are visited in increasing (j, i), so a
 // lane keeps its first strictly better candidate; the lanes' and bands'
 // candidates are merged under (score desc, j asc, i asc) by k_long_reduce.
 //
-// Traceback.  The checkpoints make every band independent: all bands of all
-// hits are recomputed at once (one warp each) over the rectangle up to the
+// Traceback.  The checkpoints make every TB_BAND-row band independent: all
+// bands of all hits are recomputed at once (one warp each, TB_ROWS rows per
+// lane) over the rectangle up to the
 // end cell, storing the 4-bit decision of every cell (as in the short-hit
 // traceback), then one warp per hit walks back through a shared-memory window
 // of the decisions.  Decision memory is half a byte per cell of the
@@ -32,6 +35,9 @@ namespace {
 
 constexpr int ROWS = 16;
 constexpr int BAND = 32 * ROWS;
+constexpr int TB_ROWS = 8;               // traceback fill: rows per lane
+constexpr int TB_BAND = 32 * TB_ROWS;    // traceback bands (checkpoint spacing)
+static_assert(BAND == 2 * TB_BAND, "a score band holds two traceback bands");
 constexpr int WARPS = 4;
 constexpr uint32_t PUBLISH = 32;   // columns between progress updates
 
@@ -102,14 +108,21 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
     const int32_t r0 = i0 + lane * ROWS;     // rows r0+1 .. r0+ROWS
     const int32_t nb = (m + BAND - 1) / BAND;
     const bool last_band = (int32_t)b == nb - 1;
-    int2* my_bnd = bnd + jb.bnd_off + (uint64_t)b * n;          // this band's bottom row
-    const int2* up_bnd = bnd + jb.bnd_off + (uint64_t)(b - 1) * n;
+    int2* my_bnd = bnd + jb.bnd_off + (uint64_t)(2 * b + 1) * n;  // checkpoint: bottom row
+    int2* my_mid = bnd + jb.bnd_off + (uint64_t)(2 * b) * n;      // checkpoint: middle row
+    const int2* up_bnd = bnd + jb.bnd_off + (uint64_t)(2 * b - 1) * n;
     uint32_t* my_prog = prog + jb.prog_off + b;
     const uint32_t* up_prog = prog + jb.prog_off + b - 1;
     // the lane that holds the band's bottom row publishes it
     const int32_t bottom = min(m, i0 + BAND);
     const int bot_lane = (bottom - 1 - i0) / ROWS;
     const bool owns_m = r0 < m && m <= r0 + ROWS;
+    // lane 15 holds the middle row (a checkpoint when rows follow it), the
+    // bottom lane the band's last row: one store instruction serves both
+    const bool stores_mid = lane == TB_BAND / ROWS - 1 && m > i0 + TB_BAND;
+    const bool stores_bot = !last_band && lane == bot_lane;
+    const bool stores_ck = stores_mid || stores_bot;
+    int2* const ck = stores_mid ? my_mid : my_bnd;
 
     // Ho = H - o of the lane's rows in the previous column (the operand both
     // gap recurrences extend), E of those rows
@@ -241,8 +254,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
         }
         sendH = hoa;
         sendF = F;
-        if (!last_band && lane == bot_lane) {
-          my_bnd[j - 1] = make_int2(hoa + o, F);
+        if (stores_ck) ck[j - 1] = make_int2(hoa + o, F);
+        if (stores_bot) {
           if ((uint32_t)j % PUBLISH == 0 || j == n) {
             __threadfence();
             st_release_u32(my_prog, (uint32_t)j);
@@ -312,9 +325,9 @@ struct RevCigar {
 // once (one warp per band, rows of the band x columns 1..je), starting from
 // the checkpoint row above it, and the 4-bit decision of every cell of the
 // rectangle up to the end cell is stored.
-// First stored column of the rows of band b (see LongTbJob).
+// First stored column of the rows of traceback band b (see LongTbJob).
 __device__ __forceinline__ int32_t band_jlo(const LongTbJob& jb, int32_t b) {
-  const int32_t want = b * BAND + 1 + jb.dlo;
+  const int32_t want = b * TB_BAND + 1 + jb.dlo;
   return max(1, min(want, jb.je - jb.wc + 1));
 }
 
@@ -346,17 +359,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
     const uint8_t* t = tcodes + jb.t_start;
     uint32_t* D = dir + jb.dir_off;
     const uint32_t wpr = jb.wpr;
-    const int32_t i0 = b * BAND;
-    const int32_t r0 = i0 + lane * ROWS;
+    const int32_t i0 = b * TB_BAND;
+    const int32_t r0 = i0 + lane * TB_ROWS;
     const int2* up = bnd + jb.bnd_off + (uint64_t)(b - 1) * jb.n;
     // columns jlo .. jlo + wc - 1 of this band; a wall (-inf) left of jlo > 1
     const int32_t jlo = band_jlo(jb, b), jhi = jlo + jb.wc - 1;
     const bool wall = jlo > 1;
-    int32_t H[ROWS], E[ROWS];
-    uint32_t nbw[ROWS];
-    uint32_t qv[ROWS];   // BYTES: S row of the query residue as bytes; else its matrix offset
+    int32_t H[TB_ROWS], E[TB_ROWS];
+    uint32_t nbw[TB_ROWS];
+    uint32_t qv[TB_ROWS];   // BYTES: S row of the query residue as bytes; else its matrix offset
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) {
+    for (int r = 0; r < TB_ROWS; ++r) {
       const int32_t ii = r0 + r + 1;
       H[r] = wall ? NEG32 : h_col0(mode, fe, ii, o, e);
       E[r] = NEG32;
@@ -421,7 +434,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
         const int sh = 4 * (jc & 7);
         const bool flushw = ((jc & 7) == 7) || jj == jhi;
 #pragma unroll
-        for (int r = 0; r < ROWS; ++r) {
+        for (int r = 0; r < TB_ROWS; ++r) {
           const int32_t ii = r0 + r + 1;
           if (ii <= ie) {
             const int32_t fo = Hp - o, fx = F - e;
@@ -532,12 +545,12 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
       // a cell left of the band's stored columns ends the walk (only a corrupt
       // decision leads there)
       const int32_t ci = __shfl_sync(FULL, i, 0), cj = __shfl_sync(FULL, j, 0);
-      wb = (ci - 1) / BAND;
+      wb = (ci - 1) / TB_BAND;
       const int32_t jlo = band_jlo(jb, wb);
       if (cj < jlo || cj >= jlo + jb.wc) break;
       const int32_t wi = (cj - jlo) >> 3;
       wlo = max(0, wi - (WIN_WORDS - 1));
-      wr1 = ci - wb * BAND;
+      wr1 = ci - wb * TB_BAND;
       wr0 = max(0, wr1 - WIN_ROWS);
       rr = wr1 - 1;
       jc = cj - jlo;
@@ -548,7 +561,7 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
 #pragma unroll 32
       for (int r = wr0; r < wr1; ++r)
         win[(r - wr0) * WIN_WORDS + lane] =
-            w < (int32_t)wpr ? D[(uint64_t)(wb * BAND + r) * wpr + (uint32_t)w] : 0u;
+            w < (int32_t)wpr ? D[(uint64_t)(wb * TB_BAND + r) * wpr + (uint32_t)w] : 0u;
       __syncwarp();
     }
     if (lane == 0) {
@@ -599,6 +612,7 @@ int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const in
 
 size_t long_cand_size() { return sizeof(Cand); }
 int long_band_rows() { return BAND; }
+int long_ckpt_rows() { return TB_BAND; }
 
 int launch_long_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
                           const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
