@@ -1817,8 +1817,8 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
           je_max = std::max(je_max, tjobs[x].je);
           wc_max = std::max(wc_max, tjobs[x].wc);
         }
-        const uint64_t strips = ((uint64_t)ie_max + 15) / 16;
-        const uint64_t w = strips * (uint64_t)wc_max * 64;
+        const uint64_t strips = ((uint64_t)ie_max + TB_STRIP - 1) / TB_STRIP;
+        const uint64_t w = strips * (uint64_t)wc_max * (32 * TB_STRIP_WORDS);
         if (k1 > k0 && dir + w > dir_limit) break;
         for (size_t x = k1; x < g1; ++x) {
           const uint32_t lane = (uint32_t)(x - k1);

@@ -272,6 +272,10 @@ int launch_fill_hits(dsa_ctx* ctx, const Scores& s, const dsa_pair* d_pairs, uin
                      uint32_t n_targets, dsa_hit* d_hits);
 
 // Traceback of hits.
+// Thread-per-hit traceback: query rows per strip (a multiple of 8; each strip
+// column keeps TB_STRIP / 8 words of 4-bit decisions per hit).
+constexpr int TB_STRIP = 8;
+constexpr int TB_STRIP_WORDS = TB_STRIP / 8;
 struct TbJob {
   uint64_t q_start;   // absolute offset of the query in the query codes
   uint64_t t_start;   // absolute offset of the target window in the DB codes
@@ -283,7 +287,7 @@ struct TbJob {
   uint32_t wpr;       // direction words per row
   int32_t jlo;        // first target column of the recomputed band (0 = whole rectangle);
                       // > 0: column jlo is a wall (H = -inf below row 0)
-  // thread-per-hit kernel: diagonal window of each 16-row strip (relative to
+  // thread-per-hit kernel: diagonal window of each TB_STRIP-row strip (relative to
   // the band): wc stored columns from clamp(i0 + 1 + dlo, 1, je - wc + 1)
   int32_t dlo;
   int32_t wc;
@@ -325,7 +329,7 @@ __host__ __device__ inline bool tb_diag_window(const TbBounds& B, int32_t ie, in
 }
 
 // The thread-per-hit job of a hit with end cell (ie, je) (1-based) and score:
-// column band (free target begin) and the diagonal window of its 16-row strips.
+// column band (free target begin) and the diagonal window of its TB_STRIP-row strips.
 __host__ __device__ inline void tb_short_job(const TbBounds& B, int32_t ie, int32_t je,
                                              int32_t score, uint64_t q_start, uint64_t t_start,
                                              uint32_t hit, TbJob& j) {
@@ -362,7 +366,7 @@ __host__ __device__ inline void tb_short_job(const TbBounds& B, int32_t ie, int3
     }
   }
   j.dlo = (int32_t)(dlo > -(int64_t)ie ? dlo : -(int64_t)ie);
-  const int64_t wc = 16 + dhi - j.dlo;
+  const int64_t wc = TB_STRIP + dhi - j.dlo;
   j.wc = (int32_t)(wc < j.je ? wc : j.je);
   j.wpr = (uint32_t)((j.je + 7) / 8);
 }

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(STAGE_T) k_tb_groups(TbJob* __restrict__ jobs,
       jcig[x] = (uint64_t)j.ie + j.je + 1;
     }
     for (uint64_t x = x0; x < x1; ++x) jobs[x].wpr = (uint32_t)wc_max;
-    gdir[g] = ((uint64_t)ie_max + 15) / 16 * (uint64_t)wc_max * 64;
+    gdir[g] = ((uint64_t)ie_max + TB_STRIP - 1) / TB_STRIP * (uint64_t)wc_max * (32 * TB_STRIP_WORDS);
     gscr[g] = (uint64_t)je_max * 32;
   }
 }

@@ -213,10 +213,10 @@ __global__ void __launch_bounds__(128) k_traceback(
 // Thread-per-hit variant for large batches of small rectangles (reads in
 // windows): one thread recomputes its hit's rectangle in strips of TROWS
 // query rows held in registers, column by column, with the same 4-bit
-// decisions as above.  The decisions of a strip column (TROWS nibbles, two
-// words) go to a layout interleaved over the 32 hits of a warp,
-//   word (strip s, stored column c, half h) of lane l at
-//   dir_off + ((s * cols + c) * 2 + h) * 32        (dir_off = group base + l),
+// decisions as above.  The decisions of a strip column (TROWS nibbles, NW =
+// TROWS / 8 words) go to a layout interleaved over the 32 hits of a warp,
+//   word (strip s, stored column c, part h) of lane l at
+//   dir_off + ((s * cols + c) * NW + h) * 32       (dir_off = group base + l),
 // so every store of the warp is one 128-byte line; the strip's bottom row
 // (H, F) is handed to the next strip through an interleaved scratch row
 // indexed by target column.  Each thread then walks its own hit back, so the
@@ -230,10 +230,11 @@ __global__ void __launch_bounds__(128) k_traceback(
 // band and enter as -inf; a recomputed value is then at most the full DP's
 // and at least the band-restricted DP's, which agree on every cell of an
 // optimal path and on every candidate that ties there.
-constexpr int TROWS = 16;
+constexpr int TROWS = TB_STRIP;
+constexpr int NW = TB_STRIP_WORDS;
 
 template <bool LOCAL, bool BYTES>
-__global__ void __launch_bounds__(128, 4) k_traceback_thread(
+__global__ void __launch_bounds__(128, TROWS <= 8 ? 6 : 4) k_traceback_thread(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
     const TbJob* __restrict__ jobs, uint32_t n_jobs, uint32_t* __restrict__ dir,
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(128, 4) k_traceback_thread(
       else if (jlo == 1) diag = jb.jlo > 0 ? NEG32 : h_col0(mode, fe, i0, o, e);
       else diag = (jlo - 1 >= plo && jlo - 1 <= phi) ? scr[(uint64_t)(jlo - 2) * 32].x : NEG32;
       diag -= o;
-      uint32_t* Ds = D + (uint64_t)s * cols * 64;
+      uint32_t* Ds = D + (uint64_t)s * cols * (32 * NW);
       // the column loop in four forms (first strip: top row from the boundary
       // of the matrix; last strip: nothing to hand down), with no per-column
       // branch that depends on the strip
@@ -317,7 +318,9 @@ __global__ void __launch_bounds__(128, 4) k_traceback_thread(
           diag = hoa;
           // BYTES: byte a of the row table, sign-replicated into bytes 1-3
           const uint32_t sel = (uint32_t)a + ((uint32_t)a | 8u) * 0x1110u;
-          uint32_t w0 = 0, w1 = 0;
+          uint32_t w[NW];
+#pragma unroll
+          for (int h = 0; h < NW; ++h) w[h] = 0;
 #pragma unroll
           for (int r = 0; r < TROWS; ++r) {
             if (LAST ? r < rows : true) {
@@ -336,16 +339,16 @@ __global__ void __launch_bounds__(128, 4) k_traceback_thread(
               else if (v == F) src = 1;
               else src = 2;
               const uint32_t nib = src | ebit | fbit;
-              if (r < 8) w0 |= nib << (4 * r);
-              else w1 |= nib << (4 * (r - 8));
+              w[r >> 3] |= nib << (4 * (r & 7));
               d = Ho[r];
               Ho[r] = v - o;
               hoa = Ho[r];
             }
           }
           const uint64_t c = (uint64_t)(j - jlo);
-          Ds[c * 64] = w0;
-          if (!LAST || rows > 8) Ds[c * 64 + 32] = w1;
+#pragma unroll
+          for (int h = 0; h < NW; ++h)
+            if (!LAST || rows > 8 * h) Ds[(c * NW + h) * 32] = w[h];
           if (!LAST) scr[(uint64_t)(j - 1) * 32] = make_int2(hoa + o, F);
         }
       };
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(128, 4) k_traceback_thread(
     const uint32_t r = (uint32_t)(i - 1) % TROWS, s = (uint32_t)(i - 1) / TROWS;
     const int32_t c = j - strip_jlo((int32_t)s * TROWS);
     if (c < 0 || c >= wc) return false;
-    const uint32_t w = D[(((uint64_t)s * cols + (uint32_t)c) * 2 + (r >> 3)) * 32];
+    const uint32_t w = D[(((uint64_t)s * cols + (uint32_t)c) * NW + (r >> 3)) * 32];
     nib = (w >> (4 * (r & 7))) & 15u;
     return true;
   };
