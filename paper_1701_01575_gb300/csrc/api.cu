@@ -1,4 +1,6 @@
-// Host side of the libdsa C ABI: contexts, device-resident sequence sets,
+// Host side of the libdsa C ABI (the per-core alignment of the map phase,
+// Sec. II.B.1, with its three algorithms, Sec. II.C.2, and the top K of
+// Sec. II.B.2): contexts, device-resident sequence sets,
 // planning of the score pass (packed inter-sequence kernel, long-target
 // wavefront kernel, exact int32 kernel), saturation reruns, top-k and
 // traceback orchestration.  Every arithmetic step runs in the kernels of the

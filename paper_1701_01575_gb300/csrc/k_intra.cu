@@ -1,4 +1,6 @@
-// Intra-sequence local alignment kernel for long targets, packed int16x2 DPX.
+// Intra-sequence local alignment kernel for long targets, packed int16x2 DPX
+// (the local alignment of the map phase, Sec. II.B.1, for database targets
+// too long for one thread).
 //
 // One warp aligns one long target against one packed query pair (the two
 // 16-bit halves of every register hold two queries, as in the inter-sequence

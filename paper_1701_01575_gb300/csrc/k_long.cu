@@ -1,6 +1,7 @@
 // Long explicit pairs (e.g. genome fragments of 1e4-1e5 residues), exact
-// int32, any mode: a band-pipelined wavefront for the score pass and a
-// checkpointed traceback.
+// int32, any mode (DSW / DNW / DSG, Sec. II.C.2): a band-pipelined wavefront
+// for the score pass and a checkpointed traceback for the alignment object's
+// location and CIGAR (Sec. II.B.1).
 //
 // Score pass.  The query rows of a pair are cut into bands of BAND = 32 x ROWS
 // rows.  One warp computes one band as an anti-diagonal wavefront (lane k owns

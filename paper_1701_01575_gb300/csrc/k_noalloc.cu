@@ -1,5 +1,6 @@
-// dsa_score_pairs_noalloc: the exact int32 score pass over explicit pairs,
-// for callers that cannot allocate device memory.
+// dsa_score_pairs_noalloc: the exact int32 score pass over explicit pairs
+// (the map phase's per-pair scores, Sec. II.B.1), for callers that cannot
+// allocate device memory.
 //
 // Who needs it: code that must not call cudaMalloc or any allocating
 // routine -- for example an embedding application that hands every byte of

@@ -1,4 +1,5 @@
-// Device planning of an explicit pair list (e.g. a million reads, each against
+// Device planning of an explicit pair list for the map phase's alignments
+// (Sec. II.B.1; e.g. a million reads, each against
 // its candidate window): validation, classification, the (query length,
 // window length) ordering and the two-pairs-per-thread job layout of the
 // packed int16 pairs kernel are all computed on the device, so the host

@@ -1,4 +1,5 @@
-// Packed int16x2 kernel for explicit short pairs (e.g. reads against windows
+// Packed int16x2 kernel for explicit short pairs of the map phase (Sec. II.B.1,
+// any of the three algorithms of Sec. II.C.2; e.g. reads against windows
 // of a genome): one thread aligns two pairs at once, one in each 16-bit half
 // of every DP register.  The two pairs of a thread have the same query length
 // (pairs are sorted by query length, then window length), so the strips and

@@ -1,4 +1,5 @@
-// Instruction issue-rate microbenchmark: warp-instructions per SM per clock
+// Measurement only (no counterpart in the paper, which reports no kernel
+// throughput).  Instruction issue-rate microbenchmark: warp-instructions per SM per clock
 // of one instruction form, measured with eight interleaved dependency chains
 // per thread (each step also reads the neighbouring chain, so no chain can be
 // folded at compile time) and a 32-warp CTA per SM, so the result is the

@@ -1,5 +1,6 @@
-// Device staging of the thread-per-hit traceback (large hit batches, e.g.
-// every read of a reads-in-windows search): the jobs are built from the
+// Device staging of the thread-per-hit traceback (location and CIGAR of the
+// alignment object, Sec. II.B.1) for large hit batches (e.g. every read of
+// a reads-in-windows search): the jobs are built from the
 // device-resident hits, compacted, and laid out in groups of 32 on the
 // device, so the host touches no per-hit data.  The job of a hit and its
 // score-derived windows come from tb_short_job, the same function the host
