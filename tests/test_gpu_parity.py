@@ -825,6 +825,33 @@ def test_packed_pairs_small_alphabet_asymmetric(ctx, mode, fe):
     assert r.phase_cells()["inter16"] > 0
 
 
+@pytest.mark.parametrize("mode,fe", [(dsa.LOCAL, 15), (dsa.GLOBAL, 15), (dsa.SEMIGLOBAL, 12)])
+@pytest.mark.parametrize("case", ["protein", "dna_wide_open"])
+def test_thread_traceback_shared_table_form(ctx, case, mode, fe, monkeypatch):
+    """The thread-per-hit traceback's shared-memory substitution form (more
+    than 4 letters, or S + o outside int8 so the byte tables cannot hold it)
+    against the oracle, forced onto the thread path."""
+    monkeypatch.setenv("DSA_TB_THREAD_MIN", "1")
+    rng = np.random.default_rng(77 + mode + fe + (0 if case == "protein" else 1000))
+    if case == "protein":
+        bg = W.protein_background()
+        base = [rng.choice(20, int(n), p=bg).astype(np.uint8) for n in rng.integers(20, 200, 6)]
+        targets = [W.mutate(rng, base[k % 6], 0.15, 0.04, alphabet=20) for k in range(30)]
+        S, o, e, A = W.blosum62(), 11, 1, 24
+    else:
+        base = [rng.integers(0, 4, int(n)).astype(np.uint8) for n in rng.integers(20, 200, 6)]
+        targets = [W.mutate(rng, base[k % 6], 0.05, 0.02) for k in range(30)]
+        S, o, e, A = W.dna_matrix(5, -4), 125, 3, 4    # S + o up to 130
+    targets = [t if len(t) else np.zeros(1, np.uint8) for t in targets]
+    qs = W.SeqSet.from_list(base)
+    db = W.SeqSet.from_list(targets)
+    d = ctx.load_set(db, A)
+    q = ctx.load_set(qs, A)
+    r = ctx.align(d, q, S, o, e, mode=mode, free_ends=fe)
+    ctx.traceback(r)
+    check_traceback(r.hits(), r.cigar(), qs, db, S, o, e, mode, fe)
+
+
 BAND_PARAMS = [
     ("dna_1_-4_6_1", W.dna_matrix(1, -4), 6, 1),
     ("o_eq_e", W.dna_matrix(2, -3), 3, 3),
