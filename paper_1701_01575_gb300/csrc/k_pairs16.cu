@@ -37,6 +37,8 @@ constexpr int NT = 128;
 constexpr int BLOCKS_PER_SM = 4;
 constexpr int ROWS_LDS = 16;     // strip rows, shared-memory substitution form
 constexpr int ROWS_BYTES = 16;   // strip rows, byte-permute form (two table registers per row)
+constexpr int RING_SLOTS = 8;    // boundary-row ring: slots per thread (a power of two)
+constexpr int AHEAD = RING_SLOTS - 1;   // columns copied ahead of the arithmetic
 
 __device__ __forceinline__ int32_t h_row0(int mode, uint32_t fe, int64_t j, int o, int e) {
   if (j == 0 || mode == DSA_LOCAL || (mode == DSA_SEMIGLOBAL && (fe & DSA_FREE_T_BEGIN))) return 0;
@@ -68,6 +70,7 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
   __shared__ int16_t Sp[32 * 32];                       // S + o
   __shared__ uint32_t Sb[4];                            // BYTES: row q of S + o as 4 bytes
   __shared__ uint32_t park[2][ROWS][NT];                // parked columns (local mode)
+  __shared__ uint2 ring[RING_SLOTS * NT];               // boundary-row columns in flight
   for (int x = threadIdx.x; x < A * A; x += blockDim.x) Sp[x] = (int16_t)(Sg[x] + o);
   if (BYTES && threadIdx.x < 4) {
     uint32_t w = 0;
@@ -139,16 +142,34 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
         // loads run one column ahead of the arithmetic (target residues and
         // the boundary row handed down by the previous strip); the last
         // iteration re-reads a valid column instead of branching
+        // the previous strip's boundary row arrives through a per-thread ring
+        // of RING_SLOTS columns, copied AHEAD columns ahead by cp.async (one
+        // commit group per column); the copy issued at column j refills the
+        // slot read at column j - 1, and it reads a column this strip has not
+        // yet overwritten (the strip writes column j - 1 at column j)
+        uint2* const rt = ring + tid;
+        if (!FIRST) {
+#pragma unroll
+          for (int c = 1; c <= AHEAD; ++c) {
+            if (c <= nmax) cp_async8(rt + (c & (RING_SLOTS - 1)) * NT, scr + (uint64_t)(c - 1) * stride);
+            cp_async_commit();
+          }
+        }
         uint32_t n_alo = tlo[0], n_ahi = thi[0];
-        uint2 n_v = FIRST ? make_uint2(0u, 0u) : scr[0];
         for (int32_t j = 1; j <= nmax; ++j) {
           const uint32_t a_lo = j <= nlo ? n_alo : 0u;
           const uint32_t a_hi = j <= nhi ? n_ahi : 0u;
-          const uint2 v = n_v;
+          uint2 v = make_uint2(0u, 0u);
+          if (!FIRST) {
+            cp_async_wait<AHEAD - 1>();   // column j has landed
+            v = rt[(j & (RING_SLOTS - 1)) * NT];
+            const int32_t c = j + AHEAD;
+            if (c <= nmax) cp_async8(rt + (c & (RING_SLOTS - 1)) * NT, scr + (uint64_t)(c - 1) * stride);
+            cp_async_commit();
+          }
           const int32_t jn = min(j, nmax - 1);
           n_alo = tlo[min(jn, max(nlo - 1, 0))];
           n_ahi = thi[min(jn, max(nhi - 1, 0))];
-          if (!FIRST) n_v = scr[(uint64_t)jn * stride];
           uint32_t topHo, F;
           if (FIRST) {
             const int32_t h0l = h_row0(mode, fe, min(j, nlo), o, e) - o;
@@ -227,6 +248,7 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
             }
           }
         }
+        if (!FIRST) cp_async_wait<0>();   // nothing in flight into the ring past the strip
       };
       using T_ = std::true_type;
       using F_ = std::false_type;
