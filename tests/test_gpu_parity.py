@@ -676,6 +676,24 @@ def test_pssm_saturation_rerun_and_top_k(ctx):
         assert got["score"].tolist() == sc[qi, order].tolist()
 
 
+@pytest.mark.parametrize("flags", ["force_int32", "plain_form"])
+def test_pssm_search_int32_forms(ctx, flags):
+    """Position-specific local search through the exact int32 kernel (every
+    pair) and through the plain per-query form: the int32 profile builder
+    reads the profile's rows."""
+    rng = np.random.default_rng(640 + len(flags))
+    qs, db, P = _pssm_case(rng, n_q=3, n_t=70)
+    d = ctx.load_set(db, 24)
+    q = ctx.load_set(qs, 24)
+    f = dsa.FORCE_INT32 if flags == "force_int32" else dsa.PLAIN_FORM
+    r = ctx.align_pssm(d, q, P, 11, 1, flags=f)
+    ctx.sync()
+    h = r.hits()
+    sc, qe, te = oracle.score_all_vs_all(qs, db, W.blosum62(), 11, 1, pssm=P)
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc.ravel(), qe.ravel(), te.ravel()), flags)
+    assert r.phase_cells()["int32"] > 0
+
+
 def test_pssm_of_the_matrix_equals_matrix_search(ctx):
     """The profile whose row i is S[q_i] gives the matrix search's results
     bit for bit (scores, ends, rerun flags), locally and globally."""
@@ -692,6 +710,26 @@ def test_pssm_of_the_matrix_equals_matrix_search(ctx):
             assert np.array_equal(a[f], b[f]), (mode, f)
     with pytest.raises(ValueError):
         ctx.align_pssm(d, q, P[:-1], 11, 1)
+
+
+def test_partitioned_search_scores_only(ctx):
+    """Partition + reduce without traceback: the merged top K (scores, ends,
+    global target ids) equals the resident search's and carries no CIGAR."""
+    rng = np.random.default_rng(405)
+    bg = W.protein_background()
+    db = W.SeqSet.from_list([rng.choice(20, int(n), p=bg).astype(np.uint8)
+                             for n in rng.integers(30, 300, 90)])
+    qs = W.SeqSet.from_list([rng.choice(20, int(n), p=bg).astype(np.uint8) for n in (40, 120)])
+    S = W.blosum62()
+    d = ctx.load_set(db, 24)
+    q = ctx.load_set(qs, 24)
+    want = ctx.align(d, q, S, 11, 1, top_k=7).hits()
+    part = ctx.search_partitioned(db.codes, db.offsets, 24, q, S, 11, 1, top_k=7,
+                                  partition_residues=2_000, traceback=False)
+    got = part.hits()
+    for f in ("score", "q_end", "t_end", "query_id", "target_id"):
+        assert np.array_equal(got[f], want[f]), f
+    assert (got["cigar_len"] == 0).all() and len(part.cigar()) == 0
 
 
 def test_pair_range_errors(ctx):
