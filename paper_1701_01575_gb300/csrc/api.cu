@@ -1507,6 +1507,15 @@ int traceback_device_staged(dsa_ctx* ctx, dsa_res* res, const TbBounds& B) {
                             d_jobs.as<TbJob>()));
   d_full.reset();
   d_valid.reset();
+  {
+    // a warp of the thread kernel runs as long as its longest hit: order the
+    // jobs by (rows, stored columns) so each group of 32 does similar work
+    DevBuf d_sorted;
+    DSA_TRY(d_sorted.alloc(ctx, nv * sizeof(TbJob)));
+    DSA_TRY(launch_tb_order(ctx, d_jobs.as<TbJob>(), nv, d_sorted.as<TbJob>()));
+    std::swap(d_jobs.p, d_sorted.p);
+    std::swap(d_jobs.bytes, d_sorted.bytes);
+  }
   DSA_TRY(d_gdir.alloc(ctx, n_groups * sizeof(uint64_t)));
   DSA_TRY(d_gscr.alloc(ctx, n_groups * sizeof(uint64_t)));
   DSA_TRY(d_jcig.alloc(ctx, nv * sizeof(uint64_t)));

@@ -373,6 +373,8 @@ __host__ __device__ inline void tb_short_job(const TbBounds& B, int32_t ie, int3
 
 // Device-side staging kernels (k_tbstage.cu).
 int launch_scan_u64(dsa_ctx* ctx, uint64_t* d_data, uint64_t n, uint64_t* d_total);
+// d_out = the jobs of d_in stably ordered by (rows, stored columns).
+int launch_tb_order(dsa_ctx* ctx, const TbJob* d_in, uint64_t n, TbJob* d_out);
 int launch_tb_stage(dsa_ctx* ctx, const dsa_hit* d_hits, uint64_t n, const uint64_t* d_q_off,
                     const uint64_t* d_t_off, const TbBounds& B, TbJob* d_full, uint64_t* d_valid,
                     uint32_t* d_not_small);

@@ -14,6 +14,7 @@ constexpr int SCAN_T = 256;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_T * SCAN_ITEMS;
 constexpr int STAGE_T = 256;
+constexpr int TB_ORDER_WC_CAP = 65535;   // ordering key: wider windows sort together
 
 // exclusive scan of one tile per block; the tile's sum goes to sums[block]
 __global__ void __launch_bounds__(SCAN_T) k_scan_tile(uint64_t* __restrict__ data, uint64_t n,
@@ -122,6 +123,26 @@ __global__ void __launch_bounds__(STAGE_T) k_tb_assign(TbJob* __restrict__ jobs,
   }
 }
 
+// sort key of a job: (rows, stored columns), the work of its thread
+__global__ void __launch_bounds__(STAGE_T) k_tb_keys(const TbJob* __restrict__ jobs, uint64_t n,
+                                                      uint64_t* __restrict__ key,
+                                                      uint32_t* __restrict__ idx) {
+  for (uint64_t x = blockIdx.x * (uint64_t)STAGE_T + threadIdx.x; x < n;
+       x += (uint64_t)gridDim.x * STAGE_T) {
+    const TbJob& j = jobs[x];
+    key[x] = ((uint64_t)(uint32_t)j.ie << 32) | (uint32_t)min(j.wc, TB_ORDER_WC_CAP);
+    idx[x] = (uint32_t)x;
+  }
+}
+
+__global__ void __launch_bounds__(STAGE_T) k_tb_gather(const TbJob* __restrict__ in,
+                                                        const uint32_t* __restrict__ idx,
+                                                        uint64_t n, TbJob* __restrict__ out) {
+  for (uint64_t x = blockIdx.x * (uint64_t)STAGE_T + threadIdx.x; x < n;
+       x += (uint64_t)gridDim.x * STAGE_T)
+    out[x] = in[idx[x]];
+}
+
 unsigned stage_grid(dsa_ctx* ctx, uint64_t n) {
   const uint64_t b = (n + STAGE_T - 1) / STAGE_T;
   return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(b, (uint64_t)ctx->sm_count * 16));
@@ -224,6 +245,37 @@ __global__ void k_add_u64(uint64_t* __restrict__ a, const uint64_t* __restrict__
 }
 
 }  // namespace
+
+// Jobs in (rows, stored columns) order, stable: consecutive groups of 32 --
+// one warp of the thread kernel, which runs as long as its longest hit --
+// then hold hits of about the same work.
+int launch_tb_order(dsa_ctx* ctx, const TbJob* d_in, uint64_t n, TbJob* d_out) {
+  if (n == 0) return DSA_OK;
+  DevBuf key, idx, key2, idx2;
+  DSA_TRY(key.alloc(ctx, n * sizeof(uint64_t)));
+  DSA_TRY(idx.alloc(ctx, n * sizeof(uint32_t)));
+  DSA_TRY(key2.alloc(ctx, n * sizeof(uint64_t)));
+  DSA_TRY(idx2.alloc(ctx, n * sizeof(uint32_t)));
+  k_tb_keys<<<stage_grid(ctx, n), STAGE_T, 0, ctx->stream>>>(d_in, n, key.as<uint64_t>(),
+                                                              idx.as<uint32_t>());
+  ++ctx->launches;
+  if (cudaGetLastError() != cudaSuccess) {
+    set_error("traceback job order launch failed");
+    return DSA_ERR_CUDA;
+  }
+  uint64_t* kk = key.as<uint64_t>();
+  uint32_t* vv = idx.as<uint32_t>();
+  // thread-path jobs have at most 4096 rows
+  DSA_TRY(launch_pair_sort(ctx, kk, vv, key2.as<uint64_t>(), idx2.as<uint32_t>(), n, 4096u,
+                           (uint32_t)TB_ORDER_WC_CAP));
+  k_tb_gather<<<stage_grid(ctx, n), STAGE_T, 0, ctx->stream>>>(d_in, vv, n, d_out);
+  ++ctx->launches;
+  if (cudaGetLastError() != cudaSuccess) {
+    set_error("traceback job order launch failed");
+    return DSA_ERR_CUDA;
+  }
+  return DSA_OK;
+}
 
 // CIGAR offsets of the jobs' hits from a device scan of their lengths: hit of
 // job x gets *d_base + (words of jobs before x); *d_base grows by the total.
