@@ -192,7 +192,9 @@ int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, uint64_t n)
 
 /* Access results.  Without DSA_RESULTS_ON_DEVICE the arrays are host copies
  * owned by `res` (the call synchronizes the stream); with it they are device
- * pointers.  `cigar` holds all CIGAR words; hit.cigar_off indexes it. */
+ * pointers.  `cigar` holds all CIGAR words; hit.cigar_off indexes it.  A
+ * hit's words are contiguous; the order of different hits' words in the
+ * array is unspecified (large batches are laid out in work order). */
 int dsa_res_get(dsa_res* res, const dsa_hit** hits, uint64_t* n_hits, const uint32_t** cigar,
                 uint64_t* n_cigar_words);
 /* DP cells of the score pass (sum over pairs of m*n) and the number of pairs
