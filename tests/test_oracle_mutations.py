@@ -2,7 +2,8 @@
 
 Each case below plants one mistake in a temporary copy of the oracle source
 (a transposed matrix lookup, a wrong gap cost, a wrong tie-break, a wrong
-boundary, a wrong traceback priority), builds it, and runs the brute-force
+boundary, a wrong traceback priority, a misplaced query slice or pair window
+in the batch dispatcher), builds it, and runs the brute-force
 and hand-worked pin suites against it in a child process.  Every mutant must
 fail at least one pin.  Nothing here touches a GPU.
 """
@@ -28,6 +29,12 @@ MUTANTS = {
                                      "if (AT(Fm, i, j) != AT(Fm, i - 1, j) - e) state = 0;"),
     "local_floor_missing": ("if (mode == ORC_LOCAL && h < 0) h = 0;\n      diag", "diag"),
     "profile_row_stride_dropped": ("P ? P + (size_t)(i - 1) * A", "P ? P + (size_t)(i - 1)"),
+    "pair_window_offset_dropped": ("ts += J->pair_toff[p]; n = J->pair_tlen[p];",
+                                   "n = J->pair_tlen[p];"),
+    "pair_window_offset_absolute": ("ts += J->pair_toff[p]; n = J->pair_tlen[p];",
+                                    "ts = J->t_codes + J->pair_toff[p]; n = J->pair_tlen[p];"),
+    "pair_query_slice_shifted": ("const uint8_t* qs = J->q_codes + J->q_off[qi];",
+                                 "const uint8_t* qs = J->q_codes + J->q_off[qi] + (qi > 0);"),
 }
 
 
@@ -44,7 +51,8 @@ def test_pins_catch_mutant(name, tmp_path):
     env = dict(os.environ, DSA_ORACLE_LIB=str(so_path))
     tests = [os.path.join(ROOT, "tests", "test_oracle_bruteforce.py"),
              os.path.join(ROOT, "tests", "test_oracle_golden.py"),
-             os.path.join(ROOT, "tests", "test_oracle_pssm.py")]
+             os.path.join(ROOT, "tests", "test_oracle_pssm.py"),
+             os.path.join(ROOT, "tests", "test_oracle_batch.py")]
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] + tests,
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
