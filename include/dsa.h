@@ -93,7 +93,7 @@ typedef struct {
   uint32_t target_id;
   uint64_t t_offset;
   uint32_t t_len;
-  uint32_t reserved; /* must be 0 */
+  uint32_t reserved; /* set to 0; kept for later use, no call reads it */
 } dsa_pair;
 
 /* One alignment result (the paper's alignment object, Sec. II.B.1: score,
@@ -322,8 +322,11 @@ int dsa_server_destroy(dsa_server* srv);
  * shares the array and no part of it needs to start at zero (each pair
  * writes its boundary row before reading it), so calls whose kernels overlap
  * on the GPU race on it: order them on one stream or synchronize between
- * them.  A pair whose ids, window, lengths or codes are out of range gets
- * score INT32_MIN and ends -2 instead of a result. */
+ * them.  The looked-up address belongs to the device's primary context and
+ * is kept for the life of the process: after a cudaDeviceReset of a device
+ * this entry point must not be called on that device again.  A pair whose
+ * ids, window, lengths or codes are out of range gets score INT32_MIN and
+ * ends -2 instead of a result; its `reserved` field is not read. */
 int dsa_score_pairs_noalloc(const uint8_t* d_q_codes, const uint64_t* d_q_offsets,
                             uint32_t n_queries, const uint8_t* d_t_codes,
                             const uint64_t* d_t_offsets, uint32_t n_targets,

@@ -65,7 +65,10 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) k_noalloc_pairs(
     if (ok) {
       m = (int32_t)(qoff[pr.query_id + 1] - qoff[pr.query_id]);
       const uint64_t tl = toff[pr.target_id + 1] - toff[pr.target_id];
-      ok = m >= 1 && pr.t_offset + pr.t_len <= tl && ((int64_t)m + pr.t_len + 2) < bound;
+      // window inside the target, tested without the sum t_offset + t_len (which
+      // wraps for offsets near 2^64)
+      ok = m >= 1 && pr.t_offset <= tl && pr.t_len <= tl - pr.t_offset &&
+           ((int64_t)m + pr.t_len + 2) < bound;
     }
     if (ok) {   // every residue code must index the matrix
       const uint8_t* qq = qcodes + qoff[pr.query_id];
@@ -145,7 +148,9 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) k_noalloc_pairs(
 }
 
 // Device address of g_noalloc_scratch per device, looked up once per device
-// (with that device current) on the first call made on it.
+// (with that device current) on the first call made on it.  The address
+// belongs to the device's primary context: it does not survive a
+// cudaDeviceReset of that device (the header says so).
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[64] = {};
 
