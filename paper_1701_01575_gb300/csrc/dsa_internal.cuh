@@ -387,9 +387,10 @@ int launch_cigar_offsets_scan(dsa_ctx* ctx, dsa_hit* d_hits, const TbJob* d_jobs
 
 // Device staging of the traceback of every hit of a result on the thread path
 // (jobs built, compacted and laid out on the device).  Returns DSA_OK, or
-// TB_STAGE_FALLBACK when some hit needs another path (nothing was changed).
+// TB_STAGE_FALLBACK when some hit needs another path or the decisions would
+// take more than `dir_limit` words in one launch (nothing was changed).
 constexpr int TB_STAGE_FALLBACK = 1;
-int traceback_device_staged(dsa_ctx* ctx, dsa_res* res, const TbBounds& B, const int8_t* d_matrix);
+int traceback_device_staged(dsa_ctx* ctx, dsa_res* res, const TbBounds& B, uint64_t dir_limit);
 
 int launch_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,
                      int A, int o, int e, int mode, uint32_t fe, const TbJob* d_jobs,
