@@ -292,7 +292,9 @@ def _sample_reads(rng, ref: np.ndarray, lens: np.ndarray, window: int, sub_rate:
     """Reads of the given lengths sampled from `ref` (forward strand), with their
     windows.  Per read, indel events hit its source slice (length + 64 slack) at
     rate `indel_rate`; reads without events are the slice with substitutions,
-    built in bulk.  Returns (SeqSet, pairs, origins)."""
+    built in bulk.  Returns (SeqSet, pairs, origins, clean): clean[k] is True
+    when read k is its source slice unchanged (no indel event in the slice
+    and no substitution)."""
     n_reads = len(lens)
     ref_len = len(ref)
     slack = 64
@@ -301,12 +303,14 @@ def _sample_reads(rng, ref: np.ndarray, lens: np.ndarray, window: int, sub_rate:
     off = np.zeros(n_reads + 1, dtype=np.uint64)
     off[1:] = np.cumsum(lens)
     codes = np.empty(int(off[-1]), dtype=np.uint8)
+    clean = np.zeros(n_reads, dtype=bool)
     for L in np.unique(lens):
         idx = np.flatnonzero((lens == L) & (n_events == 0))
         if len(idx) == 0:
             continue
         block = ref[origins[idx][:, None] + np.arange(L)[None, :]]
         hit = rng.random(block.shape) < sub_rate
+        clean[idx] = ~hit.any(axis=1)
         shift = rng.integers(1, 4, size=int(hit.sum())).astype(np.uint8)
         block[hit] = (block[hit] + shift) % 4
         codes[off[idx].astype(np.int64)[:, None] + np.arange(L)[None, :]] = block
@@ -324,7 +328,7 @@ def _sample_reads(rng, ref: np.ndarray, lens: np.ndarray, window: int, sub_rate:
     start = np.clip(start, 0, ref_len - window)
     pairs["t_offset"] = start.astype(np.uint64)
     pairs["t_len"] = window
-    return queries, pairs, origins
+    return queries, pairs, origins, clean
 
 
 def reads_vs_windows(seed: int = SEED_BASE + 2, n_reads: int = 1_000_000,
@@ -338,12 +342,12 @@ def reads_vs_windows(seed: int = SEED_BASE + 2, n_reads: int = 1_000_000,
     ref = rng.integers(0, 4, size=ref_len).astype(np.uint8)
     lens = np.where(np.arange(n_reads) < n_reads // 2, read_lens[0], read_lens[1]).astype(np.int64)
     rng.shuffle(lens)
-    queries, pairs, origins = _sample_reads(rng, ref, lens, window, sub_rate, indel_rate)
+    queries, pairs, origins, clean = _sample_reads(rng, ref, lens, window, sub_rate, indel_rate)
     db = SeqSet(ref, np.array([0, ref_len], dtype=np.uint64))
     return Workload("reads_vs_windows", queries, db, dna_matrix(1, -4), 6, 1, MODE_SEMIGLOBAL,
                     free_ends=FREE_T_BEGIN | FREE_T_END, pairs=pairs,
                     meta=dict(seed=seed, n_reads=n_reads, ref_len=ref_len,
-                              origins=origins.astype(np.int64)))
+                              origins=origins.astype(np.int64), clean=clean))
 
 
 def long_pairs(seed: int = SEED_BASE + 3, n_pairs: int = 64, lo: int = 10_000,
@@ -374,7 +378,7 @@ def reads_from_reference(rng, ref: np.ndarray, n_reads: int, read_len: int = 150
                          window: int = 500, sub_rate: float = 0.01, indel_rate: float = 0.001):
     """Reads sampled from `ref` (forward strand) with their windows: (SeqSet, pairs)."""
     lens = np.full(n_reads, read_len, dtype=np.int64)
-    queries, pairs, _ = _sample_reads(rng, ref, lens, window, sub_rate, indel_rate)
+    queries, pairs, _, _ = _sample_reads(rng, ref, lens, window, sub_rate, indel_rate)
     return queries, pairs
 
 

@@ -4,11 +4,15 @@
   seeded sample of targets (all queries), the top-10 of every query against
   the dense all-pairs result, and the traceback of every reported hit;
 * 1,000,000 reads in 500 bp windows: a seeded sample of 1,500 reads, score,
-  ends, begins and CIGAR;
-* 64 long DNA pairs (1e4-1e5), global and local: the three smallest pairs in
-  full against the oracle, and for every pair the CIGAR rescored under the gap
-  rule equals the reported score and spans begin..end.
+  ends, begins and CIGAR; every read planted without a mutation scores
+  exactly its length with one M run starting at its true origin;
+* 64 long DNA pairs (1e4-1e5), global and local: every pair of at most 4e8
+  cells in full against the oracle (score, ends, begins, CIGAR), and for
+  every pair the CIGAR rescored under the gap rule equals the reported score
+  and spans begin..end.
 """
+import concurrent.futures as cf
+
 import numpy as np
 import pytest
 
@@ -91,8 +95,18 @@ def test_reads_in_windows_full_size(ctx):
                                      int(x["q_end"]), int(x["t_end"]))
         got_c = cig[int(x["cigar_off"]):int(x["cigar_off"]) + int(x["cigar_len"])]
         assert (int(x["q_begin"]), int(x["t_begin"])) == (qb, tb) and got_c.tolist() == c.tolist()
-    # reads that carry no mutation score exactly their length at their origin
-    assert (h["score"] <= wl.queries.lengths).all()
+    # reads that carry no mutation score exactly their length (match +1) with
+    # one M run from their true origin; no read scores more than its length
+    lens = wl.queries.lengths
+    assert (h["score"] <= lens).all()
+    clean = wl.meta["clean"]
+    assert clean.sum() > 50_000
+    hc = h[clean]
+    assert (hc["score"] == lens[clean]).all()
+    assert ((hc["t_offset"] + hc["t_begin"].astype(np.uint64)).astype(np.int64)
+            == wl.meta["origins"][clean]).all()
+    assert (hc["q_begin"] == 0).all() and (hc["cigar_len"] == 1).all()
+    assert (cig[hc["cigar_off"].astype(np.int64)] == (lens[clean].astype(np.uint32) << 4)).all()
 
 
 @pytest.mark.parametrize("mode", [dsa.GLOBAL, dsa.LOCAL])
@@ -105,17 +119,27 @@ def test_long_pairs_full_size(ctx, mode):
     ctx.sync()
     h = r.hits()
     cig = r.cigar()
+    # the oracle's walk (12 bytes per cell of host memory) for every pair of at
+    # most 4e8 cells, three pairs at a time
     sizes = wl.queries.lengths * wl.pairs["t_len"].astype(np.int64)
-    for k in np.argsort(sizes)[:3]:
-        p = wl.pairs[k:k + 1]
-        sc, qe, te = oracle.score_pairs(wl.queries.codes, wl.queries.offsets, wl.db.codes,
-                                        wl.db.offsets, p["query_id"], p["target_id"], wl.matrix, 5, 2,
-                                        mode, 15)
-        assert (int(h["score"][k]), int(h["q_end"][k]), int(h["t_end"][k])) == (sc[0], qe[0], te[0])
-        qb, tb, c = oracle.traceback(wl.queries.seq(k), wl.db.seq(k), wl.matrix, 5, 2, mode, 15,
-                                     int(qe[0]), int(te[0]))
-        got_c = cig[int(h["cigar_off"][k]):int(h["cigar_off"][k]) + int(h["cigar_len"][k])]
-        assert (int(h["q_begin"][k]), int(h["t_begin"][k])) == (qb, tb) and got_c.tolist() == c.tolist()
+    small = [int(k) for k in np.argsort(sizes) if sizes[k] <= 400_000_000]
+    assert len(small) >= 10
+    p = wl.pairs[small]
+    sc, qe, te = oracle.score_pairs(wl.queries.codes, wl.queries.offsets, wl.db.codes,
+                                    wl.db.offsets, p["query_id"], p["target_id"], wl.matrix, 5, 2,
+                                    mode, 15)
+    assert (h["score"][small] == sc).all() and (h["q_end"][small] == qe).all()
+    assert (h["t_end"][small] == te).all()
+
+    def walk(k):
+        return oracle.traceback(wl.queries.seq(k), wl.db.seq(k), wl.matrix, 5, 2, mode, 15,
+                                int(h["q_end"][k]), int(h["t_end"][k]))
+
+    with cf.ThreadPoolExecutor(max_workers=3) as ex:
+        for k, (qb, tb, c) in zip(small, ex.map(walk, small)):
+            got_c = cig[int(h["cigar_off"][k]):int(h["cigar_off"][k]) + int(h["cigar_len"][k])]
+            assert (int(h["q_begin"][k]), int(h["t_begin"][k])) == (qb, tb), k
+            assert got_c.tolist() == c.tolist(), k
     for k, x in enumerate(h):
         c = cig[int(x["cigar_off"]):int(x["cigar_off"]) + int(x["cigar_len"])]
         ln = (c >> 4).astype(np.int64)
