@@ -247,11 +247,19 @@ struct IntraWork {
 };
 
 // d_pssm: position-specific rows (one per query residue of the set) or NULL.
+// anchored: strips end at each query's last row (global / semi-global kernel),
+// with `tpad` as the S + o of padding rows and absent queries.
 int launch_strip_profile(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix,
-                         const int8_t* d_pssm, int A, int o, const PackedPlan& plan);
+                         const int8_t* d_pssm, int A, int o, const PackedPlan& plan,
+                         bool anchored = false, int tpad = 0);
 int launch_inter_local16(dsa_ctx* ctx, const dsa_db* db, const PackedPlan& plan,
                          const InterWork& work, int o, int e, int smax, Scores out,
                          uint32_t n_targets_out);
+// Global / semi-global form of the inter-sequence kernel (end-anchored
+// strips); every target of the database, mode DSA_GLOBAL or DSA_SEMIGLOBAL.
+int launch_inter_glob16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const PackedPlan& plan,
+                        const InterWork& work, int mode, uint32_t fe, int o, int e, int smax,
+                        int smin, Scores out, uint32_t n_targets_out);
 int inter_blocks_per_sm();
 constexpr int INTER_WARPS = 8;
 constexpr int INTER_ROWS = 28;

@@ -335,19 +335,315 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
   }
 }
 
+// ---- global and semi-global form (Sec. II.C.2: DNW, DSG) ----
+//
+// Same work decomposition, staging and cell update as k_inter_local16, with
+// three differences:
+//   * no floor at 0: H = max(t, F) (max3_2u(t, F, t));
+//   * end-anchored strips: a query of m rows starts (W - m % W) % W rows into
+//     its first strip, so row m is the bottom register of its last strip.
+//     The padding rows above the query reproduce the row-0 boundary exactly
+//     (their S + o is 0 for a boundary -(o + (j-1)e), o for a free target
+//     begin), and the real rows' column-0 values are set per row;
+//   * result cells: the column at the lane's own target end n is parked in
+//     shared memory when the loop reaches it (its bottom row is H[m][n]; with
+//     a free query end its rows are scanned after the strip, smallest i
+//     first), and with a free target end the bottom row of the last strip is
+//     tracked column by column (smallest j first).  The candidates are merged
+//     by (score desc, j asc, i asc).
+// Range: every value of a real cell is at least -(3o + (m + n)e) (the path
+// along the boundaries), so pairs with 4o + (m + n + 2)e + |min S| + 64 below
+// 2^15 never wrap downward, and H - o never borrows between the halves; the
+// "-inf" of E and F is -2^15 + e, whose - e does not wrap.  Upward, as in
+// local mode, only the diagonal step raises a value, by at most max(S), so a
+// running maximum of H at or below 32767 - max(S) proves no cell wrapped.
+// Pairs outside either bound are flagged for the exact int32 rerun.  Columns
+// past a lane's own target end (its group's longer targets) are computed
+// with a profile value of 0 for the padding residue; they feed no real cell,
+// and the running maximum leaves them out.
+struct GlobArgs {
+  int mode;
+  uint32_t fe;
+  int e;
+  int smin;
+  const uint32_t* qlen;   // query lengths
+  const uint32_t* slen;   // target lengths in the length-sorted order
+};
+
+__global__ void __launch_bounds__(NT, 2) k_inter_glob16(const InterArgs A, const GlobArgs G) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint64_t bars[2];
+  __shared__ uint32_t s_item;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const uint32_t cstride = replica_stride(A.R);
+  const uint32_t bufbytes = NCOPY * cstride;
+  // the column at the lane's own target end, parked for the result: [row][thread]
+  volatile uint32_t* const park = reinterpret_cast<volatile uint32_t*>(smem + 2 * bufbytes);
+  uint2* const ring = reinterpret_cast<uint2*>(smem + 2 * bufbytes + W * NT * sizeof(uint32_t)) + tid;
+  const uint32_t strip_words = (uint32_t)A.R * PITCH;
+  constexpr uint32_t BIAS2 = 0x80008000u;
+  const uint32_t neg_e2 = A.neg_e2;
+  const uint32_t o2 = ((uint32_t)A.o << 16) | (uint32_t)A.o;
+  const int o = A.o, e = G.e;
+  const uint32_t NEGG2 = ((uint32_t)e << 16) | (uint32_t)e;   // -2^15 + e in both halves
+  const bool sg = G.mode == DSA_SEMIGLOBAL;
+  const bool tb_free = sg && (G.fe & DSA_FREE_T_BEGIN);
+  const bool qb_free = sg && (G.fe & DSA_FREE_Q_BEGIN);
+  const bool qe_free = sg && (G.fe & DSA_FREE_Q_END);
+  const bool te_free = sg && (G.fe & DSA_FREE_T_END);
+  // boundary values of H: row 0 at column j, column 0 at row i (rows <= 0:
+  // row 0 itself or the padding rows above a query)
+  auto row0 = [&](int j) { return (j == 0 || tb_free) ? 0 : -(o + (j - 1) * e); };
+  auto col0 = [&](int i) { return (i <= 0 || qb_free) ? 0 : -(o + (i - 1) * e); };
+  auto off2 = [](int lo, int hi) { return pack2(lo, hi) ^ BIAS2; };
+  const int hmax_ok = A.T;
+
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t phase0 = 0, phase1 = 0;
+  uint2* const scr_base = A.scratch + (uint64_t)blockIdx.x * A.scratch_cols * NT + tid;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(A.counter, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    __syncthreads();
+    if (item >= A.n_items) break;
+    const uint32_t p = A.items[2 * item];
+    const uint32_t g0 = A.items[2 * item + 1];
+    const uint32_t ns = A.nstrips[p];
+    const uint32_t sb = A.sbase[p];
+    const uint32_t* psrc = A.prof + (size_t)sb * strip_words;
+    if (tid == 0) {
+      issue_strip(A, smem, &bars[0], psrc, cstride);
+      if (ns > 1) issue_strip(A, smem + bufbytes, &bars[1], psrc + strip_words, cstride);
+    }
+    const uint32_t g = g0 + warp;
+    const bool gvalid = g < A.n_groups;
+    const uint32_t nlen = gvalid ? A.glen[g] : 0u;
+    const uint32_t ncol = (nlen + 3u) & ~3u;
+    const uint32_t st = g * 32u + lane;
+    const bool tvalid = gvalid && st < A.n_targets;
+    const int nl = tvalid ? (int)G.slen[st] : -1;   // this lane's target length
+    const uint4* res = reinterpret_cast<const uint4*>(A.il + (gvalid ? A.gbase[g] : 0)) + lane;
+
+    // per half, over the strips of its query: best of column n so far (free
+    // query end; starts at the candidate (0, n)) and the running maximum of H
+    int cb_lo = 0, cb_hi = 0, ci_lo = 0, ci_hi = 0;
+    uint32_t runmax = 0;
+
+    for (uint32_t s = 0; s < ns; ++s) {
+      const int b = s & 1;
+      const uint32_t par = b ? (phase1 & 1u) : (phase0 & 1u);
+      const bool ok = mbar_wait_bounded(&bars[b], par, WAIT_LIMIT_NS);
+      if (b) ++phase1; else ++phase0;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(A.status, DSA_ERR_DEVICE_TIMEOUT);
+        mbar_wait_bounded(&bars[0], phase0 & 1u, WAIT_LIMIT_NS);
+        mbar_wait_bounded(&bars[1], phase1 & 1u, WAIT_LIMIT_NS);
+        return;
+      }
+      const uint8_t* pbuf = smem + b * bufbytes + (lane & 7) * cstride;
+      const StripMeta md = A.meta[sb + s];
+      const uint32_t ka = md.ka & ~LAST, kb = md.kb & ~LAST;
+      const bool last_a = (md.ka & LAST) && md.qa != NONE;
+      const bool last_b = (md.kb & LAST) && md.qb != NONE;
+      const int ma = md.qa != NONE ? (int)G.qlen[md.qa] : 0;
+      const int mb = md.qb != NONE ? (int)G.qlen[md.qb] : 0;
+      // 0-based query row of the strip's first row (negative: padding rows)
+      const int ia0 = (int)ka * W - (W - ma % W) % W;
+      const int ib0 = (int)kb * W - (W - mb % W) % W;
+      if (ka == 0) { cb_lo = row0(nl); ci_lo = 0; runmax &= 0xFFFF0000u; }
+      if (kb == 0) { cb_hi = row0(nl); ci_hi = 0; runmax &= 0x0000FFFFu; }
+      const uint32_t keep = (ka == 0 ? 0u : 0x0000FFFFu) | (kb == 0 ? 0u : 0xFFFF0000u);
+      const bool first = keep == 0;
+
+      uint32_t Ho[W], E[W];
+#pragma unroll
+      for (int r = 0; r < W; ++r) {
+        Ho[r] = off2(col0(ia0 + r + 1) - o, col0(ib0 + r + 1) - o);
+        E[r] = NEGG2;
+      }
+      uint32_t diag = off2(col0(ia0) - o, col0(ib0) - o);
+      // row-0 boundary as (H - o, F of row 1) = (B(j) - o, B(j) - o), per column
+      uint32_t bt = off2(row0(1) - o, row0(1) - o);
+      const uint32_t bt_step = tb_free ? 0u : neg_e2;
+      // bottom row of a last strip (row m), free target end: best H - o over
+      // j <= n, smallest j first, from the candidate (m, 0); a half that does
+      // not end here holds the largest value, which nothing exceeds
+      uint32_t rthr = 0xFFFFFFFFu;
+      int rj_lo = 0, rj_hi = 0;
+      if (te_free) {
+        if (last_a) rthr = (rthr & 0xFFFF0000u) | (off2(col0(ma) - o, 0) & 0xFFFFu);
+        if (last_b) rthr = (rthr & 0x0000FFFFu) | (off2(0, col0(mb) - o) & 0xFFFF0000u);
+      }
+      uint2* scr = scr_base;
+      uint4 rv = make_uint4(0, 0, 0, 0);
+
+      auto fetch = [&](uint32_t c4x, uint32_t slot) {
+        if (c4x < ncol) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            cp_async8(ring + (slot * 4 + k) * NT, scr + (uint64_t)(c4x + k) * NT);
+        }
+        cp_async_commit();
+      };
+      if (!first) {
+        fetch(0, 0);
+        fetch(4, 1);
+      }
+      uint32_t slot = 0;
+      for (uint32_t c4 = 0; c4 < ncol; c4 += 4, slot = slot == RING - 1 ? 0 : slot + 1) {
+        if ((c4 & 15u) == 0) rv = __ldg(res + (c4 >> 4) * 32u);
+        const uint32_t sel = (c4 >> 2) & 3u;
+        const uint32_t word = sel == 0 ? rv.x : sel == 1 ? rv.y : sel == 2 ? rv.z : rv.w;
+        uint32_t bnd[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          bnd[k] = bt;
+          bt = __vadd2(bt, bt_step);
+        }
+        uint2 top[4];
+        if (!first) {
+          fetch(c4 + 8, slot == 0 ? RING - 1 : slot - 1);
+          cp_async_wait<2>();
+#pragma unroll
+          for (int k = 0; k < 4; ++k) top[k] = ring[(slot * 4 + k) * NT];
+          if (keep != 0xFFFFFFFFu) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              top[k].x = (top[k].x & keep) | (bnd[k] & ~keep);
+              top[k].y = (top[k].y & keep) | (bnd[k] & ~keep);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) top[k] = make_uint2(bnd[k], bnd[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t a = (word >> (8 * k)) & 0xFFu;
+          const uint4* prow = reinterpret_cast<const uint4*>(pbuf + a * (PITCH * 4u));
+          uint32_t F = top[k].y;
+          uint32_t d = diag;
+          diag = top[k].x;
+          uint32_t cm = 0, hprev = 0;
+#pragma unroll
+          for (int q4 = 0; q4 < W / 4; ++q4) {
+            const uint4 pv = prow[q4];
+            const uint32_t pr[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int r = q4 * 4 + u;
+              const uint32_t old = Ho[r];
+              E[r] = addmax2u(E[r], neg_e2, old);
+              const uint32_t t = addmax2u(d, pr[u], E[r]);
+              const uint32_t h = max3_2u(t, F, t);
+              Ho[r] = h - o2;
+              F = addmax2u(F, neg_e2, Ho[r]);
+              d = old;
+              if (r & 1) cm = max3_2u(cm, hprev, h);
+              else hprev = h;
+            }
+          }
+          scr[(uint64_t)(c4 + k) * NT] = make_uint2(Ho[W - 1], F);
+          const int j = (int)c4 + k + 1;
+          // columns past the lane's target end feed no real cell (values only
+          // move right and down) and may wrap in a long group: left out
+          if (j <= nl) runmax = __vmaxu2(runmax, cm);
+          if (j == nl) {   // the lane's own target end: park the column
+#pragma unroll
+            for (int r = 0; r < W; ++r) park[r * NT + tid] = Ho[r];
+          }
+          if (te_free) {
+            const uint32_t cur = Ho[W - 1];
+            if (__vmaxu2(cur, rthr) != rthr && j <= nl) {
+              if ((cur & 0xFFFFu) > (rthr & 0xFFFFu)) {
+                rthr = (rthr & 0xFFFF0000u) | (cur & 0xFFFFu);
+                rj_lo = j;
+              }
+              if ((cur >> 16) > (rthr >> 16)) {
+                rthr = (rthr & 0x0000FFFFu) | (cur & 0xFFFF0000u);
+                rj_hi = j;
+              }
+            }
+          }
+        }
+      }
+      cp_async_wait<0>();
+      if (tvalid) {
+        // H of half `sh` (0 / 16) from a packed H - o in offset binary
+        auto hval = [&](uint32_t w, int sh) { return (int)((w >> sh) & 0xFFFFu) - 0x8000 + o; };
+        auto finish = [&](int sh, int i0, bool last, int m, uint32_t q, int& cb, int& ci, int rj) {
+          if (qe_free) {   // column n of this strip's real rows, smallest i first
+            for (int r = 0; r < W; ++r) {
+              const int i = i0 + r + 1;
+              const int v = hval(park[r * NT + tid], sh);
+              if (i >= 1 && v > cb) { cb = v; ci = i; }
+            }
+          }
+          if (!last) return;
+          int bs = hval(park[(W - 1) * NT + tid], sh), bi = m, bj = nl;   // (m, n)
+          if (qe_free && (cb > bs || (cb == bs && ci < bi))) { bs = cb; bi = ci; }
+          if (te_free) {
+            const int rvv = hval(rthr, sh);
+            if (rvv > bs || (rvv == bs && rj < bj)) { bs = rvv; bi = m; bj = rj; }
+          }
+          const int hmax = (int)((runmax >> sh) & 0xFFFFu) - 0x8000;
+          const int64_t low = 4ll * o + (int64_t)(m + nl + 2) * e + (G.smin < 0 ? -G.smin : 0) + 64;
+          const uint64_t idx = (uint64_t)q * A.n_out_t + A.perm[st];
+          A.o_score[idx] = bs;
+          A.o_qend[idx] = bi - 1;
+          A.o_tend[idx] = bj - 1;
+          A.o_flag[idx] = (hmax > hmax_ok || low >= 32768) ? 1 : 0;
+        };
+        if (md.qa != NONE) finish(0, ia0, last_a, ma, md.qa, cb_lo, ci_lo, rj_lo);
+        if (md.qb != NONE) finish(16, ib0, last_b, mb, md.qb, cb_hi, ci_hi, rj_hi);
+      }
+      __syncthreads();
+      if (tid == 0 && s + 2 < ns) {
+        fence_proxy_async_smem();
+        issue_strip(A, smem + b * bufbytes, &bars[b], psrc + (s + 2) * strip_words, cstride);
+      }
+    }
+  }
+}
+
 // Packed profile of every strip: [strip][residue a][row r] int16x2 =
 // (S[qa_i][a] + o, S[qb_i][a] + o) with i = rows * (strip index in the query) + r;
 // rows past a query's end, absent queries and the padding residue a = A get
 // NEG16.  With a position-specific profile P (row per query residue of the
 // set, Sec. II.C.2's user-defined scoring) the score is P[qoff + i][a].
+//
+// End-anchored form (anchored = 1, the global / semi-global kernel): a query
+// of m rows starts (rows - m % rows) % rows rows into its first strip, so its
+// last row is the bottom row of its last strip.  The padding rows above it,
+// absent queries and the padding residue get values that keep every cell
+// inside the int16 range: `tpad` (S + o) for padding rows and absent queries,
+// 0 for the padding residue of a real row.
 __global__ void k_strip_profile(const uint8_t* __restrict__ qcodes,
                                 const uint64_t* __restrict__ qoff, const uint32_t* __restrict__ qlen,
                                 const StripMeta* __restrict__ meta, uint32_t n_strips,
                                 const int8_t* __restrict__ S, const int8_t* __restrict__ P, int A,
-                                int R, int rows, int pitch, int o, uint32_t* __restrict__ prof) {
+                                int R, int rows, int pitch, int o, int anchored, int tpad,
+                                uint32_t* __restrict__ prof) {
   auto sub = [&](uint32_t q, int i, int a) -> int {
     const uint64_t k = qoff[q] + (uint64_t)i;
     return P ? (int)P[k * A + a] : (int)S[qcodes[k] * A + a];
+  };
+  auto anchored_val = [&](uint32_t q, uint32_t kq, int r, int a) -> int {
+    if (q == NONE) return tpad;
+    const int m = (int)qlen[q];
+    const int i = (int)(kq & ~LAST) * rows + r - (rows - m % rows) % rows;
+    if (i < 0) return tpad;
+    if (a >= A) return 0;
+    return sub(q, i, a) + o;
   };
   const uint64_t total = (uint64_t)n_strips * R * pitch;
   for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < total;
@@ -359,11 +655,14 @@ __global__ void k_strip_profile(const uint8_t* __restrict__ qcodes,
     int lo = NEG16, hi = NEG16;
     if (r >= rows) {
       // row padding, never read
+    } else if (anchored) {
+      lo = anchored_val(md.qa, md.ka, r, a);
+      hi = anchored_val(md.qb, md.kb, r, a);
     } else if (a < A && md.qa != NONE) {
       const int i = (int)(md.ka & ~LAST) * rows + r;
       if (i < (int)qlen[md.qa]) lo = sub(md.qa, i, a) + o;
     }
-    if (r < rows && a < A && md.qb != NONE) {
+    if (!anchored && r < rows && a < A && md.qb != NONE) {
       const int i = (int)(md.kb & ~LAST) * rows + r;
       if (i < (int)qlen[md.qb]) hi = sub(md.qb, i, a) + o;
     }
@@ -376,14 +675,16 @@ __global__ void k_strip_profile(const uint8_t* __restrict__ qcodes,
 int inter_blocks_per_sm() { return 2; }
 
 int launch_strip_profile(dsa_ctx* ctx, const dsa_db* qs, const int8_t* d_matrix,
-                         const int8_t* d_pssm, int A, int o, const PackedPlan& plan) {
+                         const int8_t* d_pssm, int A, int o, const PackedPlan& plan,
+                         bool anchored, int tpad) {
   if (plan.n_strips == 0) return DSA_OK;
   const uint64_t total = (uint64_t)plan.n_strips * plan.R * plan.pitch;
   uint64_t blocks = std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->sm_count * 8);
   k_strip_profile<<<(unsigned)blocks, 256, 0, ctx->stream>>>(qs->d_codes, qs->d_off, qs->d_len,
                                                             plan.d_meta, plan.n_strips, d_matrix,
                                                             d_pssm, A, plan.R, plan.rows,
-                                                            plan.pitch, o, plan.d_prof);
+                                                            plan.pitch, o, anchored ? 1 : 0, tpad,
+                                                            plan.d_prof);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   return DSA_OK;
@@ -426,6 +727,50 @@ int launch_inter_local16(dsa_ctx* ctx, const dsa_db* db, const PackedPlan& plan,
   ctx->release(scr, scr_bytes);
   if (err != cudaSuccess) {
     set_error("k_inter_local16 launch: %s", cudaGetErrorString(err));
+    return DSA_ERR_CUDA;
+  }
+  return DSA_OK;
+}
+
+int launch_inter_glob16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const PackedPlan& plan,
+                        const InterWork& work, int mode, uint32_t fe, int o, int e, int smax,
+                        int smin, Scores out, uint32_t n_targets_out) {
+  if (work.n_items == 0) return DSA_OK;
+  InterArgs A;
+  A.il = db->d_il; A.gbase = db->d_gbase; A.glen = db->d_glen; A.perm = db->d_perm;
+  A.n_targets = db->n; A.n_groups = db->n_groups;
+  A.prof = plan.d_prof; A.meta = plan.d_meta; A.sbase = plan.d_sbase; A.nstrips = plan.d_ns;
+  A.R = plan.R;
+  A.neg_o2 = (uint32_t)((-o) & 0xFFFF) | ((uint32_t)((-o) & 0xFFFF) << 16);
+  A.neg_e2 = (uint32_t)((-e) & 0xFFFF) | ((uint32_t)((-e) & 0xFFFF) << 16);
+  A.o = o;
+  A.T = 32767 - (smax > 0 ? smax : 0);
+  A.items = work.d_items; A.n_items = work.n_items;
+  A.counter = ctx->d_counters;
+  GlobArgs G;
+  G.mode = mode; G.fe = fe; G.e = e; G.smin = smin;
+  G.qlen = qs->d_len; G.slen = db->d_slen;
+  const int grid = (int)std::min<uint64_t>(work.n_items, (uint64_t)ctx->sm_count * inter_blocks_per_sm());
+  const uint64_t cols = ((uint64_t)work.max_glen + 3) & ~3ull;
+  A.scratch_cols = cols;
+  const size_t scr_bytes = (size_t)grid * cols * NT * sizeof(uint2);
+  void* scr = nullptr;
+  DSA_TRY(ctx->alloc(&scr, scr_bytes));
+  A.scratch = static_cast<uint2*>(scr);
+  A.o_score = out.score; A.o_qend = out.q_end; A.o_tend = out.t_end; A.o_flag = out.flag;
+  A.n_out_t = n_targets_out;
+  A.status = ctx->d_status;
+  const size_t smem = 2ull * NCOPY * replica_stride(plan.R) + (size_t)W * NT * sizeof(uint32_t) +
+                      (size_t)RING * 4 * NT * sizeof(uint2);
+  DSA_CUDA_TRY(cudaFuncSetAttribute(k_inter_glob16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  DSA_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), ctx->stream));
+  k_inter_glob16<<<grid, NT, smem, ctx->stream>>>(A, G);
+  ++ctx->launches;
+  cudaError_t err = cudaGetLastError();
+  ctx->release(scr, scr_bytes);
+  if (err != cudaSuccess) {
+    set_error("k_inter_glob16 launch: %s", cudaGetErrorString(err));
     return DSA_ERR_CUDA;
   }
   return DSA_OK;

@@ -109,12 +109,16 @@ int ilog2_bin(uint64_t x) {
   return b;
 }
 
-// Packed score pass (local, int16x2): targets of groups longer than
+// Packed score pass (int16x2).  Local: targets of groups longer than
 // `long_thr` go to the wavefront kernel on the side stream, the rest to the
-// inter-sequence kernel.  The results do not depend on long_thr, only the time.
+// inter-sequence kernel; the results do not depend on long_thr, only the
+// time.  Global / semi-global: every target on the end-anchored form of the
+// inter-sequence kernel.
 int packed_score(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
                  const int8_t* d_mat, const int8_t* d_pssm, int A, int o, int e, const Validated& v, Scores out,
-                 uint32_t long_thr) {
+                 uint32_t long_thr, int mode = DSA_LOCAL, uint32_t fe = 15) {
+  const bool local = mode == DSA_LOCAL;
+  if (!local) long_thr = UINT32_MAX;
   const uint32_t nq = qs->n, nt = db->n;
   const int R = A + 1;
   std::vector<uint32_t> qorder(nq);
@@ -264,7 +268,10 @@ int packed_score(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
   spl.d_ns = d_sns.as<uint32_t>();
   spl.d_prof = d_sprof.as<uint32_t>();
   iw.d_items = d_items.as<uint32_t>();
-  DSA_TRY(launch_strip_profile(ctx, qs, d_mat, d_pssm, A, o, spl));
+  // end-anchored strips: the padding rows above a query reproduce row 0
+  // (S + o = 0 against the boundary -(o + (j-1)e), o against a free begin)
+  const int tpad = (mode == DSA_SEMIGLOBAL && (fe & DSA_FREE_T_BEGIN)) ? o : 0;
+  DSA_TRY(launch_strip_profile(ctx, qs, d_mat, d_pssm, A, o, spl, !local, tpad));
   if (n_long) {
     DSA_TRY(upload(ctx, d_pmeta, pmeta));
     DSA_TRY(upload(ctx, d_pbase, p_sbase));
@@ -289,7 +296,10 @@ int packed_score(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
     DSA_CUDA_TRY(cudaEventRecord(ctx->join_ev, ctx->side));
   }
   phase_begin(res, PH_INTER);
-  DSA_TRY(launch_inter_local16(ctx, db, spl, iw, o, e, v.smax, out, nt));
+  if (local)
+    DSA_TRY(launch_inter_local16(ctx, db, spl, iw, o, e, v.smax, out, nt));
+  else
+    DSA_TRY(launch_inter_glob16(ctx, db, qs, spl, iw, mode, fe, o, e, v.smax, v.smin, out, nt));
   phase_end(res, PH_INTER);
   if (n_long) DSA_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->join_ev, 0));
   return DSA_OK;
@@ -401,8 +411,11 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
                      uint32_t fe, const int8_t* d_mat, const int8_t* d_pssm, int A, int o, int e, const Validated& v,
                      uint32_t flags, Scores out, uint64_t* n_rerun) {
   const uint32_t nq = qs->n, nt = db->n;
-  const bool packed = mode == DSA_LOCAL && !(flags & (DSA_FORCE_INT32 | DSA_PLAIN_FORM)) &&
-                      o >= 1 && o + e <= 4096 && v.smax + o < 8192 && v.smin > -8192;
+  // int16x2 lanes: local with the saturation flag; global and semi-global
+  // with the range flags of the end-anchored kernel (both reruns exact)
+  const bool packed = !(flags & (DSA_FORCE_INT32 | DSA_PLAIN_FORM)) &&
+                      (mode == DSA_LOCAL ? o >= 1 : true) && o + e <= 4096 &&
+                      v.smax + o < 8192 && v.smin > -8192;
   *n_rerun = 0;
   if (!packed) {
     // exact int32: one launch per query over every target (input order)
@@ -432,7 +445,10 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
 
   // ---- packed path ----
   DSA_TRY(ensure_interleaved(ctx, db));
-  DSA_TRY(run_packed_tuned(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out));
+  if (mode == DSA_LOCAL)
+    DSA_TRY(run_packed_tuned(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out));
+  else
+    DSA_TRY(packed_score(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out, UINT32_MAX, mode, fe));
 
   // ---- exact int32 rerun of saturated pairs ----
   const uint64_t n_out = (uint64_t)nq * nt;
