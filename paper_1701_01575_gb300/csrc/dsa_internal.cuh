@@ -262,7 +262,8 @@ int launch_inter_glob16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const 
                         int smin, Scores out, uint32_t n_targets_out);
 int inter_blocks_per_sm();
 constexpr int INTER_WARPS = 8;
-constexpr int INTER_ROWS = 28;
+constexpr int INTER_ROWS = 28;         // strip rows of the packed inter-sequence kernels
+constexpr int INTER_ROWS_SHORT = 20;   // their short-strip variant (short queries)
 
 // Long-target intra-sequence (wavefront) kernel; each unit of `plan` must
 // hold one query per half (no stream switches).  Runs on `stream`

@@ -10,7 +10,7 @@
 //     instruction advances two cells; per-strip metadata says when a half
 //     starts a new query (its best and its top boundary restart) or ends one
 //     (its result is written);
-//   * a query is processed in strips of 32 rows held in registers; the loop
+//   * a query is processed in strips of W = INTER_ROWS (28) rows held in registers; the loop
 //     runs over the target's residues; the strip's bottom row (H - o and the
 //     next row's F) goes to a per-CTA boundary buffer and is read back by the
 //     next strip through a small shared-memory ring that per-thread
@@ -51,10 +51,14 @@
 #include "dsa_internal.cuh"
 #include "dpx.cuh"
 
+#include <type_traits>
+
 namespace dsa {
 namespace {
 
-constexpr int W = INTER_ROWS;    // query rows per strip
+// query rows per strip: a template parameter of both kernels (INTER_ROWS,
+// or the shorter INTER_ROWS_SHORT that wastes fewer padding rows on short
+// queries); the autotuner picks one per workload shape
 constexpr int NW = INTER_WARPS;  // warps per CTA
 constexpr int NT = NW * 32;
 constexpr int NCOPY = 8;         // profile replicas (one per lane of a quarter-warp)
@@ -93,7 +97,8 @@ struct InterArgs {
 // then sits in bank group (c + k) mod 8 whatever a is, so the 8 lanes of a
 // quarter-warp never share a bank group.
 constexpr int PITCH = 32;
-static_assert(W <= PITCH, "strip rows must fit one padded profile row");
+static_assert(INTER_ROWS <= PITCH && INTER_ROWS_SHORT <= PITCH,
+              "strip rows must fit one padded profile row");
 
 // Bytes between profile replicas: at least one strip profile (R x PITCH x 4 B),
 // a multiple of 16, and 16 (mod 128) so replica c starts in bank group c.
@@ -110,6 +115,7 @@ __device__ __forceinline__ void issue_strip(const InterArgs& A, uint8_t* buf, ui
   for (int c = 0; c < NCOPY; ++c) bulk_g2s(buf + c * cstride, src, bytes, bar);
 }
 
+template <int W>
 __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bars[2];
@@ -355,8 +361,8 @@ __global__ void __launch_bounds__(NT, 2) k_inter_local16(const InterArgs A) {
 // along the boundaries), so pairs with 4o + (m + n + 2)e + |min S| + 64 below
 // 2^15 never wrap downward, and H - o never borrows between the halves; the
 // "-inf" of E and F is -2^15 + e, whose - e does not wrap.  Upward, as in
-// local mode, only the diagonal step raises a value, by at most max(S), so a
-// running maximum of H at or below 32767 - max(S) proves no cell wrapped.
+// local mode, only the diagonal step raises a value, by at most max(S), so if
+// no column maximum of H passes 32767 - max(S), no cell wrapped.
 // Pairs outside either bound are flagged for the exact int32 rerun.  Columns
 // past a lane's own target end (its group's longer targets) are computed
 // with a profile value of 0 for the padding residue; they feed no real cell,
@@ -366,14 +372,24 @@ struct GlobArgs {
   uint32_t fe;
   int e;
   int smin;
+  uint32_t hmax2;         // 32767 - max(S) in both halves, offset binary
   const uint32_t* qlen;   // query lengths
   const uint32_t* slen;   // target lengths in the length-sorted order
 };
 
+// TB: free target begin (row 0 is 0), TE: free target end (row m is
+// tracked): compile-time, so each form carries only the state it uses.
+template <int W, bool TB, bool TE>
 __global__ void __launch_bounds__(NT, 2) k_inter_glob16(const InterArgs A, const GlobArgs G) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bars[2];
   __shared__ uint32_t s_item;
+  // per thread and half, kept out of registers (read once per strip): best
+  // of column n so far and its row (free query end; starts at (0, n)), and
+  // the column of row m's best (free target end)
+  __shared__ int s_cb[2][NT], s_ci[2][NT], s_rj[2][NT];
+  // per thread: bit h set when half h of the current query passed 32767 - max S
+  __shared__ uint32_t s_sat[NT];
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
@@ -388,17 +404,17 @@ __global__ void __launch_bounds__(NT, 2) k_inter_glob16(const InterArgs A, const
   const uint32_t o2 = ((uint32_t)A.o << 16) | (uint32_t)A.o;
   const int o = A.o, e = G.e;
   const uint32_t NEGG2 = ((uint32_t)e << 16) | (uint32_t)e;   // -2^15 + e in both halves
+  const uint32_t neg_e4 = pack2(-4 * e, -4 * e);              // four columns of the boundary
   const bool sg = G.mode == DSA_SEMIGLOBAL;
-  const bool tb_free = sg && (G.fe & DSA_FREE_T_BEGIN);
+  constexpr bool tb_free = TB;
+  constexpr bool te_free = TE;
   const bool qb_free = sg && (G.fe & DSA_FREE_Q_BEGIN);
   const bool qe_free = sg && (G.fe & DSA_FREE_Q_END);
-  const bool te_free = sg && (G.fe & DSA_FREE_T_END);
   // boundary values of H: row 0 at column j, column 0 at row i (rows <= 0:
   // row 0 itself or the padding rows above a query)
   auto row0 = [&](int j) { return (j == 0 || tb_free) ? 0 : -(o + (j - 1) * e); };
   auto col0 = [&](int i) { return (i <= 0 || qb_free) ? 0 : -(o + (i - 1) * e); };
   auto off2 = [](int lo, int hi) { return pack2(lo, hi) ^ BIAS2; };
-  const int hmax_ok = A.T;
 
   if (tid == 0) {
     mbar_init(&bars[0], 1);
@@ -433,10 +449,7 @@ __global__ void __launch_bounds__(NT, 2) k_inter_glob16(const InterArgs A, const
     const int nl = tvalid ? (int)G.slen[st] : -1;   // this lane's target length
     const uint4* res = reinterpret_cast<const uint4*>(A.il + (gvalid ? A.gbase[g] : 0)) + lane;
 
-    // per half, over the strips of its query: best of column n so far (free
-    // query end; starts at the candidate (0, n)) and the running maximum of H
-    int cb_lo = 0, cb_hi = 0, ci_lo = 0, ci_hi = 0;
-    uint32_t runmax = 0;
+    s_sat[tid] = 0;
 
     for (uint32_t s = 0; s < ns; ++s) {
       const int b = s & 1;
@@ -452,15 +465,19 @@ __global__ void __launch_bounds__(NT, 2) k_inter_glob16(const InterArgs A, const
       const uint8_t* pbuf = smem + b * bufbytes + (lane & 7) * cstride;
       const StripMeta md = A.meta[sb + s];
       const uint32_t ka = md.ka & ~LAST, kb = md.kb & ~LAST;
-      const bool last_a = (md.ka & LAST) && md.qa != NONE;
-      const bool last_b = (md.kb & LAST) && md.qb != NONE;
-      const int ma = md.qa != NONE ? (int)G.qlen[md.qa] : 0;
-      const int mb = md.qb != NONE ? (int)G.qlen[md.qb] : 0;
-      // 0-based query row of the strip's first row (negative: padding rows)
-      const int ia0 = (int)ka * W - (W - ma % W) % W;
-      const int ib0 = (int)kb * W - (W - mb % W) % W;
-      if (ka == 0) { cb_lo = row0(nl); ci_lo = 0; runmax &= 0xFFFF0000u; }
-      if (kb == 0) { cb_hi = row0(nl); ci_hi = 0; runmax &= 0x0000FFFFu; }
+      // the query rows of each half in this strip: m, the 0-based row of the
+      // strip's first row (negative: padding rows), whether row m is here
+      auto geom = [&](uint32_t q, uint32_t kq, int& m, int& i0, bool& last) {
+        m = q != NONE ? (int)G.qlen[q] : 0;
+        i0 = (int)(kq & ~LAST) * W - (W - m % W) % W;
+        last = (kq & LAST) && q != NONE;
+      };
+      int ma, mb, ia0, ib0;
+      bool last_a, last_b;
+      geom(md.qa, md.ka, ma, ia0, last_a);
+      geom(md.qb, md.kb, mb, ib0, last_b);
+      if (ka == 0) { s_cb[0][tid] = row0(nl); s_ci[0][tid] = 0; s_sat[tid] &= ~1u; }
+      if (kb == 0) { s_cb[1][tid] = row0(nl); s_ci[1][tid] = 0; s_sat[tid] &= ~2u; }
       const uint32_t keep = (ka == 0 ? 0u : 0x0000FFFFu) | (kb == 0 ? 0u : 0xFFFF0000u);
       const bool first = keep == 0;
 
@@ -471,14 +488,16 @@ __global__ void __launch_bounds__(NT, 2) k_inter_glob16(const InterArgs A, const
         E[r] = NEGG2;
       }
       uint32_t diag = off2(col0(ia0) - o, col0(ib0) - o);
-      // row-0 boundary as (H - o, F of row 1) = (B(j) - o, B(j) - o), per column
+      // row-0 boundary as (H - o, F of row 1) = (B(j) - o, B(j) - o) at the
+      // first column of the current block of 4 (only read where a half starts
+      // a query)
       uint32_t bt = off2(row0(1) - o, row0(1) - o);
-      const uint32_t bt_step = tb_free ? 0u : neg_e2;
       // bottom row of a last strip (row m), free target end: best H - o over
       // j <= n, smallest j first, from the candidate (m, 0); a half that does
       // not end here holds the largest value, which nothing exceeds
       uint32_t rthr = 0xFFFFFFFFu;
-      int rj_lo = 0, rj_hi = 0;
+      s_rj[0][tid] = 0;
+      s_rj[1][tid] = 0;
       if (te_free) {
         if (last_a) rthr = (rthr & 0xFFFF0000u) | (off2(col0(ma) - o, 0) & 0xFFFFu);
         if (last_b) rthr = (rthr & 0x0000FFFFu) | (off2(0, col0(mb) - o) & 0xFFFF0000u);
@@ -503,12 +522,6 @@ __global__ void __launch_bounds__(NT, 2) k_inter_glob16(const InterArgs A, const
         if ((c4 & 15u) == 0) rv = __ldg(res + (c4 >> 4) * 32u);
         const uint32_t sel = (c4 >> 2) & 3u;
         const uint32_t word = sel == 0 ? rv.x : sel == 1 ? rv.y : sel == 2 ? rv.z : rv.w;
-        uint32_t bnd[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          bnd[k] = bt;
-          bt = __vadd2(bt, bt_step);
-        }
         uint2 top[4];
         if (!first) {
           fetch(c4 + 8, slot == 0 ? RING - 1 : slot - 1);
@@ -516,16 +529,23 @@ __global__ void __launch_bounds__(NT, 2) k_inter_glob16(const InterArgs A, const
 #pragma unroll
           for (int k = 0; k < 4; ++k) top[k] = ring[(slot * 4 + k) * NT];
           if (keep != 0xFFFFFFFFu) {
+            uint32_t bk = bt;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              top[k].x = (top[k].x & keep) | (bnd[k] & ~keep);
-              top[k].y = (top[k].y & keep) | (bnd[k] & ~keep);
+              top[k].x = (top[k].x & keep) | (bk & ~keep);
+              top[k].y = (top[k].y & keep) | (bk & ~keep);
+              if (!tb_free) bk = __vadd2(bk, neg_e2);
             }
           }
         } else {
+          uint32_t bk = bt;
 #pragma unroll
-          for (int k = 0; k < 4; ++k) top[k] = make_uint2(bnd[k], bnd[k]);
+          for (int k = 0; k < 4; ++k) {
+            top[k] = make_uint2(bk, bk);
+            if (!tb_free) bk = __vadd2(bk, neg_e2);
+          }
         }
+        if (keep != 0xFFFFFFFFu && !tb_free) bt = __vadd2(bt, neg_e4);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const uint32_t a = (word >> (8 * k)) & 0xFFu;
@@ -554,9 +574,12 @@ __global__ void __launch_bounds__(NT, 2) k_inter_glob16(const InterArgs A, const
           }
           scr[(uint64_t)(c4 + k) * NT] = make_uint2(Ho[W - 1], F);
           const int j = (int)c4 + k + 1;
-          // columns past the lane's target end feed no real cell (values only
-          // move right and down) and may wrap in a long group: left out
-          if (j <= nl) runmax = __vmaxu2(runmax, cm);
+          // upward range test of the column (rare); columns past the lane's
+          // target end feed no real cell (values only move right and down)
+          // and may wrap in a long group: left out
+          if (__vmaxu2(cm, G.hmax2) != G.hmax2 && j <= nl)
+            s_sat[tid] |= ((cm & 0xFFFFu) > (G.hmax2 & 0xFFFFu) ? 1u : 0u) |
+                          ((cm >> 16) > (G.hmax2 >> 16) ? 2u : 0u);
           if (j == nl) {   // the lane's own target end: park the column
 #pragma unroll
             for (int r = 0; r < W; ++r) park[r * NT + tid] = Ho[r];
@@ -566,11 +589,11 @@ __global__ void __launch_bounds__(NT, 2) k_inter_glob16(const InterArgs A, const
             if (__vmaxu2(cur, rthr) != rthr && j <= nl) {
               if ((cur & 0xFFFFu) > (rthr & 0xFFFFu)) {
                 rthr = (rthr & 0xFFFF0000u) | (cur & 0xFFFFu);
-                rj_lo = j;
+                s_rj[0][tid] = j;
               }
               if ((cur >> 16) > (rthr >> 16)) {
                 rthr = (rthr & 0x0000FFFFu) | (cur & 0xFFFF0000u);
-                rj_hi = j;
+                s_rj[1][tid] = j;
               }
             }
           }
@@ -580,7 +603,13 @@ __global__ void __launch_bounds__(NT, 2) k_inter_glob16(const InterArgs A, const
       if (tvalid) {
         // H of half `sh` (0 / 16) from a packed H - o in offset binary
         auto hval = [&](uint32_t w, int sh) { return (int)((w >> sh) & 0xFFFFu) - 0x8000 + o; };
-        auto finish = [&](int sh, int i0, bool last, int m, uint32_t q, int& cb, int& ci, int rj) {
+        auto finish = [&](int h, uint32_t q, uint32_t kq) {
+          const int sh = 16 * h;
+          int m, i0;
+          bool last;
+          geom(q, kq, m, i0, last);
+          int cb = s_cb[h][tid], ci = s_ci[h][tid];
+          const int rj = s_rj[h][tid];
           if (qe_free) {   // column n of this strip's real rows, smallest i first
             for (int r = 0; r < W; ++r) {
               const int i = i0 + r + 1;
@@ -588,6 +617,8 @@ __global__ void __launch_bounds__(NT, 2) k_inter_glob16(const InterArgs A, const
               if (i >= 1 && v > cb) { cb = v; ci = i; }
             }
           }
+          s_cb[h][tid] = cb;
+          s_ci[h][tid] = ci;
           if (!last) return;
           int bs = hval(park[(W - 1) * NT + tid], sh), bi = m, bj = nl;   // (m, n)
           if (qe_free && (cb > bs || (cb == bs && ci < bi))) { bs = cb; bi = ci; }
@@ -595,16 +626,17 @@ __global__ void __launch_bounds__(NT, 2) k_inter_glob16(const InterArgs A, const
             const int rvv = hval(rthr, sh);
             if (rvv > bs || (rvv == bs && rj < bj)) { bs = rvv; bi = m; bj = rj; }
           }
-          const int hmax = (int)((runmax >> sh) & 0xFFFFu) - 0x8000;
+          const bool up = (s_sat[tid] >> h) & 1u;
           const int64_t low = 4ll * o + (int64_t)(m + nl + 2) * e + (G.smin < 0 ? -G.smin : 0) + 64;
           const uint64_t idx = (uint64_t)q * A.n_out_t + A.perm[st];
           A.o_score[idx] = bs;
           A.o_qend[idx] = bi - 1;
           A.o_tend[idx] = bj - 1;
-          A.o_flag[idx] = (hmax > hmax_ok || low >= 32768) ? 1 : 0;
+          A.o_flag[idx] = (up || low >= 32768) ? 1 : 0;
         };
-        if (md.qa != NONE) finish(0, ia0, last_a, ma, md.qa, cb_lo, ci_lo, rj_lo);
-        if (md.qb != NONE) finish(16, ib0, last_b, mb, md.qb, cb_hi, ci_hi, rj_hi);
+        const StripMeta mr = A.meta[sb + s];   // reloaded: not kept live over the column loop
+        if (mr.qa != NONE) finish(0, mr.qa, mr.ka);
+        if (mr.qb != NONE) finish(1, mr.qb, mr.kb);
       }
       __syncthreads();
       if (tid == 0 && s + 2 < ns) {
@@ -715,13 +747,19 @@ int launch_inter_local16(dsa_ctx* ctx, const dsa_db* db, const PackedPlan& plan,
   A.o_score = out.score; A.o_qend = out.q_end; A.o_tend = out.t_end; A.o_flag = out.flag;
   A.n_out_t = n_targets_out;
   A.status = ctx->d_status;
-  const size_t smem = 2ull * NCOPY * replica_stride(plan.R) + 2ull * W * NT * sizeof(int16_t) +
+  const size_t smem = 2ull * NCOPY * replica_stride(plan.R) + 2ull * plan.rows * NT * sizeof(int16_t) +
                       (size_t)RING * 4 * NT * sizeof(uint2);
+  auto kern = plan.rows == INTER_ROWS_SHORT ? k_inter_local16<INTER_ROWS_SHORT>
+                                            : k_inter_local16<INTER_ROWS>;
+  if (plan.rows != INTER_ROWS && plan.rows != INTER_ROWS_SHORT) {
+    ctx->release(scr, scr_bytes);
+    set_error("strip height %d has no kernel", plan.rows);
+    return DSA_ERR_INVALID_ARG;
+  }
   // the attribute belongs to the current device: set it on every launch (cheap)
-  DSA_CUDA_TRY(cudaFuncSetAttribute(k_inter_local16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+  DSA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   DSA_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), ctx->stream));
-  k_inter_local16<<<grid, NT, smem, ctx->stream>>>(A);
+  kern<<<grid, NT, smem, ctx->stream>>>(A);
   ++ctx->launches;
   cudaError_t err = cudaGetLastError();
   ctx->release(scr, scr_bytes);
@@ -750,6 +788,7 @@ int launch_inter_glob16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const 
   GlobArgs G;
   G.mode = mode; G.fe = fe; G.e = e; G.smin = smin;
   G.qlen = qs->d_len; G.slen = db->d_slen;
+  G.hmax2 = ((uint32_t)(A.T + 0x8000) << 16) | (uint32_t)(A.T + 0x8000);
   const int grid = (int)std::min<uint64_t>(work.n_items, (uint64_t)ctx->sm_count * inter_blocks_per_sm());
   const uint64_t cols = ((uint64_t)work.max_glen + 3) & ~3ull;
   A.scratch_cols = cols;
@@ -760,12 +799,25 @@ int launch_inter_glob16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const 
   A.o_score = out.score; A.o_qend = out.q_end; A.o_tend = out.t_end; A.o_flag = out.flag;
   A.n_out_t = n_targets_out;
   A.status = ctx->d_status;
-  const size_t smem = 2ull * NCOPY * replica_stride(plan.R) + (size_t)W * NT * sizeof(uint32_t) +
+  const size_t smem = 2ull * NCOPY * replica_stride(plan.R) + (size_t)plan.rows * NT * sizeof(uint32_t) +
                       (size_t)RING * 4 * NT * sizeof(uint2);
-  DSA_CUDA_TRY(cudaFuncSetAttribute(k_inter_glob16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+  const bool sg = mode == DSA_SEMIGLOBAL;
+  const bool tb = sg && (fe & DSA_FREE_T_BEGIN), te = sg && (fe & DSA_FREE_T_END);
+  auto pick = [&](auto w) {
+    constexpr int Wc = decltype(w)::value;
+    return tb ? (te ? k_inter_glob16<Wc, true, true> : k_inter_glob16<Wc, true, false>)
+              : (te ? k_inter_glob16<Wc, false, true> : k_inter_glob16<Wc, false, false>);
+  };
+  auto kern = plan.rows == INTER_ROWS_SHORT ? pick(std::integral_constant<int, INTER_ROWS_SHORT>{})
+                                            : pick(std::integral_constant<int, INTER_ROWS>{});
+  if (plan.rows != INTER_ROWS && plan.rows != INTER_ROWS_SHORT) {
+    ctx->release(scr, scr_bytes);
+    set_error("strip height %d has no kernel", plan.rows);
+    return DSA_ERR_INVALID_ARG;
+  }
+  DSA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   DSA_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(uint32_t), ctx->stream));
-  k_inter_glob16<<<grid, NT, smem, ctx->stream>>>(A, G);
+  kern<<<grid, NT, smem, ctx->stream>>>(A, G);
   ++ctx->launches;
   cudaError_t err = cudaGetLastError();
   ctx->release(scr, scr_bytes);

@@ -20,18 +20,22 @@ namespace dsa {
 namespace {
 
 
-// ---- autotuner: the long-target threshold of the packed path ----
+// ---- autotuner: kernel variant and long-target threshold of the packed path ----
 //
-// Which targets go to the wavefront kernel (long) and which to the
-// inter-sequence kernel is a speed choice only (both are exact).  For a
-// workload shape (GPU, alphabet, and log2 bins of the query count, query
-// residues, target count, database residues and longest target) the first
-// call times a small local search of thresholds -- starting at 4096, then
-// lower or higher by factors of 4 while it keeps improving by 3% or more --
-// and keeps the best in a JSON cache file.  DSA_AUTOTUNE=off (fixed 4096) | cache (default:
-// tune on a miss) | retune (always tune); DSA_AUTOTUNE_CACHE names the file
+// Two speed choices of the packed path (every choice gives the same exact
+// results): the strip height of the inter-sequence kernel (28 rows, or 20
+// rows, which wastes fewer padding rows on short queries), and, in local
+// mode, which targets go to the wavefront kernel (long) and which to the
+// inter-sequence kernel.  For a workload shape (GPU, driver, mode, alphabet,
+// and log2 bins of the query count, query residues, longest query, target
+// count, database residues and longest target) the first call times each
+// strip height at the default threshold (a switch needs a 3% gain), then a
+// local search of thresholds -- starting at 4096, then lower or higher by
+// factors of 4 while it keeps improving by 3% or more -- and keeps both in a
+// JSON cache file.  DSA_AUTOTUNE=off (28 rows, 4096) | cache (default: tune
+// on a miss) | retune (always tune); DSA_AUTOTUNE_CACHE names the file
 // (default $XDG_CACHE_HOME/dsa/autotune.json or ~/.cache/dsa/autotune.json);
-// DSA_LONG_THRESHOLD overrides everything.
+// DSA_INTER_ROWS (28 | 20) and DSA_LONG_THRESHOLD fix their choice.
 struct Tuner {
   std::mutex mu;
   bool loaded = false;
@@ -116,16 +120,17 @@ int ilog2_bin(uint64_t x) {
 // inter-sequence kernel.
 int packed_score(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
                  const int8_t* d_mat, const int8_t* d_pssm, int A, int o, int e, const Validated& v, Scores out,
-                 uint32_t long_thr, int mode = DSA_LOCAL, uint32_t fe = 15) {
+                 uint32_t long_thr, int rows, int mode = DSA_LOCAL, uint32_t fe = 15) {
   const bool local = mode == DSA_LOCAL;
   if (!local) long_thr = UINT32_MAX;
+  const uint32_t W = (uint32_t)rows;   // strip rows of the inter-sequence kernel
   const uint32_t nq = qs->n, nt = db->n;
   const int R = A + 1;
   std::vector<uint32_t> qorder(nq);
   std::iota(qorder.begin(), qorder.end(), 0u);
   std::stable_sort(qorder.begin(), qorder.end(),
                    [&](uint32_t a, uint32_t b) { return qs->h_len[a] > qs->h_len[b]; });
-  auto strips_of = [&](uint32_t q) { return (qs->h_len[q] + INTER_ROWS - 1) / INTER_ROWS; };
+  auto strips_of = [&](uint32_t q) { return (qs->h_len[q] + W - 1) / W; };
 
   // groups whose longest target exceeds the threshold go to the wavefront kernel
   uint32_t g_long = 0;
@@ -186,7 +191,7 @@ int packed_score(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
   }
   PackedPlan spl;
   spl.R = R;
-  spl.rows = INTER_ROWS;
+  spl.rows = rows;
   spl.n_units = (uint32_t)s_ns.size();
   spl.n_strips = (uint32_t)smeta.size();
 
@@ -305,90 +310,123 @@ int packed_score(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
   return DSA_OK;
 }
 
-// The packed pass with the autotuned long-target threshold.
+// Strip rows forced by DSA_INTER_ROWS (0: let the tuner choose).
+int forced_rows() {
+  if (const char* env = getenv("DSA_INTER_ROWS")) {
+    const int r = atoi(env);
+    if (r == INTER_ROWS || r == INTER_ROWS_SHORT) return r;
+  }
+  return 0;
+}
+
+// The packed pass with the autotuned kernel variant (strip rows) and, in
+// local mode, long-target threshold.
 int run_packed_tuned(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
-                     const int8_t* d_mat, const int8_t* d_pssm, int A, int o, int e, const Validated& v, Scores out) {
-  if (const char* env = getenv("DSA_LONG_THRESHOLD"))
-    return packed_score(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out,
-                        (uint32_t)strtoul(env, nullptr, 10));
-  const char* mode_env = getenv("DSA_AUTOTUNE");
-  const std::string mode = mode_env ? mode_env : "cache";
+                     const int8_t* d_mat, const int8_t* d_pssm, int A, int o, int e,
+                     const Validated& v, Scores out, int mode, uint32_t fe) {
+  const bool local = mode == DSA_LOCAL;
   constexpr uint32_t DEFAULT_THR = 4096;
-  if (mode == "off") return packed_score(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out, DEFAULT_THR);
-  // workload shape key
+  const int rows_forced = forced_rows();
+  const char* thr_env = getenv("DSA_LONG_THRESHOLD");
+  const uint32_t thr_forced = thr_env ? (uint32_t)strtoul(thr_env, nullptr, 10) : 0;
+  auto run = [&](dsa_res* r, uint32_t thr, int rows) {
+    return packed_score(ctx, r, db, qs, d_mat, d_pssm, A, o, e, v, out, thr, rows, mode, fe);
+  };
+  const char* mode_env = getenv("DSA_AUTOTUNE");
+  const std::string tmode = mode_env ? mode_env : "cache";
+  const int rows_default = rows_forced ? rows_forced : INTER_ROWS;
+  const uint32_t thr_default = thr_env ? thr_forced : DEFAULT_THR;
+  if (tmode == "off" || (rows_forced && (thr_env || !local)))
+    return run(res, thr_default, rows_default);
+  // workload shape key: GPU, driver, mode, alphabet, and log2 bins of the
+  // query count, query residues, longest query, target count, database
+  // residues and longest target
   uint64_t qres = 0;
-  for (uint32_t x : qs->h_len) qres += x;
+  uint32_t qmax = 0;
+  for (uint32_t x : qs->h_len) { qres += x; qmax = std::max(qmax, x); }
   cudaDeviceProp prop;
   DSA_CUDA_TRY(cudaGetDeviceProperties(&prop, ctx->device));
   int drv = 0;
   cudaDriverGetVersion(&drv);
   char key[512];
-  snprintf(key, sizeof key, "%s|sm%d|drv%d|A%d|q%d|qr%d|t%d|tr%d|L%d", prop.name, ctx->sm_count,
-           drv, A, ilog2_bin(qs->n), ilog2_bin(qres), ilog2_bin(db->n), ilog2_bin(db->n_res),
-           ilog2_bin(db->max_len));
+  snprintf(key, sizeof key, "%s|sm%d|drv%d|%s|A%d|q%d|qr%d|qm%d|t%d|tr%d|L%d", prop.name,
+           ctx->sm_count, drv, local ? "local" : (mode == DSA_GLOBAL ? "global" : "semi"), A,
+           ilog2_bin(qs->n), ilog2_bin(qres), ilog2_bin(qmax), ilog2_bin(db->n),
+           ilog2_bin(db->n_res), ilog2_bin(db->max_len));
+  const std::string key_thr = std::string(key) + "|thr", key_rows = std::string(key) + "|rows";
   Tuner& t = tuner();
   {
     std::lock_guard<std::mutex> lk(t.mu);
     const std::string path = tune_cache_path();
     if (!t.loaded || path != t.path) tune_load(t, path);   // first use, or another file
-    auto it = t.cache.find(key);
-    if (mode != "retune" && it != t.cache.end())
-      return packed_score(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out, it->second);
+    auto it_r = t.cache.find(key_rows);
+    auto it_t = t.cache.find(key_thr);
+    if (tmode != "retune" && it_r != t.cache.end() && (!local || it_t != t.cache.end()))
+      return run(res, thr_env ? thr_forced : (local ? it_t->second : UINT32_MAX),
+                 rows_forced ? rows_forced : (int)it_r->second);
   }
   if (!ctx->tune)   // contexts that must not spend calls on tuning (serving workers)
-    return packed_score(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out, DEFAULT_THR);
-  // thresholds are compared by the number of target groups they move
+    return run(res, thr_default, rows_default);
+  std::map<std::pair<uint32_t, int>, double> timed;   // (long groups, rows) -> ms
   auto groups_over = [&](uint32_t thr) {
     uint32_t g = 0;
-    while (g < db->n_groups && db->h_glen[g] > thr) ++g;
+    while (local && g < db->n_groups && db->h_glen[g] > thr) ++g;
     return g;
   };
-  std::map<uint32_t, double> timed;   // long groups -> ms
   cudaEvent_t ev0, ev1;
   DSA_CUDA_TRY(cudaEventCreate(&ev0));
   DSA_CUDA_TRY(cudaEventCreate(&ev1));
   int rc = DSA_OK;
-  auto measure = [&](uint32_t thr) -> double {
-    const uint32_t g = groups_over(thr);
-    auto it = timed.find(g);
+  auto measure = [&](uint32_t thr, int rows) -> double {
+    const auto k = std::make_pair(groups_over(thr), rows);
+    auto it = timed.find(k);
     if (it != timed.end()) return it->second;
     float ms = 0.f;
     if (rc == DSA_OK && cudaEventRecord(ev0, ctx->stream) != cudaSuccess) rc = DSA_ERR_CUDA;
-    if (rc == DSA_OK) rc = packed_score(ctx, nullptr, db, qs, d_mat, d_pssm, A, o, e, v, out, thr);
+    if (rc == DSA_OK) rc = run(nullptr, thr, rows);
     if (rc == DSA_OK && cudaEventRecord(ev1, ctx->stream) != cudaSuccess) rc = DSA_ERR_CUDA;
     if (rc == DSA_OK && cudaEventSynchronize(ev1) != cudaSuccess) rc = DSA_ERR_CUDA;
     if (rc == DSA_OK) cudaEventElapsedTime(&ms, ev0, ev1);
-    timed[g] = ms;
+    timed[k] = ms;
     return ms;
   };
-  // local search from the default by factors of 4, in each direction while it
-  // improves; thresholds that move the same groups as the last one are
-  // skipped, and a switch needs a gain of at least 3% (single timings)
-  uint32_t best = DEFAULT_THR;
-  double best_ms = measure(best);
-  for (int dir = -1; dir <= 1 && rc == DSA_OK; dir += 2) {
-    uint64_t cur = DEFAULT_THR;
-    uint32_t last_g = groups_over(DEFAULT_THR);
-    for (int step = 0; step < 12 && rc == DSA_OK; ++step) {
-      const uint64_t nx = dir < 0 ? cur / 4 : cur * 4;
-      const uint32_t thr = (dir > 0 && nx >= db->max_len) ? UINT32_MAX : (uint32_t)nx;
-      cur = nx;
-      const uint32_t g = groups_over(thr);
-      if (g == last_g) {
-        if (thr == 0 || thr == UINT32_MAX) break;
-        continue;
-      }
-      last_g = g;
-      const double ms = measure(thr);
-      if (ms < 0.97 * best_ms) {
-        best_ms = ms;
-        best = thr;
-      } else {
-        break;
-      }
-      if (thr == 0 || thr == UINT32_MAX) break;
+  // 1. the kernel variant (strip rows) at the default threshold; a switch
+  //    from the default needs a gain of at least 3% (single timings)
+  int best_rows = rows_default;
+  double best_ms = measure(thr_default, best_rows);
+  if (!rows_forced)
+    for (int rows : {INTER_ROWS_SHORT}) {
+      const double ms = measure(thr_default, rows);
+      if (ms < 0.97 * best_ms) { best_ms = ms; best_rows = rows; }
     }
-  }
+  // 2. local mode: the long-target threshold, a local search from the
+  //    default by factors of 4 in each direction while it improves;
+  //    thresholds that move the same groups as the last one are skipped
+  uint32_t best = local ? thr_default : UINT32_MAX;
+  if (local && !thr_env)
+    for (int dir = -1; dir <= 1 && rc == DSA_OK; dir += 2) {
+      uint64_t cur = DEFAULT_THR;
+      uint32_t last_g = groups_over(DEFAULT_THR);
+      for (int step = 0; step < 12 && rc == DSA_OK; ++step) {
+        const uint64_t nx = dir < 0 ? cur / 4 : cur * 4;
+        const uint32_t thr = (dir > 0 && nx >= db->max_len) ? UINT32_MAX : (uint32_t)nx;
+        cur = nx;
+        const uint32_t g = groups_over(thr);
+        if (g == last_g) {
+          if (thr == 0 || thr == UINT32_MAX) break;
+          continue;
+        }
+        last_g = g;
+        const double ms = measure(thr, best_rows);
+        if (ms < 0.97 * best_ms) {
+          best_ms = ms;
+          best = thr;
+        } else {
+          break;
+        }
+        if (thr == 0 || thr == UINT32_MAX) break;
+      }
+    }
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
   if (rc) {
@@ -397,11 +435,12 @@ int run_packed_tuned(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
   }
   {
     std::lock_guard<std::mutex> lk(t.mu);
-    t.cache[key] = best;
+    if (!rows_forced) t.cache[key_rows] = (uint32_t)best_rows;
+    if (local && !thr_env) t.cache[key_thr] = best;
     tune_store(t);
   }
-  // the final pass with the chosen threshold records the phase timings and cells
-  return packed_score(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out, best);
+  // the final pass with the chosen variant records the phase timings and cells
+  return run(res, best, best_rows);
 }
 
 }  // namespace
@@ -445,10 +484,7 @@ int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
 
   // ---- packed path ----
   DSA_TRY(ensure_interleaved(ctx, db));
-  if (mode == DSA_LOCAL)
-    DSA_TRY(run_packed_tuned(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out));
-  else
-    DSA_TRY(packed_score(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out, UINT32_MAX, mode, fe));
+  DSA_TRY(run_packed_tuned(ctx, res, db, qs, d_mat, d_pssm, A, o, e, v, out, mode, fe));
 
   // ---- exact int32 rerun of saturated pairs ----
   const uint64_t n_out = (uint64_t)nq * nt;
