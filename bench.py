@@ -36,6 +36,13 @@ METRIC = "GCUPS (bit-exact) batched protein database search"
 # 1.194 T cells); traffic grows with the cells (boundary rows per column and
 # strip), so a launch's traffic is this figure times its cells.
 INTER_DRAM_BYTES_PER_CELL = 416.40e9 / 1.194104e12
+# the same figure for the global / semi-global form k_inter_glob16 (None until
+# a capture of the current kernel exists)
+GLOB_DRAM_BYTES_PER_CELL = None
+
+# the workloads measured after the headline (each timed on its own)
+SUB_WORKLOADS = ("reads_vs_windows", "long_pairs_global", "long_pairs_local",
+                 "protein_search_global", "protein_search_semiglobal", "serving")
 
 WORKLOAD = ("protein_search: 32 queries (log-uniform 64..5000) x 500,000 targets "
             "(lognormal median 300, sigma 0.7, cap 35,000), BLOSUM62 11/1, local, "
@@ -68,9 +75,19 @@ def parse():
                     help="approximate CPU time of the oracle sample")
     ap.add_argument("--requests", type=int, default=120,
                     help="serving: requests per measured load level")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="protein_search: skip the block of the other workloads")
+    ap.add_argument("--workloads", default=",".join(SUB_WORKLOADS),
+                    help="comma list of the other workloads measured after the headline")
+    ap.add_argument("--sub-steps", type=int, default=3,
+                    help="timed steps of each other workload")
+    ap.add_argument("--sub-warmup", type=int, default=1,
+                    help="untimed steps of each other workload (the headline's own warm-up "
+                         "already ran the kernels)")
     ap.add_argument("--workload", default="protein_search",
-                    choices=["protein_search", "protein_vs_db", "reads_vs_windows", "long_pairs",
-                             "long_pairs_local", "serving"],
+                    choices=["protein_search", "protein_search_global", "protein_search_semiglobal",
+                             "protein_vs_db", "reads_vs_windows", "long_pairs", "long_pairs_local",
+                             "serving"],
                     help="the measured workload (default: the batched protein search)")
     return ap.parse_args()
 
@@ -189,11 +206,43 @@ def make_workload(args, rank=0):
     if args.workload in ("long_pairs", "long_pairs_local"):
         mode = W.MODE_LOCAL if args.workload == "long_pairs_local" else W.MODE_GLOBAL
         return W.long_pairs(seed=W.SEED_BASE + 3 + 1000 * rank, mode=mode, n_pairs=args.long_pairs)
-    return W.protein_search(seed=W.SEED_BASE + 1 + 1000 * rank, n_queries=args.queries,
-                            n_targets=args.targets)
+    # protein search: rank r holds shard r of one database (targets
+    # r * targets .. (r + 1) * targets - 1 in global numbering; shard 0 is the
+    # one-GPU database) and every rank the same queries
+    wl = W.protein_search(seed=W.SEED_BASE + 1 + 1000 * rank, n_queries=args.queries,
+                          n_targets=args.targets)
+    if rank:
+        wl.queries = W.protein_search(seed=W.SEED_BASE + 1, n_queries=args.queries,
+                                      n_targets=1).queries
+    wl.meta["target_base"] = rank * args.targets
+    if args.workload in ("protein_search_global", "protein_search_semiglobal"):
+        wl.mode = W.MODE_GLOBAL if args.workload.endswith("_global") else W.MODE_SEMIGLOBAL
+    return wl
+
+
+def gather_merge(world, rank, hits, cigar, n_queries, k, target_base):
+    """Partition top-K reduce across ranks (Sec. II.B.2): every rank's top-K
+    hits (shard-local target ids) and CIGAR words go to rank 0, which merges
+    them under (score desc, global target id asc) with dsa_merge_topk.
+    Returns (hits, cigar) with global target ids on rank 0, None elsewhere."""
+    from paper_1701_01575_gb300 import dsa
+    mine = (hits.tobytes(), cigar.tobytes(), int(target_base))
+    if world > 1:
+        import torch.distributed as dist
+        lists = [None] * world
+        dist.all_gather_object(lists, mine)
+    else:
+        lists = [mine]
+    if rank != 0:
+        return None
+    parts = [(np.frombuffer(h, dtype=dsa.HIT_DTYPE), np.frombuffer(c, dtype=np.uint32))
+             for h, c, _ in lists]
+    return dsa.merge_topk(parts, [b for _, _, b in lists], n_queries, k)
 
 
 WORKLOAD_TEXT = {
+    "protein_search_global": WORKLOAD.replace(", local,", ", global,"),
+    "protein_search_semiglobal": WORKLOAD.replace(", local,", ", semi-global (all four ends free),"),
     "protein_vs_db": "protein_vs_db: 1 query of 128 x 2,000 targets U{50..500}, BLOSUM62 11/1, local",
     "reads_vs_windows": ("reads_vs_windows: 1,000,000 reads (150/250 bp, 1% subs, 0.1% indels) vs "
                          "500 bp windows of a 10 Mb genome, +1/-4, 6/1, semi-global (target ends "
@@ -305,11 +354,26 @@ def bench_ours(args):
         reruns += r.stats()[1]
     last = results[-1]
     top_hits = last.hits()
+    top_cigar = last.cigar()
     for r in results:
         r.free()
+    merged = None
+    if args.workload.startswith("protein_search") and wl.top_k and not args.pssm:
+        # the shards' top-K lists, merged on rank 0 (outside the timed region)
+        t_m = time.perf_counter()
+        got = gather_merge(world, rank, top_hits, top_cigar, wl.queries.n, wl.top_k,
+                           wl.meta["target_base"])
+        if got is not None:
+            mh, mc = got
+            merged = {"ranks": world, "hits": int(len(mh)), "cigar_words": int(len(mc)),
+                      "top_q0": [(int(h["target_id"]), int(h["score"])) for h in mh[:3]],
+                      "host_ms": round((time.perf_counter() - t_m) * 1e3, 1)}
     ms, total_cells, value = aggregate(world, ms_local, float(cells_per_step * args.steps))
 
     wtext = WORKLOAD if args.workload == "protein_search" else WORKLOAD_TEXT[args.workload]
+    if args.workload.startswith("protein_search"):
+        wtext = wtext.replace("32 queries", f"{wl.queries.n} queries").replace(
+            "500,000 targets", f"{wl.db.n:,} targets")
     if args.workload == "reads_vs_windows":
         wtext = wtext.replace("1,000,000 reads", f"{args.reads:,} reads")
     if args.workload.startswith("long_pairs"):
@@ -326,15 +390,19 @@ def bench_ours(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i16x2+i32",
            "data": "synthetic",
            "config": {"workload": wtext, "queries": wl.queries.n, "targets": wl.db.n,
-                      "cells_per_step": cells_per_step, "parallelism": f"replicas x{world}",
+                      "cells_per_step": cells_per_step,
+                      "parallelism": (f"database shards x{world}, per-shard top-K merged on rank 0"
+                                      if args.workload.startswith("protein_search")
+                                      else f"replicas x{world}"),
                       "l2": "inputs larger than L2" if wl.db.codes.nbytes + wl.queries.codes.nbytes > (129 << 20)
                       else "inputs smaller than L2 (small workload)"},
            "clocks": clk, "gpu_launches": int(launches)}
 
     # roofline of the dominant kernel (packed inter-sequence kernel)
     inter_ms = statistics.mean(phase["inter16"]) if phase["inter16"] else None
-    if args.workload != "protein_search":
+    if not args.workload.startswith("protein_search"):
         inter_ms = None
+    kname = "k_inter_local16" if args.workload == "protein_search" else "k_inter_glob16"
     rate = ctx.probe_issue_rate(0)      # DPX s16x2 add-max, warp-instr / SM / clk
     rate_add = ctx.probe_issue_rate(3)  # 32-bit integer add, warp-instr / SM / clk
     sm_mhz = clk.get("sm_mhz") or (props.clock_rate / 1e3 if hasattr(props, "clock_rate") else None)
@@ -346,12 +414,13 @@ def bench_ours(args):
         # every instruction covers 2 cells of 32 lanes
         peak = (props.multi_processor_count * sm_mhz * 1e6 * 32 * 2 / (5 / rate + 1 / rate_add)
                 / 1e9)
+        per_cell = INTER_DRAM_BYTES_PER_CELL if kname == "k_inter_local16" else GLOB_DRAM_BYTES_PER_CELL
         out["roofline"] = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
                            "unit": "GCUPS", "frac": round(achieved / peak, 4),
-                           "traffic": round(INTER_DRAM_BYTES_PER_CELL * pcells["inter16"]),
+                           "traffic": round(per_cell * pcells["inter16"]) if per_cell else None,
                            "traffic_basis": "ncu dram__bytes_read+write of an 8-query x 350k "
                                             "capture, scaled by cells to this launch",
-                           "kernel": "k_inter_local16", "kernel_ms": round(inter_ms, 3),
+                           "kernel": kname, "kernel_ms": round(inter_ms, 3),
                            "peak_basis": f"{props.multi_processor_count} SMs x {sm_mhz:.0f} MHz x "
                                          "32 lanes x 2 cells / (5 DPX ops / "
                                          f"{rate:.3f} + 1 add / {rate_add:.3f} warp-instr/SM/clk, "
@@ -424,6 +493,18 @@ def bench_ours(args):
         out["cpu_baseline"]["parity_mismatches"] = mism
         out["top_hits_q0"] = [(int(h["target_id"]), int(h["score"])) for h in top_hits[:3]]
 
+    if rank == 0 and not args.no_workloads and args.workload == "protein_search" and \
+            not args.pssm and not args.partition_residues:
+        # the other workloads, each timed on its own after the headline
+        out["workloads"] = {}
+        for name in [x for x in args.workloads.split(",") if x]:
+            if name == "serving":
+                out["workloads"][name] = serving_block(args, bus, protein_db=wl.db)
+            else:
+                out["workloads"][name] = sub_workload(name, args, ctx, stream, bus, (wl, db, qs))
+
+    if merged is not None:
+        out["merge"] = merged
     if rank == 0:
         print(json.dumps(out), flush=True)
     qs.free(); db.free(); ctx.close()
@@ -432,22 +513,189 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------- other workloads --
+
+def timed_steps(ctx, stream, step, steps, warmup, bus):
+    """`warmup` untimed steps, then `steps` steps between CUDA events recorded on
+    the library's stream, with the clocks sampled meanwhile.  Returns (ms,
+    results, clocks, kernel launches)."""
+    import torch
+    for _ in range(warmup):
+        step().free()
+    torch.cuda.synchronize()
+    launches0 = ctx.kernel_launches()
+    clocks = ClockSampler(bus)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = [step() for _ in range(steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    return ev0.elapsed_time(ev1), results, clk, ctx.kernel_launches() - launches0
+
+
+def phase_summary(results):
+    """Mean device milliseconds and GCUPS of each phase the results recorded."""
+    from paper_1701_01575_gb300 import dsa
+    phase = {k: [] for k in dsa.PHASES}
+    for r in results:
+        for k, v in r.timing().items():
+            if v >= 0:
+                phase[k].append(v)
+    pcells = results[0].phase_cells()
+    ms = {k: round(statistics.mean(v), 3) for k, v in phase.items() if v}
+    gc = {k: round(pcells[k] / (statistics.mean(v) / 1e3) / 1e9, 1)
+          for k, v in phase.items() if v and pcells.get(k)}
+    return ms, gc
+
+
+def _pairs_parity(wl, h, cig, pick, trace_every):
+    """Oracle scores and ends of the sampled pairs, begins and CIGARs of every
+    `trace_every`-th of them: the number of fields that differ."""
+    import oracle
+    p = wl.pairs[pick]
+    sc, qe, te = oracle.score_pairs(wl.queries.codes, wl.queries.offsets, wl.db.codes,
+                                    wl.db.offsets, p["query_id"], p["target_id"], wl.matrix,
+                                    wl.gap_open, wl.gap_extend, wl.mode, wl.free_ends,
+                                    pair_toff=p["t_offset"], pair_tlen=p["t_len"])
+    hs = h[pick]
+    bad = int((hs["score"] != sc).sum() + (hs["q_end"] != qe).sum() + (hs["t_end"] != te).sum())
+    for k in range(0, len(pick), trace_every):
+        x = hs[k]
+        if wl.mode == 0 and x["score"] == 0:
+            continue
+        t0 = int(wl.db.offsets[int(x["target_id"])]) + int(x["t_offset"])
+        t = wl.db.codes[t0:t0 + int(p["t_len"][k])]
+        qb, tb, c = oracle.traceback(wl.queries.seq(int(x["query_id"])), t, wl.matrix, wl.gap_open,
+                                     wl.gap_extend, wl.mode, wl.free_ends, int(x["q_end"]),
+                                     int(x["t_end"]))
+        got = cig[int(x["cigar_off"]):int(x["cigar_off"]) + int(x["cigar_len"])]
+        bad += int((int(x["q_begin"]), int(x["t_begin"])) != (qb, tb)) + int(got.tolist() != c.tolist())
+    return bad
+
+
+def _hits_parity(wl, h, cig, max_trace_cells=30_000_000):
+    """Oracle score and ends of every reported all-vs-all hit; begins and CIGAR
+    of those whose rectangle has at most `max_trace_cells` cells."""
+    import oracle
+    sc, qe, te = oracle.score_pairs(wl.queries.codes, wl.queries.offsets, wl.db.codes,
+                                    wl.db.offsets, h["query_id"], h["target_id"], wl.matrix,
+                                    wl.gap_open, wl.gap_extend, wl.mode, wl.free_ends)
+    bad = int((h["score"] != sc).sum() + (h["q_end"] != qe).sum() + (h["t_end"] != te).sum())
+    traced = 0
+    for x in h:
+        if (int(x["q_end"]) + 1) * (int(x["t_end"]) + 1) > max_trace_cells:
+            continue
+        qb, tb, c = oracle.traceback(wl.queries.seq(int(x["query_id"])),
+                                     wl.db.seq(int(x["target_id"])), wl.matrix, wl.gap_open,
+                                     wl.gap_extend, wl.mode, wl.free_ends, int(x["q_end"]),
+                                     int(x["t_end"]))
+        got = cig[int(x["cigar_off"]):int(x["cigar_off"]) + int(x["cigar_len"])]
+        bad += int((int(x["q_begin"]), int(x["t_begin"])) != (qb, tb)) + int(got.tolist() != c.tolist())
+        traced += 1
+    return bad, traced
+
+
+def sub_workload(name, args, ctx, stream, bus, main):
+    """One of the other workloads, measured like the headline: its own warm-up,
+    timed steps (align + traceback of every hit) on the library's stream, clock
+    record and an oracle-sample parity count.  `main` = (workload, db, queries)
+    of the headline, reused by the global and semi-global searches."""
+    import torch
+    from paper_1701_01575_gb300 import dsa
+    from paper_1701_01575_gb300 import workloads as W
+    flags = dsa.TIMING | dsa.RESULTS_ON_DEVICE
+    t_gen = time.perf_counter()
+    own = []
+    if name == "reads_vs_windows":
+        wl = W.reads_vs_windows(seed=W.SEED_BASE + 2, n_reads=args.reads)
+        text = WORKLOAD_TEXT["reads_vs_windows"].replace("1,000,000 reads", f"{args.reads:,} reads")
+    elif name in ("long_pairs_global", "long_pairs_local"):
+        mode = W.MODE_LOCAL if name == "long_pairs_local" else W.MODE_GLOBAL
+        wl = W.long_pairs(seed=W.SEED_BASE + 3, mode=mode, n_pairs=args.long_pairs)
+        text = WORKLOAD_TEXT["long_pairs" if mode == W.MODE_GLOBAL else "long_pairs_local"]
+        text = text.replace("64 DNA pairs", f"{args.long_pairs} DNA pairs")
+    else:
+        mwl, db, qs = main
+        mode = W.MODE_GLOBAL if name == "protein_search_global" else W.MODE_SEMIGLOBAL
+        wl = W.Workload(name, mwl.queries, mwl.db, mwl.matrix, mwl.gap_open, mwl.gap_extend, mode,
+                        free_ends=15, top_k=mwl.top_k, meta=mwl.meta)
+        text = WORKLOAD.replace(", local,", ", global," if mode == W.MODE_GLOBAL else
+                                ", semi-global (all four ends free),")
+    gen_s = time.perf_counter() - t_gen
+    if wl.pairs is not None:
+        db = ctx.load_set(wl.db, wl.alphabet_size)
+        qs = ctx.load_set(wl.queries, wl.alphabet_size)
+        own = [db, qs]
+        pairs = torch.as_tensor(wl.pairs.view(np.uint8), device="cuda")
+    else:
+        pairs = None
+
+    def step():
+        r = ctx.align(db, qs, wl.matrix, wl.gap_open, wl.gap_extend, mode=wl.mode,
+                      free_ends=wl.free_ends, pairs=pairs, top_k=wl.top_k, flags=flags)
+        ctx.traceback(r)
+        return r
+
+    ms, results, clk, launches = timed_steps(ctx, stream, step, args.sub_steps, args.sub_warmup, bus)
+    phases_ms, phase_gcups = phase_summary(results)
+    cells = wl.cells()
+    last = results[-1]
+    h, cig = last.hits(), last.cigar()
+    for r in results:
+        r.free()
+    t_par = time.perf_counter()
+    if wl.pairs is not None:
+        if name == "reads_vs_windows":
+            pick = np.sort(np.random.default_rng(11).choice(len(wl.pairs), 2000, replace=False))
+            sample = "2,000 seeded random reads (score, ends), begins + CIGAR of every 10th"
+            bad = _pairs_parity(wl, h, cig, pick, 10)
+        else:
+            sizes = wl.queries.lengths * wl.pairs["t_len"].astype(np.int64)
+            pick = np.sort(np.argsort(sizes)[:3])
+            sample = "the 3 smallest pairs (score, ends, begins, CIGAR)"
+            bad = _pairs_parity(wl, h, cig, pick, 1)
+    else:
+        bad, traced = _hits_parity(wl, h, cig)
+        sample = (f"all {len(h)} reported hits (score, ends); begins + CIGAR of the {traced} "
+                  "hits of at most 3e7 cells")
+    out = {"workload": text, "metric": "GCUPS (bit-exact)", "value": round(cells * args.sub_steps
+                                                                          / (ms / 1e3) / 1e9, 2),
+           "unit": "GCUPS", "steps": args.sub_steps, "warmup": args.sub_warmup,
+           "ms_per_step": round(ms / args.sub_steps, 3), "cells_per_step": int(cells),
+           "phases_ms": phases_ms, "phase_gcups": phase_gcups, "gpu_launches": int(launches),
+           "clocks": clk, "parity": {"sample": sample, "mismatches": bad},
+           "host_s": {"generate": round(gen_s, 1), "oracle": round(time.perf_counter() - t_par, 1)}}
+    for x in own:
+        x.free()
+    return out
+
+
 # ---------------------------------------------------------------- serving --
 
-def bench_serving(args):
-    """Serving loop: capacity, then Poisson loads at 0.5 and 0.8 of it."""
-    import threading
-    from paper_1701_01575_gb300 import build, dsa
+SERVING_TEXT = ("serving: Poisson arrivals, 70% protein queries (log-uniform 50..2000) vs 500,000 "
+                "targets top-10 + traceback, 30% DNA read batches (log-uniform 1e3..1e5 reads of "
+                "150 bp vs 500 bp windows of a 10 Mb genome) with traceback; 2 slots")
+
+
+def serving_block(args, bus=None, protein_db=None):
+    """Serving loop: sustained capacity C (a burst of requests), then Poisson
+    loads at 0.5 C and 0.8 C; latency from arrival to result ready, queueing
+    included.  `protein_db`: the 500,000-target database (host arrays) if it
+    exists already.  Returns the capacity and the per-load figures."""
+    from paper_1701_01575_gb300 import dsa
     from paper_1701_01575_gb300 import workloads as W
-    build.build()
+    t_gen = time.perf_counter()
     rng = np.random.default_rng(W.SEED_BASE + 4)
-    pwl = W.protein_search(seed=W.SEED_BASE + 1, n_queries=1, n_targets=args.targets)
+    if protein_db is None:
+        protein_db = W.protein_search(seed=W.SEED_BASE + 1, n_queries=1, n_targets=args.targets).db
     genome = rng.integers(0, 4, 10_000_000).astype(np.uint8)
     gdb = W.SeqSet(genome, np.array([0, len(genome)], dtype=np.uint64))
     ctx = dsa.Context(0)
-    d_p = ctx.load_set(pwl.db, 24)
+    d_p = ctx.load_set(protein_db, 24)
     d_g = ctx.load_set(gdb, 4)
-    db_res = int(pwl.db.codes.nbytes)
+    db_res = int(protein_db.codes.nbytes)
     S_p, S_d = W.blosum62(), W.dna_matrix(1, -4)
 
     def cells(r):
@@ -495,26 +743,41 @@ def bench_serving(args):
 
     n = args.requests
     warm = W.serving_stream(seed=W.SEED_BASE + 40, n_requests=8, rate=1e9, genome=genome)
-    run(warm, 0)
     burst = W.serving_stream(seed=W.SEED_BASE + 41, n_requests=n, rate=1e9, genome=genome)
+    # the load streams' arrival times are scaled to the measured capacity below
+    load_reqs = {frac: W.serving_stream(seed=W.SEED_BASE + 42 + int(frac * 10), n_requests=n,
+                                        rate=1.0, genome=genome) for frac in (0.5, 0.8)}
+    gen_s = time.perf_counter() - t_gen
+    run(warm, 0)
+    clocks = ClockSampler(bus)
     cap = run(burst, 0)
     C = cap["requests"] / cap["span_s"]
     loads = {}
-    for frac in (0.5, 0.8):
-        reqs = W.serving_stream(seed=W.SEED_BASE + 42 + int(frac * 10), n_requests=n,
-                                rate=frac * C, genome=genome)
+    for frac, reqs in load_reqs.items():
+        for r in reqs:
+            r.arrival /= frac * C   # Poisson at rate 1 -> rate frac * C
         loads[f"{frac}C"] = dict(run(reqs, frac * C), rate_per_s=round(frac * C, 2))
+    clk = clocks.stop()
+    d_p.free(); d_g.free(); ctx.close()
+    return {"workload": SERVING_TEXT, "requests_per_level": n,
+            "capacity": dict(cap, requests_per_s=round(C, 2)), "loads": loads, "clocks": clk,
+            "parity": {"sample": "results identical alone and in the mix: tests/test_gpu_serving.py",
+                       "mismatches": None},
+            "host_s": {"generate": round(gen_s, 1)}}
+
+
+def bench_serving(args):
+    """Serving loop alone: capacity, then Poisson loads at 0.5 and 0.8 of it."""
+    from paper_1701_01575_gb300 import build
+    build.build()
+    blk = serving_block(args)
+    loads = blk["loads"]
     out = {"metric": "serving: p50/p99 request latency and GCUPS at 0.8 of capacity",
            "value": loads["0.8C"]["p99_ms"], "unit": "ms (p99)", "n_gpus": 1,
            "higher_is_better": False, "data": "synthetic", "dtype": "i16x2+i32",
-           "config": {"workload": "serving: Poisson arrivals, 70% protein queries "
-                                  "(log-uniform 50..2000) vs 500,000 targets top-10 + traceback, "
-                                  "30% DNA read batches (log-uniform 1e3..1e5 reads of 150 bp vs "
-                                  "500 bp windows of a 10 Mb genome) with traceback; 2 slots",
-                      "requests_per_level": n},
-           "capacity": dict(cap, requests_per_s=round(C, 2)), "loads": loads}
+           "config": {"workload": SERVING_TEXT, "requests_per_level": blk["requests_per_level"]},
+           "capacity": blk["capacity"], "loads": loads, "clocks": blk["clocks"]}
     print(json.dumps(out), flush=True)
-    d_p.free(); d_g.free(); ctx.close()
 
 
 # ------------------------------------------------------------- reference --
