@@ -24,7 +24,11 @@
 // Range: used only when (m + n) * max(|S|, o, e) + o stays far inside int16
 // for non-local modes (every value is exact), and in local mode with the
 // saturation flag of the inter-sequence kernel (best > 32767 - max S => the
-// pair is rerun in int32).
+// pair is rerun in int32).  Global / semi-global values are kept in offset
+// binary (each half + 0x8000) so that H - o is one 32-bit subtract with no borrow between the
+// halves: the pair with the longer window bounds every value of both halves
+// over all columns to |v| < 12000, with o < 4096.  Local mode keeps signed
+// halves (the ReLU maximum of DPX needs no constant register there).
 #include "dsa_internal.cuh"
 #include "dpx.cuh"
 
@@ -49,17 +53,6 @@ __device__ __forceinline__ int32_t h_col0(int mode, uint32_t fe, int64_t i, int 
   return -(o + (int32_t)(i - 1) * e);
 }
 
-// (score desc, j asc, i asc)
-struct C16 {
-  int s, i, j;
-  bool has;
-  __device__ __forceinline__ void offer(int s2, int i2, int j2) {
-    if (!has || s2 > s || (s2 == s && (j2 < j || (j2 == j && i2 < i)))) {
-      s = s2; i = i2; j = j2; has = true;
-    }
-  }
-};
-
 template <bool LOCAL, int ROWS, bool BYTES>
 __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
@@ -71,6 +64,9 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
   __shared__ uint32_t Sb[4];                            // BYTES: row q of S + o as 4 bytes
   __shared__ uint32_t park[2][ROWS][NT];                // parked columns (local mode)
   __shared__ uint2 ring[RING_SLOTS * NT];               // boundary-row columns in flight
+  // global / semi-global result state per thread and half: column n's best
+  // score and row, row m's best column
+  __shared__ int s_cb[2][NT], s_ci[2][NT], s_rj[2][NT];
   for (int x = threadIdx.x; x < A * A; x += blockDim.x) Sp[x] = (int16_t)(Sg[x] + o);
   if (BYTES && threadIdx.x < 4) {
     uint32_t w = 0;
@@ -84,8 +80,15 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
   const bool sg = mode == DSA_SEMIGLOBAL;
   const bool q_end_free = sg && (fe & DSA_FREE_Q_END);
   const bool t_end_free = sg && (fe & DSA_FREE_T_END);
-  const uint32_t neg_o2 = pack2(-o, -o), neg_e2 = pack2(-e, -e);
-  const uint32_t NEG2 = pack2(NEG16, NEG16);
+  // global / semi-global: values in offset binary (each half + 0x8000), as
+  // in the inter-sequence kernels -- unsigned DPX maxima, constants added
+  // mod 2^16, H - o one 32-bit subtract; local: signed halves, where the
+  // ReLU maximum needs no constant register
+  constexpr uint32_t BIAS2 = LOCAL ? 0u : 0x80008000u;
+  const uint32_t neg_e2 = pack2(-e, -e);
+  const uint32_t neg_o2 = pack2(-o, -o);
+  const uint32_t o2 = ((uint32_t)o << 16) | (uint32_t)o;
+  const uint32_t NEG2 = pack2(NEG16, NEG16) ^ BIAS2;
   const uint64_t gtid = blockIdx.x * (uint64_t)NT + tid;
   uint2* const scr = scratch + gtid;                   // column c at scr[c * stride]
   const uint64_t stride = (uint64_t)gridDim.x * NT;
@@ -97,16 +100,31 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
     const int32_t nmax = max(nlo, nhi);
     const uint8_t* qlo = qcodes + jb.q_lo;
     const uint8_t* qhi = qcodes + jb.q_hi;
-    const uint8_t* tlo = tcodes + jb.t_lo;
-    const uint8_t* thi = tcodes + jb.t_hi;
+    // the windows as aligned words (see the column loop)
+    // byte shifts of both windows in one register: the low half's in bits
+    // 0-4 (a funnel shift reads only those), the high half's from bit 8
+    const uint32_t sh2 = 8u * (uint32_t)(jb.t_lo & 3) | (8u * (uint32_t)(jb.t_hi & 3)) << 8;
+    const uint32_t* wlo = reinterpret_cast<const uint32_t*>(tcodes + (jb.t_lo & ~3ull));
+    const uint32_t* whi = reinterpret_cast<const uint32_t*>(tcodes + (jb.t_hi & ~3ull));
+    // a window's last word index plus one (recomputed where used: registers)
+    auto w_last = [](int32_t n) { return ((max(n, 1) - 1) >> 2) + 1; };
 
-    // local: running best per half; others: candidates
+    // local: running best per half (registers); others: the result
+    // candidates in shared memory (rarely touched) and a packed threshold
     int best_lo = 0, best_hi = 0, bj_lo = 0, bj_hi = 0, bi_lo = 0, bi_hi = 0;
-    C16 clo = {0, 0, 0, false}, chi = {0, 0, 0, false};
+    // row m (free target end): best H so far as an offset-binary threshold
+    // (a half that is not tracked holds the largest value: never exceeded)
+    uint32_t rthr = 0xFFFFFFFFu;
     if (!local) {
-      const int32_t hm0 = h_col0(mode, fe, m, o, e);
-      if (t_end_free) { clo.offer(hm0, m, 0); chi.offer(hm0, m, 0); }
-      if (q_end_free) { clo.offer(h_row0(mode, fe, nlo, o, e), 0, nlo); chi.offer(h_row0(mode, fe, nhi, o, e), 0, nhi); }
+      const int32_t hm0 = h_col0(mode, fe, m, o, e);   // the candidate (m, 0)
+      if (t_end_free) rthr = pack2(hm0, hm0) ^ BIAS2;
+      s_rj[0][tid] = 0;
+      s_rj[1][tid] = 0;
+      // column n: the candidate (0, n) with a free query end, else none yet
+      s_cb[0][tid] = q_end_free ? h_row0(mode, fe, nlo, o, e) : INT32_MIN;
+      s_cb[1][tid] = q_end_free ? h_row0(mode, fe, nhi, o, e) : INT32_MIN;
+      s_ci[0][tid] = 0;
+      s_ci[1][tid] = 0;
     }
 
     for (int32_t i0 = 0; i0 < m; i0 += ROWS) {
@@ -119,7 +137,7 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
       for (int r = 0; r < ROWS; ++r) {
         const int32_t i = i0 + r + 1;
         const int32_t hc = h_col0(mode, fe, i, o, e) - o;
-        Ho[r] = pack2(hc, hc);
+        Ho[r] = pack2(hc, hc) ^ BIAS2;
         E[r] = NEG2;
         if (BYTES) {
           sb_lo[r] = r < rows ? Sb[qlo[i - 1]] : 0u;
@@ -129,9 +147,9 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
         }
       }
       const int32_t hd = h_col0(mode, fe, i0, o, e) - o;
-      uint32_t diag = pack2(hd, hd);
+      uint32_t diag = pack2(hd, hd) ^ BIAS2;
       int pend = 0;
-      uint32_t thr2 = pack2(max(best_lo - 1, 0), max(best_hi - 1, 0));
+      uint32_t thr2 = pack2(max(best_lo - 1, 0), max(best_hi - 1, 0)) ^ BIAS2;
       // The column loop in four forms (first strip: top row from the boundary
       // of the matrix; last strip: result candidates, no boundary row to hand
       // down), so that no per-column branch depends on the strip.
@@ -139,9 +157,6 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
         constexpr bool FIRST = decltype(first_c)::value;
         constexpr bool LAST = decltype(last_c)::value;
         const bool col_n = LAST || q_end_free;   // column-n candidates in this strip
-        // loads run one column ahead of the arithmetic (target residues and
-        // the boundary row handed down by the previous strip); the last
-        // iteration re-reads a valid column instead of branching
         // the previous strip's boundary row arrives through a per-thread ring
         // of RING_SLOTS columns, copied AHEAD columns ahead by cp.async (one
         // commit group per column); the copy issued at column j refills the
@@ -155,10 +170,28 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
             cp_async_commit();
           }
         }
-        uint32_t n_alo = tlo[0], n_ahi = thi[0];
+        // window residues by aligned 32-bit words: the residues of columns
+        // 4g+1 .. 4g+4 are bytes s .. s+3 (s = the window's address mod 4)
+        // of the word pair (g, g+1) counted from the aligned address below
+        // the window; each group's second word is loaded one group (4
+        // columns) ahead, and word indices stop at the window's last word
+        // plus one, which stays inside the sequence buffer's padding
+        uint32_t wa_lo = __ldg(wlo), wb_lo = __ldg(wlo + min(1, w_last(nlo)));
+        uint32_t wa_hi = __ldg(whi), wb_hi = __ldg(whi + min(1, w_last(nhi)));
+        uint32_t r4_lo = 0, r4_hi = 0;
         for (int32_t j = 1; j <= nmax; ++j) {
-          const uint32_t a_lo = j <= nlo ? n_alo : 0u;
-          const uint32_t a_hi = j <= nhi ? n_ahi : 0u;
+          if (((j - 1) & 3) == 0) {
+            const int32_t g = (j - 1) >> 2;
+            r4_lo = __funnelshift_r(wa_lo, wb_lo, sh2);
+            r4_hi = __funnelshift_r(wa_hi, wb_hi, sh2 >> 8);
+            wa_lo = wb_lo;
+            wa_hi = wb_hi;
+            wb_lo = __ldg(wlo + min(g + 2, w_last(nlo)));
+            wb_hi = __ldg(whi + min(g + 2, w_last(nhi)));
+          }
+          const uint32_t kb = 8u * (uint32_t)((j - 1) & 3);
+          const uint32_t a_lo = j <= nlo ? (r4_lo >> kb) & 0xFFu : 0u;
+          const uint32_t a_hi = j <= nhi ? (r4_hi >> kb) & 0xFFu : 0u;
           uint2 v = make_uint2(0u, 0u);
           if (!FIRST) {
             cp_async_wait<AHEAD - 1>();   // column j has landed
@@ -167,14 +200,11 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
             if (c <= nmax) cp_async8(rt + (c & (RING_SLOTS - 1)) * NT, scr + (uint64_t)(c - 1) * stride);
             cp_async_commit();
           }
-          const int32_t jn = min(j, nmax - 1);
-          n_alo = tlo[min(jn, max(nlo - 1, 0))];
-          n_ahi = thi[min(jn, max(nhi - 1, 0))];
           uint32_t topHo, F;
           if (FIRST) {
             const int32_t h0l = h_row0(mode, fe, min(j, nlo), o, e) - o;
             const int32_t h0h = h_row0(mode, fe, min(j, nhi), o, e) - o;
-            topHo = pack2(h0l, h0h);
+            topHo = pack2(h0l, h0h) ^ BIAS2;
             F = topHo;   // F of row 1 = H[0][j] - o
           } else {
             topHo = v.x;
@@ -193,17 +223,24 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
                                         : (uint32_t)(uint16_t)Sp[(qa[r] & 0xFFFFu) + a_lo] |
                                               ((uint32_t)(uint16_t)Sp[(qa[r] >> 16) + a_hi] << 16);
               const uint32_t old = Ho[r];
-              E[r] = addmax2(E[r], neg_e2, old);
-              const uint32_t t = addmax2(d, sp, E[r]);
-              const uint32_t h = local ? max2_relu(t, F) : __vmaxs2(t, F);
-              Ho[r] = add2(h, neg_o2);
-              F = addmax2(F, neg_e2, Ho[r]);
-              d = old;
-              hlast = h;
+              uint32_t h;
               if (local) {
+                E[r] = addmax2(E[r], neg_e2, old);
+                const uint32_t t = addmax2(d, sp, E[r]);
+                h = max2_relu(t, F);
+                Ho[r] = add2(h, neg_o2);
+                F = addmax2(F, neg_e2, Ho[r]);
                 if (r & 1) cm = max3_2(cm, hprev, h);
                 else hprev = h;
+              } else {
+                E[r] = addmax2u(E[r], neg_e2, old);
+                const uint32_t t = addmax2u(d, sp, E[r]);
+                h = __vmaxu2(t, F);
+                Ho[r] = h - o2;   // no borrow between the halves (see the header)
+                F = addmax2u(F, neg_e2, Ho[r]);
               }
+              d = old;
+              hlast = h;
             }
           }
           if (local && LAST && (rows & 1)) cm = __vmaxs2(cm, hprev);
@@ -223,28 +260,35 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
                 for (int r = 0; r < ROWS; ++r) park[1][r][tid] = Ho[r];
                 best_hi = ch; bj_hi = j; pend |= 2;
               }
-              thr2 = pack2(max(best_lo - 1, 0), max(best_hi - 1, 0));
+              thr2 = pack2(max(best_lo - 1, 0), max(best_hi - 1, 0)) ^ BIAS2;
             }
           } else {
-            // row m (last strip) and column n
-            if (LAST && t_end_free) {
-              if (j <= nlo) clo.offer(lo16(hlast), m, j);
-              if (j <= nhi) chi.offer(hi16(hlast), m, j);
+            // row m (last strip, free target end): strictly better H, so the
+            // smallest j of a tie stays
+            if (LAST && __vmaxu2(hlast, rthr) != rthr) {
+              if (j <= nlo && (hlast & 0xFFFFu) > (rthr & 0xFFFFu)) {
+                rthr = (rthr & 0xFFFF0000u) | (hlast & 0xFFFFu);
+                s_rj[0][tid] = j;
+              }
+              if (j <= nhi && (hlast >> 16) > (rthr >> 16)) {
+                rthr = (rthr & 0x0000FFFFu) | (hlast & 0xFFFF0000u);
+                s_rj[1][tid] = j;
+              }
             }
-            if (col_n && j == nlo) {
-              // column n of the low pair: first row of this strip holding its maximum
-              int bs = -32768, br = 0;
+            // column n: the first row of this strip holding its maximum,
+            // strictly better than the earlier strips' (smaller i first)
+            if (col_n && (j == nlo || j == nhi)) {
 #pragma unroll
-              for (int r = ROWS - 1; r >= 0; --r)
-                if (r < rows && (q_end_free || r == rows - 1) && lo16(Ho[r]) + o >= bs) { bs = lo16(Ho[r]) + o; br = r; }
-              clo.offer(bs, i0 + br + 1, j);
-            }
-            if (col_n && j == nhi) {
-              int bs = -32768, br = 0;
+              for (int x = 0; x < 2; ++x) {
+                if (j != (x ? nhi : nlo)) continue;
+                int bs = -32768, br = 0;
 #pragma unroll
-              for (int r = ROWS - 1; r >= 0; --r)
-                if (r < rows && (q_end_free || r == rows - 1) && hi16(Ho[r]) + o >= bs) { bs = hi16(Ho[r]) + o; br = r; }
-              chi.offer(bs, i0 + br + 1, j);
+                for (int r = ROWS - 1; r >= 0; --r) {
+                  const int v16 = (x ? hi16(Ho[r] ^ BIAS2) : lo16(Ho[r] ^ BIAS2)) + o;
+                  if (r < rows && (q_end_free || r == rows - 1) && v16 >= bs) { bs = v16; br = r; }
+                }
+                if (bs > s_cb[x][tid]) { s_cb[x][tid] = bs; s_ci[x][tid] = i0 + br + 1; }
+              }
             }
           }
         }
@@ -263,14 +307,14 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
         const int want = best_lo - o;
         int rr = ROWS - 1;
         for (int r = ROWS - 1; r >= 0; --r)
-          if (lo16(park[0][r][tid]) == want) rr = r;
+          if (lo16(park[0][r][tid] ^ BIAS2) == want) rr = r;
         bi_lo = i0 + rr + 1;
       }
       if (pend & 2) {
         const int want = best_hi - o;
         int rr = ROWS - 1;
         for (int r = ROWS - 1; r >= 0; --r)
-          if (hi16(park[1][r][tid]) == want) rr = r;
+          if (hi16(park[1][r][tid] ^ BIAS2) == want) rr = r;
         bi_hi = i0 + rr + 1;
       }
     }
@@ -286,11 +330,20 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
         o_flag[jb.out_hi] = best_hi > T ? 1 : 0;
       }
     } else {
-      o_score[jb.out_lo] = clo.s; o_qend[jb.out_lo] = clo.i - 1; o_tend[jb.out_lo] = clo.j - 1;
-      o_flag[jb.out_lo] = 0;
-      if (jb.out_hi != 0xFFFFFFFFu) {
-        o_score[jb.out_hi] = chi.s; o_qend[jb.out_hi] = chi.i - 1; o_tend[jb.out_hi] = chi.j - 1;
-        o_flag[jb.out_hi] = 0;
+      // the better of row m's best (m, j) and column n's best (i, n) under
+      // (score desc, j asc, i asc): row m wins a tie only at a smaller j
+      for (int x = 0; x < 2; ++x) {
+        const uint32_t out = x ? jb.out_hi : jb.out_lo;
+        if (out == 0xFFFFFFFFu) continue;
+        const int n = x ? nhi : nlo;
+        int bs = s_cb[x][tid], bi = s_ci[x][tid], bj = n;
+        if (t_end_free) {
+          const int rb = (x ? hi16(rthr ^ BIAS2) : lo16(rthr ^ BIAS2));
+          const int rj = s_rj[x][tid];
+          if (rb > bs || (rb == bs && rj < n)) { bs = rb; bi = m; bj = rj; }
+        }
+        o_score[out] = bs; o_qend[out] = bi - 1; o_tend[out] = bj - 1;
+        o_flag[out] = 0;
       }
     }
   }
