@@ -449,12 +449,17 @@ int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const in
                       int A, int o, int e, int mode, uint32_t fe, bool bytes_ok,
                       const LongJob* d_jobs, uint32_t n_jobs, const uint32_t* d_items,
                       uint32_t n_items, int2* d_bnd, uint32_t* d_prog, void* d_cands, Scores out);
-// items: 2 words (job, band) per band of every job
-int launch_long_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
-                          const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
-                          const LongTbJob* d_jobs, uint32_t n_jobs, const uint32_t* d_items,
-                          uint32_t n_items, const int2* d_bnd, uint32_t* d_dir,
-                          uint32_t* d_cig_tmp, dsa_hit* d_hits);
+// Checkpointed traceback of long pairs, part 1: the decisions of the bands
+// named by `items` (2 words (job, band) each; job indexes d_jobs).
+int launch_long_tb_fill(dsa_ctx* ctx, cudaStream_t stream, const dsa_db* db, const dsa_db* qs,
+                        const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
+                        const LongTbJob* d_jobs, const uint32_t* d_items, uint32_t n_items,
+                        const int2* d_bnd, uint32_t* d_dir);
+// Part 2: one warp per job walks its decisions back from the end cell
+// (every band of those jobs filled before, in stream order).
+int launch_long_tb_walk(dsa_ctx* ctx, cudaStream_t stream, const LongTbJob* d_jobs,
+                        uint32_t n_jobs, int mode, uint32_t fe, const uint32_t* d_dir,
+                        uint32_t* d_cig_tmp, dsa_hit* d_hits);
 size_t long_cand_size();
 int long_band_rows();   // rows of a score-pass band
 int long_ckpt_rows();   // rows between traceback checkpoints (a traceback band)

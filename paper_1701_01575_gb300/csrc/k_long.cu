@@ -31,6 +31,8 @@
 #include "dsa_internal.cuh"
 #include "dpx.cuh"
 
+#include <type_traits>
+
 namespace dsa {
 namespace {
 
@@ -144,10 +146,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
     int32_t sendH = 0, sendF = NEG32;                  // H - o and F of the lane's last row
     int sendA = 0;
     bool timed_out = false;
-    // boundary row of the band above for columns blk+1 .. blk+32 (lane k: blk+k+1)
-    auto fetch_bnd = [&](int32_t blk) -> int2 {
-      if (b == 0 || blk >= n) return make_int2(NEG32, NEG32);
-      const uint32_t need = (uint32_t)min(blk + 32, n);
+    // bounded wait until the band above has published `need` columns
+    auto wait_for = [&](uint32_t need) {
       bool late = false;
       if (!timed_out) {
         const uint64_t t0 = global_ns();
@@ -166,9 +166,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
         if (!timed_out && lane == 0) atomicExch(status, DSA_ERR_DEVICE_TIMEOUT);
         timed_out = true;
       }
+    };
+    // boundary row of the band above for columns blk+1 .. blk+32 (lane k: blk+k+1)
+    auto fetch_bnd = [&](int32_t blk) -> int2 {
+      if (b == 0 || blk >= n) return make_int2(NEG32, NEG32);
+      wait_for((uint32_t)min(blk + 32, n));
       const int32_t jj = blk + lane + 1;
       return jj <= n ? up_bnd[jj - 1] : make_int2(NEG32, NEG32);
     };
+
     auto fetch_res = [&](int32_t blk) -> int {
       const int32_t jj = blk + lane;
       return jj < n ? (int)t[jj] : 0;
@@ -176,7 +182,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
     int2 bcur = fetch_bnd(0), bnxt = fetch_bnd(32);
     int tcur = fetch_res(0), tnxt = fetch_res(32);
     const int32_t steps = n + 31;
-    for (int32_t s = 1; s <= steps; ++s) {
+    // One step of the wavefront.  CHECK = false: every lane is on a real
+    // column (32 <= s <= n) of a band whose rows are all real rows, so no
+    // bounds are tested.
+    auto step = [&](int32_t s, auto check_c) {
+      constexpr bool CHECK = decltype(check_c)::value;
       const int k = (s - 1) & 31;
       const int32_t bx = __shfl_sync(FULL, bcur.x, k);
       const int32_t by = __shfl_sync(FULL, bcur.y, k);
@@ -184,16 +194,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
       int32_t Hup = __shfl_up_sync(FULL, sendH, 1);   // H - o of the cell above the lane
       int32_t Fup = __shfl_up_sync(FULL, sendF, 1);
       int a = __shfl_up_sync(FULL, sendA, 1);
-      if (lane == 0) {
-        a = ta;
-        if (b == 0) {
-          Hup = h_row0(mode, fe, s, o, e) - o;
-          Fup = NEG32;
-        } else {
-          Hup = bx - o;
-          Fup = by;
-        }
-      }
+      // lane 0 reads the band above (or row 0): selects, not a branch
+      const int32_t h0 = b == 0 ? h_row0(mode, fe, s, o, e) - o : bx - o;
+      const int32_t f0 = b == 0 ? NEG32 : by;
+      Hup = lane == 0 ? h0 : Hup;
+      Fup = lane == 0 ? f0 : Fup;
+      a = lane == 0 ? ta : a;
       if (k == 31) {   // block consumed: rotate, fetch the block after the next
         bcur = bnxt;
         tcur = tnxt;
@@ -203,7 +209,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
       }
       sendA = a;
       const int32_t j = s - lane;
-      if (j >= 1 && j <= n && r0 < m) {
+      if (!CHECK || (j >= 1 && j <= n && r0 < m)) {
         int32_t d = diag;   // H - o above-left
         diag = Hup;
         int32_t F = Fup, hoa = Hup;   // F and H - o of the cell above
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
           const int32_t i = r0 + r + 1;
-          if (i <= m) {
+          if (!CHECK || i <= m) {
             F = __viaddmax_s32(F, -e, hoa);                  // F = max(F - e, H_above - o)
             E[r] = __viaddmax_s32(E[r], -e, Ho[r]);          // E = max(E - e, H_left - o)
             const int32_t sv = BYTES ? (int32_t)prmt(qv[r], 0u, sel) : (int32_t)So[qv[r] + a];
@@ -256,14 +262,19 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
         sendH = hoa;
         sendF = F;
         if (stores_ck) ck[j - 1] = make_int2(hoa + o, F);
-        if (stores_bot) {
-          if ((uint32_t)j % PUBLISH == 0 || j == n) {
-            __threadfence();
-            st_release_u32(my_prog, (uint32_t)j);
-          }
-        }
+        // the release store orders this lane's own earlier row stores, the
+        // only ones the band below reads
+        if (stores_bot && ((uint32_t)j % PUBLISH == 0 || j == n)) st_release_u32(my_prog, (uint32_t)j);
       }
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    int32_t s = 1;
+    if (i0 + BAND <= m) {
+      for (; s < 32 && s <= steps; ++s) step(s, T_{});   // wavefront filling
+      for (; s <= n; ++s) step(s, F_{});                  // every lane on a real column
     }
+    for (; s <= steps; ++s) step(s, T_{});                // draining (or a short band)
     // merge the lanes' candidates (each lane's is its first best in (j, i) order)
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -521,23 +532,45 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
             break;
           }
           if (rr < wr0 || (jc >> 3) < wlo) { need = 1; break; }
-          const uint32_t nib = (win[(rr - wr0) * WIN_WORDS + ((jc >> 3) - wlo)] >> (4 * (jc & 7))) & 15u;
-          if (st == 0) {
-            const uint32_t src = nib & 3u;
-            if (src == 3) break;
-            if (src == 0) { c.emit(0); --i; --j; --rr; --jc; }
-            else st = src == 1 ? 1 : 2;
-          } else if (st == 1) {
-            c.emit(1);
-            if (nib & 8u) st = 0;
-            --i;
-            --rr;
-          } else {
-            c.emit(2);
-            if (nib & 4u) st = 0;
-            --j;
-            --jc;
+          // Every step moves up, left or both by one, so the next `safe`
+          // moves stay inside the window and off row 0 and column 0: take
+          // them with no tests, stepping the window address and the
+          // nibble's shift along.  A switch from H to a gap state reads the
+          // same cell's open bit, so it is taken in the same step.
+          const int32_t safe = min(min(rr - wr0, jc - 8 * wlo), min(i - 1, j - 1));
+          const uint32_t* p = win + (rr - wr0) * WIN_WORDS + ((jc >> 3) - wlo);
+          uint32_t sh = 4u * (uint32_t)(jc & 7);
+          bool stop = false;
+          int32_t q = 0;
+          for (; q <= safe; ++q) {
+            const uint32_t nib = (*p >> sh) & 15u;
+            if (st == 0) {
+              const uint32_t src = nib & 3u;
+              if (src == 3) { stop = true; break; }
+              if (src == 0) {   // M: up and left
+                c.emit(0);
+                p -= WIN_WORDS + (sh == 0 ? 1 : 0);
+                sh = (sh - 4u) & 31u;
+                --i; --j; --rr; --jc;
+                continue;
+              }
+              st = (int)src;   // 1: I (F state), 2: D (E state)
+            }
+            if (st == 1) {   // I: up
+              c.emit(1);
+              if (nib & 8u) st = 0;
+              p -= WIN_WORDS;
+              --i; --rr;
+            } else {         // D: left
+              c.emit(2);
+              if (nib & 4u) st = 0;
+              p -= (sh == 0 ? 1 : 0);
+              sh = (sh - 4u) & 31u;
+              --j; --jc;
+            }
           }
+          guard -= q;
+          if (stop) break;
         }
       }
       need = __shfl_sync(FULL, need, 0);
@@ -615,21 +648,26 @@ size_t long_cand_size() { return sizeof(Cand); }
 int long_band_rows() { return BAND; }
 int long_ckpt_rows() { return TB_BAND; }
 
-int launch_long_traceback(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs,
-                          const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
-                          const LongTbJob* d_jobs, uint32_t n_jobs, const uint32_t* d_items,
-                          uint32_t n_items, const int2* d_bnd, uint32_t* d_dir,
-                          uint32_t* d_cig_tmp, dsa_hit* d_hits) {
-  if (n_jobs == 0) return DSA_OK;
+int launch_long_tb_fill(dsa_ctx* ctx, cudaStream_t stream, const dsa_db* db, const dsa_db* qs,
+                        const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
+                        const LongTbJob* d_jobs, const uint32_t* d_items, uint32_t n_items,
+                        const int2* d_bnd, uint32_t* d_dir) {
+  if (n_items == 0) return DSA_OK;
   const unsigned grid = (unsigned)std::min<uint64_t>((n_items + WARPS - 1) / WARPS,
                                                      (uint64_t)ctx->sm_count * 16);
   auto fill = A <= 4 ? k_long_tb_fill<true> : k_long_tb_fill<false>;
-  fill<<<grid, WARPS * 32, 0, ctx->stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e, mode, fe,
-                                              d_jobs, d_items, n_items, d_bnd, d_dir);
+  fill<<<grid, WARPS * 32, 0, stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e, mode, fe,
+                                        d_jobs, d_items, n_items, d_bnd, d_dir);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
-  k_long_tb_walk<<<n_jobs, 32, 0, ctx->stream>>>(d_jobs, n_jobs, mode, fe, d_dir, d_cig_tmp,
-                                                 d_hits);
+  return DSA_OK;
+}
+
+int launch_long_tb_walk(dsa_ctx* ctx, cudaStream_t stream, const LongTbJob* d_jobs,
+                        uint32_t n_jobs, int mode, uint32_t fe, const uint32_t* d_dir,
+                        uint32_t* d_cig_tmp, dsa_hit* d_hits) {
+  if (n_jobs == 0) return DSA_OK;
+  k_long_tb_walk<<<n_jobs, 32, 0, stream>>>(d_jobs, n_jobs, mode, fe, d_dir, d_cig_tmp, d_hits);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   return DSA_OK;

@@ -441,11 +441,14 @@ int tb_run_long(TbRun& R, std::vector<LongTbJob>& list, const int2* bnd_rows, ui
     DSA_TRY(upload(ctx, d_shim, shim));
     DSA_TRY(d_dir.alloc(ctx, dir * 4));
     DSA_TRY(d_cig.alloc(ctx, cig * 4));
-    DSA_TRY(launch_long_traceback(ctx, res->db, res->queries, R.d_mat.as<int8_t>(), res->A,
-                                  res->gap_open, res->gap_extend, res->mode, res->free_ends,
-                                  d_lj.as<LongTbJob>(), (uint32_t)chunk.size(),
-                                  d_items.as<uint32_t>(), (uint32_t)(items.size() / 2), bnd_rows,
-                                  d_dir.as<uint32_t>(), d_cig.as<uint32_t>(), res->d_hits));
+    // every band of every hit of the chunk in one launch, then one warp per hit
+    DSA_TRY(launch_long_tb_fill(ctx, ctx->stream, res->db, res->queries, R.d_mat.as<int8_t>(),
+                                res->A, res->gap_open, res->gap_extend, res->mode,
+                                res->free_ends, d_lj.as<LongTbJob>(), d_items.as<uint32_t>(),
+                                (uint32_t)(items.size() / 2), bnd_rows, d_dir.as<uint32_t>()));
+    DSA_TRY(launch_long_tb_walk(ctx, ctx->stream, d_lj.as<LongTbJob>(), (uint32_t)chunk.size(),
+                                res->mode, res->free_ends, d_dir.as<uint32_t>(),
+                                d_cig.as<uint32_t>(), res->d_hits));
     DSA_TRY(launch_cigar_compact(ctx, res->d_hits, d_shim.as<TbJob>(), (uint32_t)shim.size(),
                                  d_cig.as<uint32_t>(), res->d_cigar, R.total,
                                  R.d_total.as<uint64_t>()));
