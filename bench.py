@@ -36,9 +36,10 @@ METRIC = "GCUPS (bit-exact) batched protein database search"
 # 1.194 T cells); traffic grows with the cells (boundary rows per column and
 # strip), so a launch's traffic is this figure times its cells.
 INTER_DRAM_BYTES_PER_CELL = 416.40e9 / 1.194104e12
-# the same figure for the global / semi-global form k_inter_glob16 (None until
-# a capture of the current kernel exists)
-GLOB_DRAM_BYTES_PER_CELL = None
+# the same figure for the global / semi-global form k_inter_glob16, from the
+# capture summarised in profiles/k_inter_glob16_global_8q_350k.md (416.6 GB
+# for the same 1.194 T cells)
+GLOB_DRAM_BYTES_PER_CELL = 416.64e9 / 1.194104e12
 
 # the workloads measured after the headline (each timed on its own)
 SUB_WORKLOADS = ("reads_vs_windows", "long_pairs_global", "long_pairs_local",
