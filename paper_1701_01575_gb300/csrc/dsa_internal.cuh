@@ -474,10 +474,13 @@ struct Pair16Job {
   uint32_t out_lo, out_hi;
   uint32_t pad;
 };
-// bytes: A <= 4 and every S + o in [-128, 127] (byte-permute substitution form)
+// bytes: A <= 4 and every S + o in [-128, 127] (byte-permute substitution
+// form); rows: strip rows of the byte form, 16 or pairs16_wide_rows() (the
+// wide variant); the shared-memory form always uses 16
 int launch_pairs16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix, int A,
-                   int o, int e, int mode, uint32_t fe, int smax, bool bytes,
+                   int o, int e, int mode, uint32_t fe, int smax, bool bytes, int rows,
                    const Pair16Job* d_jobs, uint32_t n_jobs, uint32_t max_n, Scores out);
+int pairs16_wide_rows();
 
 // Device planning of explicit pairs (k_pairplan.cu).
 struct PairPlanParams {

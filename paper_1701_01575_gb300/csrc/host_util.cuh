@@ -6,6 +6,7 @@
 
 #include "dsa_internal.cuh"
 
+#include <string>
 #include <thread>
 #include <utility>
 #include <vector>
@@ -95,6 +96,14 @@ int pairs_classify(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const PairP
 int score_pairs(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs, PairPass& pp,
                 int mode, uint32_t fe, const int8_t* matrix, const int8_t* d_mat, int A, int o,
                 int e, const Validated& v, bool local16, bool packed_ok, int64_t w16, Scores sc);
+
+// The autotuner's cache (a JSON file shared by the planners, plan_all.cu):
+// tuner_get fails on a miss and under DSA_AUTOTUNE=retune; tuner_put records
+// and writes the file.  tuner_shape_prefix: GPU name, SM count, driver.
+bool tuner_get(const std::string& key, uint32_t* val);
+void tuner_put(const std::string& key, uint32_t val);
+std::string tuner_shape_prefix(dsa_ctx* ctx);
+int tuner_bin(uint64_t x);   // floor(log2 x)
 
 // Result hits (and CIGAR words) copied to the host arrays of the result.
 int fetch_hits(dsa_res* res);

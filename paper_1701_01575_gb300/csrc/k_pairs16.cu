@@ -41,6 +41,10 @@ constexpr int NT = 128;
 constexpr int BLOCKS_PER_SM = 4;
 constexpr int ROWS_LDS = 16;     // strip rows, shared-memory substitution form
 constexpr int ROWS_BYTES = 16;   // strip rows, byte-permute form (two table registers per row)
+// the byte-permute form's wide variant: 20-row strips (the column overhead
+// spread over more rows) at 3 blocks per SM (168 registers, 12 warps)
+constexpr int ROWS_BYTES_WIDE = 20;
+constexpr int BLOCKS_PER_SM_WIDE = 3;
 constexpr int RING_SLOTS = 8;    // boundary-row ring: slots per thread (a power of two)
 constexpr int AHEAD = RING_SLOTS - 1;   // columns copied ahead of the arithmetic
 
@@ -53,8 +57,8 @@ __device__ __forceinline__ int32_t h_col0(int mode, uint32_t fe, int64_t i, int 
   return -(o + (int32_t)(i - 1) * e);
 }
 
-template <bool LOCAL, int ROWS, bool BYTES>
-__global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
+template <bool LOCAL, int ROWS, bool BYTES, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_pairs16(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe, int T,
     const Pair16Job* __restrict__ jobs, uint32_t n_jobs, uint2* __restrict__ scratch,
@@ -351,19 +355,27 @@ __global__ void __launch_bounds__(NT, BLOCKS_PER_SM) k_pairs16(
 
 }  // namespace
 
+int pairs16_wide_rows() { return ROWS_BYTES_WIDE; }
+
 int launch_pairs16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix, int A,
-                   int o, int e, int mode, uint32_t fe, int smax, bool bytes,
+                   int o, int e, int mode, uint32_t fe, int smax, bool bytes, int rows,
                    const Pair16Job* d_jobs, uint32_t n_jobs, uint32_t max_n, Scores out) {
   if (n_jobs == 0) return DSA_OK;
+  const bool wide = bytes && rows == ROWS_BYTES_WIDE;
   // persistent: every block resident at once, jobs taken in a grid stride
-  const uint64_t blocks =
-      std::min<uint64_t>((n_jobs + NT - 1) / NT, (uint64_t)ctx->sm_count * BLOCKS_PER_SM);
+  const uint64_t blocks = std::min<uint64_t>(
+      (n_jobs + NT - 1) / NT, (uint64_t)ctx->sm_count * (wide ? BLOCKS_PER_SM_WIDE : BLOCKS_PER_SM));
   const size_t scr_bytes = (size_t)blocks * NT * max_n * sizeof(uint2);
   void* scr = nullptr;
   DSA_TRY(ctx->alloc(&scr, scr_bytes));
-  auto kern = mode == DSA_LOCAL
-                  ? (bytes ? k_pairs16<true, ROWS_BYTES, true> : k_pairs16<true, ROWS_LDS, false>)
-                  : (bytes ? k_pairs16<false, ROWS_BYTES, true> : k_pairs16<false, ROWS_LDS, false>);
+  auto kern =
+      mode == DSA_LOCAL
+          ? (wide    ? k_pairs16<true, ROWS_BYTES_WIDE, true, BLOCKS_PER_SM_WIDE>
+             : bytes ? k_pairs16<true, ROWS_BYTES, true, BLOCKS_PER_SM>
+                     : k_pairs16<true, ROWS_LDS, false, BLOCKS_PER_SM>)
+          : (wide    ? k_pairs16<false, ROWS_BYTES_WIDE, true, BLOCKS_PER_SM_WIDE>
+             : bytes ? k_pairs16<false, ROWS_BYTES, true, BLOCKS_PER_SM>
+                     : k_pairs16<false, ROWS_LDS, false, BLOCKS_PER_SM>);
   kern<<<(unsigned)blocks, NT, 0, ctx->stream>>>(
       qs->d_codes, db->d_codes, d_matrix, A, o, e, mode, fe, 32767 - std::max(0, smax), d_jobs,
       n_jobs, static_cast<uint2*>(scr), max_n, out.score, out.q_end, out.t_end, out.flag);

@@ -445,6 +445,41 @@ int run_packed_tuned(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
 
 }  // namespace
 
+bool tuner_get(const std::string& key, uint32_t* val) {
+  Tuner& t = tuner();
+  std::lock_guard<std::mutex> lk(t.mu);
+  const std::string path = tune_cache_path();
+  if (!t.loaded || path != t.path) tune_load(t, path);
+  const char* mode_env = getenv("DSA_AUTOTUNE");
+  if (mode_env && std::string(mode_env) == "retune") return false;
+  auto it = t.cache.find(key);
+  if (it == t.cache.end()) return false;
+  *val = it->second;
+  return true;
+}
+
+void tuner_put(const std::string& key, uint32_t val) {
+  Tuner& t = tuner();
+  std::lock_guard<std::mutex> lk(t.mu);
+  t.cache[key] = val;
+  tune_store(t);
+}
+
+std::string tuner_shape_prefix(dsa_ctx* ctx) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return "?";
+  }
+  int drv = 0;
+  cudaDriverGetVersion(&drv);
+  char key[320];
+  snprintf(key, sizeof key, "%s|sm%d|drv%d", prop.name, ctx->sm_count, drv);
+  return key;
+}
+
+int tuner_bin(uint64_t x) { return ilog2_bin(x); }
+
 // Score pass for all queries x all targets.
 int score_all_vs_all(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs, int mode,
                      uint32_t fe, const int8_t* d_mat, const int8_t* d_pssm, int A, int o, int e, const Validated& v,

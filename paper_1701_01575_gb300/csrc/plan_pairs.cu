@@ -9,7 +9,10 @@
 #include "host_util.cuh"
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 
 namespace dsa {
 
@@ -257,10 +260,54 @@ int score_pairs(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs, 
     }
     bool bytes = A <= 4;   // byte-permute substitution form
     for (int x = 0; x < A * A; ++x) bytes = bytes && matrix[x] + o >= -128 && matrix[x] + o <= 127;
+    auto launch = [&](int rows) {
+      return launch_pairs16(ctx, db, qs, d_mat, A, o, e, mode, fe, v.smax, bytes, rows,
+                            d_pj.as<Pair16Job>(), n_pj, max_n, sc);
+    };
+    // kernel variant of the byte form (16-row strips at 4 blocks per SM, or
+    // the wide 20-row strips at 3): DSA_PAIRS_ROWS, else the autotuner, per
+    // workload shape (mode, alphabet, and log2 bins of the job count, the
+    // longest query and the longest window), timing both on the first call
+    int rows = 16;
+    const int wide = pairs16_wide_rows();
+    const char* rows_env = getenv("DSA_PAIRS_ROWS");
+    const char* tune_env = getenv("DSA_AUTOTUNE");
+    if (rows_env) {
+      rows = bytes && atoi(rows_env) == wide ? wide : 16;
+    } else if (bytes && ctx->tune && !(tune_env && std::string(tune_env) == "off")) {
+      char k[160];
+      snprintf(k, sizeof k, "|pairs|%s|A%d|j%d|m%d|n%d|rows",
+               mode == DSA_LOCAL ? "local" : (mode == DSA_GLOBAL ? "global" : "semi"), A,
+               tuner_bin(n_pj), tuner_bin(qs->max_len), tuner_bin(max_n));
+      const std::string key = tuner_shape_prefix(ctx) + k;
+      uint32_t cached = 0;
+      if (tuner_get(key, &cached)) {
+        rows = (int)cached == wide ? wide : 16;
+      } else {
+        cudaEvent_t ev[3];
+        for (auto& x : ev) DSA_CUDA_TRY(cudaEventCreate(&x));
+        int trc = DSA_OK;
+        if (cudaEventRecord(ev[0], ctx->stream) != cudaSuccess || (trc = launch(16)) ||
+            cudaEventRecord(ev[1], ctx->stream) != cudaSuccess || (trc = launch(wide)) ||
+            cudaEventRecord(ev[2], ctx->stream) != cudaSuccess ||
+            cudaEventSynchronize(ev[2]) != cudaSuccess)
+          trc = trc ? trc : DSA_ERR_CUDA;
+        float t16 = 0.f, tw = 0.f;
+        if (!trc) {
+          cudaEventElapsedTime(&t16, ev[0], ev[1]);
+          cudaEventElapsedTime(&tw, ev[1], ev[2]);
+        }
+        for (auto& x : ev) cudaEventDestroy(x);
+        if (trc) {
+          set_error("pairs autotune: %s", cudaGetErrorString(cudaGetLastError()));
+          return trc;
+        }
+        rows = tw < 0.97f * t16 ? wide : 16;   // a switch needs a 3% gain
+        tuner_put(key, (uint32_t)rows);
+      }
+    }
     phase_begin(res, PH_INTER);
-    if ((rc = launch_pairs16(ctx, db, qs, d_mat, A, o, e, mode, fe, v.smax, bytes,
-                             d_pj.as<Pair16Job>(), n_pj, max_n, sc)))
-      return (rc);
+    if ((rc = launch(rows))) return (rc);
     phase_end(res, PH_INTER);
     res->phase_cells[PH_INTER] = p16cells;
     res->phase_cells[PH_INT32] -= p16cells;

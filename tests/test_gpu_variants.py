@@ -1,11 +1,12 @@
-"""Kernel variants of the packed database search and their autotuner.
+"""Kernel variants of the packed kernels and their autotuner.
 
 The inter-sequence kernels exist for two strip heights (28 rows, and 20 rows
-that waste fewer padding rows on short queries).  Every variant must give
-the oracle's scores and end cells bit for bit in every mode; the tuner
-times the variants on the first call of a workload shape and records its
-choice of strip height (and, in local mode, long-target threshold) in its
-cache file, which the next call reads.
+that waste fewer padding rows on short queries); the explicit-pairs kernel's
+byte form for two (16 rows at 4 blocks per SM, 20 rows at 3).  Every variant
+must give the oracle's scores and end cells bit for bit in every mode; the
+tuner times the variants on the first call of a workload shape and records
+its choice (and, for local database search, the long-target threshold) in
+its cache file, which the next call reads.
 """
 import json
 
@@ -97,3 +98,61 @@ def test_tuner_records_variant_and_reuses_it(ctx, mode, tmp_path, monkeypatch):
     g2 = gpu_all(ctx, queries, db, S, 11, 1, mode=mode)
     assert_same(g2[:3], orc, "cached")
     assert cache.read_text() == before
+
+
+@pytest.mark.parametrize("rows", ["16", "20"])
+@pytest.mark.parametrize("mode,fe", [(dsa.SEMIGLOBAL, 12), (dsa.LOCAL, 15), (dsa.GLOBAL, 15),
+                                     (dsa.SEMIGLOBAL, 15)])
+def test_pairs_kernel_variants_match_oracle(ctx, rows, mode, fe, monkeypatch):
+    """The packed pairs kernel's byte form in both strip heights (16 rows at
+    4 blocks per SM, 20 rows at 3): reads of 1-300 bp in windows, strips
+    ragged against both heights."""
+    monkeypatch.setenv("DSA_PAIRS_ROWS", rows)
+    rng = np.random.default_rng(1400 + int(rows) + 16 * mode + fe)
+    genome = rng.integers(0, 4, 60_000).astype(np.uint8)
+    lens = np.concatenate([[1, 15, 16, 17, 19, 20, 21, 39, 40, 41], rng.integers(1, 300, 600)])
+    reads, starts = [], []
+    for n in lens:
+        st = int(rng.integers(0, 60_000 - 700))
+        r = W.mutate(rng, genome[st + 50: st + 50 + int(n)], 0.03, 0.02)
+        reads.append(r if len(r) else np.zeros(1, np.uint8))
+        starts.append(st)
+    qs = W.SeqSet.from_list(reads)
+    db = W.SeqSet.from_list([genome])
+    pairs = np.zeros(qs.n, dtype=W.PAIR_DTYPE)
+    pairs["query_id"] = np.arange(qs.n)
+    pairs["t_offset"] = starts
+    pairs["t_len"] = 400 + rng.integers(0, 200, qs.n)
+    S = W.dna_matrix(1, -4)
+    d = ctx.load_set(db, 4)
+    q = ctx.load_set(qs, 4)
+    r = ctx.align(d, q, S, 6, 1, mode=mode, free_ends=fe, pairs=pairs)
+    ctx.sync()
+    h = r.hits()
+    sc, qe, te = oracle.score_pairs(qs.codes, qs.offsets, db.codes, db.offsets, pairs["query_id"],
+                                    pairs["target_id"], S, 6, 1, mode, fe,
+                                    pair_toff=pairs["t_offset"], pair_tlen=pairs["t_len"])
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), f"rows={rows}")
+    assert r.phase_cells()["inter16"] > 0
+
+
+def test_pairs_tuner_records_variant(ctx, tmp_path, monkeypatch):
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("DSA_AUTOTUNE_CACHE", str(cache))
+    monkeypatch.setenv("DSA_AUTOTUNE", "retune")
+    monkeypatch.delenv("DSA_PAIRS_ROWS", raising=False)
+    wl = W.reads_vs_windows(seed=W.SEED_BASE + 1450, n_reads=4000, ref_len=100_000)
+    d = ctx.load_set(wl.db, 4)
+    q = ctx.load_set(wl.queries, 4)
+    r = ctx.align(d, q, wl.matrix, 6, 1, mode=wl.mode, free_ends=wl.free_ends, pairs=wl.pairs)
+    ctx.sync()
+    h = r.hits()
+    p = wl.pairs
+    sc, qe, te = oracle.score_pairs(wl.queries.codes, wl.queries.offsets, wl.db.codes,
+                                    wl.db.offsets, p["query_id"], p["target_id"], wl.matrix, 6, 1,
+                                    wl.mode, wl.free_ends, pair_toff=p["t_offset"],
+                                    pair_tlen=p["t_len"])
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), "tuned pairs")
+    entries = json.loads(cache.read_text())
+    keys = [k for k in entries if "|pairs|" in k]
+    assert len(keys) == 1 and entries[keys[0]] in (16, 20)
