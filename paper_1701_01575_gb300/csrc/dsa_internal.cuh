@@ -271,6 +271,10 @@ constexpr int INTER_ROWS_SHORT = 20;   // their short-strip variant (short queri
 int launch_intra_local16(dsa_ctx* ctx, cudaStream_t stream, const dsa_db* db,
                          const PackedPlan& plan, const IntraWork& work, int o, int e, int smax,
                          Scores out, uint32_t n_targets_out);
+// Its global / semi-global form: `plan` built with end-anchored 32-row strips.
+int launch_intra_glob16(dsa_ctx* ctx, cudaStream_t stream, const dsa_db* db, const dsa_db* qs,
+                        const PackedPlan& plan, const IntraWork& work, int mode, uint32_t fe,
+                        int o, int e, int smax, int smin, Scores out, uint32_t n_targets_out);
 
 // Top-k per query over a dense [n_queries][n_targets] score matrix.
 int launch_topk(dsa_ctx* ctx, const Scores& s, uint32_t n_queries, uint32_t n_targets,

@@ -653,12 +653,12 @@ __global__ void __launch_bounds__(NT, 2) k_inter_glob16(const InterArgs A, const
 // NEG16.  With a position-specific profile P (row per query residue of the
 // set, Sec. II.C.2's user-defined scoring) the score is P[qoff + i][a].
 //
-// End-anchored form (anchored = 1, the global / semi-global kernel): a query
+// End-anchored form (anchored = 1, the global / semi-global kernels): a query
 // of m rows starts (rows - m % rows) % rows rows into its first strip, so its
 // last row is the bottom row of its last strip.  The padding rows above it,
-// absent queries and the padding residue get values that keep every cell
-// inside the int16 range: `tpad` (S + o) for padding rows and absent queries,
-// 0 for the padding residue of a real row.
+// rows past its end, absent queries and the padding residue get values that
+// keep every cell inside the int16 range: `tpad` (S + o) for padding rows and
+// absent queries, 0 for the padding residue of a real row.
 __global__ void k_strip_profile(const uint8_t* __restrict__ qcodes,
                                 const uint64_t* __restrict__ qoff, const uint32_t* __restrict__ qlen,
                                 const StripMeta* __restrict__ meta, uint32_t n_strips,
@@ -673,7 +673,9 @@ __global__ void k_strip_profile(const uint8_t* __restrict__ qcodes,
     if (q == NONE) return tpad;
     const int m = (int)qlen[q];
     const int i = (int)(kq & ~LAST) * rows + r - (rows - m % rows) % rows;
-    if (i < 0) return tpad;
+    // rows above the query, and (in a unit of the wavefront kernel, whose
+    // halves can differ in strips) rows past its end
+    if (i < 0 || i >= m) return tpad;
     if (a >= A) return 0;
     return sub(q, i, a) + o;
   };

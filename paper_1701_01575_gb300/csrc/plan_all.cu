@@ -24,9 +24,9 @@ namespace {
 //
 // Two speed choices of the packed path (every choice gives the same exact
 // results): the strip height of the inter-sequence kernel (28 rows, or 20
-// rows, which wastes fewer padding rows on short queries), and, in local
-// mode, which targets go to the wavefront kernel (long) and which to the
-// inter-sequence kernel.  For a workload shape (GPU, driver, mode, alphabet,
+// rows, which wastes fewer padding rows on short queries), and which
+// targets go to the wavefront kernel (long) and which to the inter-sequence
+// kernel.  For a workload shape (GPU, driver, mode, alphabet,
 // and log2 bins of the query count, query residues, longest query, target
 // count, database residues and longest target) the first call times each
 // strip height at the default threshold (a switch needs a 3% gain), then a
@@ -113,16 +113,14 @@ int ilog2_bin(uint64_t x) {
   return b;
 }
 
-// Packed score pass (int16x2).  Local: targets of groups longer than
-// `long_thr` go to the wavefront kernel on the side stream, the rest to the
+// Packed score pass (int16x2).  Targets of groups longer than `long_thr` go
+// to the wavefront kernel on the side stream, the rest to the
 // inter-sequence kernel; the results do not depend on long_thr, only the
-// time.  Global / semi-global: every target on the end-anchored form of the
-// inter-sequence kernel.
+// time.  Global / semi-global use the end-anchored forms of both kernels.
 int packed_score(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
                  const int8_t* d_mat, const int8_t* d_pssm, int A, int o, int e, const Validated& v, Scores out,
                  uint32_t long_thr, int rows, int mode = DSA_LOCAL, uint32_t fe = 15) {
   const bool local = mode == DSA_LOCAL;
-  if (!local) long_thr = UINT32_MAX;
   const uint32_t W = (uint32_t)rows;   // strip rows of the inter-sequence kernel
   const uint32_t nq = qs->n, nt = db->n;
   const int R = A + 1;
@@ -290,13 +288,17 @@ int packed_score(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
     ppl.d_prof = d_pprof.as<uint32_t>();
     xw.d_long_ids = d_long.as<uint32_t>();
     xw.d_items = d_litems.as<uint32_t>();
-    DSA_TRY(launch_strip_profile(ctx, qs, d_mat, d_pssm, A, o, ppl));
+    DSA_TRY(launch_strip_profile(ctx, qs, d_mat, d_pssm, A, o, ppl, !local, tpad));
     // long targets on the side stream, overlapping the inter-sequence kernel:
     // the two kernels write disjoint targets' results
     DSA_CUDA_TRY(cudaEventRecord(ctx->fork_ev, ctx->stream));
     DSA_CUDA_TRY(cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0));
     phase_begin(res, PH_INTRA, ctx->side);
-    DSA_TRY(launch_intra_local16(ctx, ctx->side, db, ppl, xw, o, e, v.smax, out, nt));
+    if (local)
+      DSA_TRY(launch_intra_local16(ctx, ctx->side, db, ppl, xw, o, e, v.smax, out, nt));
+    else
+      DSA_TRY(launch_intra_glob16(ctx, ctx->side, db, qs, ppl, xw, mode, fe, o, e, v.smax, v.smin,
+                                  out, nt));
     phase_end(res, PH_INTRA, ctx->side);
     DSA_CUDA_TRY(cudaEventRecord(ctx->join_ev, ctx->side));
   }
@@ -319,8 +321,8 @@ int forced_rows() {
   return 0;
 }
 
-// The packed pass with the autotuned kernel variant (strip rows) and, in
-// local mode, long-target threshold.
+// The packed pass with the autotuned kernel variant (strip rows) and
+// long-target threshold.
 int run_packed_tuned(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs,
                      const int8_t* d_mat, const int8_t* d_pssm, int A, int o, int e,
                      const Validated& v, Scores out, int mode, uint32_t fe) {
@@ -336,7 +338,7 @@ int run_packed_tuned(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
   const std::string tmode = mode_env ? mode_env : "cache";
   const int rows_default = rows_forced ? rows_forced : INTER_ROWS;
   const uint32_t thr_default = thr_env ? thr_forced : DEFAULT_THR;
-  if (tmode == "off" || (rows_forced && (thr_env || !local)))
+  if (tmode == "off" || (rows_forced && thr_env))
     return run(res, thr_default, rows_default);
   // workload shape key: GPU, driver, mode, alphabet, and log2 bins of the
   // query count, query residues, longest query, target count, database
@@ -361,8 +363,8 @@ int run_packed_tuned(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
     if (!t.loaded || path != t.path) tune_load(t, path);   // first use, or another file
     auto it_r = t.cache.find(key_rows);
     auto it_t = t.cache.find(key_thr);
-    if (tmode != "retune" && it_r != t.cache.end() && (!local || it_t != t.cache.end()))
-      return run(res, thr_env ? thr_forced : (local ? it_t->second : UINT32_MAX),
+    if (tmode != "retune" && it_r != t.cache.end() && it_t != t.cache.end())
+      return run(res, thr_env ? thr_forced : it_t->second,
                  rows_forced ? rows_forced : (int)it_r->second);
   }
   if (!ctx->tune)   // contexts that must not spend calls on tuning (serving workers)
@@ -370,7 +372,7 @@ int run_packed_tuned(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
   std::map<std::pair<uint32_t, int>, double> timed;   // (long groups, rows) -> ms
   auto groups_over = [&](uint32_t thr) {
     uint32_t g = 0;
-    while (local && g < db->n_groups && db->h_glen[g] > thr) ++g;
+    while (g < db->n_groups && db->h_glen[g] > thr) ++g;
     return g;
   };
   cudaEvent_t ev0, ev1;
@@ -399,11 +401,11 @@ int run_packed_tuned(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
       const double ms = measure(thr_default, rows);
       if (ms < 0.97 * best_ms) { best_ms = ms; best_rows = rows; }
     }
-  // 2. local mode: the long-target threshold, a local search from the
+  // 2. the long-target threshold, a local search from the
   //    default by factors of 4 in each direction while it improves;
   //    thresholds that move the same groups as the last one are skipped
-  uint32_t best = local ? thr_default : UINT32_MAX;
-  if (local && !thr_env)
+  uint32_t best = thr_default;
+  if (!thr_env)
     for (int dir = -1; dir <= 1 && rc == DSA_OK; dir += 2) {
       uint64_t cur = DEFAULT_THR;
       uint32_t last_g = groups_over(DEFAULT_THR);
@@ -436,7 +438,7 @@ int run_packed_tuned(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db*
   {
     std::lock_guard<std::mutex> lk(t.mu);
     if (!rows_forced) t.cache[key_rows] = (uint32_t)best_rows;
-    if (local && !thr_env) t.cache[key_thr] = best;
+    if (!thr_env) t.cache[key_thr] = best;
     tune_store(t);
   }
   // the final pass with the chosen variant records the phase timings and cells

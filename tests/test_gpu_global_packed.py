@@ -35,9 +35,10 @@ def ctx():
 
 
 def _packed(g):
-    """No pair of the result went to the int32 kernel except flagged reruns."""
-    r = g[5]
-    return r.phase_cells()["inter16"] > 0
+    """The score pass ran on the packed kernels (the inter-sequence kernel,
+    and the wavefront kernel for the targets the tuner sends there)."""
+    cells = g[5].phase_cells()
+    return cells["inter16"] + cells["intra16"] > 0
 
 
 @pytest.mark.parametrize("mode,fe", GLOBAL_MODES)
@@ -147,7 +148,7 @@ def test_search_shape_sample_with_traceback(ctx, mode, fe):
                                          targets=sample)
     assert_same((got["score"], got["q_end"], got["t_end"]), (sc, qe, te), "dense sample")
     scores = dh[:, :4].contiguous().view(torch.int32).reshape(wl.queries.n, wl.db.n).cpu().numpy()
-    assert dense.phase_cells()["inter16"] > 0
+    assert _packed((None,) * 5 + (dense,))
     dense.free()
     r = ctx.align(d, q, wl.matrix, 11, 1, mode=mode, free_ends=fe, top_k=10)
     ctx.traceback(r)

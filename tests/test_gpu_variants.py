@@ -5,8 +5,8 @@ that waste fewer padding rows on short queries); the explicit-pairs kernel's
 byte form for two (16 rows at 4 blocks per SM, 20 rows at 3).  Every variant
 must give the oracle's scores and end cells bit for bit in every mode; the
 tuner times the variants on the first call of a workload shape and records
-its choice (and, for local database search, the long-target threshold) in
-its cache file, which the next call reads.
+its choice (and the long-target threshold) in its cache file, which the
+next call reads.
 """
 import json
 
@@ -89,8 +89,7 @@ def test_tuner_records_variant_and_reuses_it(ctx, mode, tmp_path, monkeypatch):
     assert len(rows) == 1 and list(rows.values())[0] in (20, 28)
     key = list(rows)[0]
     assert ("|local|" in key) == (mode == dsa.LOCAL)
-    if mode == dsa.LOCAL:
-        assert key[:-len("|rows")] + "|thr" in entries
+    assert key[:-len("|rows")] + "|thr" in entries
     # a cached choice is reused: the next call does not tune (same result,
     # cache unchanged)
     monkeypatch.setenv("DSA_AUTOTUNE", "cache")
