@@ -464,6 +464,31 @@ int launch_long_tb_fill(dsa_ctx* ctx, cudaStream_t stream, const dsa_db* db, con
 int launch_long_tb_walk(dsa_ctx* ctx, cudaStream_t stream, const LongTbJob* d_jobs,
                         uint32_t n_jobs, int mode, uint32_t fe, const uint32_t* d_dir,
                         uint32_t* d_cig_tmp, dsa_hit* d_hits);
+// Per-band end-cell candidate of a long pair, ordered (score desc, j asc,
+// i asc); has = 0: none.
+struct LongCand {
+  int32_t s, i, j;
+  int32_t has;
+};
+// Two long pairs aligned together by the packed band pipeline, one in each
+// 16-bit half (indices into the LongJob array; b = NONE: the high half is
+// empty); the unit has its own per-band progress counters.
+struct LongPair16 {
+  uint32_t a, b;
+  uint64_t prog_off;
+};
+// Packed (int16x2) form of the long-pair score pass for alphabets of up to 4
+// letters with every S + o in int8 and scores whose range passes
+// long16_range_ok; writes the same boundary rows, checkpoints and per-band
+// candidates as launch_long_score and reduces them into `out`.
+bool long16_range_ok(int o, int e, int smax, int smin);
+int launch_long_score16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,
+                        int A, int o, int e, int mode, uint32_t fe, const LongJob* d_jobs,
+                        uint32_t n_jobs, const LongPair16* d_pjobs, const uint32_t* d_items,
+                        uint32_t n_items, int2* d_bnd, uint32_t* d_prog, void* d_cands,
+                        Scores out);
+int launch_long_reduce(dsa_ctx* ctx, const LongJob* d_jobs, uint32_t n_jobs, const void* d_cands,
+                       int mode, uint32_t fe, int o, int e, Scores out);
 size_t long_cand_size();
 int long_band_rows();   // rows of a score-pass band
 int long_ckpt_rows();   // rows between traceback checkpoints (a traceback band)

@@ -53,11 +53,7 @@ __device__ __forceinline__ int32_t h_col0(int mode, uint32_t fe, int64_t i, int 
   return -(o + (int32_t)(i - 1) * e);
 }
 
-// (score desc, j asc, i asc); `has` false = no candidate
-struct Cand {
-  int32_t s, i, j;
-  int32_t has;
-};
+using Cand = LongCand;
 __device__ __forceinline__ bool cand_better(const Cand& a, const Cand& b) {
   if (!a.has) return false;
   if (!b.has) return true;
@@ -635,6 +631,11 @@ int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const in
                                               static_cast<Cand*>(d_cands), ctx->d_status);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
+  return launch_long_reduce(ctx, d_jobs, n_jobs, d_cands, mode, fe, o, e, out);
+}
+
+int launch_long_reduce(dsa_ctx* ctx, const LongJob* d_jobs, uint32_t n_jobs, const void* d_cands,
+                       int mode, uint32_t fe, int o, int e, Scores out) {
   const unsigned rb = (unsigned)std::min<uint64_t>((n_jobs + 127) / 128, 1024);
   k_long_reduce<<<rb, 128, 0, ctx->stream>>>(d_jobs, n_jobs, static_cast<const Cand*>(d_cands),
                                               mode, fe, o, e, out.score, out.q_end, out.t_end,

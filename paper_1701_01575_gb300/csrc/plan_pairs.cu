@@ -9,6 +9,7 @@
 #include "host_util.cuh"
 
 #include <algorithm>
+#include <numeric>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -143,13 +144,40 @@ int score_pairs(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs, 
   res->cells = cells;
   res->phase_cells[PH_INT32] = cells;
   if (!ljobs.empty()) {
-    // band items in latest-start order (bands in order inside a pair)
-    std::vector<std::pair<uint32_t, uint32_t>> mn(ljobs.size());
-    for (size_t k = 0; k < ljobs.size(); ++k) mn[k] = {(uint32_t)ljobs[k].m, (uint32_t)ljobs[k].n};
+    // Global and semi-global: the packed form takes two pairs per warp
+    // (sorted neighbours by query and window length) when the alphabet, the
+    // byte tables and the range bound allow it; DSA_LONG_INT32=1 keeps every
+    // pair on the int32 kernel.  Local pairs stay on the int32 kernel.
+    const char* force32 = getenv("DSA_LONG_INT32");
+    const bool l16 = mode != DSA_LOCAL && A <= 4 && s_plus_o_fits_int8(matrix, A, o) &&
+                     long16_range_ok(o, e, v.smax, v.smin) && !(force32 && atoi(force32));
+    std::vector<LongPair16> units;
+    std::vector<std::pair<uint32_t, uint32_t>> mn;
+    if (l16) {
+      std::vector<uint32_t> ord(ljobs.size());
+      std::iota(ord.begin(), ord.end(), 0u);
+      std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) {
+        return ljobs[x].m != ljobs[y].m ? ljobs[x].m > ljobs[y].m : ljobs[x].n > ljobs[y].n;
+      });
+      prog = 0;
+      for (size_t k = 0; k < ord.size(); k += 2) {
+        const uint32_t a = ord[k], b = k + 1 < ord.size() ? ord[k + 1] : NONE;
+        const uint32_t m = (uint32_t)std::max(ljobs[a].m, b != NONE ? ljobs[b].m : 0);
+        const uint32_t n = (uint32_t)std::max(ljobs[a].n, b != NONE ? ljobs[b].n : 0);
+        units.push_back({a, b, prog});
+        prog += (m + band - 1) / band;
+        mn.push_back({m, n});
+      }
+    } else {
+      mn.resize(ljobs.size());
+      for (size_t k = 0; k < ljobs.size(); ++k) mn[k] = {(uint32_t)ljobs[k].m, (uint32_t)ljobs[k].n};
+    }
+    // band items in latest-start order (bands in order inside a pair or unit)
     const std::vector<uint32_t> items = band_items(mn, band);
-    DevBuf d_ljobs, d_items, d_prog, d_cands;
+    DevBuf d_ljobs, d_items, d_prog, d_cands, d_units;
     void* pb = nullptr;
     if ((rc = upload(ctx, d_ljobs, ljobs)) || (rc = upload(ctx, d_items, items)) ||
+        (l16 && (rc = upload(ctx, d_units, units))) ||
         (rc = d_prog.alloc(ctx, prog * sizeof(uint32_t))) ||
         (rc = d_cands.alloc(ctx, cand * long_cand_size())) ||
         (rc = ctx->alloc(&pb, bnd * sizeof(int2))))
@@ -167,11 +195,18 @@ int score_pairs(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs, 
       return (DSA_ERR_CUDA);
     }
     phase_begin(res, PH_INTRA);
-    if ((rc = launch_long_score(ctx, db, qs, d_mat, A, o, e, mode, fe,
-                                s_plus_o_fits_int8(matrix, A, o), d_ljobs.as<LongJob>(), (uint32_t)ljobs.size(), d_items.as<uint32_t>(),
-                                (uint32_t)(items.size() / 2), res->d_bnd, d_prog.as<uint32_t>(),
-                                d_cands.p, sc)))
-      return (rc);
+    if (l16)
+      rc = launch_long_score16(ctx, db, qs, d_mat, A, o, e, mode, fe, d_ljobs.as<LongJob>(),
+                               (uint32_t)ljobs.size(), d_units.as<LongPair16>(),
+                               d_items.as<uint32_t>(), (uint32_t)(items.size() / 2), res->d_bnd,
+                               d_prog.as<uint32_t>(), d_cands.p, sc);
+    else
+      rc = launch_long_score(ctx, db, qs, d_mat, A, o, e, mode, fe,
+                             s_plus_o_fits_int8(matrix, A, o), d_ljobs.as<LongJob>(),
+                             (uint32_t)ljobs.size(), d_items.as<uint32_t>(),
+                             (uint32_t)(items.size() / 2), res->d_bnd, d_prog.as<uint32_t>(),
+                             d_cands.p, sc);
+    if (rc) return (rc);
     phase_end(res, PH_INTRA);
     res->phase_cells[PH_INTRA] = lcells;
     res->phase_cells[PH_INT32] = cells - lcells;
