@@ -70,7 +70,7 @@ __device__ __forceinline__ bool cand_better(const Cand& a, const Cand& b) {
 // lane with H and F.  The wait on the band above is bounded and covers a
 // whole block.
 template <bool LOCAL, bool BYTES>
-__global__ void __launch_bounds__(WARPS * 32) k_long_score(
+__global__ void __launch_bounds__(WARPS * 32, 4) k_long_score(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
     const LongJob* __restrict__ jobs, const uint32_t* __restrict__ items, uint32_t n_items,
@@ -178,12 +178,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
     int2 bcur = fetch_bnd(0), bnxt = fetch_bnd(32);
     int tcur = fetch_res(0), tnxt = fetch_res(32);
     const int32_t steps = n + 31;
-    // One step of the wavefront.  CHECK = false: every lane is on a real
-    // column (32 <= s <= n) of a band whose rows are all real rows, so no
-    // bounds are tested.
-    auto step = [&](int32_t s, auto check_c) {
+    // One step of the wavefront (k = (s - 1) mod 32).  CHECK = false: every
+    // lane is on a real column of a band whose rows are all real rows and no
+    // global / semi-global result cell lies in the block, so no bounds are
+    // tested and no result tracked.
+    auto step = [&](int32_t s, int k, auto check_c) {
       constexpr bool CHECK = decltype(check_c)::value;
-      const int k = (s - 1) & 31;
       const int32_t bx = __shfl_sync(FULL, bcur.x, k);
       const int32_t by = __shfl_sync(FULL, bcur.y, k);
       const int ta = __shfl_sync(FULL, tcur, k);
@@ -196,13 +196,6 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
       Hup = lane == 0 ? h0 : Hup;
       Fup = lane == 0 ? f0 : Fup;
       a = lane == 0 ? ta : a;
-      if (k == 31) {   // block consumed: rotate, fetch the block after the next
-        bcur = bnxt;
-        tcur = tnxt;
-        const int32_t blk = (s - 1 - k) + 64;
-        bnxt = fetch_bnd(blk);
-        tnxt = fetch_res(blk);
-      }
       sendA = a;
       const int32_t j = s - lane;
       if (!CHECK || (j >= 1 && j <= n && r0 < m)) {
@@ -241,19 +234,21 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
               if (Ho[r] == cm - o) rr = r;
             c = {cm, r0 + rr + 1, j, 1};
           }
-        } else if (j == n) {
-          // column n (query end free) or the corner (m, n), rows in order
+        } else if (CHECK) {
+          if (j == n) {
+            // column n (query end free) or the corner (m, n), rows in order
 #pragma unroll
-          for (int r = 0; r < ROWS; ++r) {
-            const int32_t i = r0 + r + 1;
-            if (i <= m && (q_end_free || i == m) && (!c.has || Ho[r] + o > c.s)) c = {Ho[r] + o, i, j, 1};
+            for (int r = 0; r < ROWS; ++r) {
+              const int32_t i = r0 + r + 1;
+              if (i <= m && (q_end_free || i == m) && (!c.has || Ho[r] + o > c.s)) c = {Ho[r] + o, i, j, 1};
+            }
+          } else if (t_end_free && owns_m) {
+            int32_t hm = Ho[0] + o;
+#pragma unroll
+            for (int r = 1; r < ROWS; ++r)
+              if (r == m - r0 - 1) hm = Ho[r] + o;
+            if (!c.has || hm > c.s) c = {hm, m, j, 1};
           }
-        } else if (t_end_free && owns_m) {
-          int32_t hm = Ho[0] + o;
-#pragma unroll
-          for (int r = 1; r < ROWS; ++r)
-            if (r == m - r0 - 1) hm = Ho[r] + o;
-          if (!c.has || hm > c.s) c = {hm, m, j, 1};
         }
         sendH = hoa;
         sendF = F;
@@ -265,12 +260,29 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_score(
     };
     using T_ = std::true_type;
     using F_ = std::false_type;
-    int32_t s = 1;
-    if (i0 + BAND <= m) {
-      for (; s < 32 && s <= steps; ++s) step(s, T_{});   // wavefront filling
-      for (; s <= n; ++s) step(s, F_{});                  // every lane on a real column
+    // Blocks of 32 steps; the steady-state body (every lane on a real
+    // column of a full band, no global / semi-global result cell in the
+    // block: the lanes' columns s0 - 30 .. s0 + 32 avoid n, and the band does
+    // not hold row m with a free target end) is unrolled by 4 only, which
+    // keeps it in the instruction cache with 16 warps per SM.
+    const bool full = i0 + BAND <= m;
+    const bool rowm = !LOCAL && t_end_free && m > i0 && m <= i0 + BAND;
+    for (int32_t s0 = 0; s0 < steps; s0 += 32) {
+      const int32_t jlo = s0 - 30, jhi = s0 + 32;
+      const bool ev = !LOCAL && (rowm || (n >= jlo && n <= jhi));
+      if (full && jlo >= 1 && jhi <= n && !ev) {
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) step(s0 + 1 + k, k, F_{});
+      } else {
+#pragma unroll 1
+        for (int k = 0; k < 32 && s0 + 1 + k <= steps; ++k) step(s0 + 1 + k, k, T_{});
+      }
+      // block consumed: rotate, fetch the block after the next
+      bcur = bnxt;
+      tcur = tnxt;
+      bnxt = fetch_bnd(s0 + 64);
+      tnxt = fetch_res(s0 + 64);
     }
-    for (; s <= steps; ++s) step(s, T_{});                // draining (or a short band)
     // merge the lanes' candidates (each lane's is its first best in (j, i) order)
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
