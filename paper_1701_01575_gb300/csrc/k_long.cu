@@ -418,8 +418,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
     };
     int2 ucur = fetch_up(0), unxt = fetch_up(32);
     int tcur = fetch_res(0), tnxt = fetch_res(32);
-    for (int32_t s = 1; s <= jb.wc + 31; ++s) {
-      const int k = (s - 1) & 31;
+    // One step (k = (s - 1) mod 32).  FAST: every lane on a stored column
+    // of a band whose rows are all real, and no lane at the window's last
+    // column: no bounds tests.
+    auto step = [&](int32_t s, int k, auto fast_c) {
+      constexpr bool FAST = decltype(fast_c)::value;
       const int32_t ux = __shfl_sync(FULL, ucur.x, k);
       const int32_t uy = __shfl_sync(FULL, ucur.y, k);
       const int ta = __shfl_sync(FULL, tcur, k);
@@ -427,36 +430,25 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
       int32_t Fup = __shfl_up_sync(FULL, sendF, 1);
       int a = __shfl_up_sync(FULL, sendA, 1);
       const int32_t jj = jlo - 1 + s - lane;
-      if (lane == 0) {
-        a = ta;
-        if (b == 0) {
-          Hup = h_row0(mode, fe, jj, o, e);
-          Fup = NEG32;
-        } else {
-          Hup = ux;
-          Fup = uy;
-        }
-      }
-      if (k == 31) {   // block consumed: rotate, fetch the block after the next
-        ucur = unxt;
-        tcur = tnxt;
-        const int32_t blk = (s - 1 - k) + 64;
-        unxt = fetch_up(blk);
-        tnxt = fetch_res(blk);
-      }
+      // lane 0 reads the checkpoint row above (or row 0): selects, not a branch
+      const int32_t h0 = b == 0 ? h_row0(mode, fe, jj, o, e) : ux;
+      const int32_t f0 = b == 0 ? NEG32 : uy;
+      Hup = lane == 0 ? h0 : Hup;
+      Fup = lane == 0 ? f0 : Fup;
+      a = lane == 0 ? ta : a;
       sendA = a;
-      if (jj >= jlo && jj <= jhi && r0 < ie) {
+      if (FAST || (jj >= jlo && jj <= jhi && r0 < ie)) {
         int32_t d = diag;
         diag = Hup;
         int32_t F = Fup, Hp = Hup;
         const uint32_t sel = (uint32_t)a + ((uint32_t)a | 8u) * 0x1110u;
         const int32_t jc = jj - jlo;   // stored column
         const int sh = 4 * (jc & 7);
-        const bool flushw = ((jc & 7) == 7) || jj == jhi;
+        const bool flushw = ((jc & 7) == 7) || (!FAST && jj == jhi);
 #pragma unroll
         for (int r = 0; r < TB_ROWS; ++r) {
           const int32_t ii = r0 + r + 1;
-          if (ii <= ie) {
+          if (FAST || ii <= ie) {
             const int32_t fo = Hp - o, fx = F - e;
             F = max(fx, fo);
             const int32_t eo = H[r] - o, ex = E[r] - e;
@@ -483,6 +475,25 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
         sendH = Hp;
         sendF = F;
       }
+    };
+    // Blocks of 32 steps; the steady-state body is unrolled by 4 only (the
+    // instruction cache).  Lanes' stored columns in block s0: s0 - 31 ..
+    // s0 + 31 (jc); steady when all lie in 0 .. wc - 2 and the band is full.
+    const bool full = i0 + TB_BAND <= ie;
+    const int32_t steps = jb.wc + 31;
+    for (int32_t s0 = 0; s0 < steps; s0 += 32) {
+      if (full && s0 >= 32 && s0 + 32 < jb.wc) {
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) step(s0 + 1 + k, k, std::true_type{});
+      } else {
+#pragma unroll 1
+        for (int k = 0; k < 32 && s0 + 1 + k <= steps; ++k) step(s0 + 1 + k, k, std::false_type{});
+      }
+      // block consumed: rotate, fetch the block after the next
+      ucur = unxt;
+      tcur = tnxt;
+      unxt = fetch_up(s0 + 64);
+      tnxt = fetch_res(s0 + 64);
     }
     __syncwarp();
   }
