@@ -335,6 +335,15 @@ struct RevCigar {
       run = 1;
     }
   }
+  __device__ void emit_run(int o, uint32_t k) {   // k >= 1 ops `o`
+    if (o == op) {
+      run += k;
+    } else {
+      flush();
+      op = o;
+      run = k;
+    }
+  }
   __device__ void flush() {
     if (run) out[n++] = (run << 4) | (uint32_t)op;
     run = 0;
@@ -562,6 +571,27 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
           bool stop = false;
           int32_t q = 0;
           for (; q <= safe; ++q) {
+            if (st == 0 && q + 7 <= safe) {
+              // a match run: the next 8 cells along the diagonal lie in the
+              // window; read them at once (independent loads) and take the
+              // leading M steps together
+              uint32_t notm = 0;
+#pragma unroll
+              for (int kk = 0; kk < 8; ++kk) {
+                const int32_t jk = jc - kk;
+                const uint32_t w = win[(rr - kk - wr0) * WIN_WORDS + ((jk >> 3) - wlo)];
+                notm |= (((w >> (4 * (jk & 7))) & 3u) != 0u ? 1u : 0u) << kk;
+              }
+              const int32_t L = notm ? __ffs(notm) - 1 : 8;
+              if (L > 0) {
+                c.emit_run(0, (uint32_t)L);
+                i -= L; j -= L; rr -= L; jc -= L;
+                q += L - 1;
+                p = win + (rr - wr0) * WIN_WORDS + ((jc >> 3) - wlo);
+                sh = 4u * (uint32_t)(jc & 7);
+                continue;
+              }
+            }
             const uint32_t nib = (*p >> sh) & 15u;
             if (st == 0) {
               const uint32_t src = nib & 3u;
