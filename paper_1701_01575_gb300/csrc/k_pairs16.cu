@@ -183,19 +183,13 @@ __global__ void __launch_bounds__(NT, MINB) k_pairs16(
         uint32_t wa_lo = __ldg(wlo), wb_lo = __ldg(wlo + min(1, w_last(nlo)));
         uint32_t wa_hi = __ldg(whi), wb_hi = __ldg(whi + min(1, w_last(nhi)));
         uint32_t r4_lo = 0, r4_hi = 0;
-        for (int32_t j = 1; j <= nmax; ++j) {
-          if (((j - 1) & 3) == 0) {
-            const int32_t g = (j - 1) >> 2;
-            r4_lo = __funnelshift_r(wa_lo, wb_lo, sh2);
-            r4_hi = __funnelshift_r(wa_hi, wb_hi, sh2 >> 8);
-            wa_lo = wb_lo;
-            wa_hi = wb_hi;
-            wb_lo = __ldg(wlo + min(g + 2, w_last(nlo)));
-            wb_hi = __ldg(whi + min(g + 2, w_last(nhi)));
-          }
-          const uint32_t kb = 8u * (uint32_t)((j - 1) & 3);
-          const uint32_t a_lo = j <= nlo ? (r4_lo >> kb) & 0xFFu : 0u;
-          const uint32_t a_hi = j <= nhi ? (r4_hi >> kb) & 0xFFu : 0u;
+        // column j = group start + kk + 1; IN: inside both windows (no
+        // residue tests)
+        auto column = [&](int32_t j, int kk, auto in_c) {
+          constexpr bool IN = decltype(in_c)::value;
+          const uint32_t kb = 8u * (uint32_t)kk;
+          const uint32_t a_lo = (IN || j <= nlo) ? (r4_lo >> kb) & 0xFFu : 0u;
+          const uint32_t a_hi = (IN || j <= nhi) ? (r4_hi >> kb) & 0xFFu : 0u;
           uint2 v = make_uint2(0u, 0u);
           if (!FIRST) {
             cp_async_wait<AHEAD - 1>();   // column j has landed
@@ -294,6 +288,26 @@ __global__ void __launch_bounds__(NT, MINB) k_pairs16(
                 if (bs > s_cb[x][tid]) { s_cb[x][tid] = bs; s_ci[x][tid] = i0 + br + 1; }
               }
             }
+          }
+        };
+        // columns in groups of 4 (one residue word): the group's body is
+        // unrolled, so the residue's byte position is a constant and the
+        // compiler can overlap the wavefronts of neighbouring columns
+        const int32_t nmin = min(nlo, nhi);
+        for (int32_t j0 = 0; j0 < nmax; j0 += 4) {
+          const int32_t g = j0 >> 2;
+          r4_lo = __funnelshift_r(wa_lo, wb_lo, sh2);
+          r4_hi = __funnelshift_r(wa_hi, wb_hi, sh2 >> 8);
+          wa_lo = wb_lo;
+          wa_hi = wb_hi;
+          wb_lo = __ldg(wlo + min(g + 2, w_last(nlo)));
+          wb_hi = __ldg(whi + min(g + 2, w_last(nhi)));
+          if (j0 + 4 <= nmin) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) column(j0 + 1 + kk, kk, std::true_type{});
+          } else {
+#pragma unroll 1
+            for (int kk = 0; kk < 4 && j0 + 1 + kk <= nmax; ++kk) column(j0 + 1 + kk, kk, std::false_type{});
           }
         }
         if (!FIRST) cp_async_wait<0>();   // nothing in flight into the ring past the strip
