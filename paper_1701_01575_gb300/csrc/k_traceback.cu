@@ -49,6 +49,15 @@ struct RevCigar {
       run = 1;
     }
   }
+  __device__ void emit_run(int o, uint32_t k) {   // k >= 1 ops `o`
+    if (o == op) {
+      run += k;
+    } else {
+      flush();
+      op = o;
+      run = k;
+    }
+  }
   __device__ void flush() {
     if (run) out[n++] = (run << 4) | (uint32_t)op;
     run = 0;
@@ -381,6 +390,27 @@ __global__ void __launch_bounds__(128, TROWS <= 8 ? 6 : 4) k_traceback_thread(
   int st = 0;  // 0 = H, 1 = F, 2 = E
   const bool sg = mode == DSA_SEMIGLOBAL;
   for (int64_t guard = 2 * ((int64_t)ie + je) + 2; guard > 0; --guard) {
+    if (st == 0 && i > 8 && j > 8) {
+      // a match run: the next 8 cells along the diagonal (all off row 0 and
+      // column 0) are read at once -- independent loads, one latency -- and
+      // the leading M steps taken together; a cell outside the window counts
+      // as the end of the run
+      uint32_t notm = 0;
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        uint32_t nib = 0;
+        const bool in = nibble(i - kk, j - kk, nib);
+        notm |= ((!in || (nib & 3u) != 0u) ? 1u : 0u) << kk;
+      }
+      const int32_t L = notm ? __ffs(notm) - 1 : 8;
+      if (L > 0) {
+        c.emit_run(0, (uint32_t)L);
+        i -= L;
+        j -= L;
+        guard -= L - 1;
+        continue;
+      }
+    }
     if (st == 0) {
       if (sg && ((i == 0 && (fe & DSA_FREE_T_BEGIN)) || (j == 0 && (fe & DSA_FREE_Q_BEGIN)))) break;
       if (i == 0 || j == 0) {
