@@ -165,3 +165,39 @@ def test_packed_long_pairs_workload_sample(ctx, monkeypatch):
     for f in ("score", "q_end", "t_end", "q_begin", "t_begin", "cigar_len"):
         assert np.array_equal(h16[f], h32[f]), f
     assert np.array_equal(r16.cigar(), r32.cigar())
+
+
+@pytest.mark.parametrize("mode,fe", [(dsa.GLOBAL, 15), (dsa.SEMIGLOBAL, 15), (dsa.LOCAL, 15),
+                                     (dsa.SEMIGLOBAL, 5)])
+def test_extreme_long_pair_shapes(ctx, mode, fe, monkeypatch):
+    """Long pairs of extreme shape in one call: 450,000 query rows against a
+    10-column window (880 bands, no base move after column 10), 10 rows
+    against 450,000 columns (one band), and a square pair, paired with each
+    other in units of the packed kernel (an odd count: one empty half).
+    Scores, ends and tracebacks against the oracle, and both kernels equal."""
+    rng = np.random.default_rng(2400 + 16 * mode + fe)
+    S = W.dna_matrix(2, -3)
+    tall = rng.integers(0, 4, 450_000).astype(np.uint8)
+    wide_t = rng.integers(0, 4, 450_000).astype(np.uint8)
+    sq = rng.integers(0, 4, 2100).astype(np.uint8)
+    qs = W.SeqSet.from_list([tall, wide_t[1000:1010], sq])
+    db = W.SeqSet.from_list([tall[5000:5010], wide_t, W.mutate(rng, sq, 0.03, 0.01)])
+    pairs = np.zeros(3, dtype=W.PAIR_DTYPE)
+    pairs["query_id"] = [0, 1, 2]
+    pairs["target_id"] = [0, 1, 2]
+    pairs["t_len"] = db.lengths
+    assert (qs.lengths * pairs["t_len"].astype(np.int64) >= (1 << 22)).all()
+    sc, qe, te = oracle.score_pairs(qs.codes, qs.offsets, db.codes, db.offsets, pairs["query_id"],
+                                    pairs["target_id"], S, 5, 2, mode, fe,
+                                    pair_toff=pairs["t_offset"], pair_tlen=pairs["t_len"])
+    monkeypatch.delenv("DSA_LONG_INT32", raising=False)
+    r16 = _run(ctx, qs, db, pairs, S, 5, 2, mode, fe)
+    h16 = r16.hits()
+    assert_same((h16["score"], h16["q_end"], h16["t_end"]), (sc, qe, te), f"extreme mode={mode} fe={fe}")
+    check_traceback(h16, r16.cigar(), qs, db, S, 5, 2, mode, fe)
+    monkeypatch.setenv("DSA_LONG_INT32", "1")
+    r32 = _run(ctx, qs, db, pairs, S, 5, 2, mode, fe)
+    h32 = r32.hits()
+    for f in ("score", "q_end", "t_end", "q_begin", "t_begin", "cigar_len"):
+        assert np.array_equal(h16[f], h32[f]), f
+    assert np.array_equal(r16.cigar(), r32.cigar())
