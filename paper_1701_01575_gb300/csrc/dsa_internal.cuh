@@ -448,11 +448,14 @@ struct LongTbJob {
   int32_t wc;
   uint32_t pad;
 };
-// bytes_ok: every S + o fits int8 (with A <= 4 the byte-permute form is used)
+// bytes_ok: every S + o fits int8 (with A <= 4 the byte-permute form is used).
+// blocks_per_sm > 0 caps the resident blocks per SM (fewer warps per SM run
+// the bands' chains faster; the autotuner chooses).
 int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,
                       int A, int o, int e, int mode, uint32_t fe, bool bytes_ok,
                       const LongJob* d_jobs, uint32_t n_jobs, const uint32_t* d_items,
-                      uint32_t n_items, int2* d_bnd, uint32_t* d_prog, void* d_cands, Scores out);
+                      uint32_t n_items, int2* d_bnd, uint32_t* d_prog, void* d_cands, Scores out,
+                      int blocks_per_sm = 0);
 // Checkpointed traceback of long pairs, part 1: the decisions of the bands
 // named by `items` (2 words (job, band) each; job indexes d_jobs).
 int launch_long_tb_fill(dsa_ctx* ctx, cudaStream_t stream, const dsa_db* db, const dsa_db* qs,
@@ -486,7 +489,7 @@ int launch_long_score16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const 
                         int A, int o, int e, int mode, uint32_t fe, const LongJob* d_jobs,
                         uint32_t n_jobs, const LongPair16* d_pjobs, const uint32_t* d_items,
                         uint32_t n_items, int2* d_bnd, uint32_t* d_prog, void* d_cands,
-                        Scores out);
+                        Scores out, int blocks_per_sm = 0);
 int launch_long_reduce(dsa_ctx* ctx, const LongJob* d_jobs, uint32_t n_jobs, const void* d_cands,
                        int mode, uint32_t fe, int o, int e, Scores out);
 size_t long_cand_size();

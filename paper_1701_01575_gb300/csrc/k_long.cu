@@ -664,7 +664,8 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
 int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,
                       int A, int o, int e, int mode, uint32_t fe, bool bytes_ok,
                       const LongJob* d_jobs, uint32_t n_jobs, const uint32_t* d_items,
-                      uint32_t n_items, int2* d_bnd, uint32_t* d_prog, void* d_cands, Scores out) {
+                      uint32_t n_items, int2* d_bnd, uint32_t* d_prog, void* d_cands, Scores out,
+                      int blocks_per_sm) {
   if (n_items == 0) return DSA_OK;
   // every warp must be resident at once (bands wait on their predecessors):
   // the grid never exceeds what the device holds simultaneously
@@ -675,6 +676,7 @@ int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const in
                                 : (bytes ? k_long_score<false, true> : k_long_score<false, false>);
   int per_sm = 0;
   DSA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, 0));
+  if (blocks_per_sm > 0) per_sm = std::min(per_sm, blocks_per_sm);
   const uint64_t resident = (uint64_t)std::max(1, per_sm) * ctx->sm_count;
   const unsigned grid = (unsigned)std::min<uint64_t>(resident, (n_items + WARPS - 1) / WARPS);
   uint32_t* counter = ctx->d_counters + 3;

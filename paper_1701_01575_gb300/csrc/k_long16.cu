@@ -404,7 +404,7 @@ int launch_long_score16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const 
                         int A, int o, int e, int mode, uint32_t fe, const LongJob* d_jobs,
                         uint32_t n_jobs, const LongPair16* d_pjobs, const uint32_t* d_items,
                         uint32_t n_items, int2* d_bnd, uint32_t* d_prog, void* d_cands,
-                        Scores out) {
+                        Scores out, int blocks_per_sm) {
   if (n_items == 0) return DSA_OK;
   if (mode == DSA_LOCAL) {
     set_error("the packed long-pair kernel takes global and semi-global pairs");
@@ -414,6 +414,7 @@ int launch_long_score16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const 
   // every warp must be resident at once (bands wait on their predecessors)
   int per_sm = 0;
   DSA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, 0));
+  if (blocks_per_sm > 0) per_sm = std::min(per_sm, blocks_per_sm);
   const uint64_t resident = (uint64_t)std::max(1, per_sm) * ctx->sm_count;
   const unsigned grid = (unsigned)std::min<uint64_t>(resident, (n_items + WARPS - 1) / WARPS);
   uint32_t* counter = ctx->d_counters + 3;

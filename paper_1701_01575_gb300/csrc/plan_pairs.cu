@@ -190,23 +190,75 @@ int score_pairs(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs, 
       res->long_bnd_off[lj.out] = lj.bnd_off;
       res->long_n[lj.out] = lj.n;
     }
-    if (cudaMemsetAsync(d_prog.p, 0, prog * sizeof(uint32_t), ctx->stream) != cudaSuccess) {
-      set_error("memset failed");
-      return (DSA_ERR_CUDA);
+    // one score pass with at most `bps` blocks per SM (0: as many as fit),
+    // from zeroed progress counters
+    auto run_long = [&](int bps) -> int {
+      if (cudaMemsetAsync(d_prog.p, 0, prog * sizeof(uint32_t), ctx->stream) != cudaSuccess) {
+        set_error("memset failed");
+        return DSA_ERR_CUDA;
+      }
+      if (l16)
+        return launch_long_score16(ctx, db, qs, d_mat, A, o, e, mode, fe, d_ljobs.as<LongJob>(),
+                                   (uint32_t)ljobs.size(), d_units.as<LongPair16>(),
+                                   d_items.as<uint32_t>(), (uint32_t)(items.size() / 2),
+                                   res->d_bnd, d_prog.as<uint32_t>(), d_cands.p, sc, bps);
+      return launch_long_score(ctx, db, qs, d_mat, A, o, e, mode, fe,
+                               s_plus_o_fits_int8(matrix, A, o), d_ljobs.as<LongJob>(),
+                               (uint32_t)ljobs.size(), d_items.as<uint32_t>(),
+                               (uint32_t)(items.size() / 2), res->d_bnd, d_prog.as<uint32_t>(),
+                               d_cands.p, sc, bps);
+    };
+    // Blocks per SM: every block fits 4 per SM; with 2, each band's warp
+    // shares its SM sub-partition with fewer others, and the bands' chains
+    // (a band waits on the band above) run faster, which wins when the
+    // longest pairs' chains bound the pass.  DSA_LONG_BLOCKS (2 | 4) fixes
+    // it, else the autotuner times both on the first call of a shape
+    // (kernel, mode, and log2 bins of the pair count, the longest query and
+    // the longest window) and keeps the faster (a switch needs 3%).
+    int bps = 4;
+    const char* bps_env = getenv("DSA_LONG_BLOCKS");
+    const char* tune_env = getenv("DSA_AUTOTUNE");
+    if (bps_env) {
+      bps = atoi(bps_env) == 2 ? 2 : 4;
+    } else if (ctx->tune && !(tune_env && std::string(tune_env) == "off")) {
+      uint32_t mmax = 0, nmax = 0;
+      for (const LongJob& lj : ljobs) {
+        mmax = std::max(mmax, (uint32_t)lj.m);
+        nmax = std::max(nmax, (uint32_t)lj.n);
+      }
+      char k[160];
+      snprintf(k, sizeof k, "|long|%s|%s|p%d|m%d|n%d|bps", l16 ? "p16" : "i32",
+               mode == DSA_LOCAL ? "local" : (mode == DSA_GLOBAL ? "global" : "semi"),
+               tuner_bin(ljobs.size()), tuner_bin(mmax), tuner_bin(nmax));
+      const std::string key = tuner_shape_prefix(ctx) + k;
+      uint32_t cached = 0;
+      if (tuner_get(key, &cached)) {
+        bps = cached == 2 ? 2 : 4;
+      } else {
+        cudaEvent_t ev[3];
+        for (auto& x : ev) DSA_CUDA_TRY(cudaEventCreate(&x));
+        int trc = DSA_OK;
+        if (cudaEventRecord(ev[0], ctx->stream) != cudaSuccess || (trc = run_long(4)) ||
+            cudaEventRecord(ev[1], ctx->stream) != cudaSuccess || (trc = run_long(2)) ||
+            cudaEventRecord(ev[2], ctx->stream) != cudaSuccess ||
+            cudaEventSynchronize(ev[2]) != cudaSuccess)
+          trc = trc ? trc : DSA_ERR_CUDA;
+        float t4 = 0.f, t2 = 0.f;
+        if (!trc) {
+          cudaEventElapsedTime(&t4, ev[0], ev[1]);
+          cudaEventElapsedTime(&t2, ev[1], ev[2]);
+        }
+        for (auto& x : ev) cudaEventDestroy(x);
+        if (trc) {
+          set_error("long-pair autotune: %s", cudaGetErrorString(cudaGetLastError()));
+          return trc;
+        }
+        bps = t2 < 0.97f * t4 ? 2 : 4;
+        tuner_put(key, (uint32_t)bps);
+      }
     }
     phase_begin(res, PH_INTRA);
-    if (l16)
-      rc = launch_long_score16(ctx, db, qs, d_mat, A, o, e, mode, fe, d_ljobs.as<LongJob>(),
-                               (uint32_t)ljobs.size(), d_units.as<LongPair16>(),
-                               d_items.as<uint32_t>(), (uint32_t)(items.size() / 2), res->d_bnd,
-                               d_prog.as<uint32_t>(), d_cands.p, sc);
-    else
-      rc = launch_long_score(ctx, db, qs, d_mat, A, o, e, mode, fe,
-                             s_plus_o_fits_int8(matrix, A, o), d_ljobs.as<LongJob>(),
-                             (uint32_t)ljobs.size(), d_items.as<uint32_t>(),
-                             (uint32_t)(items.size() / 2), res->d_bnd, d_prog.as<uint32_t>(),
-                             d_cands.p, sc);
-    if (rc) return (rc);
+    if ((rc = run_long(bps))) return (rc);
     phase_end(res, PH_INTRA);
     res->phase_cells[PH_INTRA] = lcells;
     res->phase_cells[PH_INT32] = cells - lcells;

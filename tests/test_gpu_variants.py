@@ -2,7 +2,8 @@
 
 The inter-sequence kernels exist for two strip heights (28 rows, and 20 rows
 that waste fewer padding rows on short queries); the explicit-pairs kernel's
-byte form for two (16 rows at 4 blocks per SM, 20 rows at 3).  Every variant
+byte form for two (16 rows at 4 blocks per SM, 20 rows at 3); the long-pair
+band pipeline runs at 2 or 4 blocks per SM.  Every variant
 must give the oracle's scores and end cells bit for bit in every mode; the
 tuner times the variants on the first call of a workload shape and records
 its choice (and the long-target threshold) in its cache file, which the
@@ -155,3 +156,44 @@ def test_pairs_tuner_records_variant(ctx, tmp_path, monkeypatch):
     entries = json.loads(cache.read_text())
     keys = [k for k in entries if "|pairs|" in k]
     assert len(keys) == 1 and entries[keys[0]] in (16, 20)
+
+
+@pytest.mark.parametrize("blocks", ["2", "4"])
+@pytest.mark.parametrize("mode,fe", [(dsa.GLOBAL, 15), (dsa.LOCAL, 15), (dsa.SEMIGLOBAL, 10)])
+def test_long_pair_blocks_per_sm_variants(ctx, blocks, mode, fe, monkeypatch):
+    """The long-pair band pipeline with 2 or 4 blocks per SM (a persistent
+    grid smaller than the band items: warps take several bands in turn)."""
+    monkeypatch.setenv("DSA_LONG_BLOCKS", blocks)
+    wl = W.long_pairs(seed=W.SEED_BASE + 1500 + mode + fe, n_pairs=9, lo=3000, hi=9000, mode=mode)
+    p = wl.pairs
+    d = ctx.load_set(wl.db, 4)
+    q = ctx.load_set(wl.queries, 4)
+    r = ctx.align(d, q, wl.matrix, 5, 2, mode=mode, free_ends=fe, pairs=p)
+    ctx.sync()
+    h = r.hits()
+    sc, qe, te = oracle.score_pairs(wl.queries.codes, wl.queries.offsets, wl.db.codes,
+                                    wl.db.offsets, p["query_id"], p["target_id"], wl.matrix, 5, 2,
+                                    mode, fe, pair_toff=p["t_offset"], pair_tlen=p["t_len"])
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), f"blocks={blocks} mode={mode}")
+    assert r.phase_cells()["intra16"] > 0
+
+
+def test_long_pair_tuner_records_blocks(ctx, tmp_path, monkeypatch):
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("DSA_AUTOTUNE_CACHE", str(cache))
+    monkeypatch.setenv("DSA_AUTOTUNE", "retune")
+    monkeypatch.delenv("DSA_LONG_BLOCKS", raising=False)
+    wl = W.long_pairs(seed=W.SEED_BASE + 1550, n_pairs=6, lo=3000, hi=9000)
+    p = wl.pairs
+    d = ctx.load_set(wl.db, 4)
+    q = ctx.load_set(wl.queries, 4)
+    r = ctx.align(d, q, wl.matrix, 5, 2, mode=wl.mode, pairs=p)
+    ctx.sync()
+    h = r.hits()
+    sc, qe, te = oracle.score_pairs(wl.queries.codes, wl.queries.offsets, wl.db.codes,
+                                    wl.db.offsets, p["query_id"], p["target_id"], wl.matrix, 5, 2,
+                                    wl.mode, 15, pair_toff=p["t_offset"], pair_tlen=p["t_len"])
+    assert_same((h["score"], h["q_end"], h["t_end"]), (sc, qe, te), "tuned long pairs")
+    entries = json.loads(cache.read_text())
+    keys = [k for k in entries if "|long|" in k]
+    assert len(keys) == 1 and entries[keys[0]] in (2, 4)
