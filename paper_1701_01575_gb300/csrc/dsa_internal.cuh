@@ -304,7 +304,10 @@ struct TbJob {
   // the band): wc stored columns from clamp(i0 + 1 + dlo, 1, je - wc + 1)
   int32_t dlo;
   int32_t wc;
-  uint32_t pad;
+  // index of band 0's entry in the per-band window table (int2: first
+  // stored column, stored columns) when the traceback narrows each band from
+  // the checkpoint rows; the table's widths are at most wc
+  uint32_t win_off;
 };
 // Score-derived traceback windows, shared by the host staging and the
 // device staging of the traceback (see k_traceback.cu for the argument).
@@ -446,7 +449,10 @@ struct LongTbJob {
   // dlo = 0 recompute whole rows.
   int32_t dlo;
   int32_t wc;
-  uint32_t pad;
+  // index of band 0's entry in the per-band window table (int2: first
+  // stored column, stored columns) when the traceback narrows each band from
+  // the checkpoint rows; the table's widths are at most wc
+  uint32_t win_off;
 };
 // bytes_ok: every S + o fits int8 (with A <= 4 the byte-permute form is used).
 // blocks_per_sm > 0 caps the resident blocks per SM (fewer warps per SM run
@@ -456,17 +462,28 @@ int launch_long_score(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const in
                       const LongJob* d_jobs, uint32_t n_jobs, const uint32_t* d_items,
                       uint32_t n_items, int2* d_bnd, uint32_t* d_prog, void* d_cands, Scores out,
                       int blocks_per_sm = 0);
-// Checkpointed traceback of long pairs, part 1: the decisions of the bands
-// named by `items` (2 words (job, band) each; job indexes d_jobs).
+// Checkpointed traceback of long pairs, part 0: each band's window of the
+// bands named by `items` (2 words (job, band) each) from the checkpoint rows:
+// the columns where an optimal path to the hit can cross the band's top and
+// bottom rows (H there plus the best score still reachable from the cell
+// reaches the hit's score), within the job's diagonal window; writes
+// d_win[win_off + band] and the widest band of each job into d_maxw (zeroed
+// before).  smax_pos: max(S, 0).
+int launch_long_tb_windows(dsa_ctx* ctx, cudaStream_t stream, const LongTbJob* d_jobs,
+                           const uint32_t* d_items, uint32_t n_items, const int2* d_bnd,
+                           const dsa_hit* d_hits, int mode, uint32_t fe, int o, int e,
+                           int smax_pos, int2* d_win, int32_t* d_maxw);
+// Part 1: the decisions of the bands named by `items`; d_win: the per-band
+// windows (nullptr: every band takes the job's diagonal window).
 int launch_long_tb_fill(dsa_ctx* ctx, cudaStream_t stream, const dsa_db* db, const dsa_db* qs,
                         const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
                         const LongTbJob* d_jobs, const uint32_t* d_items, uint32_t n_items,
-                        const int2* d_bnd, uint32_t* d_dir);
+                        const int2* d_bnd, uint32_t* d_dir, const int2* d_win = nullptr);
 // Part 2: one warp per job walks its decisions back from the end cell
 // (every band of those jobs filled before, in stream order).
 int launch_long_tb_walk(dsa_ctx* ctx, cudaStream_t stream, const LongTbJob* d_jobs,
                         uint32_t n_jobs, int mode, uint32_t fe, const uint32_t* d_dir,
-                        uint32_t* d_cig_tmp, dsa_hit* d_hits);
+                        uint32_t* d_cig_tmp, dsa_hit* d_hits, const int2* d_win = nullptr);
 // Per-band end-cell candidate of a long pair, ordered (score desc, j asc,
 // i asc); has = 0: none.
 struct LongCand {

@@ -359,13 +359,26 @@ __device__ __forceinline__ int32_t band_jlo(const LongTbJob& jb, int32_t b) {
   const int32_t want = b * TB_BAND + 1 + jb.dlo;
   return max(1, min(want, jb.je - jb.wc + 1));
 }
+// Band b's stored columns: the per-band window when there is one, else the
+// job's diagonal window.
+__device__ __forceinline__ void band_window(const LongTbJob& jb, const int2* win, int32_t b,
+                                            int32_t& jlo, int32_t& wcb) {
+  if (win) {
+    const int2 w = win[jb.win_off + (uint32_t)b];
+    jlo = w.x;
+    wcb = w.y;
+  } else {
+    jlo = band_jlo(jb, b);
+    wcb = jb.wc;
+  }
+}
 
 template <bool BYTES>
 __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
     const LongTbJob* __restrict__ jobs, const uint32_t* __restrict__ items, uint32_t n_items,
-    const int2* __restrict__ bnd, uint32_t* __restrict__ dir) {
+    const int2* __restrict__ bnd, uint32_t* __restrict__ dir, const int2* __restrict__ win) {
   __shared__ int8_t S[32 * 32];
   __shared__ uint32_t Sb[4];   // BYTES: row q of S as 4 bytes
   for (int x = threadIdx.x; x < A * A; x += blockDim.x) S[x] = Sg[x];
@@ -391,8 +404,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
     const int32_t i0 = b * TB_BAND;
     const int32_t r0 = i0 + lane * TB_ROWS;
     const int2* up = bnd + jb.bnd_off + (uint64_t)(b - 1) * jb.n;
-    // columns jlo .. jlo + wc - 1 of this band; a wall (-inf) left of jlo > 1
-    const int32_t jlo = band_jlo(jb, b), jhi = jlo + jb.wc - 1;
+    // columns jlo .. jlo + wcb - 1 of this band; a wall (-inf) left of jlo > 1
+    int32_t jlo, wcb;
+    band_window(jb, win, b, jlo, wcb);
+    const int32_t jhi = jlo + wcb - 1;
     const bool wall = jlo > 1;
     int32_t H[TB_ROWS], E[TB_ROWS];
     uint32_t nbw[TB_ROWS];
@@ -489,9 +504,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
     // instruction cache).  Lanes' stored columns in block s0: s0 - 31 ..
     // s0 + 31 (jc); steady when all lie in 0 .. wc - 2 and the band is full.
     const bool full = i0 + TB_BAND <= ie;
-    const int32_t steps = jb.wc + 31;
+    const int32_t steps = wcb + 31;
     for (int32_t s0 = 0; s0 < steps; s0 += 32) {
-      if (full && s0 >= 32 && s0 + 32 < jb.wc) {
+      if (full && s0 >= 32 && s0 + 32 < wcb) {
 #pragma unroll 4
         for (int k = 0; k < 32; ++k) step(s0 + 1 + k, k, std::true_type{});
       } else {
@@ -505,6 +520,91 @@ __global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
       tnxt = fetch_res(s0 + 64);
     }
     __syncwarp();
+  }
+}
+
+// Checkpointed traceback, part 0: the window of each band from the
+// checkpoint rows.  An optimal path to the hit (ie, je) with score `best`
+// crosses row R at a column c only if H(R, c) plus the most any path from
+// (R, c) to (ie, je) can still score reaches best; that most is
+// max(S, 0) min(ie - R, je - c) minus e for each diagonal step between the
+// two cells' diagonals (a gap cell costs at least e).  H at a checkpoint row
+// is exact, so the columns passing this test at a band's top row bound the
+// band's path from the left and those at its bottom row from the right (the
+// path only moves down and right), within the job's diagonal window, which
+// already contains every optimal path.  A path may also begin inside the
+// band: local alignment (from any cell whose remaining reach covers best:
+// the leftmost such column is largest-distance from the end, at the band's
+// top row) and a free query begin (column 0); those bands widen to include
+// them.  Every cell of every optimal path keeps its exact value in the
+// narrowed band, so the decisions along them are the full matrix's.
+__global__ void __launch_bounds__(128) k_long_tb_windows(
+    const LongTbJob* __restrict__ jobs, const uint32_t* __restrict__ items, uint32_t n_items,
+    const int2* __restrict__ bnd, const dsa_hit* __restrict__ hits, int mode, uint32_t fe,
+    int o, int e, int smax_pos, int2* __restrict__ win, int32_t* __restrict__ maxw) {
+  constexpr unsigned FULL = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
+  const uint32_t it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= n_items) return;
+  const uint32_t job = items[2 * it];
+  const LongTbJob jb = jobs[job];
+  const int32_t b = (int32_t)items[2 * it + 1];
+  const int64_t best = hits[jb.hit].score;
+  const int64_t ie = jb.ie, je = jb.je;
+  // the job's diagonal window for this band: no optimal path leaves it
+  const int32_t olo = band_jlo(jb, b), ohi = olo + jb.wc - 1;
+  auto reach = [&](int64_t R, int64_t c) -> int64_t {   // best score from (R, c) to the end
+    const int64_t dr = ie - R, dc = je - c;
+    const int64_t d = dr > dc ? dr - dc : dc - dr;
+    return (int64_t)smax_pos * (dr < dc ? dr : dc) - d * e;
+  };
+  auto h_at = [&](int64_t R, int64_t c) -> int64_t {   // exact H on row R (0 or a checkpoint row)
+    if (R == 0) return h_row0(mode, fe, c, o, e);
+    if (c == 0) return h_col0(mode, fe, R, o, e);
+    return bnd[jb.bnd_off + (uint64_t)(R / TB_BAND - 1) * (uint32_t)jb.n + (uint64_t)(c - 1)].x;
+  };
+  const int64_t Rt = (int64_t)b * TB_BAND, Rb = Rt + TB_BAND;
+  // left bound: crossings of the top row
+  int64_t lo = INT64_MAX;
+  const int64_t c0 = olo > 1 ? (int64_t)olo - 1 : 0;
+  for (int64_t c = c0 + lane; c <= ohi; c += 32)
+    if (h_at(Rt, c) + reach(Rt, c) >= best) { lo = c; break; }
+  // paths that begin inside the band
+  if (e > 0 && mode == DSA_LOCAL) {
+    const int64_t dr = ie - Rt;
+    if ((int64_t)smax_pos * dr >= best) {
+      const int64_t cs = je - dr - ((int64_t)smax_pos * dr - best) / e;
+      lo = min(lo, cs > 0 ? cs : (int64_t)0);
+    }
+  } else if (e == 0 && mode == DSA_LOCAL) {
+    lo = 0;
+  }
+  if (mode == DSA_SEMIGLOBAL && (fe & DSA_FREE_Q_BEGIN)) {
+    const int64_t rm = min(max(ie - je, Rt), min(Rb, ie));   // the best row for a column-0 start
+    if (reach(Rt, 0) >= best || reach(rm, 0) >= best) lo = 0;
+  }
+  // right bound: crossings of the bottom row (the end cell in the last band)
+  int64_t hi = -1;
+  if (Rb >= ie) {
+    hi = je;
+  } else {
+    for (int64_t c = ohi - lane; c >= c0; c -= 32)
+      if (h_at(Rb, c) + reach(Rb, c) >= best) { hi = c; break; }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    lo = min(lo, (int64_t)__shfl_xor_sync(FULL, (long long)lo, off));
+    hi = max(hi, (int64_t)__shfl_xor_sync(FULL, (long long)hi, off));
+  }
+  if (lane == 0) {
+    int32_t jlo = (int32_t)max(max(lo, (int64_t)olo), (int64_t)1);
+    int32_t jhi = (int32_t)min(hi, (int64_t)ohi);
+    if (lo == INT64_MAX || hi < 0 || jhi < jlo) {   // no narrower window found
+      jlo = olo;
+      jhi = ohi;
+    }
+    win[jb.win_off + (uint32_t)b] = make_int2(jlo, jhi - jlo + 1);
+    atomicMax(maxw + job, jhi - jlo + 1);
   }
 }
 
@@ -522,7 +622,8 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
                                                      uint32_t n_jobs, int mode, uint32_t fe,
                                                      const uint32_t* __restrict__ dir,
                                                      uint32_t* __restrict__ cig_tmp,
-                                                     dsa_hit* __restrict__ hits) {
+                                                     dsa_hit* __restrict__ hits,
+                                                     const int2* __restrict__ bwin) {
   __shared__ uint32_t win[WIN_ROWS * WIN_WORDS];
   constexpr unsigned FULL = 0xFFFFFFFFu;
   const int lane = threadIdx.x;
@@ -629,8 +730,9 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
       // decision leads there)
       const int32_t ci = __shfl_sync(FULL, i, 0), cj = __shfl_sync(FULL, j, 0);
       wb = (ci - 1) / TB_BAND;
-      const int32_t jlo = band_jlo(jb, wb);
-      if (cj < jlo || cj >= jlo + jb.wc) break;
+      int32_t jlo, wcb;
+      band_window(jb, bwin, wb, jlo, wcb);
+      if (cj < jlo || cj >= jlo + wcb) break;
       const int32_t wi = (cj - jlo) >> 3;
       wlo = max(0, wi - (WIN_WORDS - 1));
       wr1 = ci - wb * TB_BAND;
@@ -707,13 +809,25 @@ int long_ckpt_rows() { return TB_BAND; }
 int launch_long_tb_fill(dsa_ctx* ctx, cudaStream_t stream, const dsa_db* db, const dsa_db* qs,
                         const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
                         const LongTbJob* d_jobs, const uint32_t* d_items, uint32_t n_items,
-                        const int2* d_bnd, uint32_t* d_dir) {
+                        const int2* d_bnd, uint32_t* d_dir, const int2* d_win) {
   if (n_items == 0) return DSA_OK;
   const unsigned grid = (unsigned)std::min<uint64_t>((n_items + WARPS - 1) / WARPS,
                                                      (uint64_t)ctx->sm_count * 16);
   auto fill = A <= 4 ? k_long_tb_fill<true> : k_long_tb_fill<false>;
   fill<<<grid, WARPS * 32, 0, stream>>>(qs->d_codes, db->d_codes, d_matrix, A, o, e, mode, fe,
-                                        d_jobs, d_items, n_items, d_bnd, d_dir);
+                                        d_jobs, d_items, n_items, d_bnd, d_dir, d_win);
+  DSA_CUDA_TRY(cudaGetLastError());
+  ++ctx->launches;
+  return DSA_OK;
+}
+
+int launch_long_tb_windows(dsa_ctx* ctx, cudaStream_t stream, const LongTbJob* d_jobs,
+                           const uint32_t* d_items, uint32_t n_items, const int2* d_bnd,
+                           const dsa_hit* d_hits, int mode, uint32_t fe, int o, int e,
+                           int smax_pos, int2* d_win, int32_t* d_maxw) {
+  if (n_items == 0) return DSA_OK;
+  k_long_tb_windows<<<(n_items + 3) / 4, 128, 0, stream>>>(d_jobs, d_items, n_items, d_bnd, d_hits,
+                                                           mode, fe, o, e, smax_pos, d_win, d_maxw);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   return DSA_OK;
@@ -721,9 +835,10 @@ int launch_long_tb_fill(dsa_ctx* ctx, cudaStream_t stream, const dsa_db* db, con
 
 int launch_long_tb_walk(dsa_ctx* ctx, cudaStream_t stream, const LongTbJob* d_jobs,
                         uint32_t n_jobs, int mode, uint32_t fe, const uint32_t* d_dir,
-                        uint32_t* d_cig_tmp, dsa_hit* d_hits) {
+                        uint32_t* d_cig_tmp, dsa_hit* d_hits, const int2* d_win) {
   if (n_jobs == 0) return DSA_OK;
-  k_long_tb_walk<<<n_jobs, 32, 0, stream>>>(d_jobs, n_jobs, mode, fe, d_dir, d_cig_tmp, d_hits);
+  k_long_tb_walk<<<n_jobs, 32, 0, stream>>>(d_jobs, n_jobs, mode, fe, d_dir, d_cig_tmp, d_hits,
+                                            d_win);
   DSA_CUDA_TRY(cudaGetLastError());
   ++ctx->launches;
   return DSA_OK;

@@ -142,6 +142,7 @@ struct TbRun {
   dsa_res* res;
   DevBuf d_mat, d_total;
   uint64_t total = 0;   // CIGAR words written so far
+  int smax_pos = 0;     // max(S, 0)
 };
 
 // Traceback band window of a long job from the diagonal bound of its score.
@@ -430,14 +431,42 @@ int tb_run_long(TbRun& R, std::vector<LongTbJob>& list, const int2* bnd_rows, ui
       ++k1;
     }
     std::vector<LongTbJob> chunk(list.begin() + k0, list.begin() + k1);
+    // per-band windows from the checkpoint rows (each within the job's
+    // diagonal window); the decision rows take the widest band's words
+    uint32_t n_bands = 0;
+    for (LongTbJob& lj : chunk) {
+      lj.win_off = n_bands;
+      n_bands += (uint32_t)((lj.ie + ckpt - 1) / ckpt);
+    }
+    DevBuf d_lj, d_items, d_dir, d_cig, d_shim, d_win, d_maxw;
+    DSA_TRY(upload(ctx, d_lj, chunk));
+    DSA_TRY(upload(ctx, d_items, items));
+    DSA_TRY(d_win.alloc(ctx, (size_t)std::max<uint32_t>(n_bands, 1) * sizeof(int2)));
+    DSA_TRY(d_maxw.alloc(ctx, chunk.size() * sizeof(int32_t)));
+    DSA_CUDA_TRY(cudaMemsetAsync(d_maxw.p, 0, chunk.size() * sizeof(int32_t), ctx->stream));
+    DSA_TRY(launch_long_tb_windows(ctx, ctx->stream, d_lj.as<LongTbJob>(), d_items.as<uint32_t>(),
+                                   (uint32_t)(items.size() / 2), bnd_rows, res->d_hits, res->mode,
+                                   res->free_ends, res->gap_open, res->gap_extend,
+                                   R.smax_pos, d_win.as<int2>(),
+                                   d_maxw.as<int32_t>()));
+    std::vector<int32_t> maxw(chunk.size());
+    DSA_CUDA_TRY(cudaMemcpyAsync(maxw.data(), d_maxw.p, chunk.size() * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    dir = 0;
+    for (size_t k = 0; k < chunk.size(); ++k) {
+      LongTbJob& lj = chunk[k];
+      lj.wpr = (uint32_t)((std::max(maxw[k], 1) + 7) / 8);
+      lj.dir_off = dir;
+      dir += (uint64_t)lj.ie * lj.wpr;
+    }
+    DSA_CUDA_TRY(cudaMemcpyAsync(d_lj.p, chunk.data(), chunk.size() * sizeof(LongTbJob),
+                                 cudaMemcpyHostToDevice, ctx->stream));
     std::vector<TbJob> shim(chunk.size());   // the CIGAR packer reads hit and cig_off
     for (size_t k = 0; k < chunk.size(); ++k) {
       shim[k].hit = chunk[k].hit;
       shim[k].cig_off = chunk[k].cig_off;
     }
-    DevBuf d_lj, d_items, d_dir, d_cig, d_shim;
-    DSA_TRY(upload(ctx, d_lj, chunk));
-    DSA_TRY(upload(ctx, d_items, items));
     DSA_TRY(upload(ctx, d_shim, shim));
     DSA_TRY(d_dir.alloc(ctx, dir * 4));
     DSA_TRY(d_cig.alloc(ctx, cig * 4));
@@ -445,10 +474,11 @@ int tb_run_long(TbRun& R, std::vector<LongTbJob>& list, const int2* bnd_rows, ui
     DSA_TRY(launch_long_tb_fill(ctx, ctx->stream, res->db, res->queries, R.d_mat.as<int8_t>(),
                                 res->A, res->gap_open, res->gap_extend, res->mode,
                                 res->free_ends, d_lj.as<LongTbJob>(), d_items.as<uint32_t>(),
-                                (uint32_t)(items.size() / 2), bnd_rows, d_dir.as<uint32_t>()));
+                                (uint32_t)(items.size() / 2), bnd_rows, d_dir.as<uint32_t>(),
+                                d_win.as<int2>()));
     DSA_TRY(launch_long_tb_walk(ctx, ctx->stream, d_lj.as<LongTbJob>(), (uint32_t)chunk.size(),
                                 res->mode, res->free_ends, d_dir.as<uint32_t>(),
-                                d_cig.as<uint32_t>(), res->d_hits));
+                                d_cig.as<uint32_t>(), res->d_hits, d_win.as<int2>()));
     DSA_TRY(launch_cigar_compact(ctx, res->d_hits, d_shim.as<TbJob>(), (uint32_t)shim.size(),
                                  d_cig.as<uint32_t>(), res->d_cigar, R.total,
                                  R.d_total.as<uint64_t>()));
@@ -563,6 +593,7 @@ extern "C" int dsa_traceback(dsa_ctx* ctx, dsa_res* res, const uint64_t* which, 
   res->cigar_bytes = (old_n + P.cap_total) * sizeof(uint32_t);
 
   TbRun R{ctx, res};
+  R.smax_pos = smax_pos;
   DSA_TRY(R.d_mat.alloc(ctx, res->A * res->A));
   DSA_CUDA_TRY(cudaMemcpyAsync(R.d_mat.p, res->matrix.data(), res->A * res->A,
                                cudaMemcpyHostToDevice, ctx->stream));
