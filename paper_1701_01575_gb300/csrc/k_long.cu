@@ -374,7 +374,7 @@ __device__ __forceinline__ void band_window(const LongTbJob& jb, const int2* win
 }
 
 template <bool BYTES>
-__global__ void __launch_bounds__(WARPS * 32) k_long_tb_fill(
+__global__ void __launch_bounds__(WARPS * 32, 3) k_long_tb_fill(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
     const LongTbJob* __restrict__ jobs, const uint32_t* __restrict__ items, uint32_t n_items,
