@@ -599,35 +599,41 @@ def _hits_parity(wl, h, cig, max_trace_cells=30_000_000):
 
 
 # score-pass kernel of each other workload: (phase, kernel, packed int16x2?)
-SUB_KERNELS = {"reads_vs_windows": ("inter16", "k_pairs16", True),
-               "long_pairs_global": ("intra16", "k_long_score16", True),
-               "long_pairs_local": ("intra16", "k_long_score", False),
-               "protein_search_global": ("inter16", "k_inter_glob16", True),
-               "protein_search_semiglobal": ("inter16", "k_inter_glob16", True)}
+# phase, score-pass kernel, packed (2 cells per instruction), and the kernel's
+# ops per register and row: maxima (DPX) and plain adds
+SUB_KERNELS = {"reads_vs_windows": ("inter16", "k_pairs16", True, 5, 1),
+               "long_pairs_global": ("intra16", "k_long_score16", True, 5, 1),
+               "long_pairs_local": ("intra16", "k_long_score16", True, 5.5, 0),
+               "protein_search_global": ("inter16", "k_inter_glob16", True, 5, 1),
+               "protein_search_semiglobal": ("inter16", "k_inter_glob16", True, 5, 1)}
 
 
 def sub_roofline(name, ctx, clk, phase_gcups):
-    """The score-pass kernel against the ALU-pipe roofline of its form: 6
-    algorithmic ops per cell, five maxima at the measured DPX rate (s16x2 for
-    the packed kernels, 2 cells per instruction; s32 for the int32 kernel, 1)
-    and one add at the measured integer-add rate, 32 lanes per instruction."""
+    """The score-pass kernel against the ALU-pipe roofline of its form: the
+    maxima at the measured DPX rate (s16x2 for the packed kernels, 2 cells per
+    instruction; s32 for the int32 kernel, 1) and the adds at the measured
+    integer-add rate, 32 lanes per instruction.  Global forms take five
+    maxima and one add (H - o) per register and row; the local long-pair form
+    folds the floor into a sixth maximum in place of the add and keeps a
+    three-way running maximum every two rows (5.5 maxima)."""
     import torch
     if name not in SUB_KERNELS or not clk.get("sm_mhz"):
         return None
-    phase, kernel, packed = SUB_KERNELS[name]
+    phase, kernel, packed, n_max, n_add = SUB_KERNELS[name]
     if phase not in phase_gcups:
         return None
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     rate_max = ctx.probe_issue_rate(0 if packed else 6)
     rate_add = ctx.probe_issue_rate(3)
     cells = 2 if packed else 1
-    peak = sms * clk["sm_mhz"] * 1e6 * 32 * cells / (5 / rate_max + 1 / rate_add) / 1e9
+    peak = sms * clk["sm_mhz"] * 1e6 * 32 * cells / (n_max / rate_max + n_add / rate_add) / 1e9
     achieved = phase_gcups[phase]
+    add_txt = f" + {n_add} add / {rate_add:.3f}" if n_add else ""
     return {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 1),
             "peak": round(peak, 1), "unit": "GCUPS", "frac": round(achieved / peak, 4),
             "peak_basis": f"{sms} SMs x {clk['sm_mhz']:.0f} MHz x 32 lanes x {cells} cell(s) / "
-                          f"(5 {'DPX s16x2' if packed else 'DPX s32'} ops / {rate_max:.3f} + "
-                          f"1 add / {rate_add:.3f} warp-instr/SM/clk, both measured)"}
+                          f"({n_max} {'DPX s16x2' if packed else 'DPX s32'} ops / {rate_max:.3f}"
+                          f"{add_txt} warp-instr/SM/clk, measured)"}
 
 
 def sub_workload(name, args, ctx, stream, bus, main):

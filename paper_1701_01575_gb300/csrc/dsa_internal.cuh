@@ -500,13 +500,19 @@ struct LongPair16 {
 // Packed (int16x2) form of the long-pair score pass for alphabets of up to 4
 // letters with every S + o in int8 and scores whose range passes
 // long16_range_ok; writes the same boundary rows, checkpoints and per-band
-// candidates as launch_long_score and reduces them into `out`.
+// candidates as launch_long_score and reduces them into `out`.  Local mode
+// also takes d_litems (2 words (pair, band) for every band of every pair,
+// n_litems of them) and n_slots (the candidate slots, one per pair band):
+// the score pass keeps each band's best and a snapshot of the block where it
+// first appeared, and a second kernel locates the first cell of the pair's
+// best from those.
 bool long16_range_ok(int o, int e, int smax, int smin);
 int launch_long_score16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const int8_t* d_matrix,
                         int A, int o, int e, int mode, uint32_t fe, const LongJob* d_jobs,
                         uint32_t n_jobs, const LongPair16* d_pjobs, const uint32_t* d_items,
                         uint32_t n_items, int2* d_bnd, uint32_t* d_prog, void* d_cands,
-                        Scores out, int blocks_per_sm = 0);
+                        Scores out, int blocks_per_sm = 0, const uint32_t* d_litems = nullptr,
+                        uint32_t n_litems = 0, uint64_t n_slots = 0);
 int launch_long_reduce(dsa_ctx* ctx, const LongJob* d_jobs, uint32_t n_jobs, const void* d_cands,
                        int mode, uint32_t fe, int o, int e, Scores out);
 size_t long_cand_size();

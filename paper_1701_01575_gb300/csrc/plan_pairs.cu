@@ -144,12 +144,11 @@ int score_pairs(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs, 
   res->cells = cells;
   res->phase_cells[PH_INT32] = cells;
   if (!ljobs.empty()) {
-    // Global and semi-global: the packed form takes two pairs per warp
-    // (sorted neighbours by query and window length) when the alphabet, the
-    // byte tables and the range bound allow it; DSA_LONG_INT32=1 keeps every
-    // pair on the int32 kernel.  Local pairs stay on the int32 kernel.
+    // The packed form takes two pairs per warp (sorted neighbours by query
+    // and window length) when the alphabet, the byte tables and the range
+    // bound allow it; DSA_LONG_INT32=1 keeps every pair on the int32 kernel.
     const char* force32 = getenv("DSA_LONG_INT32");
-    const bool l16 = mode != DSA_LOCAL && A <= 4 && s_plus_o_fits_int8(matrix, A, o) &&
+    const bool l16 = A <= 4 && s_plus_o_fits_int8(matrix, A, o) &&
                      long16_range_ok(o, e, v.smax, v.smin) && !(force32 && atoi(force32));
     std::vector<LongPair16> units;
     std::vector<std::pair<uint32_t, uint32_t>> mn;
@@ -174,10 +173,19 @@ int score_pairs(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs, 
     }
     // band items in latest-start order (bands in order inside a pair or unit)
     const std::vector<uint32_t> items = band_items(mn, band);
-    DevBuf d_ljobs, d_items, d_prog, d_cands, d_units;
+    // local, packed: every band of every pair, for locating the best cell
+    std::vector<uint32_t> litems;
+    if (l16 && mode == DSA_LOCAL)
+      for (size_t k = 0; k < ljobs.size(); ++k)
+        for (uint32_t b = 0; b < (uint32_t)((ljobs[k].m + band - 1) / band); ++b) {
+          litems.push_back((uint32_t)k);
+          litems.push_back(b);
+        }
+    DevBuf d_ljobs, d_items, d_prog, d_cands, d_units, d_litems;
     void* pb = nullptr;
     if ((rc = upload(ctx, d_ljobs, ljobs)) || (rc = upload(ctx, d_items, items)) ||
         (l16 && (rc = upload(ctx, d_units, units))) ||
+        (!litems.empty() && (rc = upload(ctx, d_litems, litems))) ||
         (rc = d_prog.alloc(ctx, prog * sizeof(uint32_t))) ||
         (rc = d_cands.alloc(ctx, cand * long_cand_size())) ||
         (rc = ctx->alloc(&pb, bnd * sizeof(int2))))
@@ -201,7 +209,8 @@ int score_pairs(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs, 
         return launch_long_score16(ctx, db, qs, d_mat, A, o, e, mode, fe, d_ljobs.as<LongJob>(),
                                    (uint32_t)ljobs.size(), d_units.as<LongPair16>(),
                                    d_items.as<uint32_t>(), (uint32_t)(items.size() / 2),
-                                   res->d_bnd, d_prog.as<uint32_t>(), d_cands.p, sc, bps);
+                                   res->d_bnd, d_prog.as<uint32_t>(), d_cands.p, sc, bps,
+                                   d_litems.as<uint32_t>(), (uint32_t)(litems.size() / 2), cand);
       return launch_long_score(ctx, db, qs, d_mat, A, o, e, mode, fe,
                                s_plus_o_fits_int8(matrix, A, o), d_ljobs.as<LongJob>(),
                                (uint32_t)ljobs.size(), d_items.as<uint32_t>(),

@@ -9,8 +9,10 @@ past the shorter window), an odd number of pairs (a unit with an empty
 half), lengths that are not multiples of the 512-row bands or the 32-column
 blocks, every free-end set, and scores far outside int16 in both
 directions (the relative encoding, not the absolute value, has to fit).
-Local pairs run on the int32 kernel in both settings; the cases keep them
-to check that the choice of kernel is made per mode.
+Local pairs keep only each band's best and the start state of the 32-step
+block that first reached it, and a second kernel reruns that block to find
+the first cell holding the pair's maximum; the tie cases put equal maxima in
+several bands, several columns and lanes whose columns lag the block.
 """
 import numpy as np
 import pytest
@@ -201,3 +203,61 @@ def test_extreme_long_pair_shapes(ctx, mode, fe, monkeypatch):
     for f in ("score", "q_end", "t_end", "q_begin", "t_begin", "cigar_len"):
         assert np.array_equal(h16[f], h32[f]), f
     assert np.array_equal(r16.cigar(), r32.cigar())
+
+
+@pytest.mark.parametrize("case", ["repeats_in_bands", "repeats_in_columns", "low_complexity",
+                                  "max_in_first_block", "max_near_window_end"])
+def test_packed_local_ties(ctx, case, monkeypatch):
+    """Local pairs whose maximum is held by many cells: a 700-residue
+    segment repeated down the query (equal maxima in several bands, the
+    first row wins), repeated along the target (the first column wins), a
+    period-3 sequence against itself shifted (ties everywhere), the maximum
+    in the first block, and the maximum at the last columns of the window.
+    Scores and ends against the oracle and the int32 kernel, tracebacks
+    against the oracle."""
+    rng = np.random.default_rng(2500 + len(case))
+    S = W.dna_matrix(1, -1)
+    o, e = 2, 1
+    seg = rng.integers(0, 4, 700).astype(np.uint8)
+    if case == "repeats_in_bands":
+        q = np.concatenate([seg, rng.integers(0, 4, 77).astype(np.uint8), seg, seg,
+                            rng.integers(0, 4, 1300).astype(np.uint8), seg])
+        t = np.concatenate([rng.integers(0, 4, 900).astype(np.uint8), seg,
+                            rng.integers(0, 4, 1200).astype(np.uint8)])
+    elif case == "repeats_in_columns":
+        q = np.concatenate([rng.integers(0, 4, 1500).astype(np.uint8), seg,
+                            rng.integers(0, 4, 400).astype(np.uint8)])
+        t = np.concatenate([seg, rng.integers(0, 4, 33).astype(np.uint8), seg, seg,
+                            rng.integers(0, 4, 95).astype(np.uint8), seg])
+    elif case == "low_complexity":
+        q = np.tile(np.array([0, 1, 2], np.uint8), 1400)
+        t = np.tile(np.array([1, 2, 0], np.uint8), 1000)
+    elif case == "max_in_first_block":
+        q = np.concatenate([seg[:20], rng.integers(0, 4, 3000).astype(np.uint8)])
+        t = np.concatenate([seg[:20], rng.integers(0, 4, 2500).astype(np.uint8)])
+        S = W.dna_matrix(1, -4)
+        o, e = 6, 3
+    else:
+        q = np.concatenate([rng.integers(0, 4, 2600).astype(np.uint8), seg[:200]])
+        t = np.concatenate([rng.integers(0, 4, 2200).astype(np.uint8), seg[:200]])
+        S = W.dna_matrix(1, -4)
+        o, e = 6, 3
+    qs = W.SeqSet.from_list([q, t[:2100], q])
+    db = W.SeqSet.from_list([t, q[:2300], t])
+    pairs = np.zeros(3, dtype=W.PAIR_DTYPE)
+    pairs["query_id"] = [0, 1, 2]
+    pairs["target_id"] = [0, 1, 2]
+    pairs["t_len"] = db.lengths
+    sc, qe, te = oracle.score_pairs(qs.codes, qs.offsets, db.codes, db.offsets, pairs["query_id"],
+                                    pairs["target_id"], S, o, e, dsa.LOCAL, 15,
+                                    pair_toff=pairs["t_offset"], pair_tlen=pairs["t_len"])
+    monkeypatch.delenv("DSA_LONG_INT32", raising=False)
+    r16 = _run(ctx, qs, db, pairs, S, o, e, dsa.LOCAL, 15)
+    h16 = r16.hits()
+    assert_same((h16["score"], h16["q_end"], h16["t_end"]), (sc, qe, te), case)
+    check_traceback(h16, r16.cigar(), qs, db, S, o, e, dsa.LOCAL, 15)
+    monkeypatch.setenv("DSA_LONG_INT32", "1")
+    r32 = _run(ctx, qs, db, pairs, S, o, e, dsa.LOCAL, 15, trace=False)
+    h32 = r32.hits()
+    for f in ("score", "q_end", "t_end"):
+        assert np.array_equal(h16[f], h32[f]), f
