@@ -100,8 +100,10 @@ __device__ __forceinline__ uint32_t bias2(int32_t lo, int32_t hi) { return pack2
 // the value of half `x` of an offset-binary register
 __device__ __forceinline__ int32_t half(uint32_t v, int x) { return x ? hi16(v ^ BIAS2) : lo16(v ^ BIAS2); }
 
+// The local form's running maxima and block-start state need more than the
+// 128 registers of 4 blocks per SM (it spilled there); at 3 it takes 156.
 template <bool LOCAL>
-__global__ void __launch_bounds__(WARPS * 32, 4) k_long_score16(
+__global__ void __launch_bounds__(WARPS * 32, LOCAL ? 3 : 4) k_long_score16(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
     const LongJob* __restrict__ jobs, const LongPair16* __restrict__ pjobs,
