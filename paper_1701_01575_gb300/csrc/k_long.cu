@@ -741,12 +741,17 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
       jc = cj - jlo;
       __syncwarp();
       const int32_t w = wlo + lane;
-      // 32 independent row loads in flight per lane: a reload costs a few
-      // memory latencies, not one per 8 rows
-#pragma unroll 32
-      for (int r = wr0; r < wr1; ++r)
-        win[(r - wr0) * WIN_WORDS + lane] =
-            w < (int32_t)wpr ? D[(uint64_t)(wb * TB_BAND + r) * wpr + (uint32_t)w] : 0u;
+      // every row's word in flight at once (asynchronous copies hold no
+      // registers): a reload costs about one memory latency
+      if (w < (int32_t)wpr) {
+        const uint32_t* src = D + (uint64_t)(wb * TB_BAND + wr0) * wpr + (uint32_t)w;
+#pragma unroll 8
+        for (int r = wr0; r < wr1; ++r, src += wpr) cp_async4(win + (r - wr0) * WIN_WORDS + lane, src);
+      } else {
+        for (int r = wr0; r < wr1; ++r) win[(r - wr0) * WIN_WORDS + lane] = 0u;
+      }
+      cp_async_commit();
+      cp_async_wait<0>();
       __syncwarp();
     }
     if (lane == 0) {
