@@ -438,7 +438,7 @@ struct LongJob {
 struct LongTbJob {
   uint64_t q_start, t_start;
   uint64_t bnd_off;            // checkpoints of the score pass
-  uint64_t dir_off;            // word offset of the decision matrix (ie x wpr words)
+  uint64_t dir_off;            // word offset of the decisions (bands x TB_BAND x wpr words)
   uint64_t cig_off;
   int32_t n;                   // boundary row length (the pair's window length)
   int32_t ie, je;
@@ -479,6 +479,16 @@ int launch_long_tb_fill(dsa_ctx* ctx, cudaStream_t stream, const dsa_db* db, con
                         const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
                         const LongTbJob* d_jobs, const uint32_t* d_items, uint32_t n_items,
                         const int2* d_bnd, uint32_t* d_dir, const int2* d_win = nullptr);
+// Part 1, packed (k_long_tb16.cu): two traceback bands per warp, one per
+// 16-bit half, for alphabets of up to 4 letters with every S + o in int8 and
+// scores within long_tb16_range_ok; d_units holds 4 words per unit (job,
+// band, job, band; the second job NONE for an empty half), d_win the
+// per-band windows.  Writes the same decisions as launch_long_tb_fill.
+bool long_tb16_range_ok(int o, int e, int smax, int smin);
+int launch_long_tb_fill16(dsa_ctx* ctx, cudaStream_t stream, const dsa_db* db, const dsa_db* qs,
+                          const int8_t* d_matrix, int A, int o, int e, int mode, uint32_t fe,
+                          const LongTbJob* d_jobs, const uint32_t* d_units, uint32_t n_units,
+                          const int2* d_bnd, uint32_t* d_dir, const int2* d_win);
 // Part 2: one warp per job walks its decisions back from the end cell
 // (every band of those jobs filled before, in stream order).
 int launch_long_tb_walk(dsa_ctx* ctx, cudaStream_t stream, const LongTbJob* d_jobs,

@@ -24,10 +24,19 @@
 // Traceback.  The checkpoints make every TB_BAND-row band independent: all
 // bands of all hits are recomputed at once (one warp each, TB_ROWS rows per
 // lane) over the rectangle up to the
-// end cell, storing the 4-bit decision of every cell (as in the short-hit
-// traceback), then one warp per hit walks back through a shared-memory window
-// of the decisions.  Decision memory is half a byte per cell of the
-// rectangle (or of its diagonal band), handled in chunks of bounded size.
+// end cell, storing the 4-bit decision of every cell, then one warp per hit
+// walks back through a shared-memory window of the decisions.  Decision
+// memory is half a byte per cell of the rectangle (or of its diagonal band),
+// handled in chunks of bounded size.  Each traceback band of a hit keeps its
+// decisions as TB_BAND-row blocks of one word (8 columns) per row, the
+// words of a column block consecutive by row: word w of row i0 + k of band b
+// is at (b wpr + w) TB_BAND + k, so the 8 rows of a fill lane make whole
+// sectors and the writes in flight stay within a few lines per band (row by
+// row, a warp kept a partly written line per row, which at 2 bands per warp
+// outgrew the L2).  A decision nibble here holds the H
+// source in bits 0-1 (0 D, 1 M, 2 I, 3 stop: the empty local alignment),
+// E opened here in bit 2 and F opened here in bit 3; the packed fill
+// (k_long_tb16.cu) writes the same nibbles.
 #include "dsa_internal.cuh"
 #include "dpx.cuh"
 
@@ -473,22 +482,24 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_long_tb_fill(
         for (int r = 0; r < TB_ROWS; ++r) {
           const int32_t ii = r0 + r + 1;
           if (FAST || ii <= ie) {
-            const int32_t fo = Hp - o, fx = F - e;
-            F = max(fx, fo);
-            const int32_t eo = H[r] - o, ex = E[r] - e;
-            E[r] = max(ex, eo);
+            // each maximum also yields its decision (first operand >= second,
+            // one DPX instruction): a gap opens here on ties, M comes before
+            // the gaps and I before D
+            bool pf, pe, pg, pm;
+            F = __vibmax_s32(Hp - o, F - e, &pf);
+            E[r] = __vibmax_s32(H[r] - o, E[r] - e, &pe);
             const int32_t sv = BYTES ? (int32_t)prmt(qv[r], 0u, sel) : (int32_t)S[qv[r] + a];
             const int32_t mm = d + sv;
-            int32_t v = max(mm, max(E[r], F));
-            if (local) v = max(v, 0);
-            uint32_t src;
-            if (local && v == 0) src = 3;
-            else if (v == mm) src = 0;
-            else if (v == F) src = 1;
-            else src = 2;
-            nbw[r] |= (src | ((eo >= ex) ? 4u : 0u) | ((fo >= fx) ? 8u : 0u)) << sh;
+            const int32_t g = __vibmax_s32(F, E[r], &pg);
+            int32_t v = __vibmax_s32(mm, g, &pm);
+            uint32_t src = pm ? 1u : (pg ? 2u : 0u);
+            if (local && v <= 0) {   // the empty alignment: stop
+              v = 0;
+              src = 3u;
+            }
+            nbw[r] |= (src | (pe ? 4u : 0u) | (pf ? 8u : 0u)) << sh;
             if (flushw) {
-              D[(uint64_t)(ii - 1) * wpr + (uint32_t)jc / 8u] = nbw[r];
+              D[((uint64_t)b * wpr + (uint32_t)jc / 8u) * TB_BAND + (uint32_t)(ii - 1 - i0)] = nbw[r];
               nbw[r] = 0;
             }
             d = H[r];
@@ -617,6 +628,7 @@ __global__ void __launch_bounds__(128) k_long_tb_windows(
 // reads shared memory instead of waiting on a global load.
 constexpr int WIN_WORDS = 32;
 constexpr int WIN_ROWS = 256;
+constexpr int WIN_STRIDE = WIN_WORDS + 1;   // words per window row (padded: no bank conflicts)
 
 __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict__ jobs,
                                                      uint32_t n_jobs, int mode, uint32_t fe,
@@ -624,7 +636,7 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
                                                      uint32_t* __restrict__ cig_tmp,
                                                      dsa_hit* __restrict__ hits,
                                                      const int2* __restrict__ bwin) {
-  __shared__ uint32_t win[WIN_ROWS * WIN_WORDS];
+  __shared__ uint32_t win[WIN_ROWS * WIN_STRIDE];
   constexpr unsigned FULL = 0xFFFFFFFFu;
   const int lane = threadIdx.x;
   const bool local = mode == DSA_LOCAL;
@@ -667,7 +679,7 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
           // nibble's shift along.  A switch from H to a gap state reads the
           // same cell's open bit, so it is taken in the same step.
           const int32_t safe = min(min(rr - wr0, jc - 8 * wlo), min(i - 1, j - 1));
-          const uint32_t* p = win + (rr - wr0) * WIN_WORDS + ((jc >> 3) - wlo);
+          const uint32_t* p = win + (rr - wr0) * WIN_STRIDE + ((jc >> 3) - wlo);
           uint32_t sh = 4u * (uint32_t)(jc & 7);
           bool stop = false;
           int32_t q = 0;
@@ -680,15 +692,15 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
 #pragma unroll
               for (int kk = 0; kk < 8; ++kk) {
                 const int32_t jk = jc - kk;
-                const uint32_t w = win[(rr - kk - wr0) * WIN_WORDS + ((jk >> 3) - wlo)];
-                notm |= (((w >> (4 * (jk & 7))) & 3u) != 0u ? 1u : 0u) << kk;
+                const uint32_t w = win[(rr - kk - wr0) * WIN_STRIDE + ((jk >> 3) - wlo)];
+                notm |= (((w >> (4 * (jk & 7))) & 3u) != 1u ? 1u : 0u) << kk;
               }
               const int32_t L = notm ? __ffs(notm) - 1 : 8;
               if (L > 0) {
                 c.emit_run(0, (uint32_t)L);
                 i -= L; j -= L; rr -= L; jc -= L;
                 q += L - 1;
-                p = win + (rr - wr0) * WIN_WORDS + ((jc >> 3) - wlo);
+                p = win + (rr - wr0) * WIN_STRIDE + ((jc >> 3) - wlo);
                 sh = 4u * (uint32_t)(jc & 7);
                 continue;
               }
@@ -697,19 +709,19 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
             if (st == 0) {
               const uint32_t src = nib & 3u;
               if (src == 3) { stop = true; break; }
-              if (src == 0) {   // M: up and left
+              if (src == 1) {   // M: up and left
                 c.emit(0);
-                p -= WIN_WORDS + (sh == 0 ? 1 : 0);
+                p -= WIN_STRIDE + (sh == 0 ? 1 : 0);
                 sh = (sh - 4u) & 31u;
                 --i; --j; --rr; --jc;
                 continue;
               }
-              st = (int)src;   // 1: I (F state), 2: D (E state)
+              st = src == 2 ? 1 : 2;   // 1: I (F state), 2: D (E state)
             }
             if (st == 1) {   // I: up
               c.emit(1);
               if (nib & 8u) st = 0;
-              p -= WIN_WORDS;
+              p -= WIN_STRIDE;
               --i; --rr;
             } else {         // D: left
               c.emit(2);
@@ -740,15 +752,21 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
       rr = wr1 - 1;
       jc = cj - jlo;
       __syncwarp();
-      const int32_t w = wlo + lane;
-      // every row's word in flight at once (asynchronous copies hold no
+      // words wlo .. wlo + 31 of rows wr0 .. wr1 - 1 of band wb: each word's
+      // rows are contiguous in the decision layout, so the lanes read along
+      // rows, every copy in flight at once (asynchronous copies hold no
       // registers): a reload costs about one memory latency
-      if (w < (int32_t)wpr) {
-        const uint32_t* src = D + (uint64_t)(wb * TB_BAND + wr0) * wpr + (uint32_t)w;
-#pragma unroll 8
-        for (int r = wr0; r < wr1; ++r, src += wpr) cp_async4(win + (r - wr0) * WIN_WORDS + lane, src);
-      } else {
-        for (int r = wr0; r < wr1; ++r) win[(r - wr0) * WIN_WORDS + lane] = 0u;
+      {
+        const uint32_t* Db = D + (uint64_t)wb * wpr * TB_BAND;
+#pragma unroll 4
+        for (int k = 0; k < WIN_WORDS; ++k) {
+          const int32_t w = wlo + k;
+          for (int r = wr0 + lane; r < wr1; r += 32) {
+            uint32_t* dst = win + (r - wr0) * WIN_STRIDE + k;
+            if (w < (int32_t)wpr) cp_async4(dst, Db + (uint64_t)w * TB_BAND + (uint32_t)r);
+            else *dst = 0u;
+          }
+        }
       }
       cp_async_commit();
       cp_async_wait<0>();

@@ -413,6 +413,16 @@ int tb_run_long(TbRun& R, std::vector<LongTbJob>& list, const int2* bnd_rows, ui
   dsa_ctx* ctx = R.ctx;
   dsa_res* res = R.res;
   const int ckpt = long_ckpt_rows();
+  // The packed fill takes alphabets of up to 4 letters whose S + o fit a
+  // byte and scores whose relative values fit its range;
+  // DSA_TB_FILL_INT32=1 keeps the int32 fill.
+  int smin = 0;
+  for (int8_t v : res->matrix) smin = std::min<int>(smin, v);
+  const char* f32 = getenv("DSA_TB_FILL_INT32");
+  const bool packed = res->A <= 4 &&
+                      s_plus_o_fits_int8(res->matrix.data(), res->A, res->gap_open) &&
+                      long_tb16_range_ok(res->gap_open, res->gap_extend, R.smax_pos, smin) &&
+                      !(f32 && atoi(f32));
   size_t k0 = 0;
   while (k0 < list.size()) {
     uint64_t dir = 0, cig = 0;
@@ -420,7 +430,7 @@ int tb_run_long(TbRun& R, std::vector<LongTbJob>& list, const int2* bnd_rows, ui
     std::vector<uint32_t> items;
     while (k1 < list.size()) {
       LongTbJob& lj = list[k1];
-      const uint64_t w = (uint64_t)lj.ie * lj.wpr;
+      const uint64_t w = (uint64_t)((lj.ie + ckpt - 1) / ckpt) * ckpt * lj.wpr;
       if (k1 > k0 && dir + w > limit) break;
       lj.dir_off = dir;
       lj.cig_off = cig;
@@ -450,15 +460,19 @@ int tb_run_long(TbRun& R, std::vector<LongTbJob>& list, const int2* bnd_rows, ui
                                    R.smax_pos, d_win.as<int2>(),
                                    d_maxw.as<int32_t>()));
     std::vector<int32_t> maxw(chunk.size());
+    std::vector<int2> bwin(packed ? n_bands : 0);
     DSA_CUDA_TRY(cudaMemcpyAsync(maxw.data(), d_maxw.p, chunk.size() * sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, ctx->stream));
+    if (packed)
+      DSA_CUDA_TRY(cudaMemcpyAsync(bwin.data(), d_win.p, n_bands * sizeof(int2),
+                                   cudaMemcpyDeviceToHost, ctx->stream));
     DSA_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     dir = 0;
     for (size_t k = 0; k < chunk.size(); ++k) {
       LongTbJob& lj = chunk[k];
       lj.wpr = (uint32_t)((std::max(maxw[k], 1) + 7) / 8);
       lj.dir_off = dir;
-      dir += (uint64_t)lj.ie * lj.wpr;
+      dir += (uint64_t)((lj.ie + ckpt - 1) / ckpt) * ckpt * lj.wpr;
     }
     DSA_CUDA_TRY(cudaMemcpyAsync(d_lj.p, chunk.data(), chunk.size() * sizeof(LongTbJob),
                                  cudaMemcpyHostToDevice, ctx->stream));
@@ -471,11 +485,37 @@ int tb_run_long(TbRun& R, std::vector<LongTbJob>& list, const int2* bnd_rows, ui
     DSA_TRY(d_dir.alloc(ctx, dir * 4));
     DSA_TRY(d_cig.alloc(ctx, cig * 4));
     // every band of every hit of the chunk in one launch, then one warp per hit
-    DSA_TRY(launch_long_tb_fill(ctx, ctx->stream, res->db, res->queries, R.d_mat.as<int8_t>(),
-                                res->A, res->gap_open, res->gap_extend, res->mode,
-                                res->free_ends, d_lj.as<LongTbJob>(), d_items.as<uint32_t>(),
-                                (uint32_t)(items.size() / 2), bnd_rows, d_dir.as<uint32_t>(),
-                                d_win.as<int2>()));
+    if (packed) {
+      // bands paired by window width (widest first), two per warp
+      std::vector<uint32_t> ord(items.size() / 2);
+      std::iota(ord.begin(), ord.end(), 0u);
+      auto width = [&](uint32_t x) {
+        return bwin[chunk[items[2 * x]].win_off + items[2 * x + 1]].y;
+      };
+      std::stable_sort(ord.begin(), ord.end(),
+                       [&](uint32_t x, uint32_t y) { return width(x) > width(y); });
+      std::vector<uint32_t> units;
+      units.reserve(2 * items.size());
+      for (size_t k = 0; k < ord.size(); k += 2) {
+        units.push_back(items[2 * ord[k]]);
+        units.push_back(items[2 * ord[k] + 1]);
+        units.push_back(k + 1 < ord.size() ? items[2 * ord[k + 1]] : NONE);
+        units.push_back(k + 1 < ord.size() ? items[2 * ord[k + 1] + 1] : 0u);
+      }
+      DevBuf d_units;
+      DSA_TRY(upload(ctx, d_units, units));
+      DSA_TRY(launch_long_tb_fill16(ctx, ctx->stream, res->db, res->queries,
+                                    R.d_mat.as<int8_t>(), res->A, res->gap_open, res->gap_extend,
+                                    res->mode, res->free_ends, d_lj.as<LongTbJob>(),
+                                    d_units.as<uint32_t>(), (uint32_t)(units.size() / 4),
+                                    bnd_rows, d_dir.as<uint32_t>(), d_win.as<int2>()));
+    } else {
+      DSA_TRY(launch_long_tb_fill(ctx, ctx->stream, res->db, res->queries, R.d_mat.as<int8_t>(),
+                                  res->A, res->gap_open, res->gap_extend, res->mode,
+                                  res->free_ends, d_lj.as<LongTbJob>(), d_items.as<uint32_t>(),
+                                  (uint32_t)(items.size() / 2), bnd_rows, d_dir.as<uint32_t>(),
+                                  d_win.as<int2>()));
+    }
     DSA_TRY(launch_long_tb_walk(ctx, ctx->stream, d_lj.as<LongTbJob>(), (uint32_t)chunk.size(),
                                 res->mode, res->free_ends, d_dir.as<uint32_t>(),
                                 d_cig.as<uint32_t>(), res->d_hits, d_win.as<int2>()));

@@ -261,3 +261,38 @@ def test_packed_local_ties(ctx, case, monkeypatch):
     h32 = r32.hits()
     for f in ("score", "q_end", "t_end"):
         assert np.array_equal(h16[f], h32[f]), f
+
+
+@pytest.mark.parametrize("mode,fe", MODES)
+@pytest.mark.parametrize("case", ["ragged", "corners"])
+def test_packed_traceback_fill_matches_int32_fill(ctx, mode, fe, case, monkeypatch):
+    """The packed traceback fill (two traceback bands per warp, values
+    relative to a moving base, decisions from borrow-free differences)
+    against the int32 fill (DSA_TB_FILL_INT32=1) and the oracle: bands of
+    different window widths share a warp, windows end mid-group, the last
+    band of a pair is ragged, and an odd band count leaves a half empty."""
+    rng = np.random.default_rng(2600 + 16 * mode + fe + len(case))
+    if case == "ragged":
+        qs, db, pairs = _ragged_set(rng, mode)
+        S, o, e = W.dna_matrix(2, -3), 5, 2
+    else:
+        a = rng.integers(0, 4, 3100).astype(np.uint8)
+        qs = W.SeqSet.from_list([a, rng.integers(0, 4, 2077).astype(np.uint8), a[300:2999]])
+        db = W.SeqSet.from_list([W.mutate(rng, a, 0.08, 0.04), rng.integers(0, 4, 2600).astype(np.uint8),
+                                 W.mutate(rng, a[100:], 0.02, 0.06)])
+        pairs = np.zeros(3, dtype=W.PAIR_DTYPE)
+        pairs["query_id"] = [0, 1, 2]
+        pairs["target_id"] = [0, 1, 2]
+        pairs["t_len"] = db.lengths
+        S, o, e = np.array([[2, -3, -1, -4], [-2, 3, -3, -1], [-1, -4, 2, -2], [-3, -1, -2, 1]],
+                           np.int8), 4, 4
+    monkeypatch.delenv("DSA_TB_FILL_INT32", raising=False)
+    r16 = _run(ctx, qs, db, pairs, S, o, e, mode, fe)
+    h16 = r16.hits()
+    check_traceback(h16, r16.cigar(), qs, db, S, o, e, mode, fe)
+    monkeypatch.setenv("DSA_TB_FILL_INT32", "1")
+    r32 = _run(ctx, qs, db, pairs, S, o, e, mode, fe)
+    h32 = r32.hits()
+    for f in ("score", "q_end", "t_end", "q_begin", "t_begin", "cigar_len"):
+        assert np.array_equal(h16[f], h32[f]), f
+    assert np.array_equal(r16.cigar(), r32.cigar())
