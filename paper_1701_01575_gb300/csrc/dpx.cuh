@@ -97,10 +97,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-// 8- and 4-byte asynchronous copies global -> shared (generic proxy, per
-// thread), and their commit / wait-for-all-but-N groups.
+// 16-, 8- and 4-byte asynchronous copies global -> shared (generic proxy,
+// per thread; 16 bytes: both addresses 16-byte aligned), and their commit /
+// wait-for-all-but-N groups.
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem_dst)), "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc)
                : "memory");
 }
 __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {

@@ -627,8 +627,7 @@ __global__ void __launch_bounds__(128) k_long_tb_windows(
 // whenever the walk leaves it (the walk only moves up and left), so each step
 // reads shared memory instead of waiting on a global load.
 constexpr int WIN_WORDS = 32;
-constexpr int WIN_ROWS = 256;
-constexpr int WIN_STRIDE = WIN_WORDS + 1;   // words per window row (padded: no bank conflicts)
+constexpr int WIN_ROWS = 256;   // a window word's rows are consecutive (as in global memory)
 
 __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict__ jobs,
                                                      uint32_t n_jobs, int mode, uint32_t fe,
@@ -636,7 +635,7 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
                                                      uint32_t* __restrict__ cig_tmp,
                                                      dsa_hit* __restrict__ hits,
                                                      const int2* __restrict__ bwin) {
-  __shared__ uint32_t win[WIN_ROWS * WIN_STRIDE];
+  __shared__ __align__(16) uint32_t win[WIN_WORDS * WIN_ROWS];
   constexpr unsigned FULL = 0xFFFFFFFFu;
   const int lane = threadIdx.x;
   const bool local = mode == DSA_LOCAL;
@@ -679,7 +678,7 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
           // nibble's shift along.  A switch from H to a gap state reads the
           // same cell's open bit, so it is taken in the same step.
           const int32_t safe = min(min(rr - wr0, jc - 8 * wlo), min(i - 1, j - 1));
-          const uint32_t* p = win + (rr - wr0) * WIN_STRIDE + ((jc >> 3) - wlo);
+          const uint32_t* p = win + ((jc >> 3) - wlo) * WIN_ROWS + (rr - wr0);
           uint32_t sh = 4u * (uint32_t)(jc & 7);
           bool stop = false;
           int32_t q = 0;
@@ -692,7 +691,7 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
 #pragma unroll
               for (int kk = 0; kk < 8; ++kk) {
                 const int32_t jk = jc - kk;
-                const uint32_t w = win[(rr - kk - wr0) * WIN_STRIDE + ((jk >> 3) - wlo)];
+                const uint32_t w = win[((jk >> 3) - wlo) * WIN_ROWS + (rr - kk - wr0)];
                 notm |= (((w >> (4 * (jk & 7))) & 3u) != 1u ? 1u : 0u) << kk;
               }
               const int32_t L = notm ? __ffs(notm) - 1 : 8;
@@ -700,7 +699,7 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
                 c.emit_run(0, (uint32_t)L);
                 i -= L; j -= L; rr -= L; jc -= L;
                 q += L - 1;
-                p = win + (rr - wr0) * WIN_STRIDE + ((jc >> 3) - wlo);
+                p = win + ((jc >> 3) - wlo) * WIN_ROWS + (rr - wr0);
                 sh = 4u * (uint32_t)(jc & 7);
                 continue;
               }
@@ -711,7 +710,7 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
               if (src == 3) { stop = true; break; }
               if (src == 1) {   // M: up and left
                 c.emit(0);
-                p -= WIN_STRIDE + (sh == 0 ? 1 : 0);
+                p -= 1 + (sh == 0 ? WIN_ROWS : 0);
                 sh = (sh - 4u) & 31u;
                 --i; --j; --rr; --jc;
                 continue;
@@ -721,12 +720,12 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
             if (st == 1) {   // I: up
               c.emit(1);
               if (nib & 8u) st = 0;
-              p -= WIN_STRIDE;
+              p -= 1;
               --i; --rr;
             } else {         // D: left
               c.emit(2);
               if (nib & 4u) st = 0;
-              p -= (sh == 0 ? 1 : 0);
+              p -= (sh == 0 ? WIN_ROWS : 0);
               sh = (sh - 4u) & 31u;
               --j; --jc;
             }
@@ -748,23 +747,27 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
       const int32_t wi = (cj - jlo) >> 3;
       wlo = max(0, wi - (WIN_WORDS - 1));
       wr1 = ci - wb * TB_BAND;
-      wr0 = max(0, wr1 - WIN_ROWS);
       rr = wr1 - 1;
+      // rows from a multiple of 4 (16-byte copies), ending at or after the
+      // walk's row
+      const int32_t wr1a = min((wr1 + 3) & ~3, TB_BAND);
+      wr0 = max(0, wr1a - WIN_ROWS);
       jc = cj - jlo;
       __syncwarp();
-      // words wlo .. wlo + 31 of rows wr0 .. wr1 - 1 of band wb: each word's
-      // rows are contiguous in the decision layout, so the lanes read along
-      // rows, every copy in flight at once (asynchronous copies hold no
-      // registers): a reload costs about one memory latency
+      // words wlo .. wlo + 31 of rows wr0 .. wr1a - 1 of band wb: each
+      // word's rows are consecutive in the decision layout and in the window,
+      // so the warp copies 16-byte pieces (4 rows), every copy in flight at
+      // once: a reload costs about one memory latency
       {
         const uint32_t* Db = D + (uint64_t)wb * wpr * TB_BAND;
+        const int32_t n4 = (wr1a - wr0) >> 2;
 #pragma unroll 4
         for (int k = 0; k < WIN_WORDS; ++k) {
           const int32_t w = wlo + k;
-          for (int r = wr0 + lane; r < wr1; r += 32) {
-            uint32_t* dst = win + (r - wr0) * WIN_STRIDE + k;
-            if (w < (int32_t)wpr) cp_async4(dst, Db + (uint64_t)w * TB_BAND + (uint32_t)r);
-            else *dst = 0u;
+          for (int c = lane; c < n4; c += 32) {
+            uint32_t* dst = win + k * WIN_ROWS + 4 * c;
+            if (w < (int32_t)wpr) cp_async16(dst, Db + (uint64_t)w * TB_BAND + (uint32_t)(wr0 + 4 * c));
+            else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
           }
         }
       }
