@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <numeric>
+#include <string>
 
 namespace dsa {
 
@@ -414,15 +415,19 @@ int tb_run_long(TbRun& R, std::vector<LongTbJob>& list, const int2* bnd_rows, ui
   dsa_res* res = R.res;
   const int ckpt = long_ckpt_rows();
   // The packed fill takes alphabets of up to 4 letters whose S + o fit a
-  // byte and scores whose relative values fit its range;
-  // DSA_TB_FILL_INT32=1 keeps the int32 fill.
+  // byte and scores whose relative values fit its range, and runs when a
+  // chunk's bands fill the device twice over (it runs one warp per two
+  // bands: with fewer, the int32 fill's warps hide latency better);
+  // DSA_TB_FILL=int32 | packed fixes the choice.
   int smin = 0;
   for (int8_t v : res->matrix) smin = std::min<int>(smin, v);
-  const char* f32 = getenv("DSA_TB_FILL_INT32");
-  const bool packed = res->A <= 4 &&
-                      s_plus_o_fits_int8(res->matrix.data(), res->A, res->gap_open) &&
-                      long_tb16_range_ok(res->gap_open, res->gap_extend, R.smax_pos, smin) &&
-                      !(f32 && atoi(f32));
+  const char* fill_env = getenv("DSA_TB_FILL");
+  const std::string fill_pick = fill_env ? fill_env : "";
+  const bool packed_ok = res->A <= 4 &&
+                         s_plus_o_fits_int8(res->matrix.data(), res->A, res->gap_open) &&
+                         long_tb16_range_ok(res->gap_open, res->gap_extend, R.smax_pos, smin) &&
+                         fill_pick != "int32";
+  const uint64_t packed_min_bands = 2ull * 12 * (uint64_t)ctx->sm_count;
   size_t k0 = 0;
   while (k0 < list.size()) {
     uint64_t dir = 0, cig = 0;
@@ -448,6 +453,7 @@ int tb_run_long(TbRun& R, std::vector<LongTbJob>& list, const int2* bnd_rows, ui
       lj.win_off = n_bands;
       n_bands += (uint32_t)((lj.ie + ckpt - 1) / ckpt);
     }
+    const bool packed = packed_ok && (fill_pick == "packed" || n_bands >= packed_min_bands);
     DevBuf d_lj, d_items, d_dir, d_cig, d_shim, d_win, d_maxw;
     DSA_TRY(upload(ctx, d_lj, chunk));
     DSA_TRY(upload(ctx, d_items, items));

@@ -27,6 +27,13 @@ from test_oracle_bruteforce import MODES
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(autouse=True)
+def packed_fill(monkeypatch):
+    """Tracebacks here take the packed fill whatever the band count (the
+    library picks it only for calls whose bands fill the device twice)."""
+    monkeypatch.setenv("DSA_TB_FILL", "packed")
+
+
 @pytest.fixture(scope="module")
 def ctx():
     from paper_1701_01575_gb300 import build
@@ -268,7 +275,7 @@ def test_packed_local_ties(ctx, case, monkeypatch):
 def test_packed_traceback_fill_matches_int32_fill(ctx, mode, fe, case, monkeypatch):
     """The packed traceback fill (two traceback bands per warp, values
     relative to a moving base, decisions from borrow-free differences)
-    against the int32 fill (DSA_TB_FILL_INT32=1) and the oracle: bands of
+    against the int32 fill (DSA_TB_FILL=int32) and the oracle: bands of
     different window widths share a warp, windows end mid-group, the last
     band of a pair is ragged, and an odd band count leaves a half empty."""
     rng = np.random.default_rng(2600 + 16 * mode + fe + len(case))
@@ -286,11 +293,11 @@ def test_packed_traceback_fill_matches_int32_fill(ctx, mode, fe, case, monkeypat
         pairs["t_len"] = db.lengths
         S, o, e = np.array([[2, -3, -1, -4], [-2, 3, -3, -1], [-1, -4, 2, -2], [-3, -1, -2, 1]],
                            np.int8), 4, 4
-    monkeypatch.delenv("DSA_TB_FILL_INT32", raising=False)
+    monkeypatch.setenv("DSA_TB_FILL", "packed")
     r16 = _run(ctx, qs, db, pairs, S, o, e, mode, fe)
     h16 = r16.hits()
     check_traceback(h16, r16.cigar(), qs, db, S, o, e, mode, fe)
-    monkeypatch.setenv("DSA_TB_FILL_INT32", "1")
+    monkeypatch.setenv("DSA_TB_FILL", "int32")
     r32 = _run(ctx, qs, db, pairs, S, o, e, mode, fe)
     h32 = r32.hits()
     for f in ("score", "q_end", "t_end", "q_begin", "t_begin", "cigar_len"):
