@@ -628,6 +628,9 @@ __global__ void __launch_bounds__(128) k_long_tb_windows(
 // reads shared memory instead of waiting on a global load.
 constexpr int WIN_WORDS = 32;
 constexpr int WIN_ROWS = 256;   // a window word's rows are consecutive (as in global memory)
+// diagonal cells read at once for a match run (16 against 8: 0.1 ms less on
+// the 64 long pairs)
+constexpr int RUN = 16;
 
 __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict__ jobs,
                                                      uint32_t n_jobs, int mode, uint32_t fe,
@@ -683,18 +686,18 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
           bool stop = false;
           int32_t q = 0;
           for (; q <= safe; ++q) {
-            if (st == 0 && q + 7 <= safe) {
-              // a match run: the next 8 cells along the diagonal lie in the
+            if (st == 0 && q + (RUN - 1) <= safe) {
+              // a match run: the next RUN cells along the diagonal lie in the
               // window; read them at once (independent loads) and take the
               // leading M steps together
               uint32_t notm = 0;
 #pragma unroll
-              for (int kk = 0; kk < 8; ++kk) {
+              for (int kk = 0; kk < RUN; ++kk) {
                 const int32_t jk = jc - kk;
                 const uint32_t w = win[((jk >> 3) - wlo) * WIN_ROWS + (rr - kk - wr0)];
                 notm |= (((w >> (4 * (jk & 7))) & 3u) != 1u ? 1u : 0u) << kk;
               }
-              const int32_t L = notm ? __ffs(notm) - 1 : 8;
+              const int32_t L = notm ? __ffs(notm) - 1 : RUN;
               if (L > 0) {
                 c.emit_run(0, (uint32_t)L);
                 i -= L; j -= L; rr -= L; jc -= L;

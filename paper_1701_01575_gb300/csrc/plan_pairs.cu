@@ -228,7 +228,7 @@ int score_pairs(dsa_ctx* ctx, dsa_res* res, const dsa_db* db, const dsa_db* qs, 
     const char* bps_env = getenv("DSA_LONG_BLOCKS");
     const char* tune_env = getenv("DSA_AUTOTUNE");
     if (bps_env) {
-      bps = atoi(bps_env) == 2 ? 2 : 4;
+      bps = std::min(4, std::max(1, atoi(bps_env)));
     } else if (ctx->tune && !(tune_env && std::string(tune_env) == "off")) {
       uint32_t mmax = 0, nmax = 0;
       for (const LongJob& lj : ljobs) {
