@@ -335,6 +335,7 @@ struct RevCigar {
   uint32_t n = 0;
   int op = -1;
   uint32_t run = 0;
+  bool writer = true;   // a warp running one walk in every lane stores from one
   __device__ void emit(int o) {
     if (o == op) {
       ++run;
@@ -354,7 +355,10 @@ struct RevCigar {
     }
   }
   __device__ void flush() {
-    if (run) out[n++] = (run << 4) | (uint32_t)op;
+    if (run) {
+      if (writer) out[n] = (run << 4) | (uint32_t)op;
+      ++n;
+    }
     run = 0;
   }
 };
@@ -619,8 +623,10 @@ __global__ void __launch_bounds__(128) k_long_tb_windows(
   }
 }
 
-// Checkpointed traceback, part 2: one warp per hit.  Lane 0 walks the stored
-// decisions from the end cell (stop > M > I > D, open preferred on ties); the
+// Checkpointed traceback, part 2: one warp per hit.  Every lane runs the
+// same walk over the stored decisions from the end cell (stop > M > I > D,
+// open preferred on ties), lane 0 storing the CIGAR; a match run is tested
+// 32 diagonal cells at a time, lane k reading the k-th, by one ballot.  The
 // warp keeps a window of them in shared memory -- up to WIN_ROWS rows of the
 // current band ending at the walk's row, WIN_WORDS words (8 cells each)
 // ending at the walk's column -- and reloads it with coalesced row loads
@@ -628,9 +634,6 @@ __global__ void __launch_bounds__(128) k_long_tb_windows(
 // reads shared memory instead of waiting on a global load.
 constexpr int WIN_WORDS = 32;
 constexpr int WIN_ROWS = 256;   // a window word's rows are consecutive (as in global memory)
-// diagonal cells read at once for a match run (16 against 8: 0.1 ms less on
-// the 64 long pairs)
-constexpr int RUN = 16;
 
 __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict__ jobs,
                                                      uint32_t n_jobs, int mode, uint32_t fe,
@@ -650,17 +653,18 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
     int32_t wb = -1, wlo = 0, wr0 = 0, wr1 = 0;   // window: band, first word, rows [wr0, wr1)
     RevCigar c;
     c.out = cig_tmp + jb.cig_off;
+    c.writer = lane == 0;
     int32_t i = jb.ie, j = jb.je;
     int st = 0;
     int64_t guard = 2 * ((int64_t)jb.ie + jb.je) + 2;
-    // lane 0: the walk's cell as (row in band wb, stored column of that band),
+    // the walk's cell as (row in band wb, stored column of that band),
     // valid once a reload has placed the window around it.  The walk only
     // moves up and left, so only the window's lower bounds can be crossed;
     // crossing one (a new band included: its rows start at 0) reloads.
     int32_t rr = -1, jc = -1;
     for (;;) {
       int need = 2;   // 1: reload the window around (i, j); 2: finished
-      if (lane == 0) {
+      {
         for (; guard > 0; --guard) {
           if (st == 0) {
             if (sg && ((i == 0 && (fe & DSA_FREE_T_BEGIN)) || (j == 0 && (fe & DSA_FREE_Q_BEGIN)))) break;
@@ -686,18 +690,14 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
           bool stop = false;
           int32_t q = 0;
           for (; q <= safe; ++q) {
-            if (st == 0 && q + (RUN - 1) <= safe) {
-              // a match run: the next RUN cells along the diagonal lie in the
-              // window; read them at once (independent loads) and take the
-              // leading M steps together
-              uint32_t notm = 0;
-#pragma unroll
-              for (int kk = 0; kk < RUN; ++kk) {
-                const int32_t jk = jc - kk;
-                const uint32_t w = win[((jk >> 3) - wlo) * WIN_ROWS + (rr - kk - wr0)];
-                notm |= (((w >> (4 * (jk & 7))) & 3u) != 1u ? 1u : 0u) << kk;
-              }
-              const int32_t L = notm ? __ffs(notm) - 1 : RUN;
+            if (st == 0 && q + 31 <= safe) {
+              // a match run: the next 32 cells along the diagonal lie in the
+              // window; lane k reads the k-th, and the leading M steps are
+              // taken together
+              const int32_t jk = jc - lane;
+              const uint32_t w = win[((jk >> 3) - wlo) * WIN_ROWS + (rr - lane - wr0)];
+              const uint32_t notm = __ballot_sync(FULL, ((w >> (4 * (jk & 7))) & 3u) != 1u);
+              const int32_t L = notm ? __ffs(notm) - 1 : 32;
               if (L > 0) {
                 c.emit_run(0, (uint32_t)L);
                 i -= L; j -= L; rr -= L; jc -= L;
@@ -737,7 +737,6 @@ __global__ void __launch_bounds__(32) k_long_tb_walk(const LongTbJob* __restrict
           if (stop) break;
         }
       }
-      need = __shfl_sync(FULL, need, 0);
       if (need != 1) break;
       // reload: rows of (i, j)'s band ending at row i, words ending at j's word;
       // a cell left of the band's stored columns ends the walk (only a corrupt
