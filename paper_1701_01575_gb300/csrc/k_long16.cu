@@ -100,10 +100,14 @@ __device__ __forceinline__ uint32_t bias2(int32_t lo, int32_t hi) { return pack2
 // the value of half `x` of an offset-binary register
 __device__ __forceinline__ int32_t half(uint32_t v, int x) { return x ? hi16(v ^ BIAS2) : lo16(v ^ BIAS2); }
 
-// The local form's running maxima and block-start state need more than the
-// 128 registers of 4 blocks per SM (it spilled there); at 3 it takes 156.
-template <bool LOCAL>
-__global__ void __launch_bounds__(WARPS * 32, LOCAL ? 3 : 4) k_long_score16(
+// MINB: the blocks per SM the build keeps resident.  The local form's
+// running maxima and block-start state need more than the 128 registers of
+// 4 blocks per SM (it spilled there); at 3 it takes 156.  The global form is
+// built for 4 blocks (128 registers) and for 2 (198: the steady-state body
+// scheduled with more registers ran 2% faster on the 64 long pairs), the
+// local form for 3 and 2; the blocks-per-SM choice picks the build.
+template <bool LOCAL, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) k_long_score16(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
     const LongJob* __restrict__ jobs, const LongPair16* __restrict__ pjobs,
@@ -635,7 +639,9 @@ int launch_long_score16(dsa_ctx* ctx, const dsa_db* db, const dsa_db* qs, const 
                         uint32_t n_litems, uint64_t n_slots) {
   if (n_items == 0) return DSA_OK;
   const bool local = mode == DSA_LOCAL;
-  auto kern = local ? k_long_score16<true> : k_long_score16<false>;
+  const bool two = blocks_per_sm > 0 && blocks_per_sm <= 2;
+  auto kern = local ? (two ? k_long_score16<true, 2> : k_long_score16<true, 3>)
+                    : (two ? k_long_score16<false, 2> : k_long_score16<false, 4>);
   // every warp must be resident at once (bands wait on their predecessors)
   int per_sm = 0;
   DSA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, 0));
