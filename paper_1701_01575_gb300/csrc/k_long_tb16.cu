@@ -48,9 +48,7 @@ namespace {
 constexpr int TB_ROWS = 8;
 constexpr int TB_BAND = 32 * TB_ROWS;
 constexpr int WARPS = 4;
-#ifndef TB16_BLOCKS
-#define TB16_BLOCKS 3
-#endif
+constexpr int FILL_BLOCKS = 3;   // blocks per SM the build keeps resident (2 measured no faster)
 constexpr uint32_t BIAS2 = 0x80008000u;
 constexpr int32_t WALL = -16000;             // stands for minus infinity
 // local floor when the absolute 0 is out of range: below every real value
@@ -84,9 +82,10 @@ __device__ __forceinline__ uint32_t bfi4(uint32_t field, uint32_t base, uint32_t
 struct TbHalf {
   const uint8_t* q;
   const uint8_t* t;
-  uint16_t* D;        // decision rows as 16-bit groups of 4 cells
+  uint32_t* D;        // the job's decisions (bands x TB_BAND x wpr words)
   const int2* up;     // checkpoint row above the band (band 0: none)
-  int32_t b, i0, ie, jlo, wcb, wpr2;   // wpr2: 16-bit groups per decision row
+  int32_t b, i0, ie, jlo, wcb;
+  uint32_t wpr;       // decision words per row
   int32_t base0;      // H of (i0, jlo): the first base
 };
 
@@ -98,20 +97,20 @@ __device__ __forceinline__ TbHalf tb_half(const LongTbJob& jb, int32_t b, const 
   const int2 w = win[jb.win_off + (uint32_t)b];
   h.q = qcodes + jb.q_start;
   h.t = tcodes + jb.t_start;
-  h.D = reinterpret_cast<uint16_t*>(dir + jb.dir_off);
+  h.D = dir + jb.dir_off;
   h.up = b > 0 ? bnd + jb.bnd_off + (uint64_t)(b - 1) * (uint32_t)jb.n : nullptr;
   h.b = b;
   h.i0 = b * TB_BAND;
   h.ie = jb.ie;
   h.jlo = w.x;
   h.wcb = w.y;
-  h.wpr2 = 2 * (int32_t)jb.wpr;
+  h.wpr = jb.wpr;
   h.base0 = b > 0 ? h.up[h.jlo - 1].x : h_row0(mode, fe, h.jlo, o, e);
   return h;
 }
 
 template <bool LOCAL>
-__global__ void __launch_bounds__(WARPS * 32, TB16_BLOCKS) k_long_tb_fill16(
+__global__ void __launch_bounds__(WARPS * 32, FILL_BLOCKS) k_long_tb_fill16(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
     const LongTbJob* __restrict__ jobs, const uint32_t* __restrict__ units, uint32_t n_units,
@@ -142,13 +141,10 @@ __global__ void __launch_bounds__(WARPS * 32, TB16_BLOCKS) k_long_tb_fill16(
     // what the steps read, held as plain values: the windows' lengths, the
     // rows' limits and this lane's first decision row of each half
     const int32_t wcbA = HA.wcb, wcbB = HB.wcb, ieA = HA.ie, ieB = HB.ie;
-    const uint32_t wpr2A = (uint32_t)HA.wpr2, wpr2B = (uint32_t)HB.wpr2;
     // decision word w of the lane's row r: DA[w TB_BAND + r] (the band's
     // column blocks, rows consecutive)
-    uint32_t* const DA = reinterpret_cast<uint32_t*>(HA.D) +
-                         (uint64_t)HA.b * (wpr2A / 2) * TB_BAND + (uint32_t)(r0A - HA.i0);
-    uint32_t* const DB = reinterpret_cast<uint32_t*>(HB.D) +
-                         (uint64_t)HB.b * (wpr2B / 2) * TB_BAND + (uint32_t)(r0B - HB.i0);
+    uint32_t* const DA = HA.D + (uint64_t)HA.b * HA.wpr * TB_BAND + (uint32_t)(r0A - HA.i0);
+    uint32_t* const DB = HB.D + (uint64_t)HB.b * HB.wpr * TB_BAND + (uint32_t)(r0B - HB.i0);
     int32_t baseA = HA.base0, baseB = HB.base0;
     const bool wallA = HA.jlo > 1, wallB = HB.jlo > 1;
     // nbA / nbB: each half's decision word of the current 8 columns
