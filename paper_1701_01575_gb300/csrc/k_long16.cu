@@ -23,8 +23,9 @@
 // cell (512 + 96 for the local locate pass below, which runs up to 64 steps
 // past a block start without moving the base), so a relative value is
 // bounded by 608 D + 2o + e + |min S| + 64, which long16_range_ok checks
-// against 2^15 on the host (no rerun is ever needed).  Lane 0's input row (the band above, or row 0) is converted from
-// absolute int32 once per 32 columns; the checkpoint rows (the middle and
+// against 2^15 on the host (no rerun is ever needed).  Lane 0's input row
+// (the band above, or row 0) is converted from absolute int32 once per 32
+// columns; the checkpoint rows (the middle and
 // the bottom row of the band, absolute int2 per pair, the same layout the
 // int32 kernel writes and the traceback reads) collect in a shared-memory
 // ring and are converted and stored by the whole warp every 32 steps, before
@@ -38,10 +39,10 @@
 // H = max(t, F)), and the next row's F = max(F - e, t - o) (equal to
 // max(F - e, H - o) because e <= o), one operation per row on the F chain.
 //
-// Local.  The floor 0 of Eq. 1 enters as t - o = max(t - o, floor - o) with
-// the relative floor per half (one addmax per register); a pair's local
-// result is the first cell, in (column, row) order, holding the maximum of
-// its matrix.  Tracking that cell on every improvement costs more than the
+// Local (the DSW of Sec. II.C.2).  The floor 0 of local alignment enters as
+// t - o = max(t - o, floor - o) with the relative floor per half (one addmax
+// per register); a pair's local result is the first cell, in (column, row)
+// order, holding the maximum of its matrix.  Tracking that cell on every improvement costs more than the
 // packing gains (along a strong diagonal a lane's best rises on about a
 // quarter of the steps), so the score pass keeps only a per-register
 // running maximum over each 32-step block, reduced across the warp at the
