@@ -242,8 +242,10 @@ __global__ void __launch_bounds__(128) k_traceback(
 constexpr int TROWS = TB_STRIP;
 constexpr int NW = TB_STRIP_WORDS;
 
+// 7 blocks per SM (72 registers): the kernel waits mostly on global loads,
+// and 28 warps per SM hide more of them than 24 (8 blocks spilled at 64).
 template <bool LOCAL, bool BYTES>
-__global__ void __launch_bounds__(128, TROWS <= 8 ? 6 : 4) k_traceback_thread(
+__global__ void __launch_bounds__(128, TROWS <= 8 ? 7 : 4) k_traceback_thread(
     const uint8_t* __restrict__ qcodes, const uint8_t* __restrict__ tcodes,
     const int8_t* __restrict__ Sg, int A, int o, int e, int mode, uint32_t fe,
     const TbJob* __restrict__ jobs, uint32_t n_jobs, uint32_t* __restrict__ dir,
