@@ -427,7 +427,8 @@ int tb_run_long(TbRun& R, std::vector<LongTbJob>& list, const int2* bnd_rows, ui
                          s_plus_o_fits_int8(res->matrix.data(), res->A, res->gap_open) &&
                          long_tb16_range_ok(res->gap_open, res->gap_extend, R.smax_pos, smin) &&
                          fill_pick != "int32";
-  const uint64_t packed_min_bands = 2ull * 12 * (uint64_t)ctx->sm_count;
+  // (4 blocks of 4 warps per SM: 16 warps, one per two bands)
+  const uint64_t packed_min_bands = 2ull * 16 * (uint64_t)ctx->sm_count;
   size_t k0 = 0;
   while (k0 < list.size()) {
     uint64_t dir = 0, cig = 0;
